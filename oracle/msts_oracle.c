@@ -1,0 +1,512 @@
+/*
+ * msts_oracle.c -- plain, slow, obviously-correct CPU reference for the
+ * blocked multi-shift triangular solve of Moon & Poulson (arXiv:1607.01477).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA library is
+ * checked against.  Only the tests, the package smoke check and the bench's
+ * CPU-baseline leg may load it.  It shares no code, header, table or helper
+ * with the CUDA library, and the library never calls it.
+ *
+ * Arithmetic: IEEE binary64 throughout, complex numbers as (re, im) pairs,
+ * compiled with -ffp-contract=off so that every a*b+c rounds twice.
+ * Matrices are column-major with a leading dimension (element (r,c) of A is
+ * A[r + c*lda]).  Only the upper triangle of U / T is read.
+ * OpenMP is used only across independent shifts / grid points.
+ *
+ * Readings of the paper fixed here (each is restated in the design doc):
+ *   - Omega (the overflow threshold of Alg. 4 and Alg. 5) is 2^960.
+ *   - Magnitudes in all growth bounds are complex moduli |z| (hypot).
+ *   - A pivot U(i,i)-lambda that is exactly zero is replaced by the real
+ *     number delta = max(eps*||U||_inf, DBL_MIN), eps = 2^-52 (Sec. 3).
+ *   - Every scale factor t is a power of two 2^-k with k the smallest k >= 1
+ *     for which the rescaled quantity is below Omega; scale factors are kept
+ *     as integer exponents e (s = 2^-e) so that they cannot underflow.
+ *   - The ratio |b(i)|/|U(i,i)| is evaluated through a mantissa/exponent
+ *     split so that it can be compared with Omega without overflowing.
+ *   - After the diagonal step, M is the modulus of the computed x(i).
+ *   - Blocks are cut from the bottom; when m is not a multiple of n_b the
+ *     ragged block of m mod n_b rows is the top one.
+ */
+#include <math.h>
+#include <float.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct { double re, im; } oz;
+
+/* Reading: Omega = 2^960 leaves 2^63 of headroom below DBL_MAX. */
+#define OR_OMEGA_EXP 960
+
+static inline oz oz_make(double re, double im) { oz z; z.re = re; z.im = im; return z; }
+static inline oz oz_add(oz a, oz b) { return oz_make(a.re + b.re, a.im + b.im); }
+static inline oz oz_sub(oz a, oz b) { return oz_make(a.re - b.re, a.im - b.im); }
+static inline oz oz_mul(oz a, oz b) {
+  return oz_make(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+static inline oz oz_conj(oz a) { return oz_make(a.re, -a.im); }
+static inline oz oz_scale(oz a, double s) { return oz_make(a.re * s, a.im * s); }
+static inline double oz_abs(oz a) { return hypot(a.re, a.im); }
+static inline int oz_is_zero(oz a) { return a.re == 0.0 && a.im == 0.0; }
+
+/* Complex division a/b by Smith's algorithm (R. L. Smith, CACM 5(8), 1962). */
+static oz oz_div(oz a, oz b) {
+  if (fabs(b.re) >= fabs(b.im)) {
+    double r = b.im / b.re;
+    double d = b.re + b.im * r;
+    return oz_make((a.re + a.im * r) / d, (a.im - a.re * r) / d);
+  } else {
+    double r = b.re / b.im;
+    double d = b.re * r + b.im;
+    return oz_make((a.re * r + a.im) / d, (a.im * r - a.re) / d);
+  }
+}
+
+#define AT(A, ld, r, c) ((A)[(size_t)(r) + (size_t)(c) * (size_t)(ld)])
+
+static double omega(void) { return ldexp(1.0, OR_OMEGA_EXP); }
+
+/* Smallest k >= 1 with 2^-k * x < Omega, for a finite x >= Omega. */
+static int choose_k(double x) {
+  int e = ilogb(x);
+  int k = e - (OR_OMEGA_EXP - 1);
+  return k < 1 ? 1 : k;
+}
+
+/* The ratio q = |a|/|b| as (mantissa ratio, exponent) so that it never
+ * overflows: returns e = floor(log2 q) and writes the ratio scaled by 2^-kk
+ * (kk >= 0) into *scaled.  For a == 0 returns INT_MIN-ish and *scaled = 0. */
+static int split_ratio(double a, double b, int kk, double *scaled) {
+  if (a == 0.0) { *scaled = 0.0; return -100000; }
+  int ea = ilogb(a), eb = ilogb(b);
+  double q = ldexp(a, -ea) / ldexp(b, -eb);
+  *scaled = ldexp(q, ea - eb - kk);
+  return ilogb(q) + ea - eb;
+}
+
+/* ||U||_inf over the upper triangle (max row sum of moduli). */
+double or_norm_inf_upper(int64_t m, const oz *U, int64_t ldu) {
+  double best = 0.0;
+  for (int64_t r = 0; r < m; ++r) {
+    double s = 0.0;
+    for (int64_t c = r; c < m; ++c) s += oz_abs(AT(U, ldu, r, c));
+    if (s > best) best = s;
+  }
+  return best;
+}
+
+/* delta of Sec. 3: the replacement for an exactly-zero pivot. */
+double or_delta(int64_t m, const oz *U, int64_t ldu) {
+  double d = DBL_EPSILON * or_norm_inf_upper(m, U, ldu);
+  return d < DBL_MIN ? DBL_MIN : d;
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. 1 with a shift (Eq. 2): unblocked back substitution on U - lambda*I.
+ * This is the plain definition x = (U - lambda I)^{-1} b.
+ * ---------------------------------------------------------------------- */
+static void trsv_shift(int64_t m, const oz *U, int64_t ldu, oz lambda, oz *b) {
+  for (int64_t i = m - 1; i >= 0; --i) {
+    b[i] = oz_div(b[i], oz_sub(AT(U, ldu, i, i), lambda));  /* diagonal step */
+    oz xi = b[i];
+    for (int64_t r = 0; r < i; ++r)                            /* AXPY */
+      b[r] = oz_sub(b[r], oz_mul(xi, AT(U, ldu, r, i)));
+  }
+}
+
+/* Forward substitution on U^H - conj(lambda) I (the lower-triangular case of
+ * the footnote in Sec. 2): row r of U^H is conj(U(0:r, r))^T. */
+static void trsv_shift_conj_trans(int64_t m, const oz *U, int64_t ldu, oz lambda, oz *b) {
+  for (int64_t i = 0; i < m; ++i) {
+    oz piv = oz_sub(oz_conj(AT(U, ldu, i, i)), oz_conj(lambda));
+    b[i] = oz_div(b[i], piv);
+    oz xi = b[i];
+    for (int64_t r = i + 1; r < m; ++r)          /* (U^H)(r,i) = conj(U(i,r)) */
+      b[r] = oz_sub(b[r], oz_mul(xi, oz_conj(AT(U, ldu, i, r))));
+  }
+}
+
+/* Multi-shift solve, plain definition: every column j is solved on its own
+ * with U - shifts[j] I (Eq. 2) or, when conj_trans, with U^H - conj(shifts[j]) I. */
+void or_multishift_solve(int64_t m, const oz *U, int64_t ldu, int64_t n,
+                         const oz *shifts, oz *B, int64_t ldb, int conj_trans) {
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) {
+    if (conj_trans) trsv_shift_conj_trans(m, U, ldu, shifts[j], &AT(B, ldb, 0, j));
+    else trsv_shift(m, U, ldu, shifts[j], &AT(B, ldb, 0, j));
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. 4 (SafeTrsv) on the k x k upper-triangular matrix A - lambda I whose
+ * top-left element is A[0].  cnorm[i] = max_{r<i} |A(r,i)| are the norms of
+ * the columns of A excluding the diagonal (Sec. 3).  b (length k) is
+ * overwritten with x; the returned integer kexp gives t = 2^-kexp with
+ * (A - lambda I) x = t b.
+ * ---------------------------------------------------------------------- */
+static int safe_trsv(int64_t k, const oz *A, int64_t lda, oz lambda, double delta,
+                     const double *cnorm, oz *b) {
+  const double OM = omega();
+  if (k <= 0) return 0;
+  oz *piv = (oz *)malloc(sizeof(oz) * (size_t)k);
+  for (int64_t i = 0; i < k; ++i) {
+    piv[i] = oz_sub(AT(A, lda, i, i), lambda);
+    if (oz_is_zero(piv[i])) piv[i] = oz_make(delta, 0.0);   /* U(i,i)=0 -> delta */
+  }
+  /* Growth bounds (the recursions for M(i), G(i) in Sec. 3). */
+  double M = 0.0, G = 0.0;
+  for (int64_t i = 0; i < k; ++i) { double a = oz_abs(b[i]); if (a > G) G = a; }
+  for (int64_t i = k - 1; i >= 0; --i) {
+    double ap = oz_abs(piv[i]);
+    double q = G / ap;
+    if (q > M) M = q;
+    G = G * (1.0 + cnorm[i] / ap);
+  }
+  int kexp = 0;
+  if (M < OM && G < OM) {
+    /* Well-conditioned case: plain back substitution (Alg. 1). */
+    for (int64_t i = k - 1; i >= 0; --i) {
+      b[i] = oz_div(b[i], piv[i]);
+      oz xi = b[i];
+      for (int64_t r = 0; r < i; ++r) b[r] = oz_sub(b[r], oz_mul(xi, AT(A, lda, r, i)));
+    }
+    free(piv);
+    return 0;
+  }
+  /* Safeguarded back substitution. */
+  G = 0.0;
+  for (int64_t i = 0; i < k; ++i) { double a = oz_abs(b[i]); if (a > G) G = a; }
+  for (int64_t i = k - 1; i >= 0; --i) {
+    double Mi;
+    int eM = split_ratio(oz_abs(b[i]), oz_abs(piv[i]), 0, &Mi);
+    if (eM >= OR_OMEGA_EXP) {                 /* M >= Omega: rescale before dividing */
+      int kk = eM - (OR_OMEGA_EXP - 1);
+      if (kk < 1) kk = 1;
+      double t = ldexp(1.0, -kk);
+      for (int64_t r = 0; r < k; ++r) b[r] = oz_scale(b[r], t);
+      kexp += kk;
+      G = G * t;
+    }
+    b[i] = oz_div(b[i], piv[i]);              /* diagonal step */
+    M = oz_abs(b[i]);
+    G = G + M * cnorm[i];
+    if (G >= OM) {                            /* protect the substitution step */
+      int kk = choose_k(G);
+      double t = ldexp(1.0, -kk);
+      for (int64_t r = 0; r < k; ++r) b[r] = oz_scale(b[r], t);
+      kexp += kk;
+      M = M * t;
+      G = G * t;
+    }
+    oz xi = b[i];
+    for (int64_t r = 0; r < i; ++r) b[r] = oz_sub(b[r], oz_mul(xi, AT(A, lda, r, i)));
+  }
+  free(piv);
+  return kexp;
+}
+
+/* Unblocked SafeTrsv (Alg. 4) on the whole U - shifts[j] I for every column:
+ * the second, block-free reference for the safe solve. */
+void or_safe_trsv_unblocked(int64_t m, const oz *U, int64_t ldu, int64_t n,
+                            const oz *shifts, oz *B, int64_t ldb, int32_t *scale_exp) {
+  double delta = or_delta(m, U, ldu);
+  double *cn = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  for (int64_t i = 0; i < m; ++i) {
+    double c = 0.0;
+    for (int64_t r = 0; r < i; ++r) { double a = oz_abs(AT(U, ldu, r, i)); if (a > c) c = a; }
+    cn[i] = c;
+  }
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j)
+    scale_exp[j] = safe_trsv(m, U, ldu, shifts[j], delta, cn, &AT(B, ldb, 0, j));
+  free(cn);
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. 5 (SafeMultiShiftTrsm), blocked from the bottom with block size nb.
+ * Alg. 5 never mixes columns: the diagonal-block step, the two rescalings and
+ * the substitution GEMM act on column j only through column j, so each column
+ * is run through the block loop on its own (the GEMM restricted to column j
+ * is B(I0,j) -= U(I0,I1) B(I1,j)).
+ *
+ * shortcut != 0 declares column j of B zero in rows >= j (the strictly upper
+ * right-hand sides of Alg. 6); then column j only visits rows < j: blocks
+ * that start at or below row j are skipped and the block holding row j-1 is
+ * cut at row j (Sec. 4, the footnote on trailing zeros).
+ *
+ * Per block, the bound of Alg. 5 is G(j) += C_blk * ||B(I1,j)||_inf with the
+ * single scalar C_blk = sum_{k in I1} ||U(I0,k)||_inf of the full block.
+ * ---------------------------------------------------------------------- */
+void or_safe_multishift_solve(int64_t m, const oz *U, int64_t ldu, int64_t n,
+                              const oz *shifts, oz *B, int64_t ldb, int64_t nb,
+                              int shortcut, int32_t *scale_exp) {
+  const double OM = omega();
+  double delta = or_delta(m, U, ldu);
+  int64_t nblk = (m + nb - 1) / nb;
+  /* Per block: within-block column norms (excluding the diagonal) and C_blk. */
+  double *cin = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  double *cblk = (double *)malloc(sizeof(double) * (size_t)(nblk > 0 ? nblk : 1));
+  for (int64_t b = 0; b < nblk; ++b) {
+    int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
+    double C = 0.0;
+    for (int64_t k = lo; k < hi; ++k) {
+      double c = 0.0, cu = 0.0;
+      for (int64_t r = lo; r < k; ++r) { double a = oz_abs(AT(U, ldu, r, k)); if (a > c) c = a; }
+      for (int64_t r = 0; r < lo; ++r) { double a = oz_abs(AT(U, ldu, r, k)); if (a > cu) cu = a; }
+      cin[k] = c;
+      C += cu;
+    }
+    cblk[b] = C;
+  }
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) {
+    oz *x = &AT(B, ldb, 0, j);
+    int64_t end = shortcut ? (j < m ? j : m) : m;   /* active rows [0, end) */
+    int e = 0;
+    double G = 0.0;                                  /* G(j) = ||B(:,j)||_inf */
+    for (int64_t r = 0; r < end; ++r) { double a = oz_abs(x[r]); if (a > G) G = a; }
+    for (int64_t b = 0; b < nblk; ++b) {
+      int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
+      if (lo >= end) continue;                       /* all-zero block of column j */
+      int64_t hie = hi < end ? hi : end;
+      /* Diagonal block step: SafeTrsv(U(I1,I1) - lambda_j I, B(I1,j), t). */
+      int kk = safe_trsv(hie - lo, &AT(U, ldu, lo, lo), ldu, shifts[j], delta, &cin[lo], &x[lo]);
+      if (kk > 0) {                                  /* t < 1: rescale I0 and I2 */
+        double t = ldexp(1.0, -kk);
+        for (int64_t r = 0; r < lo; ++r) x[r] = oz_scale(x[r], t);
+        for (int64_t r = hie; r < end; ++r) x[r] = oz_scale(x[r], t);
+        e += kk;
+        G = G * t;
+      }
+      double N = 0.0;
+      for (int64_t r = lo; r < hie; ++r) { double a = oz_abs(x[r]); if (a > N) N = a; }
+      G = G + cblk[b] * N;
+      if (G >= OM) {                                 /* rescale the whole column */
+        int k2 = choose_k(G);
+        double t = ldexp(1.0, -k2);
+        for (int64_t r = 0; r < end; ++r) x[r] = oz_scale(x[r], t);
+        e += k2;
+        G = G * t;
+      }
+      /* Substitution step (xGEMM restricted to column j). */
+      for (int64_t k = lo; k < hie; ++k) {
+        oz xk = x[k];
+        for (int64_t r = 0; r < lo; ++r) x[r] = oz_sub(x[r], oz_mul(AT(U, ldu, r, k), xk));
+      }
+    }
+    scale_exp[j] = e;
+  }
+  free(cin);
+  free(cblk);
+}
+
+/* Alg. 3 (MultiShiftTrsm), blocked from the bottom: the same block loop as
+ * above without the safeguards.  Used to pin that blocking changes rounding
+ * only (Sec. 2). */
+void or_multishift_solve_blocked(int64_t m, const oz *U, int64_t ldu, int64_t n,
+                                 const oz *shifts, oz *B, int64_t ldb, int64_t nb) {
+  int64_t nblk = (m + nb - 1) / nb;
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) {
+    oz *x = &AT(B, ldb, 0, j);
+    for (int64_t b = 0; b < nblk; ++b) {
+      int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
+      trsv_shift(hi - lo, &AT(U, ldu, lo, lo), ldu, shifts[j], &x[lo]);
+      for (int64_t k = lo; k < hi; ++k) {
+        oz xk = x[k];
+        for (int64_t r = 0; r < lo; ++r) x[r] = oz_sub(x[r], oz_mul(AT(U, ldu, r, k), xk));
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. 6 (TriangEig): lambda = diag(T); Z = -T with diag(Z) = 0 (and zero
+ * below the diagonal); SafeMultiShiftTrsm with the strictly-upper shortcut;
+ * diag(Z) = s.  scales[j] = 2^-scale_exp[j] (0 once it underflows).
+ * ---------------------------------------------------------------------- */
+void or_trevc(int64_t m, const oz *T, int64_t ldt, oz *Z, int64_t ldz, int64_t nb,
+              int32_t *scale_exp, double *scales) {
+  oz *lam = (oz *)calloc((size_t)(m > 0 ? m : 1), sizeof(oz));
+  for (int64_t j = 0; j < m; ++j) {
+    lam[j] = AT(T, ldt, j, j);
+    for (int64_t r = 0; r < m; ++r)
+      AT(Z, ldz, r, j) = r < j ? oz_make(-AT(T, ldt, r, j).re, -AT(T, ldt, r, j).im)
+                               : oz_make(0.0, 0.0);
+  }
+  or_safe_multishift_solve(m, T, ldt, m, lam, Z, ldz, nb, 1, scale_exp);
+  for (int64_t j = 0; j < m; ++j) {
+    scales[j] = ldexp(1.0, -scale_exp[j]);
+    AT(Z, ldz, j, j) = oz_make(scales[j], 0.0);
+  }
+  free(lam);
+}
+
+/* ------------------------------------------------------------------------
+ * Largest eigenvalue of the real symmetric tridiagonal matrix with diagonal
+ * a[0..k) and off-diagonal b[0..k-1), by bisection on Sturm counts
+ * (Barth, Martin & Wilkinson, Numer. Math. 9, 1967).  count(x) is the number
+ * of eigenvalues below x, read off as the negative pivots of the LDL^T
+ * factorisation of (tridiag - x I).
+ * ---------------------------------------------------------------------- */
+static int sturm_count(int k, const double *a, const double *b, double x, double pivmin) {
+  int c = 0;
+  double d = a[0] - x;
+  if (d < 0.0) ++c;
+  for (int i = 1; i < k; ++i) {
+    if (fabs(d) < pivmin) d = -pivmin;
+    d = (a[i] - x) - b[i - 1] * b[i - 1] / d;
+    if (d < 0.0) ++c;
+  }
+  return c;
+}
+
+double or_tridiag_max_eig(int k, const double *a, const double *b) {
+  if (k <= 0) return 0.0;
+  double lo = a[0], hi = a[0], bmax2 = 0.0;
+  for (int i = 0; i < k; ++i) {
+    double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    if (a[i] - r < lo) lo = a[i] - r;
+    if (a[i] + r > hi) hi = a[i] + r;
+    if (i + 1 < k && b[i] * b[i] > bmax2) bmax2 = b[i] * b[i];
+  }
+  double pivmin = DBL_MIN * (bmax2 > 1.0 ? bmax2 : 1.0);
+  /* Widen the Gershgorin interval slightly so that it strictly brackets. */
+  double w = fabs(hi) > fabs(lo) ? fabs(hi) : fabs(lo);
+  lo -= 4.0 * DBL_EPSILON * w + pivmin;
+  hi += 4.0 * DBL_EPSILON * w + pivmin;
+  for (int it = 0; it < 4096; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(k, a, b, mid, pivmin) >= k) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. 7 (Van Loan / Lui) on a triangular T: for every grid point z_p the
+ * largest eigenvalue of (T - z I)^{-H} (T - z I)^{-1} is estimated by Lanczos
+ * and sigma_min(T - z I) = 1/sqrt(theta_max) (Sec. 5).  Each operator apply is
+ * two triangular solves: upper with T - z I, then lower with (T - z I)^H.
+ *
+ * Readings: the start vector of point p is column p of V0, normalised; the
+ * Lanczos vectors are fully reorthogonalised by classical Gram-Schmidt run
+ * twice; exactly min(iters, m) steps are taken, stopping earlier only when
+ * beta_k <= 1e-14 * max_{i<=k} |alpha_i|.  alpha/beta (iters x N, column p
+ * for point p; may be NULL) receive the tridiagonal, steps[p] its order.
+ * ---------------------------------------------------------------------- */
+void or_pseudospectra(int64_t m, const oz *T, int64_t ldt, int64_t N, const oz *z,
+                      const oz *V0, int64_t ldv, int iters, double *sigma_min,
+                      double *alpha_out, double *beta_out, int32_t *steps_out) {
+  int K = iters < m ? iters : (int)m;
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t p = 0; p < N; ++p) {
+    oz *V = (oz *)calloc((size_t)(K + 1) * (size_t)m, sizeof(oz));
+    oz *w = (oz *)malloc(sizeof(oz) * (size_t)m);
+    double *al = (double *)calloc((size_t)K + 1, sizeof(double));
+    double *be = (double *)calloc((size_t)K + 1, sizeof(double));
+    double nv = 0.0;
+    for (int64_t r = 0; r < m; ++r) { oz v = AT(V0, ldv, r, p); nv += v.re * v.re + v.im * v.im; }
+    nv = sqrt(nv);
+    for (int64_t r = 0; r < m; ++r) V[r] = oz_scale(AT(V0, ldv, r, p), 1.0 / nv);
+    int steps = 0;
+    double amax = 0.0;
+    for (int k = 0; k < K; ++k) {
+      oz *vk = &V[(size_t)k * m];
+      memcpy(w, vk, sizeof(oz) * (size_t)m);
+      trsv_shift(m, T, ldt, z[p], w);              /* y = (T - zI)^{-1} v_k   */
+      trsv_shift_conj_trans(m, T, ldt, z[p], w);   /* w = (T - zI)^{-H} y     */
+      double a = 0.0;                              /* alpha_k = Re(v_k^H w)   */
+      for (int64_t r = 0; r < m; ++r) a += vk[r].re * w[r].re + vk[r].im * w[r].im;
+      al[k] = a;
+      if (fabs(a) > amax) amax = fabs(a);
+      for (int64_t r = 0; r < m; ++r) w[r] = oz_sub(w[r], oz_scale(vk[r], a));
+      if (k > 0) {
+        oz *vp = &V[(size_t)(k - 1) * m];
+        for (int64_t r = 0; r < m; ++r) w[r] = oz_sub(w[r], oz_scale(vp[r], be[k - 1]));
+      }
+      for (int pass = 0; pass < 2; ++pass) {       /* CGS2 against v_0..v_k   */
+        oz h[64];
+        oz *hh = (k + 1 <= 64) ? h : (oz *)malloc(sizeof(oz) * (size_t)(k + 1));
+        for (int i = 0; i <= k; ++i) {
+          oz *vi = &V[(size_t)i * m];
+          oz s = oz_make(0.0, 0.0);
+          for (int64_t r = 0; r < m; ++r) s = oz_add(s, oz_mul(oz_conj(vi[r]), w[r]));
+          hh[i] = s;
+        }
+        for (int i = 0; i <= k; ++i) {
+          oz *vi = &V[(size_t)i * m];
+          for (int64_t r = 0; r < m; ++r) w[r] = oz_sub(w[r], oz_mul(vi[r], hh[i]));
+        }
+        if (hh != h) free(hh);
+      }
+      double bn = 0.0;
+      for (int64_t r = 0; r < m; ++r) bn += w[r].re * w[r].re + w[r].im * w[r].im;
+      bn = sqrt(bn);
+      be[k] = bn;
+      steps = k + 1;
+      if (k == K - 1) break;
+      if (bn <= 1e-14 * amax) break;               /* invariant subspace found */
+      oz *vn = &V[(size_t)(k + 1) * m];
+      for (int64_t r = 0; r < m; ++r) vn[r] = oz_scale(w[r], 1.0 / bn);
+    }
+    double theta = or_tridiag_max_eig(steps, al, be);
+    sigma_min[p] = 1.0 / sqrt(theta);
+    if (alpha_out)
+      for (int k = 0; k < iters; ++k) alpha_out[(size_t)p * iters + k] = k < steps ? al[k] : 0.0;
+    if (beta_out)
+      for (int k = 0; k < iters; ++k) beta_out[(size_t)p * iters + k] = k < steps ? be[k] : 0.0;
+    if (steps_out) steps_out[p] = steps;
+    free(V); free(w); free(al); free(be);
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint of X = MultiShiftTrsm(U, s, B) for a real loss L, with the complex
+ * gradient convention g = dL/dRe + i dL/dIm, so that dL = Re<g, d.>:
+ *   lambda_j = (U - s_j I)^{-H} g_j     (a multi-shift solve with U^H, conj s)
+ *   dL/dB    = Lambda
+ *   dL/dU    = -triu(Lambda X^H)        (only the upper triangle is a parameter)
+ *   dL/ds_j  = x_j^H lambda_j
+ * which follows from dx_j = (U - s_j I)^{-1} (db_j - dU x_j + ds_j x_j).
+ * X is recomputed here from U, s and B.
+ * ---------------------------------------------------------------------- */
+void or_adjoint(int64_t m, const oz *U, int64_t ldu, int64_t n, const oz *shifts,
+                const oz *B, int64_t ldb, const oz *GX, int64_t ldg,
+                oz *dU, int64_t lddu, oz *dB, int64_t lddb, oz *ds) {
+  oz *X = (oz *)malloc(sizeof(oz) * (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t r = 0; r < m; ++r) {
+      X[r + j * m] = AT(B, ldb, r, j);
+      AT(dB, lddb, r, j) = AT(GX, ldg, r, j);
+    }
+  or_multishift_solve(m, U, ldu, n, shifts, X, m, 0);
+  or_multishift_solve(m, U, ldu, n, shifts, dB, lddb, 1);
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < m; ++c)
+    for (int64_t r = 0; r < m; ++r) {
+      oz acc = oz_make(0.0, 0.0);
+      if (r <= c)
+        for (int64_t j = 0; j < n; ++j)
+          acc = oz_add(acc, oz_mul(AT(dB, lddb, r, j), oz_conj(X[c + j * m])));
+      AT(dU, lddu, r, c) = oz_make(-acc.re, -acc.im);
+    }
+  for (int64_t j = 0; j < n; ++j) {
+    oz acc = oz_make(0.0, 0.0);
+    for (int64_t r = 0; r < m; ++r) acc = oz_add(acc, oz_mul(oz_conj(X[r + j * m]), AT(dB, lddb, r, j)));
+    ds[j] = acc;
+  }
+  free(X);
+}
+
+/* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,77 @@
+"""Pins for the oracle's pseudospectra (Alg. 7, Sec. 5) and its tridiagonal
+eigenvalue routine."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_01477_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 20, 33])
+def test_tridiag_max_matches_eigvalsh(k):
+    g = W.rng(0, k)
+    a = g.standard_normal(k)
+    b = g.standard_normal(max(k - 1, 0))
+    T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+    ref = np.linalg.eigvalsh(T).max()
+    assert abs(oracle.tridiag_max_eig(a, b) - ref) <= 8e-16 * max(1.0, np.abs(T).max()) * k
+
+
+def svd_sigma_min(A, z):
+    return np.linalg.svd(A - z * np.eye(A.shape[0]), compute_uv=False).min()
+
+
+@pytest.mark.parametrize("m", [1, 4, 16, 20])
+def test_exact_when_krylov_space_is_full(m):
+    """m <= iters with full reorthogonalisation: Lanczos spans C^m, so sigma_min
+    equals the smallest singular value of T - zI (Sec. 5, resolvent identity)."""
+    T, z, V0 = W.pseudo_problem(m, grid=5, seed=m)
+    sig, al, be, st = oracle.pseudospectra(T, z, V0, 20)
+    ref = np.array([svd_sigma_min(np.triu(T), zz) for zz in z])
+    assert np.abs(sig - ref).max() <= 1e-11 * ref.max()
+    assert np.all(np.abs(sig - ref) <= 1e-9 * ref)
+    assert (st <= m).all()
+
+
+def test_normal_matrix_closed_form():
+    """Diagonal (normal) T: sigma_min(T - zI) = min_i |t_ii - z|."""
+    g = W.rng(0, 3)
+    d = W.disk(g, 18, 1.0)
+    T = np.asfortranarray(np.diag(d))
+    z = W.disk(g, 9, 1.5)
+    V0 = W.cn(g, (18, 9))
+    sig, *_ = oracle.pseudospectra(T, z, V0, 20)
+    ref = np.abs(d[:, None] - z[None, :]).min(axis=0)
+    assert np.all(np.abs(sig - ref) <= 1e-12 * ref)
+
+
+def test_unitary_invariance():
+    """||(zI - A)^{-1}|| is unchanged by A = Q T Q^H (Sec. 5): the oracle run on T
+    matches a dense SVD of A - zI."""
+    m = 12
+    T, z, V0 = W.pseudo_problem(m, grid=4, seed=31)
+    g = W.rng(0, 8)
+    Q, _ = np.linalg.qr(W.cn(g, (m, m)))
+    A = Q @ np.triu(T) @ Q.conj().T
+    sig, *_ = oracle.pseudospectra(T, z, V0, 20)
+    ref = np.array([svd_sigma_min(A, zz) for zz in z])
+    assert np.all(np.abs(sig - ref) <= 1e-9 * ref)
+
+
+def test_ritz_value_bounds_on_larger_matrix():
+    """m > iters: theta_max is a Rayleigh-Ritz value, so sigma_min(oracle) >=
+    sigma_min(true) up to rounding, and the residual bound beta_K |e_K^T y|
+    brackets an eigenvalue; on this workload Lanczos converges to 1e-6 or better."""
+    m = 150
+    T, z, V0 = W.pseudo_problem(m, grid=4, seed=5)
+    sig, al, be, st = oracle.pseudospectra(T, z, V0, 20)
+    for p, zz in enumerate(z):
+        true = svd_sigma_min(np.triu(T), zz)
+        assert sig[p] >= true * (1 - 1e-12)
+        K = st[p]
+        Tk = np.diag(al[p, :K]) + np.diag(be[p, :K - 1], 1) + np.diag(be[p, :K - 1], -1)
+        w, Y = np.linalg.eigh(Tk)
+        bound = be[p, K - 1] * abs(Y[-1, -1])
+        lam_true = 1 / true ** 2
+        assert lam_true - w[-1] <= max(bound, 1e-12 * lam_true) * 1.0001 + 1e-12 * lam_true
+        assert abs(sig[p] - true) <= 1e-6 * true
