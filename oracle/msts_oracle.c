@@ -20,7 +20,9 @@
  *     number delta = max(eps*||U||_inf, DBL_MIN), eps = 2^-52 (Sec. 3).
  *   - Every scale factor t is a power of two 2^-k with k the smallest k >= 1
  *     for which the rescaled quantity is below Omega; scale factors are kept
- *     as integer exponents e (s = 2^-e) so that they cannot underflow.
+ *     as integer exponents e (s = 2^-e) so that they cannot underflow, and
+ *     t * x is applied as an exponent shift of x (exact unless x * 2^-k
+ *     itself underflows), never as a multiplication by a rounded t.
  *   - The ratio |b(i)|/|U(i,i)| is evaluated through a mantissa/exponent
  *     split so that it can be compared with Omega without overflowing.
  *   - After the diagonal step, M is the modulus of the computed x(i).
@@ -51,6 +53,8 @@ static inline oz oz_conj(oz a) { return oz_make(a.re, -a.im); }
 static inline oz oz_scale(oz a, double s) { return oz_make(a.re * s, a.im * s); }
 static inline double oz_abs(oz a) { return hypot(a.re, a.im); }
 static inline int oz_is_zero(oz a) { return a.re == 0.0 && a.im == 0.0; }
+/* a * 2^k applied to the exponent of each part (exact unless it underflows). */
+static inline oz oz_ldexp(oz a, int k) { return oz_make(ldexp(a.re, k), ldexp(a.im, k)); }
 
 /* Complex division a/b by Smith's algorithm (R. L. Smith, CACM 5(8), 1962). */
 static oz oz_div(oz a, oz b) {
@@ -185,21 +189,19 @@ static int safe_trsv(int64_t k, const oz *A, int64_t lda, oz lambda, double delt
     if (eM >= OR_OMEGA_EXP) {                 /* M >= Omega: rescale before dividing */
       int kk = eM - (OR_OMEGA_EXP - 1);
       if (kk < 1) kk = 1;
-      double t = ldexp(1.0, -kk);
-      for (int64_t r = 0; r < k; ++r) b[r] = oz_scale(b[r], t);
+      for (int64_t r = 0; r < k; ++r) b[r] = oz_ldexp(b[r], -kk);
       kexp += kk;
-      G = G * t;
+      G = ldexp(G, -kk);
     }
     b[i] = oz_div(b[i], piv[i]);              /* diagonal step */
     M = oz_abs(b[i]);
     G = G + M * cnorm[i];
     if (G >= OM) {                            /* protect the substitution step */
       int kk = choose_k(G);
-      double t = ldexp(1.0, -kk);
-      for (int64_t r = 0; r < k; ++r) b[r] = oz_scale(b[r], t);
+      for (int64_t r = 0; r < k; ++r) b[r] = oz_ldexp(b[r], -kk);
       kexp += kk;
-      M = M * t;
-      G = G * t;
+      M = ldexp(M, -kk);
+      G = ldexp(G, -kk);
     }
     oz xi = b[i];
     for (int64_t r = 0; r < i; ++r) b[r] = oz_sub(b[r], oz_mul(xi, AT(A, lda, r, i)));
@@ -275,21 +277,19 @@ void or_safe_multishift_solve(int64_t m, const oz *U, int64_t ldu, int64_t n,
       /* Diagonal block step: SafeTrsv(U(I1,I1) - lambda_j I, B(I1,j), t). */
       int kk = safe_trsv(hie - lo, &AT(U, ldu, lo, lo), ldu, shifts[j], delta, &cin[lo], &x[lo]);
       if (kk > 0) {                                  /* t < 1: rescale I0 and I2 */
-        double t = ldexp(1.0, -kk);
-        for (int64_t r = 0; r < lo; ++r) x[r] = oz_scale(x[r], t);
-        for (int64_t r = hie; r < end; ++r) x[r] = oz_scale(x[r], t);
+        for (int64_t r = 0; r < lo; ++r) x[r] = oz_ldexp(x[r], -kk);
+        for (int64_t r = hie; r < end; ++r) x[r] = oz_ldexp(x[r], -kk);
         e += kk;
-        G = G * t;
+        G = ldexp(G, -kk);
       }
       double N = 0.0;
       for (int64_t r = lo; r < hie; ++r) { double a = oz_abs(x[r]); if (a > N) N = a; }
       G = G + cblk[b] * N;
       if (G >= OM) {                                 /* rescale the whole column */
         int k2 = choose_k(G);
-        double t = ldexp(1.0, -k2);
-        for (int64_t r = 0; r < end; ++r) x[r] = oz_scale(x[r], t);
+        for (int64_t r = 0; r < end; ++r) x[r] = oz_ldexp(x[r], -k2);
         e += k2;
-        G = G * t;
+        G = ldexp(G, -k2);
       }
       /* Substitution step (xGEMM restricted to column j). */
       for (int64_t k = lo; k < hie; ++k) {
