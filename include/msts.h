@@ -1,0 +1,197 @@
+/*
+ * msts.h -- C ABI of libmsts, a GB300 (sm_103a) implementation of the blocked
+ * multi-shift triangular solve of Moon & Poulson, "Accelerating eigenvector
+ * and pseudospectra computation using blocked multi-shift triangular solves"
+ * (arXiv:1607.01477).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex numbers are msts_z = {double re, im} (binary compatible with
+ *    std::complex<double>, C99 double _Complex and torch.complex128).
+ *  - Matrices are column-major with a leading dimension: element (r, c) of A
+ *    is A[r + c * lda]; lda >= max(1, rows).
+ *  - Every array argument is a DEVICE pointer unless its comment says "host".
+ *    The caller owns all memory; the library never allocates, frees or keeps
+ *    a pointer after the call returns.
+ *  - Only the upper triangle of U / T is read; the strictly lower part may
+ *    hold anything.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  They do not synchronise and can be captured in a CUDA graph.
+ *  - `workspace` is caller-owned device scratch of at least the size returned
+ *    by the matching *_workspace_size function, aligned to 256 bytes.  It must
+ *    not be used by anything else until the work queued on `stream` finishes.
+ *  - Return value: 0 on success; a negative value -k means argument k (1-based)
+ *    is invalid and nothing was launched; MSTS_ERR_CUDA means a CUDA launch
+ *    failed (cudaGetLastError() tells why).
+ *  - `status` (device, may be NULL) receives, asynchronously, the OR of the
+ *    MSTS_STATUS_* bits below raised by the kernels.  The library only ORs
+ *    bits into it: clear it before the call.
+ *  - Block size n_b: blocks of rows are cut from the bottom of the matrix; if
+ *    m is not a multiple of n_b the ragged block of m mod n_b rows is the top
+ *    one.  Allowed n_b: 16, 32, 64.
+ *
+ * Safe variant (Alg. 4, Alg. 5 of the paper): readings fixed by this library
+ *  - Omega = 2^960; growth bounds use complex moduli |z|; every scale factor
+ *    is a power of two 2^-k with the smallest k >= 1 that brings the quantity
+ *    below Omega; s_j = 2^-scale_exp[j] exactly (scales[j] underflows to 0
+ *    once scale_exp[j] > 1074, scale_exp keeps the exact value).
+ *  - An exactly zero pivot U(i,i) - s_j is replaced by the real number
+ *    delta = max(2^-52 * ||U||_inf, DBL_MIN) (Sec. 3).
+ *  - The bounds are guaranteed overflow-free for |U(i,k)| < 2^48 and
+ *    |B(i,j)| < Omega; inputs outside that range raise MSTS_STATUS_RANGE.
+ */
+#ifndef MSTS_H_
+#define MSTS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } msts_z;
+
+/* flags */
+#define MSTS_SAFE        1u  /* Alg. 5: (U - s_j I) x_j = scale_j b_j with scale_j in [0,1]  */
+#define MSTS_CONJ_TRANS  2u  /* solve (U^H - conj(s_j) I) x_j = b_j (forward substitution)  */
+
+/* status bits */
+#define MSTS_STATUS_ZERO_PIVOT  1u  /* plain solve: some U(i,i) - s_j == 0 exactly (X is undefined) */
+#define MSTS_STATUS_NONFINITE   2u  /* a NaN or Inf was found in U or B                        */
+#define MSTS_STATUS_RANGE       4u  /* safe solve: |U(i,k)| >= 2^48 or |B(i,j)| >= Omega           */
+#define MSTS_STATUS_SCALED      8u  /* safe solve: some scale_j < 1                              */
+#define MSTS_STATUS_DELTA      16u  /* safe solve: a zero pivot was replaced by delta            */
+#define MSTS_STATUS_NOT_CONVERGED 32u /* mixed solve: refinement stopped at its iteration cap   */
+
+#define MSTS_ERR_CUDA (-1000)
+
+/* Library version as 10000*major + 100*minor + patch. */
+int msts_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Multi-shift triangular solve (Sec. 2, Eq. 2, Alg. 3) and its safe variant
+ * (Sec. 3, Eq. 3 generalised to many shifts, Alg. 4 and Alg. 5).
+ *
+ *   plain:            (U - shifts[j] I) X(:,j) = B(:,j),          j = 0..n-1
+ *   MSTS_SAFE:        (U - shifts[j] I) X(:,j) = scales[j] B(:,j), scales[j] in [0,1]
+ *   MSTS_CONJ_TRANS:  (U^H - conj(shifts[j]) I) X(:,j) = B(:,j)    (plain only)
+ *
+ * U        m x m, leading dimension ldu, upper triangle read.
+ * shifts   n complex shifts lambda_j.
+ * B        m x n, leading dimension ldb; overwritten with X.
+ * scales   n doubles (MSTS_SAFE only, else may be NULL): s_j = 2^-scale_exp[j].
+ * scale_exp n int32 (MSTS_SAFE only, else may be NULL).
+ * nb       block size n_b (16, 32 or 64).
+ * A plain solve that meets an exactly zero pivot raises MSTS_STATUS_ZERO_PIVOT
+ * and leaves X undefined (Inf/NaN), as back substitution does.
+ * m == 0 or n == 0 is a no-op.  Returns 0, -k, or MSTS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+size_t msts_solve_workspace_size(int64_t m, int64_t n, int32_t nb, uint32_t flags);
+int msts_solve(const msts_z *U, int64_t ldu, int64_t m,
+               const msts_z *shifts, int64_t n,
+               msts_z *B, int64_t ldb,
+               double *scales, int32_t *scale_exp,
+               int32_t nb, void *workspace, size_t workspace_bytes,
+               uint32_t *status, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched multi-shift solves of uneven sizes: problem p is solved exactly as
+ * msts_solve would with the fields of probs[p] (host array of `batch`
+ * descriptors; the pointers inside are device pointers).  All problems share
+ * n_b, flags and stream; their block steps run together, one launch per step
+ * for all problems.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const msts_z *U; int64_t ldu; int64_t m;
+  const msts_z *shifts; int64_t n;
+  msts_z *B; int64_t ldb;
+  double *scales; int32_t *scale_exp;
+} msts_problem;
+
+size_t msts_solve_batched_workspace_size(const msts_problem *probs, int64_t batch,
+                                         int32_t nb, uint32_t flags);
+int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb,
+                       void *workspace, size_t workspace_bytes,
+                       uint32_t *status, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Triangular eigenvectors (Sec. 4, Alg. 6 "TriangEig"): for the upper
+ * triangular Schur factor T (m x m), writes the upper triangular Z (m x m,
+ * leading dimension ldz, the strictly lower part is set to zero) with
+ *   T Z(:,j) = T(j,j) Z(:,j),   Z(j,j) = scales[j] = 2^-scale_exp[j],
+ * computed as the safe multi-shift solve with shifts T(j,j) and right-hand
+ * sides -T(0:j-1, j), shortcut so that column j only visits rows < j.
+ * Columns are returned unnormalised, as Alg. 6 returns them.
+ * ------------------------------------------------------------------------- */
+size_t msts_trevc_workspace_size(int64_t m, int32_t nb);
+int msts_trevc(const msts_z *T, int64_t ldt, int64_t m,
+               msts_z *Z, int64_t ldz,
+               double *scales, int32_t *scale_exp,
+               int32_t nb, void *workspace, size_t workspace_bytes,
+               uint32_t *status, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Pseudospectra (Sec. 5, Alg. 7, Van Loan / Lui): for each grid point z[p],
+ *   sigma_min[p] = sigma_min(T - z[p] I) = 1 / ||(z[p] I - A)^{-1}||_2
+ * for A = Q T Q^H, from the largest eigenvalue of (T - zI)^{-H} (T - zI)^{-1}
+ * estimated by `iters` Lanczos steps; every operator application is a pair of
+ * multi-shift solves over all N grid points at once (upper with T - zI, then
+ * lower with its conjugate transpose).
+ * V0       m x N start vectors (leading dimension ldv), normalised inside.
+ * Lanczos readings: full reorthogonalisation (classical Gram-Schmidt, twice);
+ * exactly min(iters, m) steps unless beta_k <= 1e-14 max_i |alpha_i|.
+ * alpha, beta (optional, may be NULL): N x iters tridiagonal entries, point p
+ * at [p*iters, (p+1)*iters); steps (optional): the tridiagonal order per point.
+ * ------------------------------------------------------------------------- */
+size_t msts_pseudospectra_workspace_size(int64_t m, int64_t N, int32_t iters, int32_t nb);
+int msts_pseudospectra(const msts_z *T, int64_t ldt, int64_t m,
+                       const msts_z *z, int64_t N,
+                       const msts_z *V0, int64_t ldv, int32_t iters,
+                       double *sigma_min, double *alpha, double *beta, int32_t *steps,
+                       int32_t nb, void *workspace, size_t workspace_bytes,
+                       uint32_t *status, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint of X = (U - s_j I)^{-1} B(:,j) (not in the paper): given
+ * GX = dL/dRe X + i dL/dIm X for a real loss L, returns
+ *   dB = Lambda,  Lambda(:,j) = (U - s_j I)^{-H} GX(:,j)
+ *   dU = -triu(Lambda X^H)   (m x m, strictly lower part set to zero)
+ *   ds_j = X(:,j)^H Lambda(:,j)
+ * X is recomputed from U, shifts and B block by block; it is not an input.
+ * B and GX are read only.  dB (m x n, lddb) and dU (lddu) are written.
+ * ------------------------------------------------------------------------- */
+size_t msts_adjoint_workspace_size(int64_t m, int64_t n, int32_t nb);
+/* Single problem; the batched form below takes one descriptor per problem. */
+int msts_adjoint(const msts_z *U, int64_t ldu, int64_t m,
+                 const msts_z *shifts, int64_t n,
+                 const msts_z *B, int64_t ldb, const msts_z *GX, int64_t ldg,
+                 msts_z *dU, int64_t lddu, msts_z *dB, int64_t lddb, msts_z *ds,
+                 int32_t nb, void *workspace, size_t workspace_bytes,
+                 uint32_t *status, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched adjoint: problem p is processed exactly as msts_adjoint would with
+ * the fields of probs[p] (host array; pointers inside are device pointers).
+ * All problems share n_b and stream; their solves run in shared launches.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const msts_z *U; int64_t ldu; int64_t m;
+  const msts_z *shifts; int64_t n;
+  const msts_z *B; int64_t ldb;
+  const msts_z *GX; int64_t ldg;
+  msts_z *dU; int64_t lddu;
+  msts_z *dB; int64_t lddb;
+  msts_z *ds;
+} msts_adjoint_problem;
+
+size_t msts_adjoint_batched_workspace_size(const msts_adjoint_problem *probs, int64_t batch,
+                                           int32_t nb);
+int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32_t nb,
+                         void *workspace, size_t workspace_bytes,
+                         uint32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSTS_H_ */

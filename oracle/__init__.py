@@ -213,3 +213,16 @@ def adjoint(U, shifts, B, GX):
                        _c_int64(_ld(B)), _p(GX), _c_int64(_ld(GX)), _p(dU), _c_int64(_ld(dU)),
                        _p(dB), _c_int64(_ld(dB)), _p(ds))
     return dU, dB, ds
+
+
+def trevc_columns(T, cols, nb):
+    """Alg. 6 for the listed columns only: returns (Zc, e) with Zc[:, c] the
+    eigenvector cols[c] exactly as ``trevc`` computes it."""
+    T = _cz(T, "T")
+    m = T.shape[0]
+    cc = np.ascontiguousarray(cols, dtype=np.int64)
+    Zc = np.zeros((m, cc.size), dtype=np.complex128, order="F")
+    e = np.zeros(cc.size, dtype=np.int32)
+    _load().or_trevc_columns(_c_int64(m), _p(T), _c_int64(_ld(T)), _c_int64(cc.size), _p(cc),
+                             _p(Zc), _c_int64(_ld(Zc)), _c_int64(nb), _p(e))
+    return Zc, e

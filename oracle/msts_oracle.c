@@ -242,65 +242,99 @@ void or_safe_trsv_unblocked(int64_t m, const oz *U, int64_t ldu, int64_t n,
  * Per block, the bound of Alg. 5 is G(j) += C_blk * ||B(I1,j)||_inf with the
  * single scalar C_blk = sum_{k in I1} ||U(I0,k)||_inf of the full block.
  * ---------------------------------------------------------------------- */
-void or_safe_multishift_solve(int64_t m, const oz *U, int64_t ldu, int64_t n,
-                              const oz *shifts, oz *B, int64_t ldb, int64_t nb,
-                              int shortcut, int32_t *scale_exp) {
-  const double OM = omega();
-  double delta = or_delta(m, U, ldu);
-  int64_t nblk = (m + nb - 1) / nb;
-  /* Per block: within-block column norms (excluding the diagonal) and C_blk. */
-  double *cin = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
-  double *cblk = (double *)malloc(sizeof(double) * (size_t)(nblk > 0 ? nblk : 1));
-  for (int64_t b = 0; b < nblk; ++b) {
+/* Shift-independent data of Alg. 5: within-block column norms (Sec. 3, the
+ * note after Alg. 5 on reusing them for every right-hand side), C_blk per
+ * block, and delta. */
+typedef struct { double *cin, *cblk; double delta; int64_t nblk; } safe_prep;
+
+static safe_prep safe_prepare(int64_t m, const oz *U, int64_t ldu, int64_t nb) {
+  safe_prep P;
+  P.delta = or_delta(m, U, ldu);
+  P.nblk = (m + nb - 1) / nb;
+  P.cin = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  P.cblk = (double *)malloc(sizeof(double) * (size_t)(P.nblk > 0 ? P.nblk : 1));
+  for (int64_t b = 0; b < P.nblk; ++b) {
     int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
     double C = 0.0;
     for (int64_t k = lo; k < hi; ++k) {
       double c = 0.0, cu = 0.0;
       for (int64_t r = lo; r < k; ++r) { double a = oz_abs(AT(U, ldu, r, k)); if (a > c) c = a; }
       for (int64_t r = 0; r < lo; ++r) { double a = oz_abs(AT(U, ldu, r, k)); if (a > cu) cu = a; }
-      cin[k] = c;
+      P.cin[k] = c;
       C += cu;
     }
-    cblk[b] = C;
+    P.cblk[b] = C;
   }
+  return P;
+}
+
+static void safe_release(safe_prep *P) { free(P->cin); free(P->cblk); }
+
+/* Alg. 5 for one column x (length m) with shift lambda; rows >= end are zero
+ * and never visited.  Returns the scale exponent e (s = 2^-e). */
+static int safe_column(int64_t m, const oz *U, int64_t ldu, int64_t nb, const safe_prep *P,
+                       oz lambda, oz *x, int64_t end) {
+  const double OM = omega();
+  int e = 0;
+  double G = 0.0;                                  /* G(j) = ||B(:,j)||_inf */
+  for (int64_t r = 0; r < end; ++r) { double a = oz_abs(x[r]); if (a > G) G = a; }
+  for (int64_t b = 0; b < P->nblk; ++b) {
+    int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
+    if (lo >= end) continue;                       /* all-zero block of this column */
+    int64_t hie = hi < end ? hi : end;
+    /* Diagonal block step: SafeTrsv(U(I1,I1) - lambda I, B(I1,j), t). */
+    int kk = safe_trsv(hie - lo, &AT(U, ldu, lo, lo), ldu, lambda, P->delta, &P->cin[lo], &x[lo]);
+    if (kk > 0) {                                  /* t < 1: rescale I0 and I2 */
+      for (int64_t r = 0; r < lo; ++r) x[r] = oz_ldexp(x[r], -kk);
+      for (int64_t r = hie; r < end; ++r) x[r] = oz_ldexp(x[r], -kk);
+      e += kk;
+      G = ldexp(G, -kk);
+    }
+    double N = 0.0;
+    for (int64_t r = lo; r < hie; ++r) { double a = oz_abs(x[r]); if (a > N) N = a; }
+    G = G + P->cblk[b] * N;
+    if (G >= OM) {                                 /* rescale the whole column */
+      int k2 = choose_k(G);
+      for (int64_t r = 0; r < end; ++r) x[r] = oz_ldexp(x[r], -k2);
+      e += k2;
+      G = ldexp(G, -k2);
+    }
+    /* Substitution step (xGEMM restricted to this column). */
+    for (int64_t k = lo; k < hie; ++k) {
+      oz xk = x[k];
+      for (int64_t r = 0; r < lo; ++r) x[r] = oz_sub(x[r], oz_mul(AT(U, ldu, r, k), xk));
+    }
+  }
+  return e;
+}
+
+void or_safe_multishift_solve(int64_t m, const oz *U, int64_t ldu, int64_t n,
+                              const oz *shifts, oz *B, int64_t ldb, int64_t nb,
+                              int shortcut, int32_t *scale_exp) {
+  safe_prep P = safe_prepare(m, U, ldu, nb);
   #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t j = 0; j < n; ++j) {
-    oz *x = &AT(B, ldb, 0, j);
     int64_t end = shortcut ? (j < m ? j : m) : m;   /* active rows [0, end) */
-    int e = 0;
-    double G = 0.0;                                  /* G(j) = ||B(:,j)||_inf */
-    for (int64_t r = 0; r < end; ++r) { double a = oz_abs(x[r]); if (a > G) G = a; }
-    for (int64_t b = 0; b < nblk; ++b) {
-      int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
-      if (lo >= end) continue;                       /* all-zero block of column j */
-      int64_t hie = hi < end ? hi : end;
-      /* Diagonal block step: SafeTrsv(U(I1,I1) - lambda_j I, B(I1,j), t). */
-      int kk = safe_trsv(hie - lo, &AT(U, ldu, lo, lo), ldu, shifts[j], delta, &cin[lo], &x[lo]);
-      if (kk > 0) {                                  /* t < 1: rescale I0 and I2 */
-        for (int64_t r = 0; r < lo; ++r) x[r] = oz_ldexp(x[r], -kk);
-        for (int64_t r = hie; r < end; ++r) x[r] = oz_ldexp(x[r], -kk);
-        e += kk;
-        G = ldexp(G, -kk);
-      }
-      double N = 0.0;
-      for (int64_t r = lo; r < hie; ++r) { double a = oz_abs(x[r]); if (a > N) N = a; }
-      G = G + cblk[b] * N;
-      if (G >= OM) {                                 /* rescale the whole column */
-        int k2 = choose_k(G);
-        for (int64_t r = 0; r < end; ++r) x[r] = oz_ldexp(x[r], -k2);
-        e += k2;
-        G = ldexp(G, -k2);
-      }
-      /* Substitution step (xGEMM restricted to column j). */
-      for (int64_t k = lo; k < hie; ++k) {
-        oz xk = x[k];
-        for (int64_t r = 0; r < lo; ++r) x[r] = oz_sub(x[r], oz_mul(AT(U, ldu, r, k), xk));
-      }
-    }
-    scale_exp[j] = e;
+    scale_exp[j] = safe_column(m, U, ldu, nb, &P, shifts[j], &AT(B, ldb, 0, j), end);
   }
-  free(cin);
-  free(cblk);
+  safe_release(&P);
+}
+
+/* Alg. 6 restricted to the listed columns cols[0..ncols): column c of Zc
+ * (m x ncols) receives eigenvector cols[c] exactly as or_trevc computes it. */
+void or_trevc_columns(int64_t m, const oz *T, int64_t ldt, int64_t ncols, const int64_t *cols,
+                      oz *Zc, int64_t ldzc, int64_t nb, int32_t *scale_exp) {
+  safe_prep P = safe_prepare(m, T, ldt, nb);
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < ncols; ++c) {
+    int64_t j = cols[c];
+    oz *x = &AT(Zc, ldzc, 0, c);
+    for (int64_t r = 0; r < m; ++r)
+      x[r] = r < j ? oz_make(-AT(T, ldt, r, j).re, -AT(T, ldt, r, j).im) : oz_make(0.0, 0.0);
+    scale_exp[c] = safe_column(m, T, ldt, nb, &P, AT(T, ldt, j, j), x, j);
+    x[j] = oz_make(ldexp(1.0, -scale_exp[c]), 0.0);
+  }
+  safe_release(&P);
 }
 
 /* Alg. 3 (MultiShiftTrsm), blocked from the bottom: the same block loop as

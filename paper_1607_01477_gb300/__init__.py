@@ -1,1 +1,340 @@
-"""GB300-native blocked multi-shift triangular solves (arXiv:1607.01477)."""
+"""GB300-native blocked multi-shift triangular solves (arXiv:1607.01477).
+
+Thin Python binding over the C ABI of ``libmsts.so`` (``include/msts.h``).
+Every function here only marshals torch tensors into the C call: all the
+arithmetic runs in the library's CUDA kernels.  There is no CPU fallback; if
+the library has not been built, or the tensors are not on a CUDA device, the
+call raises.
+
+Layout: complex128 matrices are column-major, i.e. a torch tensor ``A`` of
+shape (m, n) with ``A.stride(0) == 1`` (``colmajor(x)`` makes such a copy).
+Vectors are contiguous.  Calls are queued on the current torch CUDA stream.
+
+Names follow the C ABI: ``msts_solve``, ``msts_solve_batched``, ``msts_trevc``,
+``msts_pseudospectra``, ``msts_adjoint``, ``msts_adjoint_batched``; the
+differentiable form is ``MultiShiftSolve``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+__all__ = [
+    "MSTS_SAFE", "MSTS_CONJ_TRANS", "STATUS_BITS", "colmajor", "load_library", "library_path",
+    "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
+    "msts_adjoint_batched", "MultiShiftSolve", "multishift_solve", "decode_status",
+]
+
+MSTS_SAFE = 1
+MSTS_CONJ_TRANS = 2
+STATUS_BITS = {
+    1: "ZERO_PIVOT", 2: "NONFINITE", 4: "RANGE", 8: "SCALED", 16: "DELTA", 32: "NOT_CONVERGED",
+}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmsts.so")
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("U", _vp), ("ldu", _i64), ("m", _i64), ("shifts", _vp), ("n", _i64),
+                ("B", _vp), ("ldb", _i64), ("scales", _vp), ("scale_exp", _vp)]
+
+
+class _AdjProblem(ctypes.Structure):
+    _fields_ = [("U", _vp), ("ldu", _i64), ("m", _i64), ("shifts", _vp), ("n", _i64),
+                ("B", _vp), ("ldb", _i64), ("GX", _vp), ("ldg", _i64), ("dU", _vp),
+                ("lddu", _i64), ("dB", _vp), ("lddb", _i64), ("ds", _vp)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Loads libmsts.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libmsts.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.msts_version.restype = ctypes.c_int
+        lib.msts_solve_workspace_size.restype = _sz
+        lib.msts_solve_workspace_size.argtypes = [_i64, _i64, _i32, _u32]
+        lib.msts_solve.restype = ctypes.c_int
+        lib.msts_solve.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i32, _vp, _sz,
+                                   _vp, _u32, _vp]
+        lib.msts_solve_batched_workspace_size.restype = _sz
+        lib.msts_solve_batched_workspace_size.argtypes = [_vp, _i64, _i32, _u32]
+        lib.msts_solve_batched.restype = ctypes.c_int
+        lib.msts_solve_batched.argtypes = [_vp, _i64, _i32, _vp, _sz, _vp, _u32, _vp]
+        lib.msts_trevc_workspace_size.restype = _sz
+        lib.msts_trevc_workspace_size.argtypes = [_i64, _i32]
+        lib.msts_trevc.restype = ctypes.c_int
+        lib.msts_trevc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i32, _vp, _sz, _vp, _vp]
+        lib.msts_pseudospectra_workspace_size.restype = _sz
+        lib.msts_pseudospectra_workspace_size.argtypes = [_i64, _i64, _i32, _i32]
+        lib.msts_pseudospectra.restype = ctypes.c_int
+        lib.msts_pseudospectra.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp,
+                                           _vp, _vp, _i32, _vp, _sz, _vp, _vp]
+        lib.msts_adjoint_workspace_size.restype = _sz
+        lib.msts_adjoint_workspace_size.argtypes = [_i64, _i64, _i32]
+        lib.msts_adjoint.restype = ctypes.c_int
+        lib.msts_adjoint.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                                     _vp, _i64, _vp, _i32, _vp, _sz, _vp, _vp]
+        lib.msts_adjoint_batched_workspace_size.restype = _sz
+        lib.msts_adjoint_batched_workspace_size.argtypes = [_vp, _i64, _i32]
+        lib.msts_adjoint_batched.restype = ctypes.c_int
+        lib.msts_adjoint_batched.argtypes = [_vp, _i64, _i32, _vp, _sz, _vp, _vp]
+        _lib = lib
+        return lib
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+def colmajor(x: torch.Tensor) -> torch.Tensor:
+    """A column-major (Fortran-order) copy of a 2-D tensor."""
+    return x.t().contiguous().t()
+
+
+def _mat(x: torch.Tensor, name: str, rows: int | None = None) -> int:
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.complex128:
+        raise TypeError(f"{name} must be complex128")
+    if x.dim() != 2 or (x.shape[0] > 1 and x.stride(0) != 1):
+        raise ValueError(f"{name} must be a column-major 2-D tensor (stride(0) == 1)")
+    if rows is not None and x.shape[0] != rows:
+        raise ValueError(f"{name} must have {rows} rows")
+    return max(1, x.stride(1) if x.shape[1] > 1 else x.shape[0])
+
+
+def _vec(x: torch.Tensor, name: str, dtype=torch.complex128):
+    if not x.is_cuda or x.dtype != dtype or x.dim() != 1 or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous 1-D CUDA {dtype} tensor")
+
+
+def _ptr(x: torch.Tensor | None):
+    return None if x is None else ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor | None:
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+
+
+def _ws_ptr(ws):
+    if ws is None:
+        return None, 0
+    base = ws.data_ptr()
+    aligned = (base + 255) & ~255
+    return ctypes.c_void_p(aligned), ws.numel() - (aligned - base)
+
+
+def _check(rc: int, fn: str):
+    if rc != 0:
+        if rc == -1000:
+            raise RuntimeError(f"{fn}: CUDA launch failed")
+        raise ValueError(f"{fn}: invalid argument {-rc}")
+
+
+def decode_status(status: torch.Tensor) -> list[str]:
+    v = int(status.item())
+    return [name for bit, name in STATUS_BITS.items() if v & bit]
+
+
+def _status(device, status):
+    return torch.zeros(1, dtype=torch.int32, device=device) if status is None else status
+
+
+# --------------------------------------------------------------------------
+# entry points
+# --------------------------------------------------------------------------
+def msts_solve(U, shifts, B, *, safe=False, conj_trans=False, nb=32, status=None):
+    """(U - s_j I) X(:,j) = scale_j B(:,j), in place on B (Alg. 3 / Alg. 5).
+
+    Returns (B, scales, scale_exp, status); scales/scale_exp are None unless safe.
+    """
+    lib = load_library()
+    m, n = B.shape
+    ldu = _mat(U, "U", m)
+    ldb = _mat(B, "B", m)
+    _vec(shifts, "shifts")
+    dev = B.device
+    flags = (MSTS_SAFE if safe else 0) | (MSTS_CONJ_TRANS if conj_trans else 0)
+    scales = torch.empty(n, dtype=torch.float64, device=dev) if safe else None
+    sexp = torch.empty(n, dtype=torch.int32, device=dev) if safe else None
+    ws = _workspace(lib.msts_solve_workspace_size(m, n, nb, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_solve(_ptr(U), ldu, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(scales), _ptr(sexp),
+                        nb, wp, wb, _ptr(status), flags, _stream(dev))
+    _check(rc, "msts_solve")
+    return B, scales, sexp, status
+
+
+def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, status=None):
+    """Solves every (U, shifts, B) of `problems` in shared launches, in place on each B.
+
+    Returns (list of (scales, scale_exp) or None, status).
+    """
+    lib = load_library()
+    arr = (_Problem * len(problems))()
+    outs, keep = [], []
+    dev = None
+    for i, (U, s, B) in enumerate(problems):
+        m, n = B.shape
+        dev = B.device
+        ldu, ldb = _mat(U, "U", m), _mat(B, "B", m)
+        _vec(s, "shifts")
+        sc = torch.empty(n, dtype=torch.float64, device=dev) if safe else None
+        se = torch.empty(n, dtype=torch.int32, device=dev) if safe else None
+        outs.append((sc, se) if safe else None)
+        keep += [sc, se]
+        arr[i] = _Problem(U.data_ptr(), ldu, m, s.data_ptr(), n, B.data_ptr(), ldb,
+                          sc.data_ptr() if safe else None, se.data_ptr() if safe else None)
+    if not problems:
+        return [], status
+    flags = (MSTS_SAFE if safe else 0) | (MSTS_CONJ_TRANS if conj_trans else 0)
+    ws = _workspace(lib.msts_solve_batched_workspace_size(arr, len(problems), nb, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_solve_batched(arr, len(problems), nb, wp, wb, _ptr(status), flags, _stream(dev))
+    _check(rc, "msts_solve_batched")
+    return outs, status
+
+
+def msts_trevc(T, *, nb=32, status=None):
+    """Triangular eigenvectors (Alg. 6): returns (Z, scales, scale_exp, status)."""
+    lib = load_library()
+    m = T.shape[0]
+    ldt = _mat(T, "T", m)
+    dev = T.device
+    Z = colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
+    sc = torch.empty(m, dtype=torch.float64, device=dev)
+    se = torch.empty(m, dtype=torch.int32, device=dev)
+    ws = _workspace(lib.msts_trevc_workspace_size(m, nb), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_trevc(_ptr(T), ldt, m, _ptr(Z), max(1, m), _ptr(sc), _ptr(se), nb, wp, wb,
+                        _ptr(status), _stream(dev))
+    _check(rc, "msts_trevc")
+    return Z, sc, se, status
+
+
+def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, status=None, workspace=None):
+    """sigma_min(T - z_p I) for every grid point (Alg. 7 with Lanczos).
+
+    Returns (sigma_min, alpha, beta, steps, status); alpha/beta have shape (N, iters).
+    """
+    lib = load_library()
+    m = T.shape[0]
+    ldt = _mat(T, "T", m)
+    ldv = _mat(V0, "V0", m)
+    _vec(z, "z")
+    N = z.shape[0]
+    dev = T.device
+    sig = torch.empty(N, dtype=torch.float64, device=dev)
+    al = torch.empty((N, iters), dtype=torch.float64, device=dev)
+    be = torch.empty((N, iters), dtype=torch.float64, device=dev)
+    st = torch.empty(N, dtype=torch.int32, device=dev)
+    need = lib.msts_pseudospectra_workspace_size(m, N, iters, nb)
+    ws = workspace if workspace is not None and workspace.numel() >= need + 256 else _workspace(need, dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_pseudospectra(_ptr(T), ldt, m, _ptr(z), N, _ptr(V0), ldv, iters, _ptr(sig),
+                                _ptr(al), _ptr(be), _ptr(st), nb, wp, wb, _ptr(status), _stream(dev))
+    _check(rc, "msts_pseudospectra")
+    return sig, al, be, st, status
+
+
+def msts_adjoint(U, shifts, B, GX, *, nb=32, status=None):
+    """Gradients of a real loss through X = (U - s_j I)^{-1} B(:,j): (dU, dB, ds, status)."""
+    lib = load_library()
+    m, n = B.shape
+    ldu, ldb, ldg = _mat(U, "U", m), _mat(B, "B", m), _mat(GX, "GX", m)
+    _vec(shifts, "shifts")
+    dev = B.device
+    dU = colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
+    dB = colmajor(torch.empty((m, n), dtype=torch.complex128, device=dev))
+    ds = torch.empty(n, dtype=torch.complex128, device=dev)
+    ws = _workspace(lib.msts_adjoint_workspace_size(m, n, nb), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_adjoint(_ptr(U), ldu, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(GX), ldg, _ptr(dU),
+                          max(1, m), _ptr(dB), max(1, m), _ptr(ds), nb, wp, wb, _ptr(status),
+                          _stream(dev))
+    _check(rc, "msts_adjoint")
+    return dU, dB, ds, status
+
+
+def msts_adjoint_batched(problems, *, nb=32, status=None):
+    """problems: list of (U, shifts, B, GX).  Returns (list of (dU, dB, ds), status)."""
+    lib = load_library()
+    arr = (_AdjProblem * len(problems))()
+    outs = []
+    dev = None
+    for i, (U, s, B, G) in enumerate(problems):
+        m, n = B.shape
+        dev = B.device
+        ldu, ldb, ldg = _mat(U, "U", m), _mat(B, "B", m), _mat(G, "GX", m)
+        _vec(s, "shifts")
+        dU = colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
+        dB = colmajor(torch.empty((m, n), dtype=torch.complex128, device=dev))
+        ds = torch.empty(n, dtype=torch.complex128, device=dev)
+        outs.append((dU, dB, ds))
+        arr[i] = _AdjProblem(U.data_ptr(), ldu, m, s.data_ptr(), n, B.data_ptr(), ldb, G.data_ptr(),
+                             ldg, dU.data_ptr(), max(1, m), dB.data_ptr(), max(1, m), ds.data_ptr())
+    if not problems:
+        return [], status
+    ws = _workspace(lib.msts_adjoint_batched_workspace_size(arr, len(problems), nb), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_adjoint_batched(arr, len(problems), nb, wp, wb, _ptr(status), _stream(dev))
+    _check(rc, "msts_adjoint_batched")
+    return outs, status
+
+
+class MultiShiftSolve(torch.autograd.Function):
+    """X = MultiShiftSolve.apply(U, shifts, B): X(:,j) = (triu(U) - s_j I)^{-1} B(:,j).
+
+    Backward runs the library's adjoint (a conjugate-transposed multi-shift
+    solve plus a triangular-output GEMM); X is not saved, it is recomputed.
+    """
+
+    @staticmethod
+    def forward(ctx, U, shifts, B, nb=32):
+        X = colmajor(B.detach())
+        msts_solve(U.detach(), shifts.detach(), X, nb=nb)
+        ctx.save_for_backward(U, shifts, B)
+        ctx.nb = nb
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        U, shifts, B = ctx.saved_tensors
+        dU, dB, ds, _ = msts_adjoint(U.detach(), shifts.detach(), B.detach(), colmajor(gX),
+                                     nb=ctx.nb)
+        return dU, ds, dB, None
+
+
+def multishift_solve(U, shifts, B, nb=32):
+    return MultiShiftSolve.apply(U, shifts, B, nb)

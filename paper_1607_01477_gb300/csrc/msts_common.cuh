@@ -1,0 +1,133 @@
+// msts_common.cuh -- device helpers shared by the libmsts kernels.
+//
+// Complex numbers are double2 {x = re, y = im} (the layout of msts_z).
+// Matrices are column-major: A(r, c) = A[r + c * lda].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/msts.h"
+
+namespace msts {
+
+// ---------------------------------------------------------------------------
+// Constants of the safe variant (Sec. 3).  Omega = 2^kOmegaExp; the pre-check
+// |b(i)| / |U(i,i)| >= Omega is made on exponents so it cannot overflow.
+// ---------------------------------------------------------------------------
+constexpr int kOmegaExp = 960;
+constexpr double kEps = 2.220446049250313e-16;        // 2^-52
+constexpr double kDblMin = 2.2250738585072014e-308;   // 2^-1022
+constexpr int kMaxProbs = 64;                          // problems per launch
+constexpr double kRangeLimitU = 281474976710656.0;     // 2^48
+
+__device__ __forceinline__ double omega() { return 0x1p960; }
+
+__device__ __forceinline__ double2 zmake(double re, double im) { return make_double2(re, im); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc - a * b, fused.
+__device__ __forceinline__ double2 zfms(double2 acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+// acc + a * b, fused.
+__device__ __forceinline__ double2 zfma(double2 acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc + conj(a) * b, fused.
+__device__ __forceinline__ double2 zfma_cj(double2 acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ bool zzero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
+__device__ __forceinline__ bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Complex quotient a / b following Smith's 1962 method: divide through by the
+// larger component of b so that no intermediate overflows needlessly.
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  if (fabs(b.x) >= fabs(b.y)) {
+    const double r = b.y / b.x;
+    const double d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  }
+  const double r = b.x / b.y;
+  const double d = b.x * r + b.y;
+  return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+
+__device__ __forceinline__ double2 shfl_z(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Smallest k >= 1 with 2^-k * x < Omega for finite x >= Omega.
+__device__ __forceinline__ int choose_k(double x) {
+  const int k = ilogb(x) - (kOmegaExp - 1);
+  return k < 1 ? 1 : k;
+}
+
+// floor(log2(a / b)) for a > 0, b > 0 without forming a / b (which may overflow).
+__device__ __forceinline__ int ratio_exponent(double a, double b) {
+  const int ea = ilogb(a), eb = ilogb(b);
+  const double q = scalbn(a, -ea) / scalbn(b, -eb);
+  return ilogb(q) + ea - eb;
+}
+
+__device__ __forceinline__ void raise_status(uint32_t *status, uint32_t bits) {
+  if (status) atomicOr(reinterpret_cast<unsigned int *>(status), bits);
+}
+
+// ---------------------------------------------------------------------------
+// One multi-shift problem as the kernels see it.  Workspace pointers are set
+// up by the host driver; the safe-only ones are null for plain solves.
+// ---------------------------------------------------------------------------
+struct Prob {
+  const double2 *U;         // m x m, upper triangle read
+  long long ldu;
+  const double2 *shifts;    // shift j at shifts[j * shift_stride]
+  long long shift_stride;
+  double2 *B;               // m x n, overwritten with X
+  long long ldb;
+  double *scales;           // n (safe)
+  int *scale_exp;           // n (safe)
+  // safe-variant state (workspace)
+  double *G;                // n: growth bound G(j) of Alg. 5
+  int *e;                   // n: accumulated exponent, s_j = 2^-e_j
+  int *pend;                // n: exponent still owed by B(I0, j) at this step
+  int *E;                   // nblk x n: e_j when block b was finished
+  double *cin;              // m: within-block column norms (excl. diagonal)
+  double *cup;              // m: column norms above the block
+  double *cblk;             // nblk: C_blk = sum_k cup[k] over the block
+  double *rowsum;           // m: row sums of |U| (for ||U||_inf)
+  double *delta;            // 1: zero-pivot replacement
+  int m, n, nblk;
+  int diag_z;               // TREVC: write Z(j,j) = s_j in the fixup
+};
+
+struct ProbTable {
+  int count;
+  Prob p[kMaxProbs];
+};
+
+}  // namespace msts

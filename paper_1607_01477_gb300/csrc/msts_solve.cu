@@ -1,0 +1,631 @@
+// msts_solve.cu -- the blocked multi-shift triangular solve (Sec. 2, Alg. 3)
+// and its safe variant (Sec. 3, Alg. 4 and Alg. 5) on GB300, FP64 complex.
+//
+// Schedule (the paper's right-looking order): for every block of n_b rows,
+// bottom to top,
+//   k_diag : each shift j solves its shifted n_b x n_b diagonal block with one
+//            warp (lane = row), U(I1,I1) staged once per CTA in shared memory;
+//            the safe variant also runs the Alg. 4 bounds, the careful
+//            back substitution and the Alg. 5 column bound update in the same
+//            pass (per-column state lives in the workspace);
+//   k_gemm : the substitution step B(I0,:) -= U(I0,I1) X(I1,:) shared by all
+//            shifts, an FP64 DFMA tile kernel.  In the safe variant its
+//            epilogue also applies the power-of-two rescaling that Alg. 5
+//            owes B(I0,j) for this block (lazy xSCAL, exact).
+// Rows below the current block (I2) are rescaled lazily too: the exponent of
+// each column at the time each block was finished is recorded and a final
+// k_fixup pass multiplies every block by the power of two it still owes.
+//
+// Many problems (uneven sizes) run in the same launches: each launch receives
+// a table of problem descriptors and grid.z indexes the problem.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "msts_common.cuh"
+#include "msts_engine.h"
+
+namespace msts {
+
+constexpr int kDiagWarps = 8;
+constexpr int kGemmBM = 64;
+constexpr int kGemmBN = 32;
+constexpr int kGemmThreads = 256;
+
+__device__ __forceinline__ void block_range(const Prob &P, int b, int nb, int &lo, int &hi) {
+  hi = P.m - b * nb;
+  lo = hi - nb < 0 ? 0 : hi - nb;
+}
+
+// ---------------------------------------------------------------------------
+// Safe-variant preprocessing (Alg. 5 set-up, the column norms of Sec. 3).
+// ---------------------------------------------------------------------------
+
+// One warp per column k: cin[k] = max_{lo(k) <= r < k} |U(r,k)| (within its own
+// block, diagonal excluded) and cup[k] = max_{r < lo(k)} |U(r,k)| (above it).
+__global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32_t *status) {
+  const Prob &P = tab.p[blockIdx.z];
+  if (P.n == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= P.m) return;
+  const int b = (P.m - 1 - k) / nb;
+  int lo, hi;
+  block_range(P, b, nb, lo, hi);
+  double cin = 0.0, cup = 0.0, amax = 0.0;
+  bool finite = true;
+  const double2 *col = P.U + (long long)k * P.ldu;
+  for (int r = lane; r <= k; r += 32) {
+    const double2 u = col[r];
+    finite &= zfinite(u);
+    const double a = zabs(u);
+    amax = fmax(amax, a);
+    if (r < lo) cup = fmax(cup, a);
+    else if (r < k) cin = fmax(cin, a);
+  }
+  cin = warp_max(cin);
+  cup = warp_max(cup);
+  amax = warp_max(amax);
+  const bool all_finite = __all_sync(0xffffffffu, finite);
+  if (lane == 0) {
+    P.cin[k] = cin;
+    P.cup[k] = cup;
+    if (!all_finite) raise_status(status, MSTS_STATUS_NONFINITE);
+    if (amax >= kRangeLimitU) raise_status(status, MSTS_STATUS_RANGE);
+  }
+}
+
+// One thread per row: rowsum[r] = sum_{c >= r} |U(r,c)|, summed left to right.
+__global__ void k_rowsums(const __grid_constant__ ProbTable tab) {
+  const Prob &P = tab.p[blockIdx.z];
+  if (P.n == 0) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.m) return;
+  double s = 0.0;
+  const double2 *row = P.U + r;
+  for (int c = r; c < P.m; ++c) s += zabs(row[(long long)c * P.ldu]);
+  P.rowsum[r] = s;
+}
+
+// One CTA per problem: C_blk for every block (summed in column order) and
+// delta = max(eps * ||U||_inf, DBL_MIN).
+__global__ void k_safe_finish(const __grid_constant__ ProbTable tab, int nb) {
+  const Prob &P = tab.p[blockIdx.z];
+  __shared__ double red[32];
+  if (P.m == 0 || P.n == 0) return;
+  for (int b = threadIdx.x; b < P.nblk; b += blockDim.x) {
+    int lo, hi;
+    block_range(P, b, nb, lo, hi);
+    double c = 0.0;
+    for (int k = lo; k < hi; ++k) c += P.cup[k];
+    P.cblk[b] = c;
+  }
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < P.m; r += blockDim.x) mx = fmax(mx, P.rowsum[r]);
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_max(v);
+    if (threadIdx.x == 0) {
+      const double d = kEps * v;
+      *P.delta = d < kDblMin ? kDblMin : d;
+    }
+  }
+}
+
+// One warp per column: G(j) = ||B(:,j)||_inf over the active rows, e_j = 0.
+__global__ void k_safe_init(const __grid_constant__ ProbTable tab, int shortcut, uint32_t *status) {
+  const Prob &P = tab.p[blockIdx.z];
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= P.n) return;
+  const int end = shortcut ? min(j, P.m) : P.m;
+  double g = 0.0;
+  bool finite = true;
+  const double2 *col = P.B + (long long)j * P.ldb;
+  for (int r = lane; r < end; r += 32) {
+    const double2 v = col[r];
+    finite &= zfinite(v);
+    g = fmax(g, zabs(v));
+  }
+  g = warp_max(g);
+  const bool all_finite = __all_sync(0xffffffffu, finite);
+  if (lane == 0) {
+    P.G[j] = g;
+    P.e[j] = 0;
+    P.pend[j] = 0;
+    if (!all_finite) raise_status(status, MSTS_STATUS_NONFINITE);
+    if (g >= omega()) raise_status(status, MSTS_STATUS_RANGE);
+  }
+}
+
+// TREVC set-up (Alg. 6): Z = -T strictly above the diagonal, zero elsewhere.
+__global__ void k_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z, long long ldz) {
+  const int j = blockIdx.x;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (r < j) {
+      const double2 t = T[r + (long long)j * ldt];
+      v = make_double2(-t.x, -t.y);
+    }
+    Z[r + (long long)j * ldz] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal-block step: one warp per shift, lane = row (rows lane + 32q).
+// ---------------------------------------------------------------------------
+template <int NB>
+struct Rows { static constexpr int kPerLane = NB > 32 ? NB / 32 : 1; };
+
+// Back substitution on the upper n_b x n_b block (Alg. 1 on U(I1,I1) - lambda I)
+// or forward substitution on its conjugate transpose (CONJ).  sU holds the
+// block column-major with leading dimension NB + 1.
+template <int NB, bool CONJ>
+__device__ __forceinline__ void block_subst(double2 (&y)[Rows<NB>::kPerLane],
+                                            const double2 (&piv)[Rows<NB>::kPerLane],
+                                            const double2 *sU, int nbe, int lane) {
+  constexpr int RPL = Rows<NB>::kPerLane;
+  constexpr int LD = NB + 1;
+  for (int t = 0; t < nbe; ++t) {
+    const int i = CONJ ? t : nbe - 1 - t;
+    const int qi = i >> 5, li = i & 31;
+    double2 own = y[0];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q)
+      if (q == qi) {
+        if (lane == li) y[q] = zdiv(y[q], piv[q]);   // diagonal step
+        own = y[q];
+      }
+    const double2 xi = shfl_z(own, li);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {                   // substitution (AXPY)
+      const int r = lane + 32 * q;
+      if (!CONJ) {
+        if (r < i) y[q] = zfms(y[q], xi, sU[i * LD + r]);
+      } else {
+        if (r > i && r < nbe) y[q] = zfms(y[q], xi, zconj(sU[r * LD + i]));
+      }
+    }
+  }
+}
+
+template <int NB, bool SAFE, bool CONJ>
+__global__ void __launch_bounds__(kDiagWarps * 32)
+k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *status) {
+  constexpr int RPL = Rows<NB>::kPerLane;
+  constexpr int LD = NB + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *sU = reinterpret_cast<double2 *>(smem_raw);
+  double *sC = reinterpret_cast<double *>(sU + NB * LD);
+
+  const Prob &P = tab.p[blockIdx.z];
+  if (step >= P.nblk) return;
+  const int b = CONJ ? P.nblk - 1 - step : step;
+  int lo, hi;
+  block_range(P, b, NB, lo, hi);
+  const int nbf = hi - lo;
+  const int jstart = shortcut ? lo + 1 : 0;
+  const int jcta = jstart + blockIdx.x * kDiagWarps;
+  if (jcta >= P.n) return;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < nbf * nbf; idx += blockDim.x) {
+    const int c = idx / nbf, r = idx - c * nbf;
+    double2 v = make_double2(0.0, 0.0);
+    if (r <= c) v = P.U[(lo + r) + (long long)(lo + c) * P.ldu];
+    sU[c * LD + r] = v;
+  }
+  if (SAFE)
+    for (int k = tid; k < nbf; k += blockDim.x) sC[k] = P.cin[lo + k];
+  __syncthreads();
+
+  const int j = jcta + warp;
+  if (j >= P.n) return;
+  const int nbe = shortcut ? min(hi, j) - lo : nbf;   // TREVC: rows >= j are zero
+  const double2 lam = P.shifts[(long long)j * P.shift_stride];
+  double2 *col = P.B + (long long)j * P.ldb + lo;
+
+  double2 y[RPL], piv[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int r = lane + 32 * q;
+    const bool v = r < nbe;
+    y[q] = v ? col[r] : make_double2(0.0, 0.0);
+    const double2 d = v ? sU[r * LD + r] : make_double2(0.0, 0.0);
+    piv[q] = CONJ ? zsub(zconj(d), zconj(lam)) : zsub(d, lam);
+    if (!v) piv[q] = make_double2(1.0, 0.0);
+  }
+
+  if (!SAFE) {
+    bool zp = false;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) zp |= (lane + 32 * q < nbe) && zzero(piv[q]);
+    if (__any_sync(0xffffffffu, zp) && lane == 0) raise_status(status, MSTS_STATUS_ZERO_PIVOT);
+    block_subst<NB, CONJ>(y, piv, sU, nbe, lane);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q)
+      if (lane + 32 * q < nbe) col[lane + 32 * q] = y[q];
+    return;
+  }
+
+  // ----- safe variant: Alg. 4 on the shifted block, then Alg. 5's column update
+  const double OM = omega();
+  const double dlt = *P.delta;
+  bool used_delta = false;
+  double ap[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const bool v = lane + 32 * q < nbe;
+    if (v && zzero(piv[q])) { piv[q] = make_double2(dlt, 0.0); used_delta = true; }
+    ap[q] = v ? zabs(piv[q]) : 1.0;
+  }
+  double g0 = 0.0;
+#pragma unroll
+  for (int q = 0; q < RPL; ++q)
+    if (lane + 32 * q < nbe) g0 = fmax(g0, zabs(y[q]));
+  g0 = warp_max(g0);
+
+  // Growth bounds: rows are processed bottom-up, so G before row i is
+  // G0 * prod_{k > i} (1 + c_k / |piv_k|) and M = max_i G_before(i) / |piv_i|;
+  // the products are formed as a warp suffix scan.
+  double carry = 1.0, mloc = 0.0;
+#pragma unroll
+  for (int q = RPL - 1; q >= 0; --q) {
+    const int r = lane + 32 * q;
+    const bool v = r < nbe;
+    const double f = v ? 1.0 + sC[r] / ap[q] : 1.0;
+    double S = f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_down_sync(0xffffffffu, S, o);
+      if (lane + o < 32) S *= t;
+    }
+    double ex = __shfl_down_sync(0xffffffffu, S, 1);
+    if (lane == 31) ex = 1.0;
+    if (v) {
+      const double qv = (g0 * carry * ex) / ap[q];
+      if (qv > mloc) mloc = qv;
+    }
+    carry *= __shfl_sync(0xffffffffu, S, 0);
+  }
+  const double M1 = warp_max(mloc);
+  const double G1 = g0 * carry;
+
+  int kexp = 0;
+  if (M1 < OM && G1 < OM) {
+    block_subst<NB, false>(y, piv, sU, nbe, lane);
+  } else {
+    // Safeguarded back substitution (Alg. 4, second branch).
+    double G = g0;
+    for (int i = nbe - 1; i >= 0; --i) {
+      const int qi = i >> 5, li = i & 31;
+      int eM = -100000;
+#pragma unroll
+      for (int q = 0; q < RPL; ++q)
+        if (q == qi && lane == li) {
+          const double ay = zabs(y[q]);
+          eM = ay == 0.0 ? -100000 : ratio_exponent(ay, ap[q]);
+        }
+      eM = __shfl_sync(0xffffffffu, eM, li);
+      if (eM >= kOmegaExp) {                         // M >= Omega: rescale b first
+        const int kk = eM - (kOmegaExp - 1);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) y[q] = make_double2(scalbn(y[q].x, -kk), scalbn(y[q].y, -kk));
+        kexp += kk;
+        G = scalbn(G, -kk);
+      }
+      double Mv = 0.0;
+      double2 own = y[0];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q)
+        if (q == qi) {
+          if (lane == li) { y[q] = zdiv(y[q], piv[q]); Mv = zabs(y[q]); }
+          own = y[q];
+        }
+      double2 xi = shfl_z(own, li);
+      Mv = __shfl_sync(0xffffffffu, Mv, li);
+      G = __dadd_rn(G, __dmul_rn(Mv, sC[i]));
+      if (G >= OM) {                                 // protect the AXPY
+        const int kk = choose_k(G);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) y[q] = make_double2(scalbn(y[q].x, -kk), scalbn(y[q].y, -kk));
+        xi = make_double2(scalbn(xi.x, -kk), scalbn(xi.y, -kk));
+        kexp += kk;
+        G = scalbn(G, -kk);
+      }
+      const double2 *ucol = sU + i * LD;
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int r = lane + 32 * q;
+        if (r < i) y[q] = zfms(y[q], xi, ucol[r]);
+      }
+    }
+  }
+
+  // Alg. 5: t < 1 rescales the rest of the column (lazily, see k_gemm/k_fixup),
+  // then G(j) += C_blk ||X(I1,j)||_inf and a rescale if it reaches Omega.
+  int ej = P.e[j];
+  double Gj = P.G[j];
+  int pend = 0;
+  if (kexp > 0) { ej += kexp; Gj = scalbn(Gj, -kexp); pend = kexp; }
+  double N = 0.0;
+#pragma unroll
+  for (int q = 0; q < RPL; ++q)
+    if (lane + 32 * q < nbe) N = fmax(N, zabs(y[q]));
+  N = warp_max(N);
+  Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
+  if (Gj >= OM) {
+    const int kk = choose_k(Gj);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) y[q] = make_double2(scalbn(y[q].x, -kk), scalbn(y[q].y, -kk));
+    ej += kk;
+    Gj = scalbn(Gj, -kk);
+    pend += kk;
+  }
+#pragma unroll
+  for (int q = 0; q < RPL; ++q)
+    if (lane + 32 * q < nbe) col[lane + 32 * q] = y[q];
+  const bool any_delta = __any_sync(0xffffffffu, used_delta);
+  if (lane == 0) {
+    P.e[j] = ej;
+    P.G[j] = Gj;
+    P.pend[j] = pend;
+    P.E[(long long)b * P.n + j] = ej;
+    if (pend > 0) raise_status(status, MSTS_STATUS_SCALED);
+    if (any_delta) raise_status(status, MSTS_STATUS_DELTA);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Substitution step: B(I0,:) = 2^-pend * B(I0,:) - U(I0,I1) X(I1,:)  (upper), or
+//                    B(I2,:) -= (U^H)(I2,I1) X(I1,:)                  (CONJ).
+// Tile kGemmBM x kGemmBN of B per CTA, K = the block's rows; FP64 DFMA.
+// Thread (tr, tc) owns rows {tr, tr+32} x columns {tc, tc+8, tc+16, tc+24}.
+// ---------------------------------------------------------------------------
+constexpr int kLdA = kGemmBM + 1;
+constexpr int kLdX = kGemmBN + 1;
+
+template <int NB>
+constexpr size_t gemm_smem_bytes() { return (size_t)NB * (kLdA + kLdX) * sizeof(double2); }
+
+template <int NB, bool SAFE, bool CONJ>
+__global__ void __launch_bounds__(kGemmThreads)
+k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *sA = reinterpret_cast<double2 *>(smem_raw);   // [NB][kLdA]
+  double2 *sX = sA + NB * kLdA;                           // [NB][kLdX]
+  const Prob &P = tab.p[blockIdx.z];
+  if (step >= P.nblk) return;
+  const int b = CONJ ? P.nblk - 1 - step : step;
+  int lo, hi;
+  block_range(P, b, NB, lo, hi);
+  const int K = hi - lo;
+  const int rend = CONJ ? P.m : lo;
+  const int r0 = (CONJ ? hi : 0) + blockIdx.y * kGemmBM;
+  if (r0 >= rend) return;
+  const int c0 = (shortcut ? lo + 1 : 0) + blockIdx.x * kGemmBN;
+  if (c0 >= P.n) return;
+  const int tid = threadIdx.x;
+
+  for (int idx = tid; idx < NB * kGemmBM; idx += kGemmThreads) {
+    int k, r;
+    if (!CONJ) { k = idx / kGemmBM; r = idx - k * kGemmBM; }   // coalesced along U's rows
+    else { r = idx / NB; k = idx - r * NB; }                    // coalesced along U's rows (= k)
+    double2 v = make_double2(0.0, 0.0);
+    if (k < K && r0 + r < rend)
+      v = CONJ ? zconj(P.U[(lo + k) + (long long)(r0 + r) * P.ldu])
+               : P.U[(r0 + r) + (long long)(lo + k) * P.ldu];
+    sA[k * kLdA + r] = v;
+  }
+  for (int idx = tid; idx < NB * kGemmBN; idx += kGemmThreads) {
+    const int c = idx / NB, k = idx - c * NB;
+    double2 v = make_double2(0.0, 0.0);
+    if (k < K && c0 + c < P.n) v = P.B[(lo + k) + (long long)(c0 + c) * P.ldb];
+    sX[k * kLdX + c] = v;
+  }
+  __syncthreads();
+
+  const int tr = tid & 31, tc = tid >> 5;
+  double2 acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = make_double2(0.0, 0.0);
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    const double2 a0 = sA[k * kLdA + tr];
+    const double2 a1 = sA[k * kLdA + tr + 32];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double2 x = sX[k * kLdX + tc + 8 * c];
+      acc[0][c] = zfma(acc[0][c], a0, x);
+      acc[1][c] = zfma(acc[1][c], a1, x);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int col = c0 + tc + 8 * c;
+    if (col >= P.n) continue;
+    const int pend = SAFE ? P.pend[col] : 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int row = r0 + tr + 32 * i;
+      if (row >= rend) continue;
+      double2 *p = P.B + row + (long long)col * P.ldb;
+      double2 v = *p;
+      if (SAFE && pend) v = make_double2(scalbn(v.x, -pend), scalbn(v.y, -pend));
+      *p = zsub(v, acc[i][c]);
+    }
+  }
+}
+
+// Final lazy rescale (safe variant): block b of column j was finished with
+// exponent E[b][j]; it still owes 2^-(e_j - E[b][j]).  Also writes s_j.
+__global__ void k_fixup(const __grid_constant__ ProbTable tab, int nb, int shortcut) {
+  const Prob &P = tab.p[blockIdx.z];
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= P.n) return;
+  const int ej = P.e[j];
+  const int end = shortcut ? min(j, P.m) : P.m;
+  double2 *col = P.B + (long long)j * P.ldb;
+  for (int b = 0; b < P.nblk; ++b) {
+    int lo, hi;
+    block_range(P, b, nb, lo, hi);
+    if (lo >= end) continue;
+    const int d = ej - P.E[(long long)b * P.n + j];
+    if (d == 0) continue;
+    const int top = min(hi, end);
+    for (int r = lo + lane; r < top; r += 32)
+      col[r] = make_double2(scalbn(col[r].x, -d), scalbn(col[r].y, -d));
+  }
+  if (lane == 0) {
+    const double s = scalbn(1.0, -ej);
+    if (P.scales) P.scales[j] = s;
+    if (P.scale_exp) P.scale_exp[j] = ej;
+    if (P.diag_z) col[j] = make_double2(s, 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static size_t prob_ws_bytes(int m, int n, int nb, bool safe) {
+  if (!safe || m == 0 || n == 0) return 0;
+  const size_t nblk = (size_t)(m + nb - 1) / nb;
+  size_t s = 0;
+  s += align256(sizeof(double) * n);            // G
+  s += align256(sizeof(int) * n) * 2;           // e, pend
+  s += align256(sizeof(int) * nblk * n);        // E
+  s += align256(sizeof(double) * m) * 3;        // cin, cup, rowsum
+  s += align256(sizeof(double) * nblk);         // cblk
+  s += align256(sizeof(double));                // delta
+  return s;
+}
+
+size_t engine_workspace_bytes(const EngineProblem *probs, int count, int nb, bool safe) {
+  size_t s = 0;
+  for (int p = 0; p < count; ++p) s += prob_ws_bytes(probs[p].m, probs[p].n, nb, safe);
+  return s;
+}
+
+template <typename T>
+static T *carve(char *&cur, size_t count) {
+  T *p = reinterpret_cast<T *>(cur);
+  cur += align256(sizeof(T) * count);
+  return p;
+}
+
+template <int NB, bool SAFE, bool CONJ>
+static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, int count,
+                             bool shortcut, uint32_t *status, cudaStream_t st) {
+  constexpr size_t diag_smem = (size_t)NB * (NB + 1) * sizeof(double2) + NB * sizeof(double);
+  constexpr size_t gsmem = gemm_smem_bytes<NB>();
+  cudaError_t err = cudaFuncSetAttribute(k_diag<NB, SAFE, CONJ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(k_gemm<NB, SAFE, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gsmem);
+  if (err != cudaSuccess) return err;
+  int maxblk = 0;
+  for (int p = 0; p < count; ++p) maxblk = std::max(maxblk, (probs[p].m + NB - 1) / NB);
+  for (int s = 0; s < maxblk; ++s) {
+    int dx = 0, gx = 0, gy = 0;
+    for (int p = 0; p < count; ++p) {
+      const int m = probs[p].m, n = probs[p].n, nblk = (m + NB - 1) / NB;
+      if (s >= nblk || n == 0) continue;
+      const int b = CONJ ? nblk - 1 - s : s;
+      const int hi = m - b * NB, lo = std::max(0, hi - NB);
+      const int ncols = shortcut ? n - (lo + 1) : n;
+      if (ncols <= 0) continue;
+      const int rows = CONJ ? m - hi : lo;
+      dx = std::max(dx, (ncols + kDiagWarps - 1) / kDiagWarps);
+      if (rows > 0) {
+        gx = std::max(gx, (ncols + kGemmBN - 1) / kGemmBN);
+        gy = std::max(gy, (rows + kGemmBM - 1) / kGemmBM);
+      }
+    }
+    if (dx > 0) {
+      k_diag<NB, SAFE, CONJ><<<dim3(dx, 1, tab.count), kDiagWarps * 32, diag_smem, st>>>(
+          tab, s, shortcut ? 1 : 0, status);
+    }
+    if (gx > 0 && gy > 0) {
+      k_gemm<NB, SAFE, CONJ><<<dim3(gx, gy, tab.count), kGemmThreads, gsmem, st>>>(
+          tab, s, shortcut ? 1 : 0);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <int NB>
+static cudaError_t run_nb(const ProbTable &tab, const EngineProblem *probs, int count, bool safe,
+                          bool conj, bool shortcut, uint32_t *status, cudaStream_t st) {
+  if (safe) return run_steps<NB, true, false>(tab, probs, count, shortcut, status, st);
+  if (conj) return run_steps<NB, false, true>(tab, probs, count, shortcut, status, st);
+  return run_steps<NB, false, false>(tab, probs, count, shortcut, status, st);
+}
+
+cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe, bool conj,
+                       bool shortcut, void *ws, uint32_t *status, cudaStream_t st) {
+  char *cur = static_cast<char *>(ws);
+  for (int base = 0; base < count; base += kMaxProbs) {
+    const int cnt = std::min(kMaxProbs, count - base);
+    ProbTable tab;
+    tab.count = cnt;
+    int maxm = 0, maxn = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const EngineProblem &q = probs[base + i];
+      Prob &P = tab.p[i];
+      P = Prob{};
+      P.U = q.U; P.ldu = q.ldu; P.shifts = q.shifts; P.shift_stride = q.shift_stride;
+      P.B = q.B; P.ldb = q.ldb; P.scales = q.scales; P.scale_exp = q.scale_exp;
+      P.m = q.m; P.n = q.n; P.nblk = (q.m + nb - 1) / nb; P.diag_z = q.diag_z;
+      if (safe && q.m > 0 && q.n > 0) {
+        P.G = carve<double>(cur, q.n);
+        P.e = carve<int>(cur, q.n);
+        P.pend = carve<int>(cur, q.n);
+        P.E = carve<int>(cur, (size_t)P.nblk * q.n);
+        P.cin = carve<double>(cur, q.m);
+        P.cup = carve<double>(cur, q.m);
+        P.rowsum = carve<double>(cur, q.m);
+        P.cblk = carve<double>(cur, P.nblk);
+        P.delta = carve<double>(cur, 1);
+      }
+      maxm = std::max(maxm, q.m);
+      maxn = std::max(maxn, q.n);
+    }
+    if (maxm == 0 || maxn == 0) continue;
+    const int sc = shortcut ? 1 : 0;
+    if (safe) {
+      k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status);
+      k_rowsums<<<dim3((maxm + 127) / 128, 1, cnt), 128, 0, st>>>(tab);
+      k_safe_finish<<<dim3(1, 1, cnt), 256, 0, st>>>(tab, nb);
+      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);
+    }
+    cudaError_t err;
+    switch (nb) {
+      case 16: err = run_nb<16>(tab, probs + base, cnt, safe, conj, shortcut, status, st); break;
+      case 32: err = run_nb<32>(tab, probs + base, cnt, safe, conj, shortcut, status, st); break;
+      case 64: err = run_nb<64>(tab, probs + base, cnt, safe, conj, shortcut, status, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    if (err != cudaSuccess) return err;
+    if (safe) k_fixup<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, sc);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t engine_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z, long long ldz,
+                               cudaStream_t st) {
+  if (m > 0) k_trevc_setup<<<m, 256, 0, st>>>(T, ldt, m, Z, ldz);
+  return cudaGetLastError();
+}
+
+}  // namespace msts

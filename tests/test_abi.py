@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/msts.h declares, and rejects invalid arguments before
+launching anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1607_01477_gb300 as msts
+from paper_1607_01477_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return msts.load_library()
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:int|size_t)\s+(msts_\w+)\s*\(", txt, re.M))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ["msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra",
+              "msts_adjoint", "msts_adjoint_batched", "msts_version"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert lib.msts_version() >= 10000
+
+
+def test_invalid_arguments_rejected_without_launch(lib):
+    P = ctypes.c_void_p(16)
+    # negative m
+    assert lib.msts_solve(P, 1, -1, P, 1, P, 1, None, None, 32, None, 0, None, 0, None) == -3
+    # ldu < m
+    assert lib.msts_solve(P, 3, 4, P, 1, P, 4, None, None, 32, None, 0, None, 0, None) == -2
+    # bad nb
+    assert lib.msts_solve(P, 4, 4, P, 1, P, 4, None, None, 48, None, 0, None, 0, None) == -10
+    # safe without scales
+    assert lib.msts_solve(P, 4, 4, P, 1, P, 4, None, None, 32, P, 1 << 20, None, 1, None) == -8
+    # safe | conj_trans is not offered
+    assert lib.msts_solve(P, 4, 4, P, 1, P, 4, P, P, 32, P, 1 << 20, None, 3, None) == -14
+    # workspace too small for the safe solve
+    assert lib.msts_solve(P, 4, 4, P, 1, P, 4, P, P, 32, P, 8, None, 1, None) == -12
+    # empty problems are no-ops
+    assert lib.msts_solve(None, 1, 0, None, 0, None, 1, None, None, 32, None, 0, None, 0, None) == 0
+    assert lib.msts_trevc(None, 1, 0, None, 1, None, None, 32, None, 0, None, None) == 0
+    assert lib.msts_pseudospectra(P, 4, 4, P, 2, P, 4, 0, P, None, None, None, 32, None, 0, None, None) == -8
+
+
+def test_workspace_sizes(lib):
+    assert lib.msts_solve_workspace_size(100, 10, 32, 0) == 0
+    ws = lib.msts_solve_workspace_size(100, 10, 32, 1)
+    assert ws > 100 * 8 * 3
+    assert lib.msts_trevc_workspace_size(64, 32) == lib.msts_solve_workspace_size(64, 64, 32, 1)
+    assert lib.msts_pseudospectra_workspace_size(50, 7, 20, 32) >= 21 * 50 * 7 * 16

@@ -63,3 +63,13 @@ def test_first_column_is_unit():
     T = W.trevc_problem(33, seed=2)
     Z, e, sc = oracle.trevc(T, 8)
     assert Z[0, 0] == 1 and (Z[1:, 0] == 0).all()
+
+
+def test_selected_columns_match_full_trevc():
+    """The per-column entry point repeats or_trevc's arithmetic bit for bit."""
+    T = W.trevc_problem(300, seed=9)
+    Z, e, sc = oracle.trevc(T, 32)
+    cols = [0, 1, 31, 32, 33, 150, 299]
+    Zc, ec = oracle.trevc_columns(T, cols, 32)
+    assert np.array_equal(ec, e[cols])
+    assert np.array_equal(Zc, Z[:, cols])
