@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-shift triangular solve library on GB300.
+
+Default workload (one "step"): safe triangular eigenvectors (Alg. 6 on top of
+the safe multi-shift solve, Alg. 4/5) of a 4096 x 4096 upper-triangular T with
+5% of its eigenvalues in clusters of spacing 1e-10 and strictly-upper entries
+10 * CN(0,1): all 4096 eigenvectors, n_b = 32.  The metric is TFLOP/s at the
+algorithmic count (4/3) m^3.  Inputs are synthetic and seeded; T (268 MB) is
+larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload trevc|plain|pseudo|batch] [--no-extra]
+
+One JSON line is printed by rank 0.  With N > 1 (torchrun) every rank solves
+its own, independently seeded problem of the same size (weak scaling, no
+collective on the data path); value is the total FLOPs of all ranks over the
+slowest rank's time.
+
+`--impl reference` times the CPU oracle (the only other place this script
+runs it) on the host cores for the same workload and metric, on a bounded
+sample of eigenvector columns per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multi-shift solve TFLOP/s + pseudospectra shifts/s, mixed vs FP64 at stated error"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA pipe: 2 DFMA per clock per SM (1.25 TFLOP/s nominal) x 152 SMs x
+# 2.07 GHz maximum SM clock x 2 FLOPs.
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="trevc", choices=["trevc", "plain", "pseudo", "batch"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--nb", type=int, default=32)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (one process per GPU, launched by torchrun)
+# --------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s, p in zip(sm, power) if p > 0.3 * max(power)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# roofline helpers
+# --------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_1607_01477_gb300", "csrc", "msts_solve.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    if it was taken on a different version of the kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not t or h.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def fp64_peak():
+    return {"peak": FP64_PEAK_TFLOPS, "source": "derived: 2 DFMA/clk/SM x 152 SM x 2.07 GHz x 2"}
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+def trevc_flops(m: int) -> float:
+    return 4.0 / 3.0 * m ** 3
+
+
+def run_native(args):
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    lib = msts.load_library()
+    import ctypes
+    lib.msts_launch_count.restype = ctypes.c_uint64
+    lib.msts_trace_begin.argtypes = [ctypes.c_int64]
+    lib.msts_trace_query.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+
+    wl = args.workload
+    nb = args.nb
+    stream = torch.cuda.current_stream(dev)
+    if wl == "trevc":
+        m = 4096
+        T = W.trevc_problem(m, seed=W.BASE_SEED + 2 + 1000 * rank)
+        Td = msts.colmajor(torch.from_numpy(T).to(dev))
+        Z = msts.colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
+        sc = torch.empty(m, dtype=torch.float64, device=dev)
+        se = torch.empty(m, dtype=torch.int32, device=dev)
+        ws = torch.empty(lib.msts_trevc_workspace_size(m, nb) + 256, dtype=torch.uint8, device=dev)
+        wp, wb = msts._ws_ptr(ws)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+        def step():
+            rc = lib.msts_trevc(msts._ptr(Td), m, m, msts._ptr(Z), m, msts._ptr(sc), msts._ptr(se),
+                                nb, wp, wb, msts._ptr(status), msts._stream(dev))
+            assert rc == 0, rc
+
+        flops_per_step = trevc_flops(m)
+        unit = "TFLOP/s"
+        config = {"workload": "safe TREVC (Alg. 6 on Alg. 5), T 4096x4096 complex128, 5% eigenvalues "
+                              "in clusters of 4 at spacing 1e-10, strictly-upper 10*CN(0,1), all 4096 "
+                              "eigenvectors", "m": m, "n_b": nb, "eigenvectors": m,
+                  "flops_per_step": "(4/3) m^3 algorithmic",
+                  "l2": "no flush: T (268 MB) and Z (268 MB) exceed the 129 MB L2",
+                  "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+        h2d_host = torch.from_numpy(T).pin_memory()
+        Zh = torch.empty((m, m), dtype=torch.complex128).pin_memory()
+
+        def e2e_step():
+            Td.copy_(msts.colmajor(h2d_host.to(dev, non_blocking=True)))
+            step()
+            Zh.copy_(Z, non_blocking=True)
+
+        e2e_bytes = (T.nbytes, T.nbytes + m * 12)
+    else:
+        raise SystemExit(f"workload {wl}: use the dedicated bench sections")
+
+    # warm-up
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = lib.msts_launch_count()
+    lib.msts_trace_begin(1 << 20)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    lib.msts_trace_end()
+    launches = lib.msts_launch_count() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, dist, dev)
+    total_flops = sum_over_ranks(flops_per_step, dist, dev)
+    value = total_flops / (ms_max * 1e-3) / 1e12
+
+    tms = ctypes.c_double()
+    tn = ctypes.c_int64()
+    tf = ctypes.c_double()
+    tb = ctypes.c_double()
+    lib.msts_trace_query(0, ctypes.byref(tms), ctypes.byref(tn), ctypes.byref(tf), ctypes.byref(tb))
+    gemm_ms, gemm_n, gemm_flops, gemm_bytes = tms.value, tn.value, tf.value, tb.value
+    lib.msts_trace_query(1, ctypes.byref(tms), ctypes.byref(tn), ctypes.byref(tf), ctypes.byref(tb))
+    diag_ms, diag_n, diag_flops = tms.value, tn.value, tf.value
+    peak = fp64_peak()
+    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    traffic = profiled_traffic("k_gemm", wl)
+    roofline = {"bound": "alu", "kernel": "k_gemm<32,SAFE> (FP64 DFMA substitution GEMM)",
+                "achieved": achieved, "peak": peak["peak"], "unit": "TFLOP/s",
+                "frac": achieved / peak["peak"] if achieved else None, "traffic": traffic,
+                "peak_source": peak["source"],
+                "algorithmic_flops_per_launch": gemm_flops / max(gemm_n, 1),
+                "avg_launch_ms": gemm_ms / max(gemm_n, 1),
+                "share_of_step": gemm_ms / (ms * args.steps) if ms > 0 else None,
+                "diag_kernel": {"avg_launch_ms": diag_ms / max(diag_n, 1),
+                                "tflops": diag_flops / (diag_ms * 1e-3) / 1e12 if diag_ms else None,
+                                "share_of_step": diag_ms / (ms * args.steps) if ms > 0 else None}}
+
+    # end to end through the public API with host buffers
+    for _ in range(1):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, dist, dev)
+    e2e = {"value": total_flops / (e2e_ms * 1e-3) / 1e12, "unit": unit,
+           "h2d_bytes_per_step": e2e_bytes[0], "d2h_bytes_per_step": e2e_bytes[1]}
+
+    out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
+           "clocks": clk.summary()}
+    st = int(status.item())
+    out["status_bits"] = [n for b, n in msts.STATUS_BITS.items() if st & b]
+
+    if rank == 0 and wl == "trevc":
+        out["cpu_baseline"] = cpu_baseline_trevc(T)
+    if rank == 0 and not args.no_extra:
+        out["extra"] = extra_measurements(dev, nb)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extra_measurements(dev, nb):
+    """Secondary lines of the metric on the other workloads (one GPU)."""
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    res = {}
+    # workload 1: plain 256 x 256, 64 shifts (latency-bound)
+    U, s, B = W.plain_problem()
+    Ud, sd, Bd = (msts.colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
+                  msts.colmajor(torch.from_numpy(B).to(dev)))
+    X = Bd.clone()
+    for _ in range(5):
+        X.copy_(Bd)
+        msts.msts_solve(Ud, sd, X, nb=nb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    e0.record()
+    for _ in range(reps):
+        msts.msts_solve(Ud, sd, X, nb=nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    res["plain_256x64"] = {"us_per_solve": ms * 1e3, "tflops": 4 * 256 ** 2 * 64 / (ms * 1e-3) / 1e12}
+    # workload 4: pseudospectra 2000 x 2000, 100 x 100 grid, 20 Lanczos steps
+    T, z, V0 = W.pseudo_problem()
+    Td, zd, Vd = (msts.colmajor(torch.from_numpy(T).to(dev)), torch.from_numpy(z).to(dev),
+                  msts.colmajor(torch.from_numpy(V0).to(dev)))
+    msts.msts_pseudospectra(Td, zd[:256], msts.colmajor(Vd[:, :256]), 20, nb=nb)
+    torch.cuda.synchronize()
+    e0.record()
+    sig, *_ = msts.msts_pseudospectra(Td, zd, Vd, 20, nb=nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    N = z.size
+    res["pseudospectra_2000_grid100x100"] = {
+        "shifts_per_s": N / (ms * 1e-3), "ms": ms,
+        "tflops": 20 * 2 * 4 * 2000 ** 2 * N / (ms * 1e-3) / 1e12}
+    return res
+
+
+def cpu_baseline_trevc(T, stride=2):
+    """The oracle (as it stands) on the host cores: every `stride`-th eigenvector
+    column of the same 4096 x 4096 matrix, TFLOP/s at 4 j^2 FLOPs per column j."""
+    import oracle
+    m = T.shape[0]
+    cols = np.arange(0, m, stride)
+    oracle.trevc_columns(T, cols[:8], 32)          # load / build the oracle first
+    t0 = time.perf_counter()
+    oracle.trevc_columns(T, cols, 32)
+    dt = time.perf_counter() - t0
+    fl = float(sum(4.0 * j * j for j in cols))
+    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"every {stride}nd eigenvector column of the 4096x4096 TREVC matrix "
+                      f"({cols.size} columns, {fl / 1e9:.1f} GFLOP, {dt:.1f} s wall)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1607_01477_gb300 import workloads as W
+    import oracle
+    T = W.trevc_problem(4096)
+    m = 4096
+    stride = 16
+    cols_all = np.arange(0, m, stride)
+    oracle.trevc_columns(T, cols_all[:4], 32)
+    times = []
+    for k in range(args.warmup + args.steps):
+        cols = cols_all[(k % 4)::4]                 # a bounded sample per step
+        t0 = time.perf_counter()
+        oracle.trevc_columns(T, cols, 32)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append((dt, float(sum(4.0 * j * j for j in cols))))
+    tot_t = sum(t for t, _ in times)
+    tot_f = sum(f for _, f in times)
+    value = tot_f / tot_t / 1e12
+    out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / len(times) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": "safe TREVC (Alg. 6 on Alg. 5), T 4096x4096 complex128, 5% "
+                                  "eigenvalues in clusters of 4 at spacing 1e-10, strictly-upper "
+                                  "10*CN(0,1)", "m": m, "n_b": 32},
+           "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+                            "kind": "oracle",
+                            "sample": f"{cols_all.size // 4} eigenvector columns per step "
+                                      f"(every {4 * stride}th column, rotating offset)"},
+           "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

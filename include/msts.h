@@ -191,6 +191,27 @@ int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32
                          void *workspace, size_t workspace_bytes,
                          uint32_t *status, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Instrumentation (not in the paper).
+ * msts_launch_count: number of kernels the library has launched in this
+ *   process so far (all entry points).
+ * msts_trace_begin(capacity): from now on, bracket each launch of the hot
+ *   kernels (MSTS_KERNEL_GEMM: the substitution GEMM, MSTS_KERNEL_DIAG: the
+ *   diagonal-block solve) with CUDA events on its stream, for at most
+ *   `capacity` launches, recording the algorithmic FLOPs (8 per complex
+ *   multiply-add) and algorithmic bytes of each launch.  Host-side; not for
+ *   use inside stream capture.
+ * msts_trace_end: waits for the recorded events, accumulates per-kernel
+ *   totals and stops recording.  msts_trace_query reads the totals.
+ * ------------------------------------------------------------------------- */
+#define MSTS_KERNEL_GEMM 0
+#define MSTS_KERNEL_DIAG 1
+uint64_t msts_launch_count(void);
+int msts_trace_begin(int64_t capacity);
+int msts_trace_end(void);
+int msts_trace_query(int32_t kernel, double *total_ms, int64_t *launches, double *flops,
+                     double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,8 +106,10 @@ def load_library():
 # marshalling helpers
 # --------------------------------------------------------------------------
 def colmajor(x: torch.Tensor) -> torch.Tensor:
-    """A column-major (Fortran-order) copy of a 2-D tensor."""
-    return x.t().contiguous().t()
+    """A new column-major (Fortran-order) copy of a 2-D tensor (never a view)."""
+    out = torch.empty((x.shape[1], x.shape[0]), dtype=x.dtype, device=x.device).t()
+    out.copy_(x)
+    return out
 
 
 def _mat(x: torch.Tensor, name: str, rows: int | None = None) -> int:

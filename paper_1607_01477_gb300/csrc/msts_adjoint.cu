@@ -11,6 +11,7 @@
 
 #include "msts_common.cuh"
 #include "msts_engine.h"
+#include "msts_trace.h"
 
 namespace msts {
 
@@ -160,8 +161,10 @@ cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb
       e = engine_run(adj.data(), cnt, nb, false, true, false, nullptr, status, st);
       if (e != cudaSuccess) return e;
       k_ds<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(at);
+      count_launches(2);
     }
     k_triu_gemm<<<dim3((maxm + kTBN - 1) / kTBN, (maxm + kTBM - 1) / kTBM, cnt), kTThreads, 0, st>>>(at);
+    count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

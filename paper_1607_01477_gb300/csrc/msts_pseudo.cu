@@ -15,6 +15,7 @@
 
 #include "msts_common.cuh"
 #include "msts_engine.h"
+#include "msts_trace.h"
 
 namespace msts {
 
@@ -229,6 +230,7 @@ cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z,
   P.B = S.W; P.ldb = m;
 
   k_lanczos_init<<<N, kLzThreads, 0, st>>>(S, V0, ldv);
+  count_launches(1);
   for (int k = 0; k < K; ++k) {
     k_lanczos_load<<<std::max(1, std::min(4096, (int)(((long long)m * N + 255) / 256))), 256, 0, st>>>(S, k);
     cudaError_t e = engine_run(&P, 1, nb, false, false, false, engine_ws, status, st);  // (T - zI)^{-1}
@@ -236,8 +238,10 @@ cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z,
     e = engine_run(&P, 1, nb, false, true, false, engine_ws, status, st);               // (T - zI)^{-H}
     if (e != cudaSuccess) return e;
     k_lanczos_step<<<N, kLzThreads, 0, st>>>(S, k);
+    count_launches(2);
   }
   k_ritz<<<(N + 127) / 128, 128, 0, st>>>(S, sigma_min);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 
 #include "msts_common.cuh"
 #include "msts_engine.h"
+#include "msts_trace.h"
 
 namespace msts {
 
@@ -534,8 +535,10 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
   if (err != cudaSuccess) return err;
   int maxblk = 0;
   for (int p = 0; p < count; ++p) maxblk = std::max(maxblk, (probs[p].m + NB - 1) / NB);
+  const bool tracing = trace_on();
   for (int s = 0; s < maxblk; ++s) {
     int dx = 0, gx = 0, gy = 0;
+    double gflops = 0, gbytes = 0, dflops = 0, dbytes = 0;
     for (int p = 0; p < count; ++p) {
       const int m = probs[p].m, n = probs[p].n, nblk = (m + NB - 1) / NB;
       if (s >= nblk || n == 0) continue;
@@ -544,19 +547,31 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       const int ncols = shortcut ? n - (lo + 1) : n;
       if (ncols <= 0) continue;
       const int rows = CONJ ? m - hi : lo;
+      const double K = hi - lo;
       dx = std::max(dx, (ncols + kDiagWarps - 1) / kDiagWarps);
+      // algorithmic work: 8 real FLOPs per complex multiply-add
+      dflops += 4.0 * K * K * ncols;
+      dbytes += 16.0 * K * K / 2 + 32.0 * K * ncols;
       if (rows > 0) {
         gx = std::max(gx, (ncols + kGemmBN - 1) / kGemmBN);
         gy = std::max(gy, (rows + kGemmBM - 1) / kGemmBM);
+        gflops += 8.0 * rows * K * ncols;
+        gbytes += 16.0 * rows * K + 16.0 * K * ncols + 32.0 * (double)rows * ncols;
       }
     }
     if (dx > 0) {
+      void *h = tracing ? trace_start(1, dflops, dbytes, st) : nullptr;
       k_diag<NB, SAFE, CONJ><<<dim3(dx, 1, tab.count), kDiagWarps * 32, diag_smem, st>>>(
           tab, s, shortcut ? 1 : 0, status);
+      trace_stop(h, st);
+      count_launches(1);
     }
     if (gx > 0 && gy > 0) {
+      void *h = tracing ? trace_start(0, gflops, gbytes, st) : nullptr;
       k_gemm<NB, SAFE, CONJ><<<dim3(gx, gy, tab.count), kGemmThreads, gsmem, st>>>(
           tab, s, shortcut ? 1 : 0);
+      trace_stop(h, st);
+      count_launches(1);
     }
   }
   return cudaGetLastError();
@@ -605,7 +620,7 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
       k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status);
       k_rowsums<<<dim3((maxm + 127) / 128, 1, cnt), 128, 0, st>>>(tab);
       k_safe_finish<<<dim3(1, 1, cnt), 256, 0, st>>>(tab, nb);
-      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);
+      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);  count_launches(4);
     }
     cudaError_t err;
     switch (nb) {
@@ -615,7 +630,10 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
       default: return cudaErrorInvalidValue;
     }
     if (err != cudaSuccess) return err;
-    if (safe) k_fixup<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, sc);
+    if (safe) {
+      k_fixup<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, sc);
+      count_launches(1);
+    }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
@@ -624,7 +642,10 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
 
 cudaError_t engine_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z, long long ldz,
                                cudaStream_t st) {
-  if (m > 0) k_trevc_setup<<<m, 256, 0, st>>>(T, ldt, m, Z, ldz);
+  if (m > 0) {
+    k_trevc_setup<<<m, 256, 0, st>>>(T, ldt, m, Z, ldz);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
