@@ -212,6 +212,38 @@ int msts_trace_end(void);
 int msts_trace_query(int32_t kernel, double *total_ms, int64_t *launches, double *flops,
                      double *bytes);
 
+/* ---------------------------------------------------------------------------
+ * Safe multi-shift solve without any allocation (the paper has no
+ * counterpart; this is a convenience of this library).
+ *
+ * For callers that cannot allocate device memory when they need the solve:
+ * cudaMalloc synchronises the device and may fail at run time, so code with a
+ * fixed memory budget, or whose host framework owns every allocation, often
+ * may not call it.  This entry point computes exactly what msts_solve with
+ * flags = MSTS_SAFE computes (same arguments, same meaning), but takes its
+ * scratch from a 16 MiB array that the library keeps in device memory on
+ * every GPU that loads it, until the process exits.  It calls no allocator.
+ *  - The caller still passes U, shifts, B, scales, scale_exp (and status).
+ *  - Problems whose scratch need (msts_solve_workspace_size(m, n, nb,
+ *    MSTS_SAFE)) exceeds 16 MiB are rejected with MSTS_ERR_STATIC_SCRATCH
+ *    before anything is launched (e.g. m = n = 4096 at n_b = 32 needs ~2.2 MiB).
+ *  - The first call on a device looks up the array's device address with that
+ *    device current (cudaGetSymbolAddress); make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array and the kernels write every scratch word
+ *    before reading it, so nothing needs clearing between calls; but calls
+ *    whose work overlaps on the GPU (different streams, or concurrent host
+ *    threads without ordering) race on it.  Order such calls on one stream.
+ * Returns 0, -k for invalid argument k (numbering as msts_solve without the
+ * workspace arguments), MSTS_ERR_STATIC_SCRATCH or MSTS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+#define MSTS_ERR_STATIC_SCRATCH (-1001)
+int msts_safe_solve_static(const msts_z *U, int64_t ldu, int64_t m,
+                           const msts_z *shifts, int64_t n,
+                           msts_z *B, int64_t ldb,
+                           double *scales, int32_t *scale_exp,
+                           int32_t nb, uint32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
