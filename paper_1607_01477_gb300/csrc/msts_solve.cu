@@ -28,10 +28,7 @@
 
 namespace msts {
 
-constexpr int kDiagWarps = 8;
-constexpr int kGemmBM = 64;
-constexpr int kGemmBN = 32;
-constexpr int kGemmThreads = 256;
+constexpr int kNumSMs = 152;
 
 __device__ __forceinline__ void block_range(const Prob &P, int b, int nb, int &lo, int &hi) {
   hi = P.m - b * nb;
@@ -156,51 +153,56 @@ __global__ void k_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z
 }
 
 // ---------------------------------------------------------------------------
-// Diagonal-block step: one warp per shift, lane = row (rows lane + 32q).
+// Diagonal-block step (Alg. 3's inner loop; Alg. 4 + Alg. 5's column update in
+// the safe variant): one THREAD per shift.  GB300 issues FP64 at a few lanes
+// per clock per SM, so a warp instruction costs the same whether 1 or 32 of
+// its lanes do useful work; giving each lane its own shift keeps every lane of
+// every FP64 instruction busy (the block of U is the same for all shifts and is
+// broadcast from shared memory).  Each thread's block of B lives in its own
+// column of shared memory, sY[r * kThreads + tid].
 // ---------------------------------------------------------------------------
 template <int NB>
-struct Rows { static constexpr int kPerLane = NB > 32 ? NB / 32 : 1; };
+struct DiagCfg {
+  static constexpr int kThreads = NB >= 64 ? 64 : 128;
+  static constexpr int LD = NB + 1;
+  static constexpr size_t smem = (size_t)NB * LD * sizeof(double2) + (size_t)NB * kThreads * sizeof(double2)
+                                 + NB * sizeof(double);
+};
 
-// Back substitution on the upper n_b x n_b block (Alg. 1 on U(I1,I1) - lambda I)
-// or forward substitution on its conjugate transpose (CONJ).  sU holds the
-// block column-major with leading dimension NB + 1.
-template <int NB, bool CONJ>
-__device__ __forceinline__ void block_subst(double2 (&y)[Rows<NB>::kPerLane],
-                                            const double2 (&piv)[Rows<NB>::kPerLane],
-                                            const double2 *sU, int nbe, int lane) {
-  constexpr int RPL = Rows<NB>::kPerLane;
-  constexpr int LD = NB + 1;
-  for (int t = 0; t < nbe; ++t) {
-    const int i = CONJ ? t : nbe - 1 - t;
-    const int qi = i >> 5, li = i & 31;
-    double2 own = y[0];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q)
-      if (q == qi) {
-        if (lane == li) y[q] = zdiv(y[q], piv[q]);   // diagonal step
-        own = y[q];
-      }
-    const double2 xi = shfl_z(own, li);
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {                   // substitution (AXPY)
-      const int r = lane + 32 * q;
-      if (!CONJ) {
-        if (r < i) y[q] = zfms(y[q], xi, sU[i * LD + r]);
-      } else {
-        if (r > i && r < nbe) y[q] = zfms(y[q], xi, zconj(sU[r * LD + i]));
-      }
-    }
-  }
+// |z| with the components pre-scaled by a power of two (no overflow, no
+// underflow of the squares).
+__device__ __forceinline__ double zabs_scaled(double2 z) {
+  const double mx = fmax(fabs(z.x), fabs(z.y));
+  if (!(mx > 0.0) || isinf(mx)) return mx + fabs(z.x + z.y) * 0.0;   // 0, inf or NaN
+  const int e = ilogb(mx);
+  const double a = scalbn(z.x, -e), b = scalbn(z.y, -e);
+  return scalbn(sqrt(fma(a, a, b * b)), e);
+}
+
+// y / p as y * conj(p') / |p'|^2 * 2^-e with p' = p * 2^-e: one real division.
+__device__ __forceinline__ double2 zdiv_scaled(double2 y, double2 p) {
+  const double mx = fmax(fabs(p.x), fabs(p.y));
+  const int e = ilogb(mx);
+  const double a = scalbn(p.x, -e), b = scalbn(p.y, -e);
+  const double q = 1.0 / fma(a, a, b * b);
+  const double wr = fma(y.x, a, y.y * b) * q;
+  const double wi = fma(y.y, a, -(y.x * b)) * q;
+  return make_double2(scalbn(wr, -e), scalbn(wi, -e));
+}
+
+__device__ __forceinline__ double2 zscalbn(double2 z, int k) {
+  return make_double2(scalbn(z.x, k), scalbn(z.y, k));
 }
 
 template <int NB, bool SAFE, bool CONJ>
-__global__ void __launch_bounds__(kDiagWarps * 32)
+__global__ void __launch_bounds__(DiagCfg<NB>::kThreads)
 k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *status) {
-  constexpr int RPL = Rows<NB>::kPerLane;
-  constexpr int LD = NB + 1;
+  constexpr int T = DiagCfg<NB>::kThreads;
+  constexpr int LD = DiagCfg<NB>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2 *sU = reinterpret_cast<double2 *>(smem_raw);
-  double *sC = reinterpret_cast<double *>(sU + NB * LD);
+  double2 *sU = reinterpret_cast<double2 *>(smem_raw);   // block, column-major, LD
+  double2 *sY = sU + NB * LD;                             // sY[r * T + tid]
+  double *sC = reinterpret_cast<double *>(sY + NB * T);
 
   const Prob &P = tab.p[blockIdx.z];
   if (step >= P.nblk) return;
@@ -209,175 +211,142 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   block_range(P, b, NB, lo, hi);
   const int nbf = hi - lo;
   const int jstart = shortcut ? lo + 1 : 0;
-  const int jcta = jstart + blockIdx.x * kDiagWarps;
+  const int jcta = jstart + blockIdx.x * T;
   if (jcta >= P.n) return;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int idx = tid; idx < nbf * nbf; idx += blockDim.x) {
-    const int c = idx / nbf, r = idx - c * nbf;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += T) {
+    const int c = idx / NB, r = idx - c * NB;
     double2 v = make_double2(0.0, 0.0);
-    if (r <= c) v = P.U[(lo + r) + (long long)(lo + c) * P.ldu];
+    if (r <= c && c < nbf) v = P.U[(lo + r) + (long long)(lo + c) * P.ldu];
     sU[c * LD + r] = v;
   }
   if (SAFE)
-    for (int k = tid; k < nbf; k += blockDim.x) sC[k] = P.cin[lo + k];
+    for (int k = tid; k < NB; k += T) sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
   __syncthreads();
 
-  const int j = jcta + warp;
+  const int j = jcta + tid;
   if (j >= P.n) return;
-  const int nbe = shortcut ? min(hi, j) - lo : nbf;   // TREVC: rows >= j are zero
-  const double2 lam = P.shifts[(long long)j * P.shift_stride];
+  const int nbe = shortcut ? min(hi, j) - lo : nbf;   // TREVC: rows >= j stay zero
+  double2 lam = P.shifts[(long long)j * P.shift_stride];
+  if (CONJ) lam = zconj(lam);
   double2 *col = P.B + (long long)j * P.ldb + lo;
+  double2 *y = sY + tid;                                // y[r * T]
+  for (int r = 0; r < nbe; ++r) y[r * T] = col[r];
 
-  double2 y[RPL], piv[RPL];
-#pragma unroll
-  for (int q = 0; q < RPL; ++q) {
-    const int r = lane + 32 * q;
-    const bool v = r < nbe;
-    y[q] = v ? col[r] : make_double2(0.0, 0.0);
-    const double2 d = v ? sU[r * LD + r] : make_double2(0.0, 0.0);
-    piv[q] = CONJ ? zsub(zconj(d), zconj(lam)) : zsub(d, lam);
-    if (!v) piv[q] = make_double2(1.0, 0.0);
-  }
+  auto pivot = [&](int i) {
+    const double2 d = sU[i * LD + i];
+    return zsub(CONJ ? zconj(d) : d, lam);
+  };
+  // Plain substitution on rows [0, nbe) with pivots piv(i) (Alg. 1 per shift).
+  auto substitute = [&](auto piv) {
+    for (int t = 0; t < nbe; ++t) {
+      const int i = CONJ ? t : nbe - 1 - t;
+      const double2 xi = zdiv_scaled(y[i * T], piv(i));
+      y[i * T] = xi;
+      if (!CONJ) {
+        const double2 *ucol = sU + i * LD;
+#pragma unroll 4
+        for (int r = 0; r < i; ++r) y[r * T] = zfms(y[r * T], xi, ucol[r]);
+      } else {
+#pragma unroll 4
+        for (int r = i + 1; r < nbe; ++r) y[r * T] = zfms(y[r * T], xi, zconj(sU[r * LD + i]));
+      }
+    }
+  };
 
   if (!SAFE) {
     bool zp = false;
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) zp |= (lane + 32 * q < nbe) && zzero(piv[q]);
-    if (__any_sync(0xffffffffu, zp) && lane == 0) raise_status(status, MSTS_STATUS_ZERO_PIVOT);
-    block_subst<NB, CONJ>(y, piv, sU, nbe, lane);
-#pragma unroll
-    for (int q = 0; q < RPL; ++q)
-      if (lane + 32 * q < nbe) col[lane + 32 * q] = y[q];
+    for (int i = 0; i < nbe; ++i) zp |= zzero(pivot(i));
+    if (zp) raise_status(status, MSTS_STATUS_ZERO_PIVOT);
+    substitute(pivot);
+    for (int r = 0; r < nbe; ++r) col[r] = y[r * T];
     return;
   }
 
-  // ----- safe variant: Alg. 4 on the shifted block, then Alg. 5's column update
+  // ----- safe variant (upper only): Alg. 4 on the shifted block, then Alg. 5.
   const double OM = omega();
   const double dlt = *P.delta;
   bool used_delta = false;
-  double ap[RPL];
-#pragma unroll
-  for (int q = 0; q < RPL; ++q) {
-    const bool v = lane + 32 * q < nbe;
-    if (v && zzero(piv[q])) { piv[q] = make_double2(dlt, 0.0); used_delta = true; }
-    ap[q] = v ? zabs(piv[q]) : 1.0;
-  }
+  auto spiv = [&](int i) {
+    const double2 p = pivot(i);
+    return zzero(p) ? make_double2(dlt, 0.0) : p;
+  };
+  for (int i = 0; i < nbe; ++i) used_delta |= zzero(pivot(i));
+
+  // A priori growth bounds (Sec. 3) in a conservative form: |p| >= max(|Re p|,
+  // |Im p|) and |y| <= sqrt(2) max(|Re y|, |Im y|).  They only choose between the
+  // plain and the safeguarded substitution, which give identical results
+  // whenever the plain one is chosen, so a looser bound can only cost time.
   double g0 = 0.0;
-#pragma unroll
-  for (int q = 0; q < RPL; ++q)
-    if (lane + 32 * q < nbe) g0 = fmax(g0, zabs(y[q]));
-  g0 = warp_max(g0);
-
-  // Growth bounds: rows are processed bottom-up, so G before row i is
-  // G0 * prod_{k > i} (1 + c_k / |piv_k|) and M = max_i G_before(i) / |piv_i|;
-  // the products are formed as a warp suffix scan.
-  double carry = 1.0, mloc = 0.0;
-#pragma unroll
-  for (int q = RPL - 1; q >= 0; --q) {
-    const int r = lane + 32 * q;
-    const bool v = r < nbe;
-    const double f = v ? 1.0 + sC[r] / ap[q] : 1.0;
-    double S = f;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double t = __shfl_down_sync(0xffffffffu, S, o);
-      if (lane + o < 32) S *= t;
-    }
-    double ex = __shfl_down_sync(0xffffffffu, S, 1);
-    if (lane == 31) ex = 1.0;
-    if (v) {
-      const double qv = (g0 * carry * ex) / ap[q];
-      if (qv > mloc) mloc = qv;
-    }
-    carry *= __shfl_sync(0xffffffffu, S, 0);
+  for (int r = 0; r < nbe; ++r) g0 = fmax(g0, fmax(fabs(y[r * T].x), fabs(y[r * T].y)));
+  g0 *= 1.4142135623730951;
+  double Gb = g0, Mb = 0.0;
+  for (int i = nbe - 1; i >= 0; --i) {
+    const double2 p = spiv(i);
+    const double inv = 1.0 / fmax(fabs(p.x), fabs(p.y));
+    Mb = fmax(Mb, Gb * inv);
+    Gb = Gb * fma(sC[i], inv, 1.0);
   }
-  const double M1 = warp_max(mloc);
-  const double G1 = g0 * carry;
-
   int kexp = 0;
-  if (M1 < OM && G1 < OM) {
-    block_subst<NB, false>(y, piv, sU, nbe, lane);
+  if (Mb < OM && Gb < OM) {
+    substitute(spiv);
   } else {
     // Safeguarded back substitution (Alg. 4, second branch).
-    double G = g0;
+    double G = 0.0;
+    for (int r = 0; r < nbe; ++r) G = fmax(G, zabs_scaled(y[r * T]));
     for (int i = nbe - 1; i >= 0; --i) {
-      const int qi = i >> 5, li = i & 31;
-      int eM = -100000;
-#pragma unroll
-      for (int q = 0; q < RPL; ++q)
-        if (q == qi && lane == li) {
-          const double ay = zabs(y[q]);
-          eM = ay == 0.0 ? -100000 : ratio_exponent(ay, ap[q]);
+      const double2 p = spiv(i);
+      const double ay = zabs_scaled(y[i * T]);
+      if (ay != 0.0) {
+        const int eM = ratio_exponent(ay, zabs_scaled(p));
+        if (eM >= kOmegaExp) {                       // M >= Omega: rescale b first
+          const int kk = eM - (kOmegaExp - 1);
+          for (int r = 0; r < nbe; ++r) y[r * T] = zscalbn(y[r * T], -kk);
+          kexp += kk;
+          G = scalbn(G, -kk);
         }
-      eM = __shfl_sync(0xffffffffu, eM, li);
-      if (eM >= kOmegaExp) {                         // M >= Omega: rescale b first
-        const int kk = eM - (kOmegaExp - 1);
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) y[q] = make_double2(scalbn(y[q].x, -kk), scalbn(y[q].y, -kk));
-        kexp += kk;
-        G = scalbn(G, -kk);
       }
-      double Mv = 0.0;
-      double2 own = y[0];
-#pragma unroll
-      for (int q = 0; q < RPL; ++q)
-        if (q == qi) {
-          if (lane == li) { y[q] = zdiv(y[q], piv[q]); Mv = zabs(y[q]); }
-          own = y[q];
-        }
-      double2 xi = shfl_z(own, li);
-      Mv = __shfl_sync(0xffffffffu, Mv, li);
+      double2 xi = zdiv_scaled(y[i * T], p);
+      y[i * T] = xi;
+      const double Mv = zabs_scaled(xi);
       G = __dadd_rn(G, __dmul_rn(Mv, sC[i]));
       if (G >= OM) {                                 // protect the AXPY
         const int kk = choose_k(G);
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) y[q] = make_double2(scalbn(y[q].x, -kk), scalbn(y[q].y, -kk));
-        xi = make_double2(scalbn(xi.x, -kk), scalbn(xi.y, -kk));
+        for (int r = 0; r < nbe; ++r) y[r * T] = zscalbn(y[r * T], -kk);
+        xi = y[i * T];
         kexp += kk;
         G = scalbn(G, -kk);
       }
       const double2 *ucol = sU + i * LD;
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        const int r = lane + 32 * q;
-        if (r < i) y[q] = zfms(y[q], xi, ucol[r]);
-      }
+#pragma unroll 4
+      for (int r = 0; r < i; ++r) y[r * T] = zfms(y[r * T], xi, ucol[r]);
     }
   }
 
-  // Alg. 5: t < 1 rescales the rest of the column (lazily, see k_gemm/k_fixup),
-  // then G(j) += C_blk ||X(I1,j)||_inf and a rescale if it reaches Omega.
+  // Alg. 5: t < 1 rescales the rest of the column (lazily: k_gemm applies it to
+  // I0 and k_fixup to I2), then G(j) += C_blk ||X(I1,j)||_inf, rescaling the
+  // whole column if it reaches Omega.
   int ej = P.e[j];
   double Gj = P.G[j];
   int pend = 0;
   if (kexp > 0) { ej += kexp; Gj = scalbn(Gj, -kexp); pend = kexp; }
   double N = 0.0;
-#pragma unroll
-  for (int q = 0; q < RPL; ++q)
-    if (lane + 32 * q < nbe) N = fmax(N, zabs(y[q]));
-  N = warp_max(N);
+  for (int r = 0; r < nbe; ++r) N = fmax(N, zabs_scaled(y[r * T]));
   Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
+  int k2 = 0;
   if (Gj >= OM) {
-    const int kk = choose_k(Gj);
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) y[q] = make_double2(scalbn(y[q].x, -kk), scalbn(y[q].y, -kk));
-    ej += kk;
-    Gj = scalbn(Gj, -kk);
-    pend += kk;
+    k2 = choose_k(Gj);
+    ej += k2;
+    Gj = scalbn(Gj, -k2);
+    pend += k2;
   }
-#pragma unroll
-  for (int q = 0; q < RPL; ++q)
-    if (lane + 32 * q < nbe) col[lane + 32 * q] = y[q];
-  const bool any_delta = __any_sync(0xffffffffu, used_delta);
-  if (lane == 0) {
-    P.e[j] = ej;
-    P.G[j] = Gj;
-    P.pend[j] = pend;
-    P.E[(long long)b * P.n + j] = ej;
-    if (pend > 0) raise_status(status, MSTS_STATUS_SCALED);
-    if (any_delta) raise_status(status, MSTS_STATUS_DELTA);
-  }
+  for (int r = 0; r < nbe; ++r) col[r] = k2 ? zscalbn(y[r * T], -k2) : y[r * T];
+  P.e[j] = ej;
+  P.G[j] = Gj;
+  P.pend[j] = pend;
+  P.E[(long long)b * P.n + j] = ej;
+  if (pend > 0) raise_status(status, MSTS_STATUS_SCALED);
+  if (used_delta) raise_status(status, MSTS_STATUS_DELTA);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,18 +355,23 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
 // Tile kGemmBM x kGemmBN of B per CTA, K = the block's rows; FP64 DFMA.
 // Thread (tr, tc) owns rows {tr, tr+32} x columns {tc, tc+8, tc+16, tc+24}.
 // ---------------------------------------------------------------------------
-constexpr int kLdA = kGemmBM + 1;
-constexpr int kLdX = kGemmBN + 1;
+template <int BM, int BN>
+struct GemmCfg {
+  static constexpr int kThreads = 256;
+  static constexpr int LDA = BM + 1, LDX = BN + 1;
+  static constexpr int TM = BM / 32, TN = BN / 8;   // outputs per thread
+  template <int NB>
+  static constexpr size_t smem() { return (size_t)NB * (LDA + LDX) * sizeof(double2); }
+};
 
-template <int NB>
-constexpr size_t gemm_smem_bytes() { return (size_t)NB * (kLdA + kLdX) * sizeof(double2); }
-
-template <int NB, bool SAFE, bool CONJ>
-__global__ void __launch_bounds__(kGemmThreads)
+template <int NB, int BM, int BN, bool SAFE, bool CONJ>
+__global__ void __launch_bounds__(256)
 k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
+  using C = GemmCfg<BM, BN>;
+  constexpr int LDA = C::LDA, LDX = C::LDX, TM = C::TM, TN = C::TN, NT = C::kThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2 *sA = reinterpret_cast<double2 *>(smem_raw);   // [NB][kLdA]
-  double2 *sX = sA + NB * kLdA;                           // [NB][kLdX]
+  double2 *sA = reinterpret_cast<double2 *>(smem_raw);   // [NB][LDA]
+  double2 *sX = sA + NB * LDA;                            // [NB][LDX]
   const Prob &P = tab.p[blockIdx.z];
   if (step >= P.nblk) return;
   const int b = CONJ ? P.nblk - 1 - step : step;
@@ -405,54 +379,55 @@ k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
   block_range(P, b, NB, lo, hi);
   const int K = hi - lo;
   const int rend = CONJ ? P.m : lo;
-  const int r0 = (CONJ ? hi : 0) + blockIdx.y * kGemmBM;
+  const int r0 = (CONJ ? hi : 0) + blockIdx.y * BM;
   if (r0 >= rend) return;
-  const int c0 = (shortcut ? lo + 1 : 0) + blockIdx.x * kGemmBN;
+  const int c0 = (shortcut ? lo + 1 : 0) + blockIdx.x * BN;
   if (c0 >= P.n) return;
   const int tid = threadIdx.x;
 
-  for (int idx = tid; idx < NB * kGemmBM; idx += kGemmThreads) {
+  for (int idx = tid; idx < NB * BM; idx += NT) {
     int k, r;
-    if (!CONJ) { k = idx / kGemmBM; r = idx - k * kGemmBM; }   // coalesced along U's rows
-    else { r = idx / NB; k = idx - r * NB; }                    // coalesced along U's rows (= k)
+    if (!CONJ) { k = idx / BM; r = idx - k * BM; }   // coalesced along U's rows
+    else { r = idx / NB; k = idx - r * NB; }          // coalesced along U's rows (= k)
     double2 v = make_double2(0.0, 0.0);
     if (k < K && r0 + r < rend)
       v = CONJ ? zconj(P.U[(lo + k) + (long long)(r0 + r) * P.ldu])
                : P.U[(r0 + r) + (long long)(lo + k) * P.ldu];
-    sA[k * kLdA + r] = v;
+    sA[k * LDA + r] = v;
   }
-  for (int idx = tid; idx < NB * kGemmBN; idx += kGemmThreads) {
+  for (int idx = tid; idx < NB * BN; idx += NT) {
     const int c = idx / NB, k = idx - c * NB;
     double2 v = make_double2(0.0, 0.0);
     if (k < K && c0 + c < P.n) v = P.B[(lo + k) + (long long)(c0 + c) * P.ldb];
-    sX[k * kLdX + c] = v;
+    sX[k * LDX + c] = v;
   }
   __syncthreads();
 
   const int tr = tid & 31, tc = tid >> 5;
-  double2 acc[2][4];
+  double2 acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[i][c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < TN; ++c) acc[i][c] = make_double2(0.0, 0.0);
 #pragma unroll 4
   for (int k = 0; k < K; ++k) {
-    const double2 a0 = sA[k * kLdA + tr];
-    const double2 a1 = sA[k * kLdA + tr + 32];
+    double2 a[TM];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const double2 x = sX[k * kLdX + tc + 8 * c];
-      acc[0][c] = zfma(acc[0][c], a0, x);
-      acc[1][c] = zfma(acc[1][c], a1, x);
+    for (int i = 0; i < TM; ++i) a[i] = sA[k * LDA + tr + 32 * i];
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const double2 x = sX[k * LDX + tc + 8 * c];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) acc[i][c] = zfma(acc[i][c], a[i], x);
     }
   }
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < TN; ++c) {
     const int col = c0 + tc + 8 * c;
     if (col >= P.n) continue;
     const int pend = SAFE ? P.pend[col] : 0;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < TM; ++i) {
       const int row = r0 + tr + 32 * i;
       if (row >= rend) continue;
       double2 *p = P.B + row + (long long)col * P.ldb;
@@ -522,22 +497,28 @@ static T *carve(char *&cur, size_t count) {
   return p;
 }
 
+template <int NB, int BM, int BN, bool SAFE, bool CONJ>
+static void launch_gemm(const ProbTable &tab, int gx, int gy, int s, bool shortcut, cudaStream_t st) {
+  constexpr size_t smem = GemmCfg<BM, BN>::template smem<NB>();
+  cudaFuncSetAttribute(k_gemm<NB, BM, BN, SAFE, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  k_gemm<NB, BM, BN, SAFE, CONJ><<<dim3(gx, gy, tab.count), 256, smem, st>>>(tab, s, shortcut ? 1 : 0);
+}
+
 template <int NB, bool SAFE, bool CONJ>
 static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, int count,
                              bool shortcut, uint32_t *status, cudaStream_t st) {
-  constexpr size_t diag_smem = (size_t)NB * (NB + 1) * sizeof(double2) + NB * sizeof(double);
-  constexpr size_t gsmem = gemm_smem_bytes<NB>();
+  constexpr size_t diag_smem = DiagCfg<NB>::smem;
+  constexpr int diag_threads = DiagCfg<NB>::kThreads;
   cudaError_t err = cudaFuncSetAttribute(k_diag<NB, SAFE, CONJ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
-  if (err != cudaSuccess) return err;
-  err = cudaFuncSetAttribute(k_gemm<NB, SAFE, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)gsmem);
   if (err != cudaSuccess) return err;
   int maxblk = 0;
   for (int p = 0; p < count; ++p) maxblk = std::max(maxblk, (probs[p].m + NB - 1) / NB);
   const bool tracing = trace_on();
   for (int s = 0; s < maxblk; ++s) {
-    int dx = 0, gx = 0, gy = 0;
+    int dx = 0, rows_max = 0, cols_max = 0;
+    long long tiles_big = 0, tiles_mid = 0;
     double gflops = 0, gbytes = 0, dflops = 0, dbytes = 0;
     for (int p = 0; p < count; ++p) {
       const int m = probs[p].m, n = probs[p].n, nblk = (m + NB - 1) / NB;
@@ -548,28 +529,36 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       if (ncols <= 0) continue;
       const int rows = CONJ ? m - hi : lo;
       const double K = hi - lo;
-      dx = std::max(dx, (ncols + kDiagWarps - 1) / kDiagWarps);
+      dx = std::max(dx, (ncols + diag_threads - 1) / diag_threads);
       // algorithmic work: 8 real FLOPs per complex multiply-add
       dflops += 4.0 * K * K * ncols;
       dbytes += 16.0 * K * K / 2 + 32.0 * K * ncols;
       if (rows > 0) {
-        gx = std::max(gx, (ncols + kGemmBN - 1) / kGemmBN);
-        gy = std::max(gy, (rows + kGemmBM - 1) / kGemmBM);
+        rows_max = std::max(rows_max, rows);
+        cols_max = std::max(cols_max, ncols);
+        tiles_big += (long long)((rows + 63) / 64) * ((ncols + 31) / 32);
+        tiles_mid += (long long)((rows + 31) / 32) * ((ncols + 15) / 16);
         gflops += 8.0 * rows * K * ncols;
         gbytes += 16.0 * rows * K + 16.0 * K * ncols + 32.0 * (double)rows * ncols;
       }
     }
     if (dx > 0) {
       void *h = tracing ? trace_start(1, dflops, dbytes, st) : nullptr;
-      k_diag<NB, SAFE, CONJ><<<dim3(dx, 1, tab.count), kDiagWarps * 32, diag_smem, st>>>(
+      k_diag<NB, SAFE, CONJ><<<dim3(dx, 1, tab.count), diag_threads, diag_smem, st>>>(
           tab, s, shortcut ? 1 : 0, status);
       trace_stop(h, st);
       count_launches(1);
     }
-    if (gx > 0 && gy > 0) {
+    if (rows_max > 0) {
+      // FP64 throughput per SM is low, so the tile is chosen to give the grid
+      // at least two waves of CTAs over the 152 SMs when the problem allows.
       void *h = tracing ? trace_start(0, gflops, gbytes, st) : nullptr;
-      k_gemm<NB, SAFE, CONJ><<<dim3(gx, gy, tab.count), kGemmThreads, gsmem, st>>>(
-          tab, s, shortcut ? 1 : 0);
+      if (tiles_big >= 2 * kNumSMs)
+        launch_gemm<NB, 64, 32, SAFE, CONJ>(tab, (cols_max + 31) / 32, (rows_max + 63) / 64, s, shortcut, st);
+      else if (tiles_mid >= kNumSMs)
+        launch_gemm<NB, 32, 16, SAFE, CONJ>(tab, (cols_max + 15) / 16, (rows_max + 31) / 32, s, shortcut, st);
+      else
+        launch_gemm<NB, 32, 8, SAFE, CONJ>(tab, (cols_max + 7) / 8, (rows_max + 31) / 32, s, shortcut, st);
       trace_stop(h, st);
       count_launches(1);
     }
