@@ -30,6 +30,64 @@ namespace msts {
 
 constexpr int kNumSMs = 152;
 
+// ----- cheap exact helpers: power-of-two scaling through the exponent field,
+// so that the per-row work of the diagonal step stays off the (slow) FP64 pipe
+// wherever possible.
+__device__ __forceinline__ double pow2i(int k) {            // 2^k, k in [-1022, 1023]
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+__device__ __forceinline__ long long absbits(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+// floor(log2 max(|Re z|, |Im z|)) clamped to [-1022, 1022] (exponent field).
+__device__ __forceinline__ int zexp(double2 z) {
+  const long long m = max(absbits(z.x), absbits(z.y));
+  const int e = (int)(m >> 52) - 1023;
+  return min(max(e, -1022), 1022);
+}
+__device__ __forceinline__ bool zzero_bits(double2 z) { return (absbits(z.x) | absbits(z.y)) == 0; }
+
+// y / p = y conj(p') / |p'|^2 * 2^-e with p' = p 2^-e (|p'|^2 in [1, 8)): one
+// real division and no overflow in the intermediate products.
+__device__ __forceinline__ double2 zdiv_fast(double2 y, double2 p) {
+  const int e = zexp(p);
+  const double s = pow2i(-e);
+  const double a = p.x * s, b = p.y * s;
+  const double q = 1.0 / fma(a, a, b * b);
+  const double wr = fma(y.x, a, y.y * b) * q;
+  const double wi = fma(y.y, a, -(y.x * b)) * q;
+  return make_double2(wr * s, wi * s);
+}
+// |z| from the scaled components (one square root).
+__device__ __forceinline__ double zabs_fast(double2 z) {
+  if (zzero_bits(z)) return 0.0;
+  const int e = zexp(z);
+  const double s = pow2i(-e);
+  const double a = z.x * s, b = z.y * s;
+  return sqrt(fma(a, a, b * b)) * pow2i(e);
+}
+// floor(log2(|y| / |p|)) for y, p != 0 without a division or a square root:
+// |y| = sqrt(ny) 2^fy with ny in [1, 4), likewise p.
+__device__ __forceinline__ int ratio_exp_fast(double2 y, double2 p) {
+  int fy = zexp(y), fp = zexp(p);
+  const double sy = pow2i(-fy), sp = pow2i(-fp);
+  const double ya = y.x * sy, yb = y.y * sy, pa = p.x * sp, pb = p.y * sp;
+  double ny = fma(ya, ya, yb * yb), np = fma(pa, pa, pb * pb);
+  if (ny >= 4.0) { fy += 1; ny *= 0.25; }
+  if (np >= 4.0) { fp += 1; np *= 0.25; }
+  return fy - fp - (ny < np ? 1 : 0);
+}
+// z * 2^-k for k >= 0 (exact unless the result is subnormal).
+__device__ __forceinline__ double2 zshift(double2 z, int k) {
+  if (k > 1022) { z = zscale(z, pow2i(-1022)); k -= 1022; }
+  const double t = k > 1022 ? 0.0 : pow2i(-k);
+  return zscale(z, t);
+}
+__device__ __forceinline__ double dshift(double x, int k) {
+  if (k > 1022) { x *= pow2i(-1022); k -= 1022; }
+  return x * (k > 1022 ? 0.0 : pow2i(-k));
+}
+
 __device__ __forceinline__ void block_range(const Prob &P, int b, int nb, int &lo, int &hi) {
   hi = P.m - b * nb;
   lo = hi - nb < 0 ? 0 : hi - nb;
@@ -50,20 +108,22 @@ __global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32
   const int b = (P.m - 1 - k) / nb;
   int lo, hi;
   block_range(P, b, nb, lo, hi);
+  // Maxima of squared moduli, one square root per column at the end
+  // (|U(i,k)| < 2^48 is the documented range, so the squares cannot overflow).
   double cin = 0.0, cup = 0.0, amax = 0.0;
   bool finite = true;
   const double2 *col = P.U + (long long)k * P.ldu;
   for (int r = lane; r <= k; r += 32) {
     const double2 u = col[r];
     finite &= zfinite(u);
-    const double a = zabs(u);
-    amax = fmax(amax, a);
-    if (r < lo) cup = fmax(cup, a);
-    else if (r < k) cin = fmax(cin, a);
+    const double a2 = fma(u.x, u.x, u.y * u.y);
+    amax = fmax(amax, a2);
+    if (r < lo) cup = fmax(cup, a2);
+    else if (r < k) cin = fmax(cin, a2);
   }
-  cin = warp_max(cin);
-  cup = warp_max(cup);
-  amax = warp_max(amax);
+  cin = sqrt(warp_max(cin));
+  cup = sqrt(warp_max(cup));
+  amax = sqrt(warp_max(amax));
   const bool all_finite = __all_sync(0xffffffffu, finite);
   if (lane == 0) {
     P.cin[k] = cin;
@@ -73,16 +133,23 @@ __global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32
   }
 }
 
-// One thread per row: rowsum[r] = sum_{c >= r} |U(r,c)|, summed left to right.
+// One warp per row: rowsum[r] = sum_{c >= r} |U(r,c)| (lanes stride over the
+// columns, then a fixed-order warp reduction: deterministic).
 __global__ void k_rowsums(const __grid_constant__ ProbTable tab) {
   const Prob &P = tab.p[blockIdx.z];
   if (P.n == 0) return;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= P.m) return;
   double s = 0.0;
   const double2 *row = P.U + r;
-  for (int c = r; c < P.m; ++c) s += zabs(row[(long long)c * P.ldu]);
-  P.rowsum[r] = s;
+  for (int c = r + lane; c < P.m; c += 32) {
+    const double2 u = row[(long long)c * P.ldu];
+    s += sqrt(fma(u.x, u.x, u.y * u.y));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) P.rowsum[r] = s;
 }
 
 // One CTA per problem: C_blk for every block (summed in column order) and
@@ -120,15 +187,23 @@ __global__ void k_safe_init(const __grid_constant__ ProbTable tab, int shortcut,
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= P.n) return;
   const int end = shortcut ? min(j, P.m) : P.m;
-  double g = 0.0;
   bool finite = true;
   const double2 *col = P.B + (long long)j * P.ldb;
+  int E = -1022;
   for (int r = lane; r < end; r += 32) {
     const double2 v = col[r];
     finite &= zfinite(v);
-    g = fmax(g, zabs(v));
+    E = max(E, zexp(v));
   }
-  g = warp_max(g);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+  const double sc = pow2i(-E);
+  double g2 = 0.0;
+  for (int r = lane; r < end; r += 32) {
+    const double a = col[r].x * sc, b = col[r].y * sc;
+    g2 = fmax(g2, fma(a, a, b * b));
+  }
+  const double g = sqrt(warp_max(g2)) * pow2i(E);
   const bool all_finite = __all_sync(0xffffffffu, finite);
   if (lane == 0) {
     P.G[j] = g;
@@ -163,36 +238,11 @@ __global__ void k_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z
 // ---------------------------------------------------------------------------
 template <int NB>
 struct DiagCfg {
-  static constexpr int kThreads = NB >= 64 ? 64 : 128;
+  static constexpr int kThreads = 32;   // one warp per CTA: spread the shifts over the SMs
   static constexpr int LD = NB + 1;
   static constexpr size_t smem = (size_t)NB * LD * sizeof(double2) + (size_t)NB * kThreads * sizeof(double2)
                                  + NB * sizeof(double);
 };
-
-// |z| with the components pre-scaled by a power of two (no overflow, no
-// underflow of the squares).
-__device__ __forceinline__ double zabs_scaled(double2 z) {
-  const double mx = fmax(fabs(z.x), fabs(z.y));
-  if (!(mx > 0.0) || isinf(mx)) return mx + fabs(z.x + z.y) * 0.0;   // 0, inf or NaN
-  const int e = ilogb(mx);
-  const double a = scalbn(z.x, -e), b = scalbn(z.y, -e);
-  return scalbn(sqrt(fma(a, a, b * b)), e);
-}
-
-// y / p as y * conj(p') / |p'|^2 * 2^-e with p' = p * 2^-e: one real division.
-__device__ __forceinline__ double2 zdiv_scaled(double2 y, double2 p) {
-  const double mx = fmax(fabs(p.x), fabs(p.y));
-  const int e = ilogb(mx);
-  const double a = scalbn(p.x, -e), b = scalbn(p.y, -e);
-  const double q = 1.0 / fma(a, a, b * b);
-  const double wr = fma(y.x, a, y.y * b) * q;
-  const double wi = fma(y.y, a, -(y.x * b)) * q;
-  return make_double2(scalbn(wr, -e), scalbn(wi, -e));
-}
-
-__device__ __forceinline__ double2 zscalbn(double2 z, int k) {
-  return make_double2(scalbn(z.x, k), scalbn(z.y, k));
-}
 
 template <int NB, bool SAFE, bool CONJ>
 __global__ void __launch_bounds__(DiagCfg<NB>::kThreads)
@@ -241,7 +291,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   auto substitute = [&](auto piv) {
     for (int t = 0; t < nbe; ++t) {
       const int i = CONJ ? t : nbe - 1 - t;
-      const double2 xi = zdiv_scaled(y[i * T], piv(i));
+      const double2 xi = zdiv_fast(y[i * T], piv(i));
       y[i * T] = xi;
       if (!CONJ) {
         const double2 *ucol = sU + i * LD;
@@ -256,7 +306,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
 
   if (!SAFE) {
     bool zp = false;
-    for (int i = 0; i < nbe; ++i) zp |= zzero(pivot(i));
+    for (int i = 0; i < nbe; ++i) zp |= zzero_bits(pivot(i));
     if (zp) raise_status(status, MSTS_STATUS_ZERO_PIVOT);
     substitute(pivot);
     for (int r = 0; r < nbe; ++r) col[r] = y[r * T];
@@ -269,21 +319,37 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   bool used_delta = false;
   auto spiv = [&](int i) {
     const double2 p = pivot(i);
-    return zzero(p) ? make_double2(dlt, 0.0) : p;
+    return zzero_bits(p) ? make_double2(dlt, 0.0) : p;
   };
-  for (int i = 0; i < nbe; ++i) used_delta |= zzero(pivot(i));
+  for (int i = 0; i < nbe; ++i) used_delta |= zzero_bits(pivot(i));
+  // max_r |y_r| over the block: common power-of-two scale, then squares.
+  auto maxabs = [&]() {
+    int E = -1022;
+    long long any = 0;
+    for (int r = 0; r < nbe; ++r) {
+      E = max(E, zexp(y[r * T]));
+      any |= absbits(y[r * T].x) | absbits(y[r * T].y);
+    }
+    if (!any) return 0.0;
+    const double sc = pow2i(-E);
+    double m2 = 0.0;
+    for (int r = 0; r < nbe; ++r) {
+      const double a = y[r * T].x * sc, bb = y[r * T].y * sc;
+      m2 = fmax(m2, fma(a, a, bb * bb));
+    }
+    return sqrt(m2) * pow2i(E);
+  };
 
   // A priori growth bounds (Sec. 3) in a conservative form: |p| >= max(|Re p|,
   // |Im p|) and |y| <= sqrt(2) max(|Re y|, |Im y|).  They only choose between the
   // plain and the safeguarded substitution, which give identical results
   // whenever the plain one is chosen, so a looser bound can only cost time.
-  double g0 = 0.0;
-  for (int r = 0; r < nbe; ++r) g0 = fmax(g0, fmax(fabs(y[r * T].x), fabs(y[r * T].y)));
-  g0 *= 1.4142135623730951;
-  double Gb = g0, Mb = 0.0;
+  long long g0b = 0;
+  for (int r = 0; r < nbe; ++r) g0b = max(g0b, max(absbits(y[r * T].x), absbits(y[r * T].y)));
+  double Gb = __longlong_as_double(g0b) * 1.4142135623730951, Mb = 0.0;
   for (int i = nbe - 1; i >= 0; --i) {
     const double2 p = spiv(i);
-    const double inv = 1.0 / fmax(fabs(p.x), fabs(p.y));
+    const double inv = 1.0 / __longlong_as_double(max(absbits(p.x), absbits(p.y)));
     Mb = fmax(Mb, Gb * inv);
     Gb = Gb * fma(sC[i], inv, 1.0);
   }
@@ -292,30 +358,27 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     substitute(spiv);
   } else {
     // Safeguarded back substitution (Alg. 4, second branch).
-    double G = 0.0;
-    for (int r = 0; r < nbe; ++r) G = fmax(G, zabs_scaled(y[r * T]));
+    double G = maxabs();
     for (int i = nbe - 1; i >= 0; --i) {
       const double2 p = spiv(i);
-      const double ay = zabs_scaled(y[i * T]);
-      if (ay != 0.0) {
-        const int eM = ratio_exponent(ay, zabs_scaled(p));
+      if (!zzero_bits(y[i * T])) {
+        const int eM = ratio_exp_fast(y[i * T], p);
         if (eM >= kOmegaExp) {                       // M >= Omega: rescale b first
           const int kk = eM - (kOmegaExp - 1);
-          for (int r = 0; r < nbe; ++r) y[r * T] = zscalbn(y[r * T], -kk);
+          for (int r = 0; r < nbe; ++r) y[r * T] = zshift(y[r * T], kk);
           kexp += kk;
-          G = scalbn(G, -kk);
+          G = dshift(G, kk);
         }
       }
-      double2 xi = zdiv_scaled(y[i * T], p);
+      double2 xi = zdiv_fast(y[i * T], p);
       y[i * T] = xi;
-      const double Mv = zabs_scaled(xi);
-      G = __dadd_rn(G, __dmul_rn(Mv, sC[i]));
+      G = __dadd_rn(G, __dmul_rn(zabs_fast(xi), sC[i]));
       if (G >= OM) {                                 // protect the AXPY
         const int kk = choose_k(G);
-        for (int r = 0; r < nbe; ++r) y[r * T] = zscalbn(y[r * T], -kk);
+        for (int r = 0; r < nbe; ++r) y[r * T] = zshift(y[r * T], kk);
         xi = y[i * T];
         kexp += kk;
-        G = scalbn(G, -kk);
+        G = dshift(G, kk);
       }
       const double2 *ucol = sU + i * LD;
 #pragma unroll 4
@@ -329,18 +392,17 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   int ej = P.e[j];
   double Gj = P.G[j];
   int pend = 0;
-  if (kexp > 0) { ej += kexp; Gj = scalbn(Gj, -kexp); pend = kexp; }
-  double N = 0.0;
-  for (int r = 0; r < nbe; ++r) N = fmax(N, zabs_scaled(y[r * T]));
+  if (kexp > 0) { ej += kexp; Gj = dshift(Gj, kexp); pend = kexp; }
+  const double N = maxabs();
   Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
   int k2 = 0;
   if (Gj >= OM) {
     k2 = choose_k(Gj);
     ej += k2;
-    Gj = scalbn(Gj, -k2);
+    Gj = dshift(Gj, k2);
     pend += k2;
   }
-  for (int r = 0; r < nbe; ++r) col[r] = k2 ? zscalbn(y[r * T], -k2) : y[r * T];
+  for (int r = 0; r < nbe; ++r) col[r] = k2 ? zshift(y[r * T], k2) : y[r * T];
   P.e[j] = ej;
   P.G[j] = Gj;
   P.pend[j] = pend;
@@ -349,12 +411,6 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   if (used_delta) raise_status(status, MSTS_STATUS_DELTA);
 }
 
-// ---------------------------------------------------------------------------
-// Substitution step: B(I0,:) = 2^-pend * B(I0,:) - U(I0,I1) X(I1,:)  (upper), or
-//                    B(I2,:) -= (U^H)(I2,I1) X(I1,:)                  (CONJ).
-// Tile kGemmBM x kGemmBN of B per CTA, K = the block's rows; FP64 DFMA.
-// Thread (tr, tc) owns rows {tr, tr+32} x columns {tc, tc+8, tc+16, tc+24}.
-// ---------------------------------------------------------------------------
 template <int BM, int BN>
 struct GemmCfg {
   static constexpr int kThreads = 256;
@@ -432,7 +488,7 @@ k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
       if (row >= rend) continue;
       double2 *p = P.B + row + (long long)col * P.ldb;
       double2 v = *p;
-      if (SAFE && pend) v = make_double2(scalbn(v.x, -pend), scalbn(v.y, -pend));
+      if (SAFE && pend) v = zshift(v, pend);
       *p = zsub(v, acc[i][c]);
     }
   }
@@ -455,8 +511,7 @@ __global__ void k_fixup(const __grid_constant__ ProbTable tab, int nb, int short
     const int d = ej - P.E[(long long)b * P.n + j];
     if (d == 0) continue;
     const int top = min(hi, end);
-    for (int r = lo + lane; r < top; r += 32)
-      col[r] = make_double2(scalbn(col[r].x, -d), scalbn(col[r].y, -d));
+    for (int r = lo + lane; r < top; r += 32) col[r] = zshift(col[r], d);
   }
   if (lane == 0) {
     const double s = scalbn(1.0, -ej);
@@ -607,7 +662,7 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
     const int sc = shortcut ? 1 : 0;
     if (safe) {
       k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status);
-      k_rowsums<<<dim3((maxm + 127) / 128, 1, cnt), 128, 0, st>>>(tab);
+      k_rowsums<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab);
       k_safe_finish<<<dim3(1, 1, cnt), 256, 0, st>>>(tab, nb);
       k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);  count_launches(4);
     }
