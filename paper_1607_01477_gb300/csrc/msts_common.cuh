@@ -98,6 +98,64 @@ __device__ __forceinline__ void raise_status(uint32_t *status, uint32_t bits) {
   if (status) atomicOr(reinterpret_cast<unsigned int *>(status), bits);
 }
 
+// ----- cheap exact helpers: power-of-two scaling through the exponent field,
+// so that the per-row work of the diagonal step stays off the (slow) FP64 pipe
+// wherever possible.
+__device__ __forceinline__ double pow2i(int k) {            // 2^k, k in [-1022, 1023]
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+__device__ __forceinline__ long long absbits(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+// floor(log2 max(|Re z|, |Im z|)) clamped to [-1022, 1022] (exponent field).
+__device__ __forceinline__ int zexp(double2 z) {
+  const long long m = max(absbits(z.x), absbits(z.y));
+  const int e = (int)(m >> 52) - 1023;
+  return min(max(e, -1022), 1022);
+}
+__device__ __forceinline__ bool zzero_bits(double2 z) { return (absbits(z.x) | absbits(z.y)) == 0; }
+
+// y / p = y conj(p') / |p'|^2 * 2^-e with p' = p 2^-e (|p'|^2 in [1, 8)): one
+// real division and no overflow in the intermediate products.
+__device__ __forceinline__ double2 zdiv_fast(double2 y, double2 p) {
+  const int e = zexp(p);
+  const double s = pow2i(-e);
+  const double a = p.x * s, b = p.y * s;
+  const double q = 1.0 / fma(a, a, b * b);
+  const double wr = fma(y.x, a, y.y * b) * q;
+  const double wi = fma(y.y, a, -(y.x * b)) * q;
+  return make_double2(wr * s, wi * s);
+}
+// |z| from the scaled components (one square root).
+__device__ __forceinline__ double zabs_fast(double2 z) {
+  if (zzero_bits(z)) return 0.0;
+  const int e = zexp(z);
+  const double s = pow2i(-e);
+  const double a = z.x * s, b = z.y * s;
+  return sqrt(fma(a, a, b * b)) * pow2i(e);
+}
+// floor(log2(|y| / |p|)) for y, p != 0 without a division or a square root:
+// |y| = sqrt(ny) 2^fy with ny in [1, 4), likewise p.
+__device__ __forceinline__ int ratio_exp_fast(double2 y, double2 p) {
+  int fy = zexp(y), fp = zexp(p);
+  const double sy = pow2i(-fy), sp = pow2i(-fp);
+  const double ya = y.x * sy, yb = y.y * sy, pa = p.x * sp, pb = p.y * sp;
+  double ny = fma(ya, ya, yb * yb), np = fma(pa, pa, pb * pb);
+  if (ny >= 4.0) { fy += 1; ny *= 0.25; }
+  if (np >= 4.0) { fp += 1; np *= 0.25; }
+  return fy - fp - (ny < np ? 1 : 0);
+}
+// z * 2^-k for k >= 0 (exact unless the result is subnormal).
+__device__ __forceinline__ double2 zshift(double2 z, int k) {
+  if (k > 1022) { z = zscale(z, pow2i(-1022)); k -= 1022; }
+  const double t = k > 1022 ? 0.0 : pow2i(-k);
+  return zscale(z, t);
+}
+__device__ __forceinline__ double dshift(double x, int k) {
+  if (k > 1022) { x *= pow2i(-1022); k -= 1022; }
+  return x * (k > 1022 ? 0.0 : pow2i(-k));
+}
+
 // ---------------------------------------------------------------------------
 // One multi-shift problem as the kernels see it.  Workspace pointers are set
 // up by the host driver; the safe-only ones are null for plain solves.
@@ -129,5 +187,11 @@ struct ProbTable {
   int count;
   Prob p[kMaxProbs];
 };
+
+// Rows [lo, hi) of block b (blocks cut from the bottom, ragged block on top).
+__device__ __forceinline__ void block_range(const Prob &P, int b, int nb, int &lo, int &hi) {
+  hi = P.m - b * nb;
+  lo = hi - nb < 0 ? 0 : hi - nb;
+}
 
 }  // namespace msts

@@ -1,0 +1,309 @@
+// msts_diag.cu -- the diagonal-block step of the blocked multi-shift solve:
+// for every shift j, back substitution on U(I1,I1) - lambda_j I (Alg. 3), or
+// in the safe variant Alg. 4 on that block followed by the column update of
+// Alg. 5; forward substitution on the conjugate transpose for MSTS_CONJ_TRANS.
+//
+// GB300 mapping.  The FP64 unit of each SM sub-partition retires one warp
+// instruction per ~64 cycles whatever the number of active lanes, and an FP64
+// division costs ~10 dependent instructions.  So
+//   - each shift is handled by a group of L lanes (L = 4..32, chosen per launch
+//     so that enough warps exist to occupy every sub-partition); lane l of the
+//     group owns rows l, l + L, l + 2L, ... of the block in registers;
+//   - the reciprocals of all pivots are formed up front, in parallel over the
+//     rows, so the serial chain of the substitution has no division in it;
+//   - U(I1,I1) is staged once per CTA in shared memory and read by broadcast.
+// All warp shuffles sit outside data-dependent branches; decisions that need
+// them (the safe variant's plain/safeguarded choice) are made warp-uniform.
+#include <algorithm>
+
+#include "msts_common.cuh"
+#include "msts_diag.h"
+
+namespace msts {
+
+constexpr int kDiagThreads = 128;
+
+template <int L>
+__device__ __forceinline__ double gshfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src, L); }
+template <int L>
+__device__ __forceinline__ int gshfl_i(int v, int src) { return __shfl_sync(0xffffffffu, v, src, L); }
+template <int L>
+__device__ __forceinline__ double2 gshfl_z(double2 v, int src) {
+  return make_double2(gshfl<L>(v.x, src), gshfl<L>(v.y, src));
+}
+template <int L>
+__device__ __forceinline__ double gmax(double v) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o, L));
+  return v;
+}
+template <int L>
+__device__ __forceinline__ int gmax_i(int v) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o, L));
+  return v;
+}
+template <int L>
+__device__ __forceinline__ long long gmax_ll(long long v) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v = max(v, (long long)__shfl_xor_sync(0xffffffffu, v, o, L));
+  return v;
+}
+
+// 1 / p with p scaled by a power of two first (one real division).
+__device__ __forceinline__ double2 zrecip(double2 p) { return zdiv_fast(make_double2(1.0, 0.0), p); }
+
+template <int NB, int L, bool SAFE, bool CONJ>
+__global__ void __launch_bounds__(kDiagThreads)
+k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *status) {
+  constexpr int RPL = NB / L;            // rows per lane
+  constexpr int SPW = 32 / L;            // shifts per warp
+  constexpr int SPC = (kDiagThreads / 32) * SPW;
+  constexpr int LD = NB + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *sU = reinterpret_cast<double2 *>(smem_raw);   // U(I1,I1) column-major, LD
+  double *sC = reinterpret_cast<double *>(sU + NB * LD);  // within-block column norms
+
+  const Prob &P = tab.p[blockIdx.z];
+  if (step >= P.nblk) return;
+  const int b = CONJ ? P.nblk - 1 - step : step;
+  int lo, hi;
+  block_range(P, b, NB, lo, hi);
+  const int nbf = hi - lo;
+  const int jcta = (shortcut ? lo + 1 : 0) + blockIdx.x * SPC;
+  if (jcta >= P.n) return;
+  for (int idx = threadIdx.x; idx < NB * NB; idx += kDiagThreads) {
+    const int c = idx / NB, r = idx - c * NB;
+    double2 v = make_double2(0.0, 0.0);
+    if (r <= c && c < nbf) v = P.U[(lo + r) + (long long)(lo + c) * P.ldu];
+    sU[c * LD + r] = v;
+  }
+  if (SAFE)
+    for (int k = threadIdx.x; k < NB; k += kDiagThreads) sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = lane & (L - 1);
+  const int j = jcta + warp * SPW + lane / L;
+  const bool active = j < P.n;
+  const int nbe = !active ? 0 : (shortcut ? min(hi, j) - lo : nbf);   // TREVC: rows >= j stay zero
+  double2 lam = active ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
+  if (CONJ) lam = zconj(lam);
+  double2 *col = P.B + (long long)(active ? j : 0) * P.ldb + lo;
+  const double dlt = SAFE ? *P.delta : 0.0;
+
+  auto pivot = [&](int i) {
+    const double2 d = sU[i * LD + i];
+    double2 p = zsub(CONJ ? zconj(d) : d, lam);
+    if (SAFE && zzero_bits(p)) p = make_double2(dlt, 0.0);   // U(i,i) = lambda -> delta (Sec. 3)
+    return p;
+  };
+
+  double2 y[RPL], inv[RPL];
+  bool zero_piv = false;
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int r = l + L * q;
+    const bool v = r < nbe;
+    y[q] = v ? col[r] : make_double2(0.0, 0.0);
+    const double2 d = sU[r * LD + r];
+    const double2 p0 = zsub(CONJ ? zconj(d) : d, lam);
+    zero_piv |= v && zzero_bits(p0);
+    inv[q] = v ? zrecip(pivot(r)) : make_double2(0.0, 0.0);
+  }
+  if (zero_piv) raise_status(status, SAFE ? MSTS_STATUS_DELTA : MSTS_STATUS_ZERO_PIVOT);
+
+  // One row of the substitution: x_i = y_i / piv_i by the owner lane, broadcast
+  // in the group, AXPY on the rows each lane owns.
+  auto axpy = [&](int i, double2 xi) {
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = l + L * q;
+      if (!CONJ) {
+        if (r < i) y[q] = zfms(y[q], xi, sU[i * LD + r]);
+      } else {
+        if (r > i) y[q] = zfms(y[q], xi, zconj(sU[r * LD + i]));
+      }
+    }
+  };
+  auto substitute = [&]() {
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int i = CONJ ? t : NB - 1 - t;
+      const int qi = i / L, li = i % L;
+      const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);   // zero for rows >= nbe
+      if (l == li) y[qi] = xi;
+      axpy(i, xi);
+    }
+  };
+
+  if (!SAFE) {
+    substitute();
+#pragma unroll
+    for (int q = 0; q < RPL; ++q)
+      if (l + L * q < nbe) col[l + L * q] = y[q];
+    return;
+  }
+
+  // ----- safe variant (upper only) ------------------------------------------
+  const double OM = omega();
+  // max_r |y_r| over the block: common power-of-two scale, then squares.
+  auto maxabs = [&]() {
+    int E = -1022;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) E = max(E, zexp(y[q]));
+    E = gmax_i<L>(E);
+    const double sc = pow2i(-E);
+    double m2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const double a = y[q].x * sc, bb = y[q].y * sc;
+      m2 = fmax(m2, fma(a, a, bb * bb));
+    }
+    return sqrt(gmax<L>(m2)) * pow2i(E);
+  };
+
+  // A priori growth bounds (Sec. 3), conservative: 1/|p| <= sqrt(2) max(|Re|,
+  // |Im|) of 1/p and |y| <= sqrt(2) max(|Re y|, |Im y|).  They only choose
+  // between the plain and the safeguarded substitution, which give identical
+  // results whenever the plain one is chosen, so looser bounds only cost time.
+  long long gb = 0;
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) gb = max(gb, max(absbits(y[q].x), absbits(y[q].y)));
+  double Gb = __longlong_as_double(gmax_ll<L>(gb)) * 1.4142135623730951, Mb = 0.0;
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    const int i = NB - 1 - t;
+    const int qi = i / L, li = i % L;
+    const double ia = gshfl<L>(__longlong_as_double(max(absbits(inv[qi].x), absbits(inv[qi].y))) *
+                                   1.4142135623730951, li);
+    if (i < nbe) {
+      Mb = fmax(Mb, Gb * ia);
+      Gb = Gb * fma(sC[i], ia, 1.0);
+    }
+  }
+  const bool careful = __any_sync(0xffffffffu, active && !(Mb < OM && Gb < OM));
+  int kexp = 0;
+  if (!careful) {
+    substitute();
+  } else {
+    // Safeguarded back substitution (Alg. 4, second branch), group-uniform.
+    double G = maxabs();
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int i = NB - 1 - t;
+      const int qi = i / L, li = i % L;
+      const double2 yi = gshfl_z<L>(y[qi], li);
+      int eM = -100000;
+      if (i < nbe && !zzero_bits(yi)) eM = ratio_exp_fast(yi, pivot(i));
+      if (eM >= kOmegaExp) {                          // M >= Omega: rescale b first
+        const int kk = eM - (kOmegaExp - 1);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) y[q] = zshift(y[q], kk);
+        kexp += kk;
+        G = dshift(G, kk);
+      }
+      double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);   // diagonal step
+      if (l == li) y[qi] = xi;
+      if (i < nbe) {
+        G = __dadd_rn(G, __dmul_rn(zabs_fast(xi), sC[i]));
+        if (G >= OM) {                                   // protect the AXPY
+          const int kk = choose_k(G);
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) y[q] = zshift(y[q], kk);
+          xi = zshift(xi, kk);
+          kexp += kk;
+          G = dshift(G, kk);
+        }
+      }
+      axpy(i, xi);
+    }
+  }
+
+  // Alg. 5: t < 1 rescales the rest of the column (lazily: the substitution
+  // GEMM applies it to I0 and the final fix-up to I2), then
+  // G(j) += C_blk ||X(I1,j)||_inf with a whole-column rescale at Omega.
+  const double N = maxabs();
+  if (!active) return;
+  int ej = P.e[j];
+  double Gj = P.G[j];
+  int pend = 0;
+  if (kexp > 0) { ej += kexp; Gj = dshift(Gj, kexp); pend = kexp; }
+  Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
+  int k2 = 0;
+  if (Gj >= OM) {
+    k2 = choose_k(Gj);
+    ej += k2;
+    Gj = dshift(Gj, k2);
+    pend += k2;
+  }
+#pragma unroll
+  for (int q = 0; q < RPL; ++q)
+    if (l + L * q < nbe) col[l + L * q] = k2 ? zshift(y[q], k2) : y[q];
+  if (l == 0) {
+    P.e[j] = ej;
+    P.G[j] = Gj;
+    P.pend[j] = pend;
+    P.E[(long long)b * P.n + j] = ej;
+    if (pend > 0) raise_status(status, MSTS_STATUS_SCALED);
+  }
+}
+
+template <int NB, int L, bool SAFE, bool CONJ>
+static cudaError_t launch(const ProbTable &tab, int step, int shortcut, int ncols_max,
+                          uint32_t *status, cudaStream_t st) {
+  constexpr size_t smem = (size_t)NB * (NB + 1) * sizeof(double2) + NB * sizeof(double);
+  constexpr int SPC = (kDiagThreads / 32) * (32 / L);
+  cudaError_t e = cudaFuncSetAttribute(k_diag<NB, L, SAFE, CONJ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_diag<NB, L, SAFE, CONJ><<<dim3((ncols_max + SPC - 1) / SPC, 1, tab.count), kDiagThreads, smem, st>>>(
+      tab, step, shortcut, status);
+  return cudaSuccess;
+}
+
+template <int NB, bool SAFE, bool CONJ>
+static cudaError_t launch_nb(int L, const ProbTable &tab, int step, int shortcut, int ncols_max,
+                             uint32_t *status, cudaStream_t st) {
+  if constexpr (NB == 64) {
+    if (L <= 16) return launch<64, 16, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    return launch<64, 32, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+  } else if constexpr (NB == 32) {
+    if (L <= 4) return launch<32, 4, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    if (L == 8) return launch<32, 8, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    if (L == 16) return launch<32, 16, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    return launch<32, 32, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+  } else {
+    if (L <= 4) return launch<16, 4, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    if (L == 8) return launch<16, 8, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    return launch<16, 16, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+  }
+}
+
+// Lanes per shift: the smallest of 4, 8, min(NB, 32) that yields at least
+// 4 warps per SM (one per sub-partition) over the 152 SMs.
+int diag_lanes(int nb, long long total_cols) {
+  const int lmax = nb < 32 ? nb : 32;
+  for (int L = nb >= 64 ? 16 : 4; L < lmax; L *= 2)
+    if (total_cols * L >= 32LL * 4 * 152) return L;
+  return lmax;
+}
+
+cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int step, int shortcut,
+                        int ncols_max, long long total_cols, uint32_t *status, cudaStream_t st) {
+  const int L = diag_lanes(nb, total_cols);
+#define MSTS_DIAG_CASE(NBV)                                                                   \
+  case NBV:                                                                                   \
+    if (safe) return launch_nb<NBV, true, false>(L, tab, step, shortcut, ncols_max, status, st); \
+    if (conj) return launch_nb<NBV, false, true>(L, tab, step, shortcut, ncols_max, status, st); \
+    return launch_nb<NBV, false, false>(L, tab, step, shortcut, ncols_max, status, st);
+  switch (nb) {
+    MSTS_DIAG_CASE(16)
+    MSTS_DIAG_CASE(32)
+    MSTS_DIAG_CASE(64)
+    default: return cudaErrorInvalidValue;
+  }
+#undef MSTS_DIAG_CASE
+}
+
+}  // namespace msts

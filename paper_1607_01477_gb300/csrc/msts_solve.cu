@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "msts_common.cuh"
+#include "msts_diag.h"
 #include "msts_engine.h"
 #include "msts_trace.h"
 
@@ -30,68 +31,6 @@ namespace msts {
 
 constexpr int kNumSMs = 152;
 
-// ----- cheap exact helpers: power-of-two scaling through the exponent field,
-// so that the per-row work of the diagonal step stays off the (slow) FP64 pipe
-// wherever possible.
-__device__ __forceinline__ double pow2i(int k) {            // 2^k, k in [-1022, 1023]
-  return __longlong_as_double((long long)(k + 1023) << 52);
-}
-__device__ __forceinline__ long long absbits(double x) {
-  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
-}
-// floor(log2 max(|Re z|, |Im z|)) clamped to [-1022, 1022] (exponent field).
-__device__ __forceinline__ int zexp(double2 z) {
-  const long long m = max(absbits(z.x), absbits(z.y));
-  const int e = (int)(m >> 52) - 1023;
-  return min(max(e, -1022), 1022);
-}
-__device__ __forceinline__ bool zzero_bits(double2 z) { return (absbits(z.x) | absbits(z.y)) == 0; }
-
-// y / p = y conj(p') / |p'|^2 * 2^-e with p' = p 2^-e (|p'|^2 in [1, 8)): one
-// real division and no overflow in the intermediate products.
-__device__ __forceinline__ double2 zdiv_fast(double2 y, double2 p) {
-  const int e = zexp(p);
-  const double s = pow2i(-e);
-  const double a = p.x * s, b = p.y * s;
-  const double q = 1.0 / fma(a, a, b * b);
-  const double wr = fma(y.x, a, y.y * b) * q;
-  const double wi = fma(y.y, a, -(y.x * b)) * q;
-  return make_double2(wr * s, wi * s);
-}
-// |z| from the scaled components (one square root).
-__device__ __forceinline__ double zabs_fast(double2 z) {
-  if (zzero_bits(z)) return 0.0;
-  const int e = zexp(z);
-  const double s = pow2i(-e);
-  const double a = z.x * s, b = z.y * s;
-  return sqrt(fma(a, a, b * b)) * pow2i(e);
-}
-// floor(log2(|y| / |p|)) for y, p != 0 without a division or a square root:
-// |y| = sqrt(ny) 2^fy with ny in [1, 4), likewise p.
-__device__ __forceinline__ int ratio_exp_fast(double2 y, double2 p) {
-  int fy = zexp(y), fp = zexp(p);
-  const double sy = pow2i(-fy), sp = pow2i(-fp);
-  const double ya = y.x * sy, yb = y.y * sy, pa = p.x * sp, pb = p.y * sp;
-  double ny = fma(ya, ya, yb * yb), np = fma(pa, pa, pb * pb);
-  if (ny >= 4.0) { fy += 1; ny *= 0.25; }
-  if (np >= 4.0) { fp += 1; np *= 0.25; }
-  return fy - fp - (ny < np ? 1 : 0);
-}
-// z * 2^-k for k >= 0 (exact unless the result is subnormal).
-__device__ __forceinline__ double2 zshift(double2 z, int k) {
-  if (k > 1022) { z = zscale(z, pow2i(-1022)); k -= 1022; }
-  const double t = k > 1022 ? 0.0 : pow2i(-k);
-  return zscale(z, t);
-}
-__device__ __forceinline__ double dshift(double x, int k) {
-  if (k > 1022) { x *= pow2i(-1022); k -= 1022; }
-  return x * (k > 1022 ? 0.0 : pow2i(-k));
-}
-
-__device__ __forceinline__ void block_range(const Prob &P, int b, int nb, int &lo, int &hi) {
-  hi = P.m - b * nb;
-  lo = hi - nb < 0 ? 0 : hi - nb;
-}
 
 // ---------------------------------------------------------------------------
 // Safe-variant preprocessing (Alg. 5 set-up, the column norms of Sec. 3).
@@ -225,190 +164,6 @@ __global__ void k_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z
     }
     Z[r + (long long)j * ldz] = v;
   }
-}
-
-// ---------------------------------------------------------------------------
-// Diagonal-block step (Alg. 3's inner loop; Alg. 4 + Alg. 5's column update in
-// the safe variant): one THREAD per shift.  GB300 issues FP64 at a few lanes
-// per clock per SM, so a warp instruction costs the same whether 1 or 32 of
-// its lanes do useful work; giving each lane its own shift keeps every lane of
-// every FP64 instruction busy (the block of U is the same for all shifts and is
-// broadcast from shared memory).  Each thread's block of B lives in its own
-// column of shared memory, sY[r * kThreads + tid].
-// ---------------------------------------------------------------------------
-template <int NB>
-struct DiagCfg {
-  static constexpr int kThreads = 32;   // one warp per CTA: spread the shifts over the SMs
-  static constexpr int LD = NB + 1;
-  static constexpr size_t smem = (size_t)NB * LD * sizeof(double2) + (size_t)NB * kThreads * sizeof(double2)
-                                 + NB * sizeof(double);
-};
-
-template <int NB, bool SAFE, bool CONJ>
-__global__ void __launch_bounds__(DiagCfg<NB>::kThreads)
-k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *status) {
-  constexpr int T = DiagCfg<NB>::kThreads;
-  constexpr int LD = DiagCfg<NB>::LD;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2 *sU = reinterpret_cast<double2 *>(smem_raw);   // block, column-major, LD
-  double2 *sY = sU + NB * LD;                             // sY[r * T + tid]
-  double *sC = reinterpret_cast<double *>(sY + NB * T);
-
-  const Prob &P = tab.p[blockIdx.z];
-  if (step >= P.nblk) return;
-  const int b = CONJ ? P.nblk - 1 - step : step;
-  int lo, hi;
-  block_range(P, b, NB, lo, hi);
-  const int nbf = hi - lo;
-  const int jstart = shortcut ? lo + 1 : 0;
-  const int jcta = jstart + blockIdx.x * T;
-  if (jcta >= P.n) return;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += T) {
-    const int c = idx / NB, r = idx - c * NB;
-    double2 v = make_double2(0.0, 0.0);
-    if (r <= c && c < nbf) v = P.U[(lo + r) + (long long)(lo + c) * P.ldu];
-    sU[c * LD + r] = v;
-  }
-  if (SAFE)
-    for (int k = tid; k < NB; k += T) sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
-  __syncthreads();
-
-  const int j = jcta + tid;
-  if (j >= P.n) return;
-  const int nbe = shortcut ? min(hi, j) - lo : nbf;   // TREVC: rows >= j stay zero
-  double2 lam = P.shifts[(long long)j * P.shift_stride];
-  if (CONJ) lam = zconj(lam);
-  double2 *col = P.B + (long long)j * P.ldb + lo;
-  double2 *y = sY + tid;                                // y[r * T]
-  for (int r = 0; r < nbe; ++r) y[r * T] = col[r];
-
-  auto pivot = [&](int i) {
-    const double2 d = sU[i * LD + i];
-    return zsub(CONJ ? zconj(d) : d, lam);
-  };
-  // Plain substitution on rows [0, nbe) with pivots piv(i) (Alg. 1 per shift).
-  auto substitute = [&](auto piv) {
-    for (int t = 0; t < nbe; ++t) {
-      const int i = CONJ ? t : nbe - 1 - t;
-      const double2 xi = zdiv_fast(y[i * T], piv(i));
-      y[i * T] = xi;
-      if (!CONJ) {
-        const double2 *ucol = sU + i * LD;
-#pragma unroll 4
-        for (int r = 0; r < i; ++r) y[r * T] = zfms(y[r * T], xi, ucol[r]);
-      } else {
-#pragma unroll 4
-        for (int r = i + 1; r < nbe; ++r) y[r * T] = zfms(y[r * T], xi, zconj(sU[r * LD + i]));
-      }
-    }
-  };
-
-  if (!SAFE) {
-    bool zp = false;
-    for (int i = 0; i < nbe; ++i) zp |= zzero_bits(pivot(i));
-    if (zp) raise_status(status, MSTS_STATUS_ZERO_PIVOT);
-    substitute(pivot);
-    for (int r = 0; r < nbe; ++r) col[r] = y[r * T];
-    return;
-  }
-
-  // ----- safe variant (upper only): Alg. 4 on the shifted block, then Alg. 5.
-  const double OM = omega();
-  const double dlt = *P.delta;
-  bool used_delta = false;
-  auto spiv = [&](int i) {
-    const double2 p = pivot(i);
-    return zzero_bits(p) ? make_double2(dlt, 0.0) : p;
-  };
-  for (int i = 0; i < nbe; ++i) used_delta |= zzero_bits(pivot(i));
-  // max_r |y_r| over the block: common power-of-two scale, then squares.
-  auto maxabs = [&]() {
-    int E = -1022;
-    long long any = 0;
-    for (int r = 0; r < nbe; ++r) {
-      E = max(E, zexp(y[r * T]));
-      any |= absbits(y[r * T].x) | absbits(y[r * T].y);
-    }
-    if (!any) return 0.0;
-    const double sc = pow2i(-E);
-    double m2 = 0.0;
-    for (int r = 0; r < nbe; ++r) {
-      const double a = y[r * T].x * sc, bb = y[r * T].y * sc;
-      m2 = fmax(m2, fma(a, a, bb * bb));
-    }
-    return sqrt(m2) * pow2i(E);
-  };
-
-  // A priori growth bounds (Sec. 3) in a conservative form: |p| >= max(|Re p|,
-  // |Im p|) and |y| <= sqrt(2) max(|Re y|, |Im y|).  They only choose between the
-  // plain and the safeguarded substitution, which give identical results
-  // whenever the plain one is chosen, so a looser bound can only cost time.
-  long long g0b = 0;
-  for (int r = 0; r < nbe; ++r) g0b = max(g0b, max(absbits(y[r * T].x), absbits(y[r * T].y)));
-  double Gb = __longlong_as_double(g0b) * 1.4142135623730951, Mb = 0.0;
-  for (int i = nbe - 1; i >= 0; --i) {
-    const double2 p = spiv(i);
-    const double inv = 1.0 / __longlong_as_double(max(absbits(p.x), absbits(p.y)));
-    Mb = fmax(Mb, Gb * inv);
-    Gb = Gb * fma(sC[i], inv, 1.0);
-  }
-  int kexp = 0;
-  if (Mb < OM && Gb < OM) {
-    substitute(spiv);
-  } else {
-    // Safeguarded back substitution (Alg. 4, second branch).
-    double G = maxabs();
-    for (int i = nbe - 1; i >= 0; --i) {
-      const double2 p = spiv(i);
-      if (!zzero_bits(y[i * T])) {
-        const int eM = ratio_exp_fast(y[i * T], p);
-        if (eM >= kOmegaExp) {                       // M >= Omega: rescale b first
-          const int kk = eM - (kOmegaExp - 1);
-          for (int r = 0; r < nbe; ++r) y[r * T] = zshift(y[r * T], kk);
-          kexp += kk;
-          G = dshift(G, kk);
-        }
-      }
-      double2 xi = zdiv_fast(y[i * T], p);
-      y[i * T] = xi;
-      G = __dadd_rn(G, __dmul_rn(zabs_fast(xi), sC[i]));
-      if (G >= OM) {                                 // protect the AXPY
-        const int kk = choose_k(G);
-        for (int r = 0; r < nbe; ++r) y[r * T] = zshift(y[r * T], kk);
-        xi = y[i * T];
-        kexp += kk;
-        G = dshift(G, kk);
-      }
-      const double2 *ucol = sU + i * LD;
-#pragma unroll 4
-      for (int r = 0; r < i; ++r) y[r * T] = zfms(y[r * T], xi, ucol[r]);
-    }
-  }
-
-  // Alg. 5: t < 1 rescales the rest of the column (lazily: k_gemm applies it to
-  // I0 and k_fixup to I2), then G(j) += C_blk ||X(I1,j)||_inf, rescaling the
-  // whole column if it reaches Omega.
-  int ej = P.e[j];
-  double Gj = P.G[j];
-  int pend = 0;
-  if (kexp > 0) { ej += kexp; Gj = dshift(Gj, kexp); pend = kexp; }
-  const double N = maxabs();
-  Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
-  int k2 = 0;
-  if (Gj >= OM) {
-    k2 = choose_k(Gj);
-    ej += k2;
-    Gj = dshift(Gj, k2);
-    pend += k2;
-  }
-  for (int r = 0; r < nbe; ++r) col[r] = k2 ? zshift(y[r * T], k2) : y[r * T];
-  P.e[j] = ej;
-  P.G[j] = Gj;
-  P.pend[j] = pend;
-  P.E[(long long)b * P.n + j] = ej;
-  if (pend > 0) raise_status(status, MSTS_STATUS_SCALED);
-  if (used_delta) raise_status(status, MSTS_STATUS_DELTA);
 }
 
 template <int BM, int BN>
@@ -563,17 +318,12 @@ static void launch_gemm(const ProbTable &tab, int gx, int gy, int s, bool shortc
 template <int NB, bool SAFE, bool CONJ>
 static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, int count,
                              bool shortcut, uint32_t *status, cudaStream_t st) {
-  constexpr size_t diag_smem = DiagCfg<NB>::smem;
-  constexpr int diag_threads = DiagCfg<NB>::kThreads;
-  cudaError_t err = cudaFuncSetAttribute(k_diag<NB, SAFE, CONJ>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
-  if (err != cudaSuccess) return err;
   int maxblk = 0;
   for (int p = 0; p < count; ++p) maxblk = std::max(maxblk, (probs[p].m + NB - 1) / NB);
   const bool tracing = trace_on();
   for (int s = 0; s < maxblk; ++s) {
     int dx = 0, rows_max = 0, cols_max = 0;
-    long long tiles_big = 0, tiles_mid = 0;
+    long long tiles_big = 0, tiles_mid = 0, total_cols = 0;
     double gflops = 0, gbytes = 0, dflops = 0, dbytes = 0;
     for (int p = 0; p < count; ++p) {
       const int m = probs[p].m, n = probs[p].n, nblk = (m + NB - 1) / NB;
@@ -584,7 +334,8 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       if (ncols <= 0) continue;
       const int rows = CONJ ? m - hi : lo;
       const double K = hi - lo;
-      dx = std::max(dx, (ncols + diag_threads - 1) / diag_threads);
+      dx = std::max(dx, ncols);
+      total_cols += ncols;
       // algorithmic work: 8 real FLOPs per complex multiply-add
       dflops += 4.0 * K * K * ncols;
       dbytes += 16.0 * K * K / 2 + 32.0 * K * ncols;
@@ -599,8 +350,9 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
     }
     if (dx > 0) {
       void *h = tracing ? trace_start(1, dflops, dbytes, st) : nullptr;
-      k_diag<NB, SAFE, CONJ><<<dim3(dx, 1, tab.count), diag_threads, diag_smem, st>>>(
-          tab, s, shortcut ? 1 : 0, status);
+      const cudaError_t e = launch_diag(tab, NB, SAFE, CONJ, s, shortcut ? 1 : 0, dx, total_cols,
+                                        status, st);
+      if (e != cudaSuccess) return e;
       trace_stop(h, st);
       count_launches(1);
     }
