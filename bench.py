@@ -361,7 +361,55 @@ def extra_measurements(dev, nb):
     res["pseudospectra_2000_grid100x100"] = {
         "shifts_per_s": N / (ms * 1e-3), "ms": ms,
         "tflops": 20 * 2 * 4 * 2000 ** 2 * N / (ms * 1e-3) / 1e12}
+    res["mixed_8192x2048"] = mixed_vs_fp64(dev, nb)
     return res
+
+
+def eta_dev(Ud, sd, Bd, X):
+    """max_j normwise backward error on the GPU (complex128 torch product; a check)."""
+    import torch
+    Ut = torch.triu(Ud)
+    R = Bd - (Ut @ X - X * sd[None, :])
+    rown = Ut.abs().sum(dim=1) - torch.diagonal(Ut).abs()
+    an = (rown[:, None] + (torch.diagonal(Ut)[:, None] - sd[None, :]).abs()).amax(dim=0)
+    return float((R.abs().amax(dim=0) / (an * X.abs().amax(dim=0) + Bd.abs().amax(dim=0))).max())
+
+
+def mixed_vs_fp64(dev, nb, flags=0):
+    """Workload 3 (8192 x 8192, 2048 shifts): the plain FP64 solve and the mixed
+    solve with refinement to eta <= 1e-12, TFLOP/s at 4 m^2 n (refinement not
+    credited), each with its measured eta."""
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    U, s, B = W.mixed_problem()
+    m, n = B.shape
+    Ud, sd, Bd = (msts.colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
+                  msts.colmajor(torch.from_numpy(B).to(dev)))
+    fl = 4.0 * m * m * n
+    X = Bd.clone()
+    msts.msts_solve(Ud, sd, X, nb=nb)            # warm-up
+    X.copy_(Bd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    msts.msts_solve(Ud, sd, X, nb=nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    eta64 = eta_dev(Ud, sd, Bd, X)
+    msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, nb=nb, flags=flags)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xm, info, st = msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, nb=nb, flags=flags)
+    torch.cuda.synchronize()
+    msm = (time.perf_counter() - t0) * 1e3
+    etam = eta_dev(Ud, sd, Bd, Xm)
+    return {"fp64": {"ms": ms64, "tflops": fl / (ms64 * 1e-3) / 1e12, "eta": eta64},
+            "mixed": {"ms": msm, "tflops": fl / (msm * 1e-3) / 1e12, "eta": etam,
+                      "eta_before_refinement": info["eta_before"], "corrections": info["iters"],
+                      "residual": "ozaki-bf16-tcgen05" if flags else "fp64-dfma"},
+            "speedup_mixed_vs_fp64": ms64 / msm}
 
 
 def cpu_baseline_trevc(T, stride=2):

@@ -192,6 +192,31 @@ int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32
                          uint32_t *status, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Mixed-precision multi-shift solve with FP64 iterative refinement (not in the
+ * paper, which is FP64 throughout).  Solves (U - s_j I) X(:,j) = B(:,j) with
+ *   X_0 = solve_lp(B);  repeat  R = B - (U - S) X  (FP64),
+ *                               eta = max_j ||R_j||_inf / (||U - s_j I||_inf ||x_j||_inf + ||b_j||_inf),
+ *                               stop if eta <= tol or after max_iter corrections,
+ *                               X += solve_lp(R)
+ * where solve_lp is the blocked solve of Alg. 3 whose substitution GEMM
+ * multiplies in FP32 (diagonal blocks in FP64).
+ * B (read only) and X (written, ldx) are m x n.  flags must be 0.
+ * SYNCHRONOUS: the convergence test reads eta on the host every iteration, so
+ * the call returns after the work is done.  *iters (host, may be NULL)
+ * receives the number of corrections, *eta the final max eta and
+ * *eta_before the max eta of X_0 (host pointers).  If eta > tol at the cap,
+ * MSTS_STATUS_NOT_CONVERGED is OR-ed into *status.
+ * ------------------------------------------------------------------------- */
+size_t msts_solve_mixed_workspace_size(int64_t m, int64_t n, int32_t nb, uint32_t flags);
+int msts_solve_mixed(const msts_z *U, int64_t ldu, int64_t m,
+                     const msts_z *shifts, int64_t n,
+                     const msts_z *B, int64_t ldb, msts_z *X, int64_t ldx,
+                     double tol, int32_t max_iter,
+                     int32_t nb, void *workspace, size_t workspace_bytes,
+                     uint32_t *status, uint32_t flags,
+                     int32_t *iters, double *eta, double *eta_before, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (not in the paper).
  * msts_launch_count: number of kernels the library has launched in this
  *   process so far (all entry points).

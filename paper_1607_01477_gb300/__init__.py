@@ -25,7 +25,8 @@ import torch
 __all__ = [
     "MSTS_SAFE", "MSTS_CONJ_TRANS", "STATUS_BITS", "colmajor", "load_library", "library_path",
     "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
-    "msts_adjoint_batched", "MultiShiftSolve", "multishift_solve", "decode_status",
+    "msts_adjoint_batched", "msts_solve_mixed", "MultiShiftSolve", "multishift_solve",
+    "decode_status",
 ]
 
 MSTS_SAFE = 1
@@ -98,6 +99,12 @@ def load_library():
         lib.msts_adjoint_batched_workspace_size.argtypes = [_vp, _i64, _i32]
         lib.msts_adjoint_batched.restype = ctypes.c_int
         lib.msts_adjoint_batched.argtypes = [_vp, _i64, _i32, _vp, _sz, _vp, _vp]
+        lib.msts_solve_mixed_workspace_size.restype = _sz
+        lib.msts_solve_mixed_workspace_size.argtypes = [_i64, _i64, _i32, _u32]
+        lib.msts_solve_mixed.restype = ctypes.c_int
+        lib.msts_solve_mixed.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                                         ctypes.c_double, _i32, _i32, _vp, _sz, _vp, _u32, _vp,
+                                         _vp, _vp, _vp]
         _lib = lib
         return lib
 
@@ -313,6 +320,30 @@ def msts_adjoint_batched(problems, *, nb=32, status=None):
     rc = lib.msts_adjoint_batched(arr, len(problems), nb, wp, wb, _ptr(status), _stream(dev))
     _check(rc, "msts_adjoint_batched")
     return outs, status
+
+
+def msts_solve_mixed(U, shifts, B, *, tol=1e-12, max_iter=10, nb=32, flags=0, status=None):
+    """Mixed-precision solve with FP64 iterative refinement (synchronous).
+
+    Returns (X, info, status) with info = {"iters", "eta", "eta_before"}.
+    """
+    lib = load_library()
+    m, n = B.shape
+    ldu, ldb = _mat(U, "U", m), _mat(B, "B", m)
+    _vec(shifts, "shifts")
+    dev = B.device
+    X = colmajor(torch.empty((m, n), dtype=torch.complex128, device=dev))
+    ws = _workspace(lib.msts_solve_mixed_workspace_size(m, n, nb, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    it = ctypes.c_int32()
+    eta = ctypes.c_double()
+    eta0 = ctypes.c_double()
+    rc = lib.msts_solve_mixed(_ptr(U), ldu, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(X), max(1, m),
+                              tol, max_iter, nb, wp, wb, _ptr(status), flags, ctypes.byref(it),
+                              ctypes.byref(eta), ctypes.byref(eta0), _stream(dev))
+    _check(rc, "msts_solve_mixed")
+    return X, {"iters": it.value, "eta": eta.value, "eta_before": eta0.value}, status
 
 
 class MultiShiftSolve(torch.autograd.Function):

@@ -27,8 +27,10 @@ size_t engine_workspace_bytes(const EngineProblem *probs, int count, int nb, boo
 
 // Runs Alg. 3 (plain), Alg. 5 (safe) or the conjugate-transposed plain solve
 // on all problems; `shortcut` declares column j of B zero in rows >= j.
+// lp: the substitution GEMM multiplies in FP32 (the low-precision solve of the
+// mixed-precision form; plain upper solves only).
 cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe, bool conj,
-                       bool shortcut, void *ws, uint32_t *status, cudaStream_t st);
+                       bool shortcut, void *ws, uint32_t *status, cudaStream_t st, bool lp = false);
 
 cudaError_t engine_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z, long long ldz,
                                cudaStream_t st);

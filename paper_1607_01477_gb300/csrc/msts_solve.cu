@@ -249,6 +249,86 @@ k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
   }
 }
 
+// The same substitution step with the product in FP32 (operands rounded to
+// float, FP32 accumulation, the update applied to the FP64 B): the
+// low-precision solve of the mixed-precision form.  Plain upper solves only.
+template <int NB, int BM, int BN, bool SAFE, bool CONJ>
+__global__ void __launch_bounds__(256)
+k_gemm_f32(const __grid_constant__ ProbTable tab, int step, int shortcut) {
+  using C = GemmCfg<BM, BN>;
+  constexpr int LDA = C::LDA, LDX = C::LDX, TM = C::TM, TN = C::TN, NT = C::kThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *sA = reinterpret_cast<float2 *>(smem_raw);     // [NB][LDA]
+  float2 *sX = sA + NB * LDA;                             // [NB][LDX]
+  const Prob &P = tab.p[blockIdx.z];
+  if (step >= P.nblk) return;
+  const int b = CONJ ? P.nblk - 1 - step : step;
+  int lo, hi;
+  block_range(P, b, NB, lo, hi);
+  const int K = hi - lo;
+  const int rend = CONJ ? P.m : lo;
+  const int r0 = (CONJ ? hi : 0) + blockIdx.y * BM;
+  if (r0 >= rend) return;
+  const int c0 = (shortcut ? lo + 1 : 0) + blockIdx.x * BN;
+  if (c0 >= P.n) return;
+  const int tid = threadIdx.x;
+
+  for (int idx = tid; idx < NB * BM; idx += NT) {
+    int k, r;
+    if (!CONJ) { k = idx / BM; r = idx - k * BM; }   // coalesced along U's rows
+    else { r = idx / NB; k = idx - r * NB; }          // coalesced along U's rows (= k)
+    double2 v = make_double2(0.0, 0.0);
+    if (k < K && r0 + r < rend)
+      v = CONJ ? zconj(P.U[(lo + k) + (long long)(r0 + r) * P.ldu])
+               : P.U[(r0 + r) + (long long)(lo + k) * P.ldu];
+    sA[k * LDA + r] = make_float2((float)v.x, (float)v.y);
+  }
+  for (int idx = tid; idx < NB * BN; idx += NT) {
+    const int c = idx / NB, k = idx - c * NB;
+    double2 v = make_double2(0.0, 0.0);
+    if (k < K && c0 + c < P.n) v = P.B[(lo + k) + (long long)(c0 + c) * P.ldb];
+    sX[k * LDX + c] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+
+  const int tr = tid & 31, tc = tid >> 5;
+  float2 acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[i][c] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    float2 a[TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) a[i] = sA[k * LDA + tr + 32 * i];
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const float2 x = sX[k * LDX + tc + 8 * c];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        acc[i][c].x = fmaf(a[i].x, x.x, fmaf(-a[i].y, x.y, acc[i][c].x));
+        acc[i][c].y = fmaf(a[i].x, x.y, fmaf(a[i].y, x.x, acc[i][c].y));
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < TN; ++c) {
+    const int col = c0 + tc + 8 * c;
+    if (col >= P.n) continue;
+    const int pend = SAFE ? P.pend[col] : 0;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int row = r0 + tr + 32 * i;
+      if (row >= rend) continue;
+      double2 *p = P.B + row + (long long)col * P.ldb;
+      double2 v = *p;
+      if (SAFE && pend) v = zshift(v, pend);
+      *p = make_double2(v.x - (double)acc[i][c].x, v.y - (double)acc[i][c].y);
+    }
+  }
+}
+
 // Final lazy rescale (safe variant): block b of column j was finished with
 // exponent E[b][j]; it still owes 2^-(e_j - E[b][j]).  Also writes s_j.
 __global__ void k_fixup(const __grid_constant__ ProbTable tab, int nb, int shortcut) {
@@ -308,8 +388,15 @@ static T *carve(char *&cur, size_t count) {
 }
 
 template <int NB, int BM, int BN, bool SAFE, bool CONJ>
-static void launch_gemm(const ProbTable &tab, int gx, int gy, int s, bool shortcut, cudaStream_t st) {
+static void launch_gemm(const ProbTable &tab, int gx, int gy, int s, bool shortcut, bool lp,
+                        cudaStream_t st) {
   constexpr size_t smem = GemmCfg<BM, BN>::template smem<NB>();
+  if (lp && !SAFE && !CONJ) {
+    cudaFuncSetAttribute(k_gemm_f32<NB, BM, BN, SAFE, CONJ>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gemm_f32<NB, BM, BN, SAFE, CONJ><<<dim3(gx, gy, tab.count), 256, smem, st>>>(tab, s, shortcut ? 1 : 0);
+    return;
+  }
   cudaFuncSetAttribute(k_gemm<NB, BM, BN, SAFE, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   k_gemm<NB, BM, BN, SAFE, CONJ><<<dim3(gx, gy, tab.count), 256, smem, st>>>(tab, s, shortcut ? 1 : 0);
@@ -317,7 +404,7 @@ static void launch_gemm(const ProbTable &tab, int gx, int gy, int s, bool shortc
 
 template <int NB, bool SAFE, bool CONJ>
 static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, int count,
-                             bool shortcut, uint32_t *status, cudaStream_t st) {
+                             bool shortcut, bool lp, uint32_t *status, cudaStream_t st) {
   int maxblk = 0;
   for (int p = 0; p < count; ++p) maxblk = std::max(maxblk, (probs[p].m + NB - 1) / NB);
   const bool tracing = trace_on();
@@ -361,11 +448,11 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       // at least two waves of CTAs over the 152 SMs when the problem allows.
       void *h = tracing ? trace_start(0, gflops, gbytes, st) : nullptr;
       if (tiles_big >= 2 * kNumSMs)
-        launch_gemm<NB, 64, 32, SAFE, CONJ>(tab, (cols_max + 31) / 32, (rows_max + 63) / 64, s, shortcut, st);
+        launch_gemm<NB, 64, 32, SAFE, CONJ>(tab, (cols_max + 31) / 32, (rows_max + 63) / 64, s, shortcut, lp, st);
       else if (tiles_mid >= kNumSMs)
-        launch_gemm<NB, 32, 16, SAFE, CONJ>(tab, (cols_max + 15) / 16, (rows_max + 31) / 32, s, shortcut, st);
+        launch_gemm<NB, 32, 16, SAFE, CONJ>(tab, (cols_max + 15) / 16, (rows_max + 31) / 32, s, shortcut, lp, st);
       else
-        launch_gemm<NB, 32, 8, SAFE, CONJ>(tab, (cols_max + 7) / 8, (rows_max + 31) / 32, s, shortcut, st);
+        launch_gemm<NB, 32, 8, SAFE, CONJ>(tab, (cols_max + 7) / 8, (rows_max + 31) / 32, s, shortcut, lp, st);
       trace_stop(h, st);
       count_launches(1);
     }
@@ -375,14 +462,14 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
 
 template <int NB>
 static cudaError_t run_nb(const ProbTable &tab, const EngineProblem *probs, int count, bool safe,
-                          bool conj, bool shortcut, uint32_t *status, cudaStream_t st) {
-  if (safe) return run_steps<NB, true, false>(tab, probs, count, shortcut, status, st);
-  if (conj) return run_steps<NB, false, true>(tab, probs, count, shortcut, status, st);
-  return run_steps<NB, false, false>(tab, probs, count, shortcut, status, st);
+                          bool conj, bool shortcut, bool lp, uint32_t *status, cudaStream_t st) {
+  if (safe) return run_steps<NB, true, false>(tab, probs, count, shortcut, false, status, st);
+  if (conj) return run_steps<NB, false, true>(tab, probs, count, shortcut, false, status, st);
+  return run_steps<NB, false, false>(tab, probs, count, shortcut, lp, status, st);
 }
 
 cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe, bool conj,
-                       bool shortcut, void *ws, uint32_t *status, cudaStream_t st) {
+                       bool shortcut, void *ws, uint32_t *status, cudaStream_t st, bool lp) {
   char *cur = static_cast<char *>(ws);
   for (int base = 0; base < count; base += kMaxProbs) {
     const int cnt = std::min(kMaxProbs, count - base);
@@ -420,9 +507,9 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
     }
     cudaError_t err;
     switch (nb) {
-      case 16: err = run_nb<16>(tab, probs + base, cnt, safe, conj, shortcut, status, st); break;
-      case 32: err = run_nb<32>(tab, probs + base, cnt, safe, conj, shortcut, status, st); break;
-      case 64: err = run_nb<64>(tab, probs + base, cnt, safe, conj, shortcut, status, st); break;
+      case 16: err = run_nb<16>(tab, probs + base, cnt, safe, conj, shortcut, lp, status, st); break;
+      case 32: err = run_nb<32>(tab, probs + base, cnt, safe, conj, shortcut, lp, status, st); break;
+      case 64: err = run_nb<64>(tab, probs + base, cnt, safe, conj, shortcut, lp, status, st); break;
       default: return cudaErrorInvalidValue;
     }
     if (err != cudaSuccess) return err;
