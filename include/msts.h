@@ -55,6 +55,8 @@ typedef struct { double re, im; } msts_z;
 /* flags */
 #define MSTS_SAFE        1u  /* Alg. 5: (U - s_j I) x_j = scale_j b_j with scale_j in [0,1]  */
 #define MSTS_CONJ_TRANS  2u  /* solve (U^H - conj(s_j) I) x_j = b_j (forward substitution)  */
+#define MSTS_RESIDUAL_OZAKI 4u /* msts_solve_mixed / msts_residual: FP64-accurate product on the
+                                  BF16 tensor cores (error-free digit splitting) instead of FP64 FMA */
 
 /* status bits */
 #define MSTS_STATUS_ZERO_PIVOT  1u  /* plain solve: some U(i,i) - s_j == 0 exactly (X is undefined) */
@@ -63,6 +65,8 @@ typedef struct { double re, im; } msts_z;
 #define MSTS_STATUS_SCALED      8u  /* safe solve: some scale_j < 1                              */
 #define MSTS_STATUS_DELTA      16u  /* safe solve: a zero pivot was replaced by delta            */
 #define MSTS_STATUS_NOT_CONVERGED 32u /* mixed solve: refinement stopped at its iteration cap   */
+#define MSTS_STATUS_TIMEOUT    64u  /* a bounded wait inside a tensor-core kernel expired: the
+                                       results of that call are invalid                     */
 
 #define MSTS_ERR_CUDA (-1000)
 
@@ -200,7 +204,13 @@ int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32
  *                               X += solve_lp(R)
  * where solve_lp is the blocked solve of Alg. 3 whose substitution GEMM
  * multiplies in FP32 (diagonal blocks in FP64).
- * B (read only) and X (written, ldx) are m x n.  flags must be 0.
+ * B (read only) and X (written, ldx) are m x n.  flags: 0 computes the
+ * residual with FP64 FMAs; MSTS_RESIDUAL_OZAKI computes the product triu(U) X
+ * on the BF16 tensor cores from 8 seven-bit digit planes per operand with
+ * exact FP32 accumulation per 64-wide K chunk and integer accumulation across
+ * chunks (accurate to ~2^-50 relative to K max|U(r,:)| max|X(:,j)|), and
+ * needs msts_solve_mixed_workspace_size(m, n, nb, flags) bytes (about
+ * 32 m (m + n) bytes more).
  * SYNCHRONOUS: the convergence test reads eta on the host every iteration, so
  * the call returns after the work is done.  *iters (host, may be NULL)
  * receives the number of corrections, *eta the final max eta and
@@ -215,6 +225,20 @@ int msts_solve_mixed(const msts_z *U, int64_t ldu, int64_t m,
                      int32_t nb, void *workspace, size_t workspace_bytes,
                      uint32_t *status, uint32_t flags,
                      int32_t *iters, double *eta, double *eta_before, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Residual R = B - (U - diag(s)) X of a multi-shift solve (not in the paper):
+ * R(:,j) = B(:,j) - triu(U) X(:,j) + s_j X(:,j), all m x n, asynchronous.
+ * flags = 0: FP64 FMA; MSTS_RESIDUAL_OZAKI: the tensor-core product described
+ * under msts_solve_mixed (workspace from msts_residual_workspace_size).
+ * ------------------------------------------------------------------------- */
+size_t msts_residual_workspace_size(int64_t m, int64_t n, uint32_t flags);
+int msts_residual(const msts_z *U, int64_t ldu, int64_t m,
+                  const msts_z *shifts, int64_t n,
+                  const msts_z *B, int64_t ldb, const msts_z *X, int64_t ldx,
+                  msts_z *R, int64_t ldr,
+                  void *workspace, size_t workspace_bytes,
+                  uint32_t *status, uint32_t flags, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation (not in the paper).

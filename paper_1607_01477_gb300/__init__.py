@@ -25,14 +25,17 @@ import torch
 __all__ = [
     "MSTS_SAFE", "MSTS_CONJ_TRANS", "STATUS_BITS", "colmajor", "load_library", "library_path",
     "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
-    "msts_adjoint_batched", "msts_solve_mixed", "MultiShiftSolve", "multishift_solve",
+    "msts_adjoint_batched", "msts_solve_mixed", "msts_residual", "MSTS_RESIDUAL_OZAKI",
+    "MultiShiftSolve", "multishift_solve",
     "decode_status",
 ]
 
 MSTS_SAFE = 1
 MSTS_CONJ_TRANS = 2
+MSTS_RESIDUAL_OZAKI = 4
 STATUS_BITS = {
     1: "ZERO_PIVOT", 2: "NONFINITE", 4: "RANGE", 8: "SCALED", 16: "DELTA", 32: "NOT_CONVERGED",
+    64: "TIMEOUT",
 }
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,6 +108,11 @@ def load_library():
         lib.msts_solve_mixed.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                                          ctypes.c_double, _i32, _i32, _vp, _sz, _vp, _u32, _vp,
                                          _vp, _vp, _vp]
+        lib.msts_residual_workspace_size.restype = _sz
+        lib.msts_residual_workspace_size.argtypes = [_i64, _i64, _u32]
+        lib.msts_residual.restype = ctypes.c_int
+        lib.msts_residual.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                                      _vp, _sz, _vp, _u32, _vp]
         _lib = lib
         return lib
 
@@ -320,6 +328,24 @@ def msts_adjoint_batched(problems, *, nb=32, status=None):
     rc = lib.msts_adjoint_batched(arr, len(problems), nb, wp, wb, _ptr(status), _stream(dev))
     _check(rc, "msts_adjoint_batched")
     return outs, status
+
+
+def msts_residual(U, shifts, B, X, *, ozaki=False, status=None):
+    """R = B - (triu(U) - diag(s)) X; ozaki=True uses the tensor-core product."""
+    lib = load_library()
+    m, n = B.shape
+    ldu, ldb, ldx = _mat(U, "U", m), _mat(B, "B", m), _mat(X, "X", m)
+    _vec(shifts, "shifts")
+    dev = B.device
+    flags = MSTS_RESIDUAL_OZAKI if ozaki else 0
+    R = colmajor(torch.empty((m, n), dtype=torch.complex128, device=dev))
+    ws = _workspace(lib.msts_residual_workspace_size(m, n, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_residual(_ptr(U), ldu, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(X), ldx, _ptr(R),
+                           max(1, m), wp, wb, _ptr(status), flags, _stream(dev))
+    _check(rc, "msts_residual")
+    return R, status
 
 
 def msts_solve_mixed(U, shifts, B, *, tol=1e-12, max_iter=10, nb=32, flags=0, status=None):

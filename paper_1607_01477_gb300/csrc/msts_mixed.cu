@@ -9,13 +9,15 @@
 //
 // solve_lp is the blocked multi-shift solve whose substitution GEMM multiplies
 // in FP32 (the diagonal blocks stay FP64).  The residual is computed in FP64
-// DFMA (k_residual).
+// DFMA (k_residual) or, with MSTS_RESIDUAL_OZAKI, by the FP64-accurate
+// tensor-core product of msts_ozaki.cu.
 #include <algorithm>
 #include <vector>
 
 #include "msts_common.cuh"
 #include "msts_engine.h"
 #include "msts_mixed.h"
+#include "msts_ozaki.h"
 #include "msts_trace.h"
 
 namespace msts {
@@ -153,14 +155,17 @@ size_t mixed_workspace_bytes(int m, int n, int nb, uint32_t flags) {
   s += a256(sizeof(double) * (size_t)n);              // eta
   s += a256(sizeof(double) * (size_t)m);              // off-diagonal row sums
   s += a256(sizeof(double) * 2);                      // max eta
+  if (flags & MSTS_RESIDUAL_OZAKI) s += ozaki_workspace_bytes(m, n);
   (void)nb;
-  (void)flags;
   return s;
 }
 
-static cudaError_t residual(const double2 *U, long long ldu, int m, const double2 *s, int n,
-                            const double2 *B, long long ldb, const double2 *X, long long ldx,
-                            double2 *R, long long ldr, cudaStream_t st) {
+cudaError_t residual_run(const double2 *U, long long ldu, int m, const double2 *s, int n,
+                         const double2 *B, long long ldb, const double2 *X, long long ldx,
+                         double2 *R, long long ldr, uint32_t flags, void *oz_ws, uint32_t *status,
+                         cudaStream_t st) {
+  if (flags & MSTS_RESIDUAL_OZAKI)
+    return ozaki_residual(U, ldu, m, s, n, B, ldb, X, ldx, R, ldr, oz_ws, status, st);
   const double fl = 4.0 * (double)m * m * n;
   void *h = trace_on() ? trace_start(0, fl, 16.0 * ((double)m * m / 2 + 3.0 * m * n), st) : nullptr;
   k_residual<<<dim3((n + kRBN - 1) / kRBN, (m + kRBM - 1) / kRBM), kRThreads, 0, st>>>(
@@ -179,6 +184,7 @@ cudaError_t mixed_run(const double2 *U, long long ldu, int m, const double2 *s, 
   double *eta = reinterpret_cast<double *>(cur); cur += a256(sizeof(double) * (size_t)n);
   double *rs = reinterpret_cast<double *>(cur); cur += a256(sizeof(double) * (size_t)m);
   double *emax = reinterpret_cast<double *>(cur); cur += a256(sizeof(double) * 2);
+  void *oz_ws = cur;
   const int cgrid = std::max(1, std::min(8192, (int)(((long long)m * n + 255) / 256)));
 
   EngineProblem Px{};
@@ -188,7 +194,10 @@ cudaError_t mixed_run(const double2 *U, long long ldu, int m, const double2 *s, 
   Pr.B = R; Pr.ldb = m;
 
   cudaError_t e;
-  (void)flags;
+  if (flags & MSTS_RESIDUAL_OZAKI) {
+    e = ozaki_prepare(U, ldu, m, n, oz_ws, st);
+    if (e != cudaSuccess) return e;
+  }
   k_offdiag_rowsums<<<(m + 7) / 8, 256, 0, st>>>(U, ldu, m, rs);
   k_copy_or_add<<<cgrid, 256, 0, st>>>(B, ldb, X, ldx, m, n, 0);
   count_launches(2);
@@ -197,7 +206,7 @@ cudaError_t mixed_run(const double2 *U, long long ldu, int m, const double2 *s, 
   double eta_h = 0.0;
   int it = 0;
   for (;; ++it) {
-    e = residual(U, ldu, m, s, n, B, ldb, X, ldx, R, m, st);
+    e = residual_run(U, ldu, m, s, n, B, ldb, X, ldx, R, m, flags, oz_ws, status, st);
     if (e != cudaSuccess) return e;
     k_eta<<<(n + 7) / 8, 256, 0, st>>>(U, ldu, m, s, n, rs, B, ldb, X, ldx, R, m, eta);
     k_max<<<1, 256, 0, st>>>(eta, n, emax);
@@ -254,7 +263,7 @@ int msts_solve_mixed(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shif
   if (!(tol >= 0.0)) return -10;
   if (max_iter < 0) return -11;
   if (nb != 16 && nb != 32 && nb != 64) return -12;
-  if (flags != 0) return -16;
+  if ((flags & ~(uint32_t)MSTS_RESIDUAL_OZAKI) != 0) return -16;
   if (m == 0 || n == 0) {
     if (iters) *iters = 0;
     if (eta) *eta = 0.0;
@@ -272,6 +281,41 @@ int msts_solve_mixed(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shif
   if (iters) *iters = it;
   if (eta) *eta = e_final;
   if (eta_before) *eta_before = e0;
+  return e == cudaSuccess ? 0 : MSTS_ERR_CUDA;
+}
+
+size_t msts_residual_workspace_size(int64_t m, int64_t n, uint32_t flags) {
+  if (m < 0 || n < 0) return 0;
+  return (flags & MSTS_RESIDUAL_OZAKI) ? msts::ozaki_workspace_bytes((int)m, (int)n) : 0;
+}
+
+int msts_residual(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shifts, int64_t n,
+                  const msts_z *B, int64_t ldb, const msts_z *X, int64_t ldx, msts_z *R, int64_t ldr,
+                  void *workspace, size_t workspace_bytes, uint32_t *status, uint32_t flags,
+                  void *stream) {
+  const int64_t kMax = (int64_t)1 << 30;
+  if (m < 0 || m > kMax) return -3;
+  if (m > 0 && !U) return -1;
+  if (ldu < (m > 1 ? m : 1)) return -2;
+  if (n < 0 || n > kMax) return -5;
+  if (n > 0 && !shifts) return -4;
+  if (m > 0 && n > 0 && (!B || !X || !R)) return !B ? -6 : (!X ? -8 : -10);
+  if (ldb < (m > 1 ? m : 1)) return -7;
+  if (ldx < (m > 1 ? m : 1)) return -9;
+  if (ldr < (m > 1 ? m : 1)) return -11;
+  if ((flags & ~(uint32_t)MSTS_RESIDUAL_OZAKI) != 0) return -15;
+  if (m == 0 || n == 0) return 0;
+  const size_t need = msts_residual_workspace_size(m, n, flags);
+  if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -13 : -12;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double2 *Ud = reinterpret_cast<const double2 *>(U);
+  if (flags & MSTS_RESIDUAL_OZAKI) {
+    if (msts::ozaki_prepare(Ud, ldu, (int)m, (int)n, workspace, st) != cudaSuccess) return MSTS_ERR_CUDA;
+  }
+  const cudaError_t e = msts::residual_run(
+      Ud, ldu, (int)m, reinterpret_cast<const double2 *>(shifts), (int)n,
+      reinterpret_cast<const double2 *>(B), ldb, reinterpret_cast<const double2 *>(X), ldx,
+      reinterpret_cast<double2 *>(R), ldr, flags, workspace, status, st);
   return e == cudaSuccess ? 0 : MSTS_ERR_CUDA;
 }
 

@@ -1,0 +1,413 @@
+// msts_ozaki.cu -- FP64-accurate complex product P = triu(U) X on the BF16
+// tensor cores (tcgen05), used for the refinement residual
+// R = B - (U - S) X = B - P + X diag(s) of the mixed-precision solve.
+//
+// Method: error-free splitting of both operands into integer digit planes
+// (the splitting of Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012),
+// written here for the tcgen05 pipeline:
+//  * real embedding: with A'(2r, 2k..2k+1) = (Re U, -Im U),
+//    A'(2r+1, 2k..2k+1) = (Im U, Re U) and B' = X read as real numbers
+//    (its interleaved storage already is [Re X(k); Im X(k)]), the real
+//    product A' B' holds Re P in its even rows and Im P in its odd rows;
+//  * every row r of U gets an exponent e_r with |Re U(r,k)|, |Im U(r,k)| <
+//    2^e_r, every column j of X an exponent f_j likewise; each entry then is
+//    2^e sum_{s=1..8} d_s 2^{-7s} + (remainder < 2^{e-56}) with signed integer
+//    digits |d_s| <= 127, exactly representable in BF16;
+//  * A' B' = 2^{e_r + f_j} sum_{d=2..9} 2^{-7d} D_d with D_d = sum_{s+t=d}
+//    (digit plane s of A') (digit plane t of B'); products with s + t > 9 are
+//    dropped (each below 2^{-49} of the leading term's scale);
+//  * K' is processed in chunks of 64: within a chunk every |D_d| <= 8 * 64 *
+//    127^2 < 2^24, so the FP32 accumulation in tensor memory is exact; the
+//    epilogue warps turn each chunk's D_d into integers and add them into two
+//    int64 accumulators per output (HI for d <= 4, LO for d >= 5), so nothing
+//    is rounded until the final conversion to FP64.
+// The result is accurate to about 2^-50 relative to K' max|U(r,:)| max|X(:,j)|.
+//
+// Kernel layout (one CTA per 128 x 32 output tile of A' B'; 6 warps):
+//  warp 4  : TMA producer (B digit planes per chunk, A planes through a ring);
+//  warp 5  : one thread issues the 36 x 4 MMAs of each chunk into 8 TMEM
+//            accumulators (double-buffered: 2 x 8 x 32 = 512 columns);
+//  warps 0-3: epilogue, one thread per TMEM lane (= output row).
+// Every mbarrier wait is bounded; a timeout raises MSTS_STATUS_TIMEOUT in the
+// status word (which also makes the waits of all other CTAs give up) and the
+// kernel drains without hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "msts_common.cuh"
+#include "msts_ozaki.h"
+#include "msts_tc.cuh"
+#include "msts_trace.h"
+
+namespace msts {
+
+constexpr int kOzS = 8;          // digit planes per operand
+constexpr int kOzBits = 7;       // bits per digit
+constexpr int kOzKC = 64;        // K' per chunk: one 128-byte swizzle row of BF16
+constexpr int kOzBM = 128;       // real rows per tile (= TMEM lanes)
+constexpr int kOzBN = 32;        // columns per tile
+constexpr int kOzRing = 6;       // A-plane ring depth
+constexpr int kOzThreads = 192;  // 4 epilogue warps + producer + MMA
+constexpr int kOzAccCols = kOzS * kOzBN;   // 8 diagonals x 32 columns per buffer
+constexpr uint32_t kOzABytes = kOzBM * kOzKC * 2;          // 16 KB per A plane
+constexpr uint32_t kOzBBytes = kOzS * kOzBN * kOzKC * 2;   // 32 KB for all B planes
+constexpr size_t kOzSmem = 2 * kOzBBytes + kOzRing * kOzABytes + 1024;
+
+static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+static int kpad(int m) { return ((2 * m + kOzKC - 1) / kOzKC) * kOzKC; }
+
+size_t ozaki_workspace_bytes(int m, int n) {
+  const size_t K = (size_t)kpad(m);
+  return a256((size_t)kOzS * 2 * m * K * 2) + a256((size_t)kOzS * n * K * 2) + a256(4 * (size_t)m) +
+         a256(4 * (size_t)n);
+}
+
+struct OzakiBufs {
+  __nv_bfloat16 *Ap, *Bp;
+  int *rexp, *cexp;
+  int K;
+};
+static OzakiBufs carve(void *ws, int m, int n) {
+  OzakiBufs o;
+  o.K = kpad(m);
+  char *c = static_cast<char *>(ws);
+  o.Ap = reinterpret_cast<__nv_bfloat16 *>(c); c += a256((size_t)kOzS * 2 * m * o.K * 2);
+  o.Bp = reinterpret_cast<__nv_bfloat16 *>(c); c += a256((size_t)kOzS * n * o.K * 2);
+  o.rexp = reinterpret_cast<int *>(c); c += a256(4 * (size_t)m);
+  o.cexp = reinterpret_cast<int *>(c);
+  return o;
+}
+
+// floor(log2 max(|Re z|, |Im z|)) + 1, or INT_MIN/2 for z == 0.
+__device__ __forceinline__ int bound_exp(double2 z) {
+  const double a = fmax(fabs(z.x), fabs(z.y));
+  return a == 0.0 ? -(1 << 29) : ilogb(a) + 1;
+}
+
+// The 8 signed 7-bit digits of a * 2^-e (|a| < 2^e), most significant first.
+__device__ __forceinline__ void digits8(double a, int e, float (&d)[kOzS]) {
+  const long long N = __double2ll_rz(scalbn(a, kOzS * kOzBits - e));
+  const unsigned long long M = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
+#pragma unroll
+  for (int s = 0; s < kOzS; ++s) {
+    const float c = (float)((M >> (kOzBits * (kOzS - 1 - s))) & 127ull);
+    d[s] = N < 0 ? -c : c;
+  }
+}
+
+// e_r for every row of triu(U): one warp per row.
+__global__ void k_oz_rowexp(const double2 *U, long long ldu, int m, int *rexp) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= m) return;
+  int e = -(1 << 29);
+  for (int k = r + lane; k < m; k += 32) e = max(e, bound_exp(U[r + (long long)k * ldu]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (lane == 0) rexp[r] = e < -(1 << 28) ? 0 : e;
+}
+
+// Digit planes of A': plane s, row i, column k' at Ap[(s * 2m + i) * K + k'].
+// Thread (k, r) writes rows 2r, 2r+1 at columns 2k, 2k+1 of every plane
+// (zero outside the upper triangle and in the padding).
+__global__ void k_oz_slice_A(const double2 *U, long long ldu, int m, const int *rexp,
+                             __nv_bfloat16 *Ap, int K) {
+  const int r = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * k >= K) return;
+  float dr[kOzS], di[kOzS];
+  if (k >= r && k < m) {
+    const double2 u = U[r + (long long)k * ldu];
+    digits8(u.x, rexp[r], dr);
+    digits8(u.y, rexp[r], di);
+  } else {
+#pragma unroll
+    for (int s = 0; s < kOzS; ++s) dr[s] = di[s] = 0.f;
+  }
+  const size_t rows = 2 * (size_t)m;
+#pragma unroll
+  for (int s = 0; s < kOzS; ++s) {
+    __nv_bfloat162 *p0 = reinterpret_cast<__nv_bfloat162 *>(Ap + (s * rows + 2 * (size_t)r) * K + 2 * k);
+    __nv_bfloat162 *p1 = reinterpret_cast<__nv_bfloat162 *>(Ap + (s * rows + 2 * (size_t)r + 1) * K + 2 * k);
+    *p0 = __floats2bfloat162_rn(dr[s], -di[s]);   // row 2r:   (Re U, -Im U)
+    *p1 = __floats2bfloat162_rn(di[s], dr[s]);    // row 2r+1: (Im U,  Re U)
+  }
+}
+
+// Digit planes of B' = X (as real): plane t, column j, k' at Bp[(t * n + j) * K + k'],
+// with the column exponent f_j; one CTA per column.
+__global__ void k_oz_slice_B(const double2 *X, long long ldx, int m, int n, int *cexp,
+                             __nv_bfloat16 *Bp, int K) {
+  __shared__ int red[32];
+  const int j = blockIdx.x;
+  const double2 *col = X + (long long)j * ldx;
+  int e = -(1 << 29);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) e = max(e, bound_exp(col[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  e = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, red[w]);
+  if (e < -(1 << 28)) e = 0;
+  if (threadIdx.x == 0) cexp[j] = e;
+  for (int k = threadIdx.x; 2 * k < K; k += blockDim.x) {
+    float dr[kOzS], di[kOzS];
+    if (k < m) {
+      const double2 x = col[k];
+      digits8(x.x, e, dr);
+      digits8(x.y, e, di);
+    } else {
+#pragma unroll
+      for (int s = 0; s < kOzS; ++s) dr[s] = di[s] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < kOzS; ++t)
+      *reinterpret_cast<__nv_bfloat162 *>(Bp + ((size_t)t * n + j) * K + 2 * k) =
+          __floats2bfloat162_rn(dr[t], di[t]);
+  }
+}
+
+struct OzArgs {
+  const double2 *B; long long ldb;
+  const double2 *X; long long ldx;
+  const double2 *s;
+  double2 *R; long long ldr;
+  const int *rexp, *cexp;
+  int m, n, K;
+  uint32_t *status;
+};
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const __grid_constant__ OzArgs args) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  uint8_t *sB = base;                         // 2 buffers x 32 KB
+  uint8_t *sA = base + 2 * kOzBBytes;         // ring of kOzRing x 16 KB
+  __shared__ uint64_t bfull[2], bempty[2], afull[kOzRing], aempty[kOzRing], accfull[2], accempty[2];
+  __shared__ uint64_t mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * kOzBM;          // first real row of the tile
+  const int j0 = blockIdx.x * kOzBN;
+  const int c_begin = i0 / kOzKC;             // U is upper: columns k' < i0 vanish
+  const int c_end = args.K / kOzKC;
+  const int nch = c_end - c_begin;
+
+  if (warp == 0) tmem_alloc(&tmem_base, 512);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1);
+      mbar_init(&accfull[i], 1); mbar_init(&accempty[i], kOzBM);
+    }
+    for (int i = 0; i < kOzRing; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 1); }
+    mbar_init(&mma_done, 1);
+    fail = 0;
+    fence_barrier_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  auto wait = [&](uint64_t *bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity, args.status, MSTS_STATUS_TIMEOUT);
+    if (!ok) raise_status(args.status, MSTS_STATUS_TIMEOUT);   // tell the other CTAs at once
+    return ok;
+  };
+
+  if (warp == 4) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      int ia = 0;
+      for (int c = 0; c < nch; ++c) {
+        const int kk = (c_begin + c) * kOzKC;
+        const int bb = c & 1;
+        if (c >= 2 && !wait(&bempty[bb], ((c >> 1) - 1) & 1)) { fail = 1; break; }
+        mbar_arrive_expect_tx(&bfull[bb], kOzBBytes);
+        tma_load_3d(sB + bb * kOzBBytes, &tmB, &bfull[bb], kk, j0, 0);
+        for (int s = 0; s < kOzS; ++s, ++ia) {
+          const int slot = ia % kOzRing;
+          if (ia >= kOzRing && !wait(&aempty[slot], ((ia / kOzRing) - 1) & 1)) { fail = 1; break; }
+          mbar_arrive_expect_tx(&afull[slot], kOzABytes);
+          tma_load_3d(sA + slot * kOzABytes, &tmA, &afull[slot], kk, i0, s);
+        }
+        if (fail) break;
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kOzBM, kOzBN);
+      int ia = 0;
+      for (int c = 0; c < nch && !fail; ++c) {
+        const int bb = c & 1, ab = c & 1;
+        if (c >= 2 && !wait(&accempty[ab], ((c >> 1) - 1) & 1)) { fail = 1; break; }
+        if (!wait(&bfull[bb], (c >> 1) & 1)) { fail = 1; break; }
+        tc_fence_after();
+        const uint32_t bbase = smem_u32(sB + bb * kOzBBytes);
+        const uint32_t dbase = tmem + ab * kOzAccCols;
+        for (int s = 0; s < kOzS; ++s, ++ia) {
+          const int slot = ia % kOzRing;
+          if (!wait(&afull[slot], (ia / kOzRing) & 1)) { fail = 1; break; }
+          tc_fence_after();
+          const uint32_t abase = smem_u32(sA + slot * kOzABytes);
+          for (int t = 0; t + s < kOzS; ++t) {               // pair (s+1, t+1): diagonal s + t
+            const uint32_t d = dbase + (uint32_t)((s + t) * kOzBN);
+#pragma unroll
+            for (int k = 0; k < kOzKC / 16; ++k)
+              mma_bf16(d, sdesc_k128(abase + 32 * k), sdesc_k128(bbase + t * (kOzBN * 128) + 32 * k),
+                       idesc, (s > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(&aempty[slot]);                         // A plane consumed
+        }
+        if (fail) break;
+        mma_commit(&bempty[bb]);                             // B planes consumed
+        mma_commit(&accfull[ab]);                            // accumulators ready
+      }
+      // Drain: every MMA this thread issued has finished before TMEM is freed.
+      mma_commit(&mma_done);
+      if (!wait(&mma_done, 0)) fail = 1;
+    }
+  } else {
+    // ---------------- epilogue: warps 0-3, one thread per output row -------
+    long long hi[kOzBN], lo[kOzBN];
+#pragma unroll
+    for (int j = 0; j < kOzBN; ++j) hi[j] = lo[j] = 0;
+    const uint32_t lane_addr = (uint32_t)(32 * warp) << 16;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      const int ab = c & 1;
+      if (!wait(&accfull[ab], (c >> 1) & 1)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int d = 0; d < kOzS; ++d) {                       // diagonal s + t = d + 2
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_addr + ab * kOzAccCols + d * kOzBN, v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < kOzBN; ++j) {
+          const long long q = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact integer
+          if (d <= 2) hi[j] += q << (kOzBits * (2 - d));
+          else lo[j] += q << (kOzBits * (7 - d));
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&accempty[ab]);
+    }
+    if (!ok) fail = 1;
+    // value = 2^(e_r + f_j) (hi 2^-28 + lo 2^-63); R = B - P + s_j X.
+    const int i = i0 + 32 * warp + lane;                     // real row of A' B'
+    if (ok && i < 2 * args.m) {
+      const int r = i >> 1, part = i & 1;
+      const int er = args.rexp[r];
+#pragma unroll
+      for (int j = 0; j < kOzBN; ++j) {
+        const int col = j0 + j;
+        if (col >= args.n) continue;
+        const double p = scalbn(fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-63), er + args.cexp[col]);
+        const double2 x = args.X[r + (long long)col * args.ldx];
+        const double2 sj = args.s[col];
+        const double2 b = args.B[r + (long long)col * args.ldb];
+        const double sx = part ? fma(sj.x, x.y, sj.y * x.x) : fma(sj.x, x.x, -sj.y * x.y);
+        double *out = reinterpret_cast<double *>(args.R + r + (long long)col * args.ldr) + part;
+        *out = ((part ? b.y : b.x) - p) + sx;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (fail && threadIdx.x == 0) raise_status(args.status, MSTS_STATUS_TIMEOUT);
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ----- host side -------------------------------------------------------------
+// A status word of the library's own for calls made without one (the bounded
+// waits still need somewhere to publish a timeout to the other CTAs).
+__device__ uint32_t g_oz_abort_word;
+static uint32_t *abort_word() {
+  static uint32_t *p = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *a = nullptr;
+    if (cudaGetSymbolAddress(&a, g_oz_abort_word) == cudaSuccess) p = static_cast<uint32_t *>(a);
+  });
+  return p;
+}
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 3-D map over digit planes: dims (K, rows, kOzS), box (64, box_rows, box_planes).
+static bool make_map(CUtensorMap *map, void *ptr, int K, int rows, int box_rows, int box_planes) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)kOzS};
+  const cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)K * 2 * (cuuint64_t)rows};
+  const cuuint32_t box[3] = {(cuuint32_t)kOzKC, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t ozaki_prepare(const double2 *U, long long ldu, int m, int n, void *ws, cudaStream_t st) {
+  OzakiBufs o = carve(ws, m, n);
+  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(U, ldu, m, o.rexp);
+  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(U, ldu, m, o.rexp, o.Ap, o.K);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2 *s, int n,
+                           const double2 *B, long long ldb, const double2 *X, long long ldx,
+                           double2 *R, long long ldr, void *ws, uint32_t *status, cudaStream_t st) {
+  (void)U; (void)ldu;
+  OzakiBufs o = carve(ws, m, n);
+  k_oz_slice_B<<<n, 256, 0, st>>>(X, ldx, m, n, o.cexp, o.Bp, o.K);
+  count_launches(1);
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, o.Ap, o.K, 2 * m, kOzBM, 1) || !make_map(&tmB, o.Bp, o.K, n, kOzBN, kOzS))
+    return cudaErrorNotSupported;
+  OzArgs a;
+  a.B = B; a.ldb = ldb; a.X = X; a.ldx = ldx; a.s = s; a.R = R; a.ldr = ldr;
+  a.rexp = o.rexp; a.cexp = o.cexp; a.m = m; a.n = n; a.K = o.K; a.status = status ? status : abort_word();
+  if (!status && a.status) {
+    const cudaError_t ce = cudaMemsetAsync(a.status, 0, sizeof(uint32_t), st);
+    if (ce != cudaSuccess) return ce;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  if (e != cudaSuccess) return e;
+  const double kp = o.K;
+  const double fl = 4.0 * (double)m * m * n;   // algorithmic: 8 flops per complex MAC, triangular
+  void *h = trace_on() ? trace_start(0, fl, 16.0 * ((double)m * m / 2 + 3.0 * m * n), st) : nullptr;
+  (void)kp;
+  k_oz_gemm<<<dim3((n + kOzBN - 1) / kOzBN, (2 * m + kOzBM - 1) / kOzBM), kOzThreads, kOzSmem, st>>>(tmA, tmB, a);
+  trace_stop(h, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace msts
