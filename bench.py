@@ -375,13 +375,16 @@ def eta_dev(Ud, sd, Bd, X):
     return float((R.abs().amax(dim=0) / (an * X.abs().amax(dim=0) + Bd.abs().amax(dim=0))).max())
 
 
-def mixed_vs_fp64(dev, nb, flags=0):
+def mixed_vs_fp64(dev, nb):
     """Workload 3 (8192 x 8192, 2048 shifts): the plain FP64 solve and the mixed
-    solve with refinement to eta <= 1e-12, TFLOP/s at 4 m^2 n (refinement not
-    credited), each with its measured eta."""
+    solve refined to eta <= 1e-12 with the FP64-FMA residual and with the
+    tensor-core residual; TFLOP/s at 4 m^2 n (refinement not credited), each
+    with its measured eta, and the tensor-core residual kernel's roofline."""
+    import ctypes
     import torch
     import paper_1607_01477_gb300 as msts
     from paper_1607_01477_gb300 import workloads as W
+    lib = msts.load_library()
     U, s, B = W.mixed_problem()
     m, n = B.shape
     Ud, sd, Bd = (msts.colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
@@ -397,19 +400,41 @@ def mixed_vs_fp64(dev, nb, flags=0):
     e1.record()
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1)
-    eta64 = eta_dev(Ud, sd, Bd, X)
-    msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, nb=nb, flags=flags)   # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    Xm, info, st = msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, nb=nb, flags=flags)
-    torch.cuda.synchronize()
-    msm = (time.perf_counter() - t0) * 1e3
-    etam = eta_dev(Ud, sd, Bd, Xm)
-    return {"fp64": {"ms": ms64, "tflops": fl / (ms64 * 1e-3) / 1e12, "eta": eta64},
-            "mixed": {"ms": msm, "tflops": fl / (msm * 1e-3) / 1e12, "eta": etam,
-                      "eta_before_refinement": info["eta_before"], "corrections": info["iters"],
-                      "residual": "ozaki-bf16-tcgen05" if flags else "fp64-dfma"},
-            "speedup_mixed_vs_fp64": ms64 / msm}
+    out = {"fp64": {"ms": ms64, "tflops": fl / (ms64 * 1e-3) / 1e12, "eta": eta_dev(Ud, sd, Bd, X)}}
+    del X
+    for name, flags in (("mixed_fp64_residual", 0), ("mixed_tensor_core_residual", msts.MSTS_RESIDUAL_OZAKI)):
+        msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, nb=nb, flags=flags)   # warm-up
+        torch.cuda.synchronize()
+        lib.msts_trace_begin(1 << 16)
+        t0 = time.perf_counter()
+        Xm, info, st = msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, nb=nb, flags=flags)
+        torch.cuda.synchronize()
+        msm = (time.perf_counter() - t0) * 1e3
+        lib.msts_trace_end()
+        rec = {"ms": msm, "tflops": fl / (msm * 1e-3) / 1e12, "eta": eta_dev(Ud, sd, Bd, Xm),
+               "eta_before_refinement": info["eta_before"], "corrections": info["iters"],
+               "speedup_vs_fp64": ms64 / msm}
+        if flags:
+            tms, tn, tf, tb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            lib.msts_trace_query(2, ctypes.byref(tms), ctypes.byref(tn), ctypes.byref(tf), ctypes.byref(tb))
+            if tn.value:
+                ach = tf.value / (tms.value * 1e-3) / 1e12
+                peak = measured_peak("bf16_tflops")
+                rec["residual_kernel"] = {
+                    "bound": "tensor", "avg_launch_ms": tms.value / tn.value,
+                    "bf16_mma_tflops": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak if peak else None,
+                    "fp64_equivalent_tflops": fl / (tms.value / tn.value * 1e-3) / 1e12}
+        out[name] = rec
+        del Xm
+    return out
+
+
+def measured_peak(key):
+    try:
+        return float(json.load(open(PEAKS))[key])
+    except (OSError, ValueError, KeyError):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}.get(key)
 
 
 def cpu_baseline_trevc(T, stride=2):

@@ -245,8 +245,9 @@ int msts_residual(const msts_z *U, int64_t ldu, int64_t m,
  * msts_launch_count: number of kernels the library has launched in this
  *   process so far (all entry points).
  * msts_trace_begin(capacity): from now on, bracket each launch of the hot
- *   kernels (MSTS_KERNEL_GEMM: the substitution GEMM, MSTS_KERNEL_DIAG: the
- *   diagonal-block solve) with CUDA events on its stream, for at most
+ *   kernels (MSTS_KERNEL_GEMM: the substitution GEMM or FP64 residual,
+ *   MSTS_KERNEL_DIAG: the diagonal-block solve, MSTS_KERNEL_OZAKI: the
+ *   tensor-core residual) with CUDA events on its stream, for at most
  *   `capacity` launches, recording the algorithmic FLOPs (8 per complex
  *   multiply-add) and algorithmic bytes of each launch.  Host-side; not for
  *   use inside stream capture.
@@ -255,6 +256,7 @@ int msts_residual(const msts_z *U, int64_t ldu, int64_t m,
  * ------------------------------------------------------------------------- */
 #define MSTS_KERNEL_GEMM 0
 #define MSTS_KERNEL_DIAG 1
+#define MSTS_KERNEL_OZAKI 2   /* tensor-core residual; FLOPs = BF16 MMA FLOPs issued */
 uint64_t msts_launch_count(void);
 int msts_trace_begin(int64_t capacity);
 int msts_trace_end(void);

@@ -400,10 +400,15 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
   }
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
-  const double kp = o.K;
-  const double fl = 4.0 * (double)m * m * n;   // algorithmic: 8 flops per complex MAC, triangular
-  void *h = trace_on() ? trace_start(0, fl, 16.0 * ((double)m * m / 2 + 3.0 * m * n), st) : nullptr;
-  (void)kp;
+  // BF16 MMA FLOPs issued: per tile, (K/64 - first chunk) chunks of 36 pairs x 4
+  // MMAs of 128 x 32 x 16.
+  double mma_flops = 0.0;
+  const int tiles_n = (n + kOzBN - 1) / kOzBN, tiles_m = (2 * m + kOzBM - 1) / kOzBM;
+  for (int y = 0; y < tiles_m; ++y)
+    mma_flops += (double)(o.K / kOzKC - (y * kOzBM) / kOzKC) * tiles_n;
+  mma_flops *= 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+  void *h = trace_on() ? trace_start(2, mma_flops, (double)kOzS * (2.0 * m * o.K + (double)n * o.K), st)
+                       : nullptr;
   k_oz_gemm<<<dim3((n + kOzBN - 1) / kOzBN, (2 * m + kOzBM - 1) / kOzBM), kOzThreads, kOzSmem, st>>>(tmA, tmB, a);
   trace_stop(h, st);
   count_launches(1);
