@@ -1,0 +1,43 @@
+"""The oracle against the closed-form fixtures in tests/golden/closed_forms.json."""
+import json
+import os
+
+import numpy as np
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+G = json.load(open(os.path.join(HERE, "golden", "closed_forms.json")))
+
+
+def test_bidiagonal_pow2_fixture():
+    for c in G["bidiagonal_pow2"]["cases"]:
+        m, d, p, nb = c["m"], c["d"], c["p"], c["nb"]
+        U = np.zeros((m, m), dtype=np.complex128, order="F")
+        U[np.arange(m), np.arange(m)] = 2.0 ** d
+        U[np.arange(m - 1), np.arange(1, m)] = -(2.0 ** p)
+        b = np.zeros((m, 1), dtype=np.complex128, order="F")
+        b[-1, 0] = 1.0
+        s = np.zeros(1, dtype=np.complex128)
+        X, e = oracle.safe_trsv_unblocked(U, s, b) if nb == 0 else oracle.safe_solve(U, s, b, nb)
+        expect = [np.ldexp(1.0, -d + (p - d) * (m - 1 - i) - int(e[0])) for i in range(m)]
+        assert np.array_equal(X[:, 0].real, np.array(expect))
+
+
+def test_trevc_2x2_fixture():
+    for c in G["trevc_2x2"]["cases"]:
+        a, b, cc = (complex(*c[k]) for k in ("a", "b", "c"))
+        T = np.asfortranarray(np.array([[a, b], [0, cc]], dtype=np.complex128))
+        Z, e, sc = oracle.trevc(T, 32)
+        assert Z[0, 0] == 1 and Z[1, 0] == 0 and Z[1, 1] == 1
+        assert abs(Z[0, 1] - b / (cc - a)) <= 4e-16 * abs(b / (cc - a))
+
+
+def test_diagonal_pseudospectra_fixture():
+    for c in G["diagonal_pseudospectra"]["cases"]:
+        d = np.array([complex(*x) for x in c["diag"]])
+        z = np.array([complex(*x) for x in c["z"]])
+        T = np.asfortranarray(np.diag(d))
+        V0 = np.asfortranarray(np.ones((d.size, z.size), dtype=np.complex128) + 0.1j)
+        sig, *_ = oracle.pseudospectra(T, z, V0, 20)
+        assert np.allclose(sig, c["sigma_min"], rtol=1e-12, atol=0)
