@@ -9,7 +9,10 @@ algorithmic count (4/3) m^3.  Inputs are synthetic and seeded; T (268 MB) is
 larger than the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload trevc|plain|pseudo|batch] [--no-extra]
+                    [--workload trevc|residual [--m M --n N]] [--no-extra]
+
+`--workload residual` times the tensor-core residual R = B - (U - S)X alone
+(workload 3's distributions at order m with n shifts).
 
 One JSON line is printed by rank 0.  With N > 1 (torchrun) every rank solves
 its own, independently seeded problem of the same size (weak scaling, no
@@ -50,7 +53,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="trevc", choices=["trevc", "plain", "pseudo", "batch"])
+    ap.add_argument("--workload", default="trevc", choices=["trevc", "residual"])
+    ap.add_argument("--m", type=int, default=8192, help="residual workload: matrix order")
+    ap.add_argument("--n", type=int, default=2048, help="residual workload: number of shifts")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--nb", type=int, default=32)
     return ap.parse_args()
@@ -492,10 +497,68 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_residual(args):
+    """The tensor-core FP64-accurate residual alone: TFLOP/s at the FP64
+    product's 4 m^2 n, and its BF16 MMA rate against the measured BF16 peak."""
+    import ctypes
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    lib = msts.load_library()
+    U, s, B = W.mixed_problem(args.m, args.n)
+    m, n = B.shape
+    X = W.cn(W.rng(0, 7), (m, n))
+    Ud, sd, Bd, Xd = (msts.colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
+                      msts.colmajor(torch.from_numpy(B).to(dev)), msts.colmajor(torch.from_numpy(X).to(dev)))
+    flags = msts.MSTS_RESIDUAL_OZAKI
+    R = msts.colmajor(torch.empty((m, n), dtype=torch.complex128, device=dev))
+    ws = torch.empty(lib.msts_residual_workspace_size(m, n, flags) + 256, dtype=torch.uint8, device=dev)
+    wp, wb = msts._ws_ptr(ws)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def step():
+        rc = lib.msts_residual(msts._ptr(Ud), m, m, msts._ptr(sd), n, msts._ptr(Bd), m, msts._ptr(Xd), m,
+                               msts._ptr(R), m, wp, wb, msts._ptr(st), flags, msts._stream(dev))
+        assert rc == 0, rc
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    lib.msts_trace_begin(1 << 16)
+    launches0 = lib.msts_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    lib.msts_trace_end()
+    ms = e0.elapsed_time(e1) / args.steps
+    tms, tn, tf, tb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    lib.msts_trace_query(2, ctypes.byref(tms), ctypes.byref(tn), ctypes.byref(tf), ctypes.byref(tb))
+    peak = measured_peak("bf16_tflops")
+    ach = tf.value / (tms.value * 1e-3) / 1e12 if tms.value else None
+    fl = 4.0 * m * m * n
+    print(json.dumps({
+        "metric": "tensor-core FP64-accurate residual TFLOP/s (FP64-equivalent, 4 m^2 n)",
+        "value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "bf16-digits",
+        "data": "synthetic", "config": {"workload": f"residual R = B - (U - S)X, m={m}, n={n}"},
+        "roofline": {"bound": "tensor", "kernel": "k_oz_gemm", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak if (ach and peak) else None,
+                     "avg_launch_ms": tms.value / max(tn.value, 1), "traffic": None},
+        "gpu_launches": int(lib.msts_launch_count() - launches0), "clocks": clk.summary(),
+        "status": int(st.item())}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "residual":
+        run_residual(args)
     else:
         run_native(args)
 
