@@ -25,8 +25,10 @@
 //
 // Kernel layout (one CTA per 128 x 32 output tile of A' B'; 6 warps):
 //  warp 4  : TMA producer (B digit planes per chunk, A planes through a ring);
-//  warp 5  : one thread issues the 36 x 4 MMAs of each chunk into 8 TMEM
-//            accumulators (double-buffered: 2 x 8 x 32 = 512 columns);
+//  warp 5  : one thread issues the MMAs of each chunk: for every A plane one
+//            MMA per 16-wide K step against all the B planes it pairs with
+//            (N = 32 x (9 - s)), into 8 TMEM accumulators laid out by diagonal
+//            (double-buffered: 2 x 8 x 32 = 512 columns);
 //  warps 0-3: epilogue, one thread per TMEM lane (= output row).
 // Every mbarrier wait is bounded; a timeout raises MSTS_STATUS_TIMEOUT in the
 // status word (which also makes the waits of all other CTAs give up) and the
@@ -246,7 +248,6 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   } else if (warp == 5) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kOzBM, kOzBN);
       int ia = 0;
       for (int c = 0; c < nch && !fail; ++c) {
         const int bb = c & 1, ab = c & 1;
@@ -260,13 +261,16 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           if (!wait(&afull[slot], (ia / kOzRing) & 1)) { fail = 1; break; }
           tc_fence_after();
           const uint32_t abase = smem_u32(sA + slot * kOzABytes);
-          for (int t = 0; t + s < kOzS; ++t) {               // pair (s+1, t+1): diagonal s + t
-            const uint32_t d = dbase + (uint32_t)((s + t) * kOzBN);
+          // A plane s+1 against B planes 1..8-s at once: the B planes sit one
+          // after another in shared memory and the diagonal accumulators one
+          // after another in TMEM, so the N = 32 (8 - s) wide product written at
+          // column 32 s puts (A_{s+1} B_{t+1}) into accumulator s + t.
+          const uint32_t idesc_s = idesc_bf16(kOzBM, kOzBN * (kOzS - s));
+          const uint32_t d = dbase + (uint32_t)(s * kOzBN);
 #pragma unroll
-            for (int k = 0; k < kOzKC / 16; ++k)
-              mma_bf16(d, sdesc_k128(abase + 32 * k), sdesc_k128(bbase + t * (kOzBN * 128) + 32 * k),
-                       idesc, (s > 0 || k > 0) ? 1u : 0u);
-          }
+          for (int k = 0; k < kOzKC / 16; ++k)
+            mma_bf16(d, sdesc_k128(abase + 32 * k), sdesc_k128(bbase + 32 * k), idesc_s,
+                     (s > 0 || k > 0) ? 1u : 0u);
           mma_commit(&aempty[slot]);                         // A plane consumed
         }
         if (fail) break;
@@ -400,8 +404,8 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
   }
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
-  // BF16 MMA FLOPs issued: per tile, (K/64 - first chunk) chunks of 36 pairs x 4
-  // MMAs of 128 x 32 x 16.
+  // BF16 MMA FLOPs issued: per tile, (K/64 - first chunk) chunks of 36 digit
+  // pairs x 4 K-steps of 128 x 32 x 16.
   double mma_flops = 0.0;
   const int tiles_n = (n + kOzBN - 1) / kOzBN, tiles_m = (2 * m + kOzBM - 1) / kOzBM;
   for (int y = 0; y < tiles_m; ++y)
