@@ -366,8 +366,60 @@ def extra_measurements(dev, nb):
     res["pseudospectra_2000_grid100x100"] = {
         "shifts_per_s": N / (ms * 1e-3), "ms": ms,
         "tflops": 20 * 2 * 4 * 2000 ** 2 * N / (ms * 1e-3) / 1e12}
+    # the same 20-iteration pseudospectra call captured once in a CUDA graph and replayed
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            sig_g, *_ = msts.msts_pseudospectra(Td, zd, Vd, 20, nb=nb)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    msg = e0.elapsed_time(e1)
+    res["pseudospectra_2000_grid100x100"]["cuda_graph"] = {
+        "ms": msg, "shifts_per_s": N / (msg * 1e-3),
+        "matches_eager": bool(torch.equal(sig_g, sig))}
+    del graph, sig_g
+    res["batched_adjoint_64x(256..2048)x32"] = batched_fwd_bwd(dev, nb)
     res["mixed_8192x2048"] = mixed_vs_fp64(dev, nb)
     return res
+
+
+def batched_fwd_bwd(dev, nb):
+    """Workload 5: 64 problems of uneven order m in [256, 2048], 32 shifts each,
+    loss sum |x|^2: forward batched solve and the batched adjoint (which
+    recomputes X) -- FLOPs 4 m^2 n forward, 12 m^2 n backward per problem."""
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    probs = W.batch_problem()
+    dp = [(msts.colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
+           msts.colmajor(torch.from_numpy(B).to(dev))) for U, s, B in probs]
+    Xs = [B.clone() for _, _, B in dp]
+    fwd_fl = sum(4.0 * B.shape[0] ** 2 * B.shape[1] for _, _, B in probs)
+
+    def forward():
+        for X, (_, _, B) in zip(Xs, dp):
+            X.copy_(B)
+        msts.msts_solve_batched([(U, s, X) for (U, s, _), X in zip(dp, Xs)], nb=nb)
+
+    def backward():
+        return msts.msts_adjoint_batched([(U, s, B, 2 * X) for (U, s, B), X in zip(dp, Xs)], nb=nb)
+
+    forward(); backward()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(); forward(); e[1].record(); backward(); e[2].record()
+    torch.cuda.synchronize()
+    fms, bms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    return {"forward_ms": fms, "backward_ms": bms,
+            "tflops": 4 * fwd_fl / ((fms + bms) * 1e-3) / 1e12,
+            "note": "forward 4 m^2 n, backward 12 m^2 n FLOPs (X recomputed, adjoint solve, triu(Lambda X^H))"}
 
 
 def eta_dev(Ud, sd, Bd, X):
