@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--n", type=int, default=2048, help="residual workload: number of shifts")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--nb", type=int, default=32)
+    ap.add_argument("--tensor", type=int, default=1,
+                    help="1: substitution GEMM on the tensor cores (MSTS_TENSOR_GEMM); 0: FP64 FMA")
     return ap.parse_args()
 
 
@@ -166,7 +168,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
     if it was taken on a different version of the kernel source."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}4096.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -214,13 +216,14 @@ def run_native(args):
         Z = msts.colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
         sc = torch.empty(m, dtype=torch.float64, device=dev)
         se = torch.empty(m, dtype=torch.int32, device=dev)
-        ws = torch.empty(lib.msts_trevc_workspace_size(m, nb) + 256, dtype=torch.uint8, device=dev)
+        tflags = msts.MSTS_TENSOR_GEMM if args.tensor else 0
+        ws = torch.empty(lib.msts_trevc_workspace_size(m, nb, tflags) + 256, dtype=torch.uint8, device=dev)
         wp, wb = msts._ws_ptr(ws)
         status = torch.zeros(1, dtype=torch.int32, device=dev)
 
         def step():
             rc = lib.msts_trevc(msts._ptr(Td), m, m, msts._ptr(Z), m, msts._ptr(sc), msts._ptr(se),
-                                nb, wp, wb, msts._ptr(status), msts._stream(dev))
+                                nb, wp, wb, msts._ptr(status), tflags, msts._stream(dev))
             assert rc == 0, rc
 
         flops_per_step = trevc_flops(m)

@@ -57,6 +57,9 @@ typedef struct { double re, im; } msts_z;
 #define MSTS_CONJ_TRANS  2u  /* solve (U^H - conj(s_j) I) x_j = b_j (forward substitution)  */
 #define MSTS_RESIDUAL_OZAKI 4u /* msts_solve_mixed / msts_residual: FP64-accurate product on the
                                   BF16 tensor cores (error-free digit splitting) instead of FP64 FMA */
+#define MSTS_TENSOR_GEMM 8u    /* msts_solve / msts_trevc / msts_pseudospectra: the substitution GEMM
+                                  of every block step as the same FP64-accurate digit-plane product
+                                  on the BF16 tensor cores instead of FP64 FMA (single problem) */
 
 /* status bits */
 #define MSTS_STATUS_ZERO_PIVOT  1u  /* plain solve: some U(i,i) - s_j == 0 exactly (X is undefined) */
@@ -128,12 +131,12 @@ int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb,
  * sides -T(0:j-1, j), shortcut so that column j only visits rows < j.
  * Columns are returned unnormalised, as Alg. 6 returns them.
  * ------------------------------------------------------------------------- */
-size_t msts_trevc_workspace_size(int64_t m, int32_t nb);
+size_t msts_trevc_workspace_size(int64_t m, int32_t nb, uint32_t flags);
 int msts_trevc(const msts_z *T, int64_t ldt, int64_t m,
                msts_z *Z, int64_t ldz,
                double *scales, int32_t *scale_exp,
                int32_t nb, void *workspace, size_t workspace_bytes,
-               uint32_t *status, void *stream);
+               uint32_t *status, uint32_t flags, void *stream);   /* flags: 0 or MSTS_TENSOR_GEMM */
 
 /* ---------------------------------------------------------------------------
  * Pseudospectra (Sec. 5, Alg. 7, Van Loan / Lui): for each grid point z[p],
@@ -148,13 +151,14 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m,
  * alpha, beta (optional, may be NULL): N x iters tridiagonal entries, point p
  * at [p*iters, (p+1)*iters); steps (optional): the tridiagonal order per point.
  * ------------------------------------------------------------------------- */
-size_t msts_pseudospectra_workspace_size(int64_t m, int64_t N, int32_t iters, int32_t nb);
+size_t msts_pseudospectra_workspace_size(int64_t m, int64_t N, int32_t iters, int32_t nb,
+                                         uint32_t flags);
 int msts_pseudospectra(const msts_z *T, int64_t ldt, int64_t m,
                        const msts_z *z, int64_t N,
                        const msts_z *V0, int64_t ldv, int32_t iters,
                        double *sigma_min, double *alpha, double *beta, int32_t *steps,
                        int32_t nb, void *workspace, size_t workspace_bytes,
-                       uint32_t *status, void *stream);
+                       uint32_t *status, uint32_t flags, void *stream);   /* flags: 0 or MSTS_TENSOR_GEMM */
 
 /* ---------------------------------------------------------------------------
  * Adjoint of X = (U - s_j I)^{-1} B(:,j) (not in the paper): given

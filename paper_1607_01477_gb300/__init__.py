@@ -26,6 +26,7 @@ __all__ = [
     "MSTS_SAFE", "MSTS_CONJ_TRANS", "STATUS_BITS", "colmajor", "load_library", "library_path",
     "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
     "msts_adjoint_batched", "msts_solve_mixed", "msts_residual", "MSTS_RESIDUAL_OZAKI",
+    "MSTS_TENSOR_GEMM",
     "MultiShiftSolve", "multishift_solve",
     "decode_status",
 ]
@@ -33,6 +34,7 @@ __all__ = [
 MSTS_SAFE = 1
 MSTS_CONJ_TRANS = 2
 MSTS_RESIDUAL_OZAKI = 4
+MSTS_TENSOR_GEMM = 8
 STATUS_BITS = {
     1: "ZERO_PIVOT", 2: "NONFINITE", 4: "RANGE", 8: "SCALED", 16: "DELTA", 32: "NOT_CONVERGED",
     64: "TIMEOUT",
@@ -85,14 +87,14 @@ def load_library():
         lib.msts_solve_batched.restype = ctypes.c_int
         lib.msts_solve_batched.argtypes = [_vp, _i64, _i32, _vp, _sz, _vp, _u32, _vp]
         lib.msts_trevc_workspace_size.restype = _sz
-        lib.msts_trevc_workspace_size.argtypes = [_i64, _i32]
+        lib.msts_trevc_workspace_size.argtypes = [_i64, _i32, _u32]
         lib.msts_trevc.restype = ctypes.c_int
-        lib.msts_trevc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i32, _vp, _sz, _vp, _vp]
+        lib.msts_trevc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i32, _vp, _sz, _vp, _u32, _vp]
         lib.msts_pseudospectra_workspace_size.restype = _sz
-        lib.msts_pseudospectra_workspace_size.argtypes = [_i64, _i64, _i32, _i32]
+        lib.msts_pseudospectra_workspace_size.argtypes = [_i64, _i64, _i32, _i32, _u32]
         lib.msts_pseudospectra.restype = ctypes.c_int
         lib.msts_pseudospectra.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp,
-                                           _vp, _vp, _i32, _vp, _sz, _vp, _vp]
+                                           _vp, _vp, _i32, _vp, _sz, _vp, _u32, _vp]
         lib.msts_adjoint_workspace_size.restype = _sz
         lib.msts_adjoint_workspace_size.argtypes = [_i64, _i64, _i32]
         lib.msts_adjoint.restype = ctypes.c_int
@@ -185,9 +187,10 @@ def _status(device, status):
 # --------------------------------------------------------------------------
 # entry points
 # --------------------------------------------------------------------------
-def msts_solve(U, shifts, B, *, safe=False, conj_trans=False, nb=32, status=None):
+def msts_solve(U, shifts, B, *, safe=False, conj_trans=False, nb=32, tensor=False, status=None):
     """(U - s_j I) X(:,j) = scale_j B(:,j), in place on B (Alg. 3 / Alg. 5).
 
+    tensor=True runs the substitution GEMM on the tensor cores (MSTS_TENSOR_GEMM).
     Returns (B, scales, scale_exp, status); scales/scale_exp are None unless safe.
     """
     lib = load_library()
@@ -196,7 +199,8 @@ def msts_solve(U, shifts, B, *, safe=False, conj_trans=False, nb=32, status=None
     ldb = _mat(B, "B", m)
     _vec(shifts, "shifts")
     dev = B.device
-    flags = (MSTS_SAFE if safe else 0) | (MSTS_CONJ_TRANS if conj_trans else 0)
+    flags = ((MSTS_SAFE if safe else 0) | (MSTS_CONJ_TRANS if conj_trans else 0)
+             | (MSTS_TENSOR_GEMM if tensor else 0))
     scales = torch.empty(n, dtype=torch.float64, device=dev) if safe else None
     sexp = torch.empty(n, dtype=torch.int32, device=dev) if safe else None
     ws = _workspace(lib.msts_solve_workspace_size(m, n, nb, flags), dev)
@@ -239,8 +243,10 @@ def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, status=
     return outs, status
 
 
-def msts_trevc(T, *, nb=32, status=None):
-    """Triangular eigenvectors (Alg. 6): returns (Z, scales, scale_exp, status)."""
+def msts_trevc(T, *, nb=32, tensor=False, status=None):
+    """Triangular eigenvectors (Alg. 6): returns (Z, scales, scale_exp, status).
+
+    tensor=True runs the substitution GEMM on the tensor cores (MSTS_TENSOR_GEMM)."""
     lib = load_library()
     m = T.shape[0]
     ldt = _mat(T, "T", m)
@@ -248,16 +254,17 @@ def msts_trevc(T, *, nb=32, status=None):
     Z = colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
     sc = torch.empty(m, dtype=torch.float64, device=dev)
     se = torch.empty(m, dtype=torch.int32, device=dev)
-    ws = _workspace(lib.msts_trevc_workspace_size(m, nb), dev)
+    flags = MSTS_TENSOR_GEMM if tensor else 0
+    ws = _workspace(lib.msts_trevc_workspace_size(m, nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
     rc = lib.msts_trevc(_ptr(T), ldt, m, _ptr(Z), max(1, m), _ptr(sc), _ptr(se), nb, wp, wb,
-                        _ptr(status), _stream(dev))
+                        _ptr(status), flags, _stream(dev))
     _check(rc, "msts_trevc")
     return Z, sc, se, status
 
 
-def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, status=None, workspace=None):
+def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, tensor=False, status=None, workspace=None):
     """sigma_min(T - z_p I) for every grid point (Alg. 7 with Lanczos).
 
     Returns (sigma_min, alpha, beta, steps, status); alpha/beta have shape (N, iters).
@@ -273,12 +280,14 @@ def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, status=None, workspace=None
     al = torch.empty((N, iters), dtype=torch.float64, device=dev)
     be = torch.empty((N, iters), dtype=torch.float64, device=dev)
     st = torch.empty(N, dtype=torch.int32, device=dev)
-    need = lib.msts_pseudospectra_workspace_size(m, N, iters, nb)
+    flags = MSTS_TENSOR_GEMM if tensor else 0
+    need = lib.msts_pseudospectra_workspace_size(m, N, iters, nb, flags)
     ws = workspace if workspace is not None and workspace.numel() >= need + 256 else _workspace(need, dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
     rc = lib.msts_pseudospectra(_ptr(T), ldt, m, _ptr(z), N, _ptr(V0), ldv, iters, _ptr(sig),
-                                _ptr(al), _ptr(be), _ptr(st), nb, wp, wb, _ptr(status), _stream(dev))
+                                _ptr(al), _ptr(be), _ptr(st), nb, wp, wb, _ptr(status), flags,
+                                _stream(dev))
     _check(rc, "msts_pseudospectra")
     return sig, al, be, st, status
 

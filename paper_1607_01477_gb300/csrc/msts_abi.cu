@@ -5,6 +5,7 @@
 
 #include "../../include/msts.h"
 #include "msts_engine.h"
+#include "msts_ozaki.h"
 
 namespace {
 
@@ -27,6 +28,7 @@ msts::EngineProblem make_problem(const msts_z *U, int64_t ldu, int64_t m, const 
   p.scales = scales;
   p.scale_exp = scale_exp;
   p.diag_z = diag_z;
+  p.oz = nullptr;
   return p;
 }
 
@@ -38,10 +40,14 @@ extern "C" {
 
 int msts_version(void) { return 10000; }
 
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
 size_t msts_solve_workspace_size(int64_t m, int64_t n, int32_t nb, uint32_t flags) {
   if (m < 0 || n < 0 || !nb_ok(nb)) return 0;
   msts::EngineProblem p = make_problem(nullptr, 1, m, nullptr, 1, n, nullptr, 1, nullptr, nullptr, 0);
-  return msts::engine_workspace_bytes(&p, 1, nb, (flags & MSTS_SAFE) != 0);
+  size_t s = align256(msts::engine_workspace_bytes(&p, 1, nb, (flags & MSTS_SAFE) != 0));
+  if ((flags & MSTS_TENSOR_GEMM) && m > 0 && n > 0) s += msts::ozaki_plan_bytes((int)m, (int)n, nb);
+  return s;
 }
 
 int msts_solve(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shifts, int64_t n,
@@ -58,13 +64,21 @@ int msts_solve(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shifts, in
   if (ldb < std::max<int64_t>(1, m)) return -7;
   if (safe && n > 0 && (!scales || !scale_exp)) return scales ? -9 : -8;
   if (!nb_ok(nb)) return -10;
-  if ((flags & ~(MSTS_SAFE | MSTS_CONJ_TRANS)) != 0 || (safe && conj)) return -14;
+  if ((flags & ~(MSTS_SAFE | MSTS_CONJ_TRANS | MSTS_TENSOR_GEMM)) != 0 || (safe && conj)) return -14;
   const size_t need = msts_solve_workspace_size(m, n, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -12 : -11;
   if (m == 0 || n == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   msts::EngineProblem p = make_problem(U, ldu, m, shifts, 1, n, B, ldb, scales, scale_exp, 0);
-  return cuda_rc(msts::engine_run(&p, 1, nb, safe, conj, false, workspace, status,
-                                  static_cast<cudaStream_t>(stream)));
+  msts::OzPlan plan;
+  char *ws = static_cast<char *>(workspace);
+  if (flags & MSTS_TENSOR_GEMM) {
+    const size_t eng = align256(msts::engine_workspace_bytes(&p, 1, nb, safe));
+    if (msts::ozaki_plan_prepare(&plan, p.U, ldu, (int)m, (int)n, nb, conj, ws + eng, st) != cudaSuccess)
+      return MSTS_ERR_CUDA;
+    p.oz = &plan;
+  }
+  return cuda_rc(msts::engine_run(&p, 1, nb, safe, conj, false, workspace, status, st));
 }
 
 size_t msts_solve_batched_workspace_size(const msts_problem *probs, int64_t batch, int32_t nb,
@@ -101,14 +115,14 @@ int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb, voi
                                   static_cast<cudaStream_t>(stream)));
 }
 
-size_t msts_trevc_workspace_size(int64_t m, int32_t nb) {
+size_t msts_trevc_workspace_size(int64_t m, int32_t nb, uint32_t flags) {
   if (m < 0 || !nb_ok(nb)) return 0;
-  return msts_solve_workspace_size(m, m, nb, MSTS_SAFE);
+  return msts_solve_workspace_size(m, m, nb, MSTS_SAFE | (flags & MSTS_TENSOR_GEMM));
 }
 
 int msts_trevc(const msts_z *T, int64_t ldt, int64_t m, msts_z *Z, int64_t ldz, double *scales,
                int32_t *scale_exp, int32_t nb, void *workspace, size_t workspace_bytes,
-               uint32_t *status, void *stream) {
+               uint32_t *status, uint32_t flags, void *stream) {
   if (m < 0 || m > kMaxDim) return -3;
   if (m > 0 && !T) return -1;
   if (ldt < std::max<int64_t>(1, m)) return -2;
@@ -117,7 +131,8 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m, msts_z *Z, int64_t ldz, 
   if (m > 0 && !scales) return -6;
   if (m > 0 && !scale_exp) return -7;
   if (!nb_ok(nb)) return -8;
-  const size_t need = msts_trevc_workspace_size(m, nb);
+  if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -12;
+  const size_t need = msts_trevc_workspace_size(m, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -10 : -9;
   if (m == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -126,6 +141,14 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m, msts_z *Z, int64_t ldz, 
   if (e != cudaSuccess) return MSTS_ERR_CUDA;
   // Shifts are the diagonal of T, read with stride ldt + 1.
   msts::EngineProblem p = make_problem(T, ldt, m, T, ldt + 1, m, Z, ldz, scales, scale_exp, 1);
+  msts::OzPlan plan;
+  if (flags & MSTS_TENSOR_GEMM) {
+    const size_t eng = align256(msts::engine_workspace_bytes(&p, 1, nb, true));
+    if (msts::ozaki_plan_prepare(&plan, p.U, ldt, (int)m, (int)m, nb, false,
+                                 static_cast<char *>(workspace) + eng, st) != cudaSuccess)
+      return MSTS_ERR_CUDA;
+    p.oz = &plan;
+  }
   return cuda_rc(msts::engine_run(&p, 1, nb, true, false, true, workspace, status, st));
 }
 

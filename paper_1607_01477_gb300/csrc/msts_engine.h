@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 namespace msts {
+struct OzPlan;
 
 // One multi-shift problem as the host driver describes it.  Shift j is read
 // from shifts[j * shift_stride] (TREVC passes the diagonal of T this way).
@@ -21,6 +22,7 @@ struct EngineProblem {
   double *scales;
   int *scale_exp;
   int diag_z;  // write Z(j,j) = s_j at the end (TREVC)
+  const struct OzPlan *oz;  // non-null: substitution GEMM on the tensor cores (single problem)
 };
 
 size_t engine_workspace_bytes(const EngineProblem *probs, int count, int nb, bool safe);

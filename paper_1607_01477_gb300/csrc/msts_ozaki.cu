@@ -173,16 +173,32 @@ __global__ void k_oz_slice_B(const double2 *X, long long ldx, int m, int n, int 
   }
 }
 
+// Arguments of the digit-plane product kernel.  Two epilogues share it:
+//  kResidual: R = B - P + s_j X over rows [0, 2m) of A' (K' from the tile's
+//             diagonal to the end: U is upper triangular);
+//  kUpdate:   the substitution step of the blocked solve,
+//             B(r, col) = 2^-pend(col) B(r, col) - P(r, col) over real rows
+//             [row_lo, row_hi) of A' and `ncols` columns starting at col_base,
+//             K' = the chunks of this block (a_x0 = its first column in the
+//             block-layout planes).
 struct OzArgs {
-  const double2 *B; long long ldb;
-  const double2 *X; long long ldx;
-  const double2 *s;
-  double2 *R; long long ldr;
-  const int *rexp, *cexp;
-  int m, n, K;
+  const double2 *B; long long ldb;    // residual: right-hand side; update: matrix updated in place
+  const double2 *X; long long ldx;    // residual only
+  const double2 *s;                   // residual only
+  double2 *R; long long ldr;          // residual: output; update: = B
+  const int *rexp;                    // exponent of complex row r (update: of this block's panel)
+  const int *cexp;                    // exponent of local column c
+  const int *pend;                    // update: pending rescale per global column (safe), or null
+  int m, n, K;                        // residual: order, columns, K'; update: K = chunks * 64
+  int a_x0;                           // update: first K' column of this block in the A planes
+  int row_lo, row_hi;                 // update: real rows of A' updated
+  int col_base, ncols;                // update: global column of local column 0, local columns
   uint32_t *status;
 };
 
+enum { kResidual = 0, kUpdate = 1 };
+
+template <int MODE>
 __global__ void __launch_bounds__(kOzThreads, 1)
 k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ OzArgs args) {
@@ -197,11 +213,12 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __shared__ int fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.y * kOzBM;          // first real row of the tile
-  const int j0 = blockIdx.x * kOzBN;
-  const int c_begin = i0 / kOzKC;             // U is upper: columns k' < i0 vanish
-  const int c_end = args.K / kOzKC;
-  const int nch = c_end - c_begin;
+  const int i0 = (MODE == kUpdate ? args.row_lo : 0) + blockIdx.y * kOzBM;   // first real row
+  const int j0 = blockIdx.x * kOzBN;                                         // first local column
+  // Residual: U is upper, so K' columns below the tile's first row vanish.
+  const int c_begin = MODE == kResidual ? i0 / kOzKC : 0;
+  const int nch = args.K / kOzKC - c_begin;
+  const int ax0 = MODE == kUpdate ? args.a_x0 : 0;
 
   if (warp == 0) tmem_alloc(&tmem_base, 512);
   if (threadIdx.x == 0) {
@@ -240,7 +257,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           const int slot = ia % kOzRing;
           if (ia >= kOzRing && !wait(&aempty[slot], ((ia / kOzRing) - 1) & 1)) { fail = 1; break; }
           mbar_arrive_expect_tx(&afull[slot], kOzABytes);
-          tma_load_3d(sA + slot * kOzABytes, &tmA, &afull[slot], kk, i0, s);
+          tma_load_3d(sA + slot * kOzABytes, &tmA, &afull[slot], ax0 + kk, i0, s);
         }
         if (fail) break;
       }
@@ -308,22 +325,31 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       mbar_arrive(&accempty[ab]);
     }
     if (!ok) fail = 1;
-    // value = 2^(e_r + f_j) (hi 2^-28 + lo 2^-63); R = B - P + s_j X.
-    const int i = i0 + 32 * warp + lane;                     // real row of A' B'
-    if (ok && i < 2 * args.m) {
+    // P = 2^(e_r + f_j) (hi 2^-28 + lo 2^-63)
+    const int i = i0 + 32 * warp + lane;                     // real row of A'
+    const bool row_ok = MODE == kResidual ? i < 2 * args.m : i < args.row_hi;
+    if (ok && row_ok) {
       const int r = i >> 1, part = i & 1;
       const int er = args.rexp[r];
 #pragma unroll
       for (int j = 0; j < kOzBN; ++j) {
-        const int col = j0 + j;
-        if (col >= args.n) continue;
-        const double p = scalbn(fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-63), er + args.cexp[col]);
-        const double2 x = args.X[r + (long long)col * args.ldx];
-        const double2 sj = args.s[col];
-        const double2 b = args.B[r + (long long)col * args.ldb];
-        const double sx = part ? fma(sj.x, x.y, sj.y * x.x) : fma(sj.x, x.x, -sj.y * x.y);
-        double *out = reinterpret_cast<double *>(args.R + r + (long long)col * args.ldr) + part;
-        *out = ((part ? b.y : b.x) - p) + sx;
+        const int lc = j0 + j;
+        if (lc >= (MODE == kResidual ? args.n : args.ncols)) continue;
+        const double p = scalbn(fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-63), er + args.cexp[lc]);
+        if (MODE == kResidual) {
+          const double2 x = args.X[r + (long long)lc * args.ldx];
+          const double2 sj = args.s[lc];
+          const double2 b = args.B[r + (long long)lc * args.ldb];
+          const double sx = part ? fma(sj.x, x.y, sj.y * x.x) : fma(sj.x, x.x, -sj.y * x.y);
+          double *out = reinterpret_cast<double *>(args.R + r + (long long)lc * args.ldr) + part;
+          *out = ((part ? b.y : b.x) - p) + sx;
+        } else {
+          const int col = args.col_base + lc;
+          double *out = reinterpret_cast<double *>(args.R + r + (long long)col * args.ldr) + part;
+          double v = *out;
+          if (args.pend) { const int pe = args.pend[col]; if (pe) v = dshift(v, pe); }
+          *out = v - p;
+        }
       }
     }
   }
@@ -395,14 +421,14 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, o.Ap, o.K, 2 * m, kOzBM, 1) || !make_map(&tmB, o.Bp, o.K, n, kOzBN, kOzS))
     return cudaErrorNotSupported;
-  OzArgs a;
+  OzArgs a{};
   a.B = B; a.ldb = ldb; a.X = X; a.ldx = ldx; a.s = s; a.R = R; a.ldr = ldr;
   a.rexp = o.rexp; a.cexp = o.cexp; a.m = m; a.n = n; a.K = o.K; a.status = status ? status : abort_word();
   if (!status && a.status) {
     const cudaError_t ce = cudaMemsetAsync(a.status, 0, sizeof(uint32_t), st);
     if (ce != cudaSuccess) return ce;
   }
-  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kResidual>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
   // BF16 MMA FLOPs issued: per tile, (K/64 - first chunk) chunks of 36 digit
   // pairs x 4 K-steps of 128 x 32 x 16.
@@ -413,9 +439,137 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
   mma_flops *= 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
   void *h = trace_on() ? trace_start(2, mma_flops, (double)kOzS * (2.0 * m * o.K + (double)n * o.K), st)
                        : nullptr;
-  k_oz_gemm<<<dim3((n + kOzBN - 1) / kOzBN, (2 * m + kOzBM - 1) / kOzBM), kOzThreads, kOzSmem, st>>>(tmA, tmB, a);
+  k_oz_gemm<kResidual><<<dim3((n + kOzBN - 1) / kOzBN, (2 * m + kOzBM - 1) / kOzBM), kOzThreads, kOzSmem, st>>>(tmA, tmB, a);
   trace_stop(h, st);
   count_launches(1);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Substitution step of the blocked solve on the tensor cores.
+//
+// Block layout of the A digit planes: block b (rows [lo_b, hi_b) of U) owns
+// K' columns [b KB, b KB + 2 (hi_b - lo_b)) of every plane (zero-padded to KB,
+// a multiple of 64), so each block's panel starts on a 128-byte TMA boundary.
+//  upper (Alg. 3/5): A'(2r.., b KB + 2(k - lo_b)) from U(r, k), r < lo_b;
+//  conj (forward substitution with U^H): from conj(U(k, r)), r >= hi_b.
+// Row exponents are per (block, row): rexp[b m + r] over the block's columns,
+// which keeps the digits of each panel as fine as the panel itself allows.
+// ===========================================================================
+static int kb_of(int nb) { return ((2 * nb + kOzKC - 1) / kOzKC) * kOzKC; }
+
+size_t ozaki_plan_bytes(int m, int n, int nb) {
+  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb);
+  return a256((size_t)kOzS * 2 * m * (size_t)nblk * KB * 2) + a256(4 * (size_t)nblk * m) +
+         a256((size_t)kOzS * n * KB * 2) + a256(4 * (size_t)n);
+}
+
+template <bool CONJ>
+__global__ void k_ozs_prepare(const double2 *U, long long ldu, int m, int nb, int KB,
+                              __nv_bfloat16 *planes, int *rexp) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int b = blockIdx.x;
+  if (r >= m) return;
+  const int nblk = gridDim.x;
+  const int hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb, w = hi - lo;
+  const bool used = CONJ ? r >= hi : r < lo;
+  auto entry = [&](int k) {   // the complex entry of A' row r at column k of the block
+    if (!used || k >= w) return make_double2(0.0, 0.0);
+    return CONJ ? zconj(U[(lo + k) + (long long)r * ldu]) : U[r + (long long)(lo + k) * ldu];
+  };
+  int e = -(1 << 29);
+  for (int k = lane; k < w; k += 32) e = max(e, bound_exp(entry(k)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (e < -(1 << 28)) e = 0;
+  if (lane == 0) rexp[(size_t)b * m + r] = e;
+  const size_t rows = 2 * (size_t)m, width = (size_t)nblk * KB;
+  for (int k = lane; 2 * k < KB; k += 32) {
+    float dr[kOzS], di[kOzS];
+    const double2 u = entry(k);
+    digits8(u.x, e, dr);
+    digits8(u.y, e, di);
+#pragma unroll
+    for (int q = 0; q < kOzS; ++q) {
+      const size_t col = (size_t)b * KB + 2 * k;
+      *reinterpret_cast<__nv_bfloat162 *>(planes + (q * rows + 2 * (size_t)r) * width + col) =
+          __floats2bfloat162_rn(dr[q], -di[q]);
+      *reinterpret_cast<__nv_bfloat162 *>(planes + (q * rows + 2 * (size_t)r + 1) * width + col) =
+          __floats2bfloat162_rn(di[q], dr[q]);
+    }
+  }
+}
+
+// Digit planes of X(lo:hi, jstart + c) for this block step: plane t, local
+// column c, K' = 2 (k - lo) + {0,1}; one warp per column.
+__global__ void k_ozs_slice_X(const double2 *B, long long ldb, int lo, int w, int jstart, int ncols,
+                              int KB, __nv_bfloat16 *bp, int *cexp) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= ncols) return;
+  const double2 *col = B + (long long)(jstart + c) * ldb + lo;
+  int e = -(1 << 29);
+  for (int k = lane; k < w; k += 32) e = max(e, bound_exp(col[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (e < -(1 << 28)) e = 0;
+  if (lane == 0) cexp[c] = e;
+  for (int k = lane; 2 * k < KB; k += 32) {
+    float dr[kOzS], di[kOzS];
+    const double2 x = k < w ? col[k] : make_double2(0.0, 0.0);
+    digits8(x.x, e, dr);
+    digits8(x.y, e, di);
+#pragma unroll
+    for (int t = 0; t < kOzS; ++t)
+      *reinterpret_cast<__nv_bfloat162 *>(bp + ((size_t)t * ncols + c) * KB + 2 * k) =
+          __floats2bfloat162_rn(dr[t], di[t]);
+  }
+}
+
+cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, int m, int n, int nb,
+                               bool conj, void *ws, cudaStream_t st) {
+  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb);
+  char *c = static_cast<char *>(ws);
+  plan->planes = reinterpret_cast<__nv_bfloat16 *>(c); c += a256((size_t)kOzS * 2 * m * (size_t)nblk * KB * 2);
+  plan->rexp = reinterpret_cast<int *>(c); c += a256(4 * (size_t)nblk * m);
+  plan->bp = reinterpret_cast<__nv_bfloat16 *>(c); c += a256((size_t)kOzS * n * KB * 2);
+  plan->cexp = reinterpret_cast<int *>(c);
+  plan->m = m; plan->nb = nb; plan->nblk = nblk; plan->KB = KB; plan->nmax = n; plan->conj = conj;
+  if (!make_map(&plan->tmA, plan->planes, nblk * KB, 2 * m, kOzBM, 1)) return cudaErrorNotSupported;
+  const dim3 grid(nblk, (m + 7) / 8);
+  if (conj) k_ozs_prepare<true><<<grid, 256, 0, st>>>(U, ldu, m, nb, KB, plan->planes, plan->rexp);
+  else k_ozs_prepare<false><<<grid, 256, 0, st>>>(U, ldu, m, nb, KB, plan->planes, plan->rexp);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
+                         int jstart, int ncols, const int *pend, uint32_t *status, double flops,
+                         cudaStream_t st) {
+  const int row_lo = plan.conj ? 2 * hi : 0, row_hi = plan.conj ? 2 * plan.m : 2 * lo;
+  if (ncols <= 0 || row_hi <= row_lo) return cudaSuccess;
+  k_ozs_slice_X<<<(ncols + 7) / 8, 256, 0, st>>>(B, ldb, lo, hi - lo, jstart, ncols, plan.KB, plan.bp,
+                                                plan.cexp);
+  CUtensorMap tmB;
+  if (!make_map(&tmB, plan.bp, plan.KB, ncols, kOzBN, kOzS)) return cudaErrorNotSupported;
+  OzArgs a{};
+  a.B = B; a.ldb = ldb; a.R = B; a.ldr = ldb;
+  a.rexp = plan.rexp + (size_t)b * plan.m;
+  a.cexp = plan.cexp;
+  a.pend = pend;
+  a.m = plan.m; a.n = ncols; a.K = plan.KB;
+  a.a_x0 = b * plan.KB;
+  a.row_lo = row_lo; a.row_hi = row_hi;
+  a.col_base = jstart; a.ncols = ncols;
+  a.status = status ? status : abort_word();
+  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  if (e != cudaSuccess) return e;
+  void *h = trace_on() ? trace_start(0, flops, 0.0, st) : nullptr;
+  k_oz_gemm<kUpdate><<<dim3((ncols + kOzBN - 1) / kOzBN, (row_hi - row_lo + kOzBM - 1) / kOzBM), kOzThreads,
+                       kOzSmem, st>>>(plan.tmA, tmB, a);
+  trace_stop(h, st);
+  count_launches(2);
   return cudaGetLastError();
 }
 

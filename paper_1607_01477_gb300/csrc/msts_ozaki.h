@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <cuda.h>
+#include <cuda_bf16.h>
 
 namespace msts {
 // Workspace for the digit planes of triu(U) and X and their exponents.
@@ -14,4 +16,24 @@ cudaError_t ozaki_prepare(const double2 *U, long long ldu, int m, int n, void *w
 cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2 *s, int n,
                            const double2 *B, long long ldb, const double2 *X, long long ldx,
                            double2 *R, long long ldr, void *ws, uint32_t *status, cudaStream_t st);
+// Tensor-core substitution step of the blocked solve: the block-layout digit
+// planes of U (upper, or conjugate-transposed for forward substitution) and
+// a per-step buffer for the planes of the solved block X(I1,:).
+struct OzPlan {
+  __nv_bfloat16 *planes;
+  int *rexp;
+  __nv_bfloat16 *bp;
+  int *cexp;
+  int m, nb, nblk, KB, nmax;
+  bool conj;
+  CUtensorMap tmA;
+};
+size_t ozaki_plan_bytes(int m, int n, int nb);
+cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, int m, int n, int nb,
+                               bool conj, void *ws, cudaStream_t st);
+// B(rows, jstart..jstart+ncols) = 2^-pend B - U-panel(b) X(I1, .), rows above the
+// block (upper) or below it (conj); `flops` is recorded by the tracer.
+cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
+                         int jstart, int ncols, const int *pend, uint32_t *status, double flops,
+                         cudaStream_t st);
 }  // namespace msts

@@ -15,6 +15,7 @@
 
 #include "msts_common.cuh"
 #include "msts_engine.h"
+#include "msts_ozaki.h"
 #include "msts_trace.h"
 
 namespace msts {
@@ -190,7 +191,7 @@ __global__ void k_ritz(LanczosState S, double *sigma_min) {
 
 static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t pseudo_workspace_bytes(int m, int N, int iters, int nb) {
+size_t pseudo_workspace_bytes(int m, int N, int iters, int nb, uint32_t flags) {
   const int K = std::min(iters, m);
   size_t s = 0;
   s += a256(sizeof(double2) * (size_t)(K + 1) * m * N);  // V
@@ -200,13 +201,14 @@ size_t pseudo_workspace_bytes(int m, int N, int iters, int nb) {
   s += a256(sizeof(double) * (size_t)N);                 // amax
   EngineProblem p{};
   p.m = m; p.n = N;
-  s += engine_workspace_bytes(&p, 1, nb, false);
+  s += a256(engine_workspace_bytes(&p, 1, nb, false));
+  if (flags & MSTS_TENSOR_GEMM) s += 2 * a256(ozaki_plan_bytes(m, N, nb));   // upper and conj plans
   return s;
 }
 
 cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z, int N,
                        const double2 *V0, long long ldv, int iters, double *sigma_min,
-                       double *alpha, double *beta, int *steps, int nb, void *ws,
+                       double *alpha, double *beta, int *steps, int nb, uint32_t flags, void *ws,
                        uint32_t *status, cudaStream_t st) {
   const int K = std::min(iters, m);
   char *cur = static_cast<char *>(ws);
@@ -228,6 +230,19 @@ cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z,
   EngineProblem P{};
   P.U = T; P.ldu = ldt; P.m = m; P.shifts = z; P.shift_stride = 1; P.n = N;
   P.B = S.W; P.ldb = m;
+  EngineProblem Pc = P;
+  OzPlan up, lo;
+  if (flags & MSTS_TENSOR_GEMM) {
+    // Digit planes of T for both solves, made once for all Lanczos steps.
+    cur += a256(engine_workspace_bytes(&P, 1, nb, false));
+    cudaError_t e = ozaki_plan_prepare(&up, T, ldt, m, N, nb, false, cur, st);
+    if (e != cudaSuccess) return e;
+    cur += a256(ozaki_plan_bytes(m, N, nb));
+    e = ozaki_plan_prepare(&lo, T, ldt, m, N, nb, true, cur, st);
+    if (e != cudaSuccess) return e;
+    P.oz = &up;
+    Pc.oz = &lo;
+  }
 
   k_lanczos_init<<<N, kLzThreads, 0, st>>>(S, V0, ldv);
   count_launches(1);
@@ -235,7 +250,7 @@ cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z,
     k_lanczos_load<<<std::max(1, std::min(4096, (int)(((long long)m * N + 255) / 256))), 256, 0, st>>>(S, k);
     cudaError_t e = engine_run(&P, 1, nb, false, false, false, engine_ws, status, st);  // (T - zI)^{-1}
     if (e != cudaSuccess) return e;
-    e = engine_run(&P, 1, nb, false, true, false, engine_ws, status, st);               // (T - zI)^{-H}
+    e = engine_run(&Pc, 1, nb, false, true, false, engine_ws, status, st);              // (T - zI)^{-H}
     if (e != cudaSuccess) return e;
     k_lanczos_step<<<N, kLzThreads, 0, st>>>(S, k);
     count_launches(2);
@@ -249,16 +264,17 @@ cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z,
 
 extern "C" {
 
-size_t msts_pseudospectra_workspace_size(int64_t m, int64_t N, int32_t iters, int32_t nb) {
+size_t msts_pseudospectra_workspace_size(int64_t m, int64_t N, int32_t iters, int32_t nb,
+                                         uint32_t flags) {
   if (m < 0 || N < 0 || iters < 1 || iters > msts::kMaxIters) return 0;
   if (nb != 16 && nb != 32 && nb != 64) return 0;
-  return msts::pseudo_workspace_bytes((int)m, (int)N, iters, nb);
+  return msts::pseudo_workspace_bytes((int)m, (int)N, iters, nb, flags);
 }
 
 int msts_pseudospectra(const msts_z *T, int64_t ldt, int64_t m, const msts_z *z, int64_t N,
                        const msts_z *V0, int64_t ldv, int32_t iters, double *sigma_min,
                        double *alpha, double *beta, int32_t *steps, int32_t nb, void *workspace,
-                       size_t workspace_bytes, uint32_t *status, void *stream) {
+                       size_t workspace_bytes, uint32_t *status, uint32_t flags, void *stream) {
   const int64_t kMax = (int64_t)1 << 30;
   if (m < 0 || m > kMax) return -3;
   if (m > 0 && !T) return -1;
@@ -270,13 +286,14 @@ int msts_pseudospectra(const msts_z *T, int64_t ldt, int64_t m, const msts_z *z,
   if (iters < 1 || iters > msts::kMaxIters) return -8;
   if (N > 0 && !sigma_min) return -9;
   if (nb != 16 && nb != 32 && nb != 64) return -13;
+  if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -17;
   if (m == 0 || N == 0) return 0;
-  const size_t need = msts_pseudospectra_workspace_size(m, N, iters, nb);
+  const size_t need = msts_pseudospectra_workspace_size(m, N, iters, nb, flags);
   if (!workspace || workspace_bytes < need) return workspace ? -15 : -14;
   const cudaError_t e = msts::pseudo_run(
       reinterpret_cast<const double2 *>(T), ldt, (int)m, reinterpret_cast<const double2 *>(z),
       (int)N, reinterpret_cast<const double2 *>(V0), ldv, iters, sigma_min, alpha, beta, steps,
-      nb, workspace, status, static_cast<cudaStream_t>(stream));
+      nb, flags, workspace, status, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? 0 : MSTS_ERR_CUDA;
 }
 

@@ -25,6 +25,7 @@
 #include "msts_common.cuh"
 #include "msts_diag.h"
 #include "msts_engine.h"
+#include "msts_ozaki.h"
 #include "msts_trace.h"
 
 namespace msts {
@@ -443,7 +444,17 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       trace_stop(h, st);
       count_launches(1);
     }
-    if (rows_max > 0) {
+    if (rows_max > 0 && count == 1 && probs[0].oz) {
+      // Substitution step on the tensor cores (digit-plane product).
+      const int m = probs[0].m, nblk = (m + NB - 1) / NB;
+      const int b = CONJ ? nblk - 1 - s : s;
+      const int hi = m - b * NB, lo = std::max(0, hi - NB);
+      const int jstart = shortcut ? lo + 1 : 0;
+      const cudaError_t e = ozaki_update(*probs[0].oz, b, lo, hi, probs[0].B, probs[0].ldb, jstart,
+                                         probs[0].n - jstart, SAFE ? tab.p[0].pend : nullptr, status,
+                                         gflops, st);
+      if (e != cudaSuccess) return e;
+    } else if (rows_max > 0) {
       // FP64 throughput per SM is low, so the tile is chosen to give the grid
       // at least two waves of CTAs over the 152 SMs when the problem allows.
       void *h = tracing ? trace_start(0, gflops, gbytes, st) : nullptr;

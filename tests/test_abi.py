@@ -60,13 +60,16 @@ def test_invalid_arguments_rejected_without_launch(lib):
     assert lib.msts_solve(P, 4, 4, P, 1, P, 4, P, P, 32, P, 8, None, 1, None) == -12
     # empty problems are no-ops
     assert lib.msts_solve(None, 1, 0, None, 0, None, 1, None, None, 32, None, 0, None, 0, None) == 0
-    assert lib.msts_trevc(None, 1, 0, None, 1, None, None, 32, None, 0, None, None) == 0
-    assert lib.msts_pseudospectra(P, 4, 4, P, 2, P, 4, 0, P, None, None, None, 32, None, 0, None, None) == -8
+    assert lib.msts_trevc(None, 1, 0, None, 1, None, None, 32, None, 0, None, 0, None) == 0
+    assert lib.msts_pseudospectra(P, 4, 4, P, 2, P, 4, 0, P, None, None, None, 32, None, 0, None, 0, None) == -8
+    # unknown flag bits are rejected
+    assert lib.msts_solve(P, 4, 4, P, 1, P, 4, None, None, 32, P, 1 << 20, None, 64, None) == -14
 
 
 def test_workspace_sizes(lib):
     assert lib.msts_solve_workspace_size(100, 10, 32, 0) == 0
     ws = lib.msts_solve_workspace_size(100, 10, 32, 1)
     assert ws > 100 * 8 * 3
-    assert lib.msts_trevc_workspace_size(64, 32) == lib.msts_solve_workspace_size(64, 64, 32, 1)
-    assert lib.msts_pseudospectra_workspace_size(50, 7, 20, 32) >= 21 * 50 * 7 * 16
+    assert lib.msts_trevc_workspace_size(64, 32, 0) == lib.msts_solve_workspace_size(64, 64, 32, 1)
+    assert lib.msts_trevc_workspace_size(64, 32, 8) > lib.msts_trevc_workspace_size(64, 32, 0)
+    assert lib.msts_pseudospectra_workspace_size(50, 7, 20, 32, 0) >= 21 * 50 * 7 * 16

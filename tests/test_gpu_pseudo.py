@@ -10,10 +10,12 @@ from gpu_util import to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("m,grid,nb", [(150, 5, 32), (16, 4, 16), (77, 3, 64), (1, 2, 32)])
-def test_pseudospectra_matches_oracle(m, grid, nb):
+@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("m,grid,nb", [(150, 5, 32), (16, 4, 16), (77, 3, 64), (1, 2, 32), (400, 6, 32)])
+def test_pseudospectra_matches_oracle(m, grid, nb, tensor):
     T, z, V0 = W.pseudo_problem(m, grid=grid, seed=m)
-    sig, al, be, st, status = msts.msts_pseudospectra(to_dev(T), to_dev(z), to_dev(V0), 20, nb=nb)
+    sig, al, be, st, status = msts.msts_pseudospectra(to_dev(T), to_dev(z), to_dev(V0), 20, nb=nb,
+                                                      tensor=tensor)
     so, alo, beo, sto = oracle.pseudospectra(T, z, V0, 20)
     assert np.array_equal(to_np(st), sto)
     assert np.all(np.abs(to_np(sig) - so) <= 1e-10 * so)
@@ -28,11 +30,13 @@ def test_pseudospectra_exact_for_small_matrix():
     assert np.all(np.abs(to_np(sig) - ref) <= 1e-9 * ref)
 
 
-def test_pseudospectra_full_size_sampled_points():
+@pytest.mark.parametrize("tensor", [False, True])
+def test_pseudospectra_full_size_sampled_points(tensor):
     """Workload 4 at full size (2000 x 2000, 100 x 100 grid, 20 iterations):
     8 sampled grid points against the oracle run on the same start vectors."""
     T, z, V0 = W.pseudo_problem()
-    sig, al, be, st, status = msts.msts_pseudospectra(to_dev(T), to_dev(z), to_dev(V0), 20, nb=32)
+    sig, al, be, st, status = msts.msts_pseudospectra(to_dev(T), to_dev(z), to_dev(V0), 20, nb=32,
+                                                      tensor=tensor)
     sg = to_np(sig)
     assert np.isfinite(sg).all() and (sg > 0).all()
     idx = np.array([0, 99, 4949, 5050, 7321, 9900, 9999, 2500])

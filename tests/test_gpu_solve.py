@@ -13,12 +13,13 @@ from gpu_util import EPS, cond_inf, forward_close, to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("m,n,nb", [(256, 64, 32), (1, 1, 32), (5, 3, 16), (37, 9, 16), (100, 70, 32),
-                                    (200, 33, 64), (129, 40, 64), (64, 1, 32)])
-def test_plain_solve_matches_oracle(m, n, nb):
+                                    (200, 33, 64), (129, 40, 64), (64, 1, 32), (700, 130, 32)])
+def test_plain_solve_matches_oracle(m, n, nb, tensor):
     U, s, B = W.plain_problem(m, n, seed=1000 + m + n)
     X = to_dev(B)
-    _, _, _, st = msts.msts_solve(to_dev(U), to_dev(s), X, nb=nb)
+    _, _, _, st = msts.msts_solve(to_dev(U), to_dev(s), X, nb=nb, tensor=tensor)
     Xg = to_np(X)
     Xo = oracle.solve(U, s, B)
     err, tol = forward_close(Xg, Xo, cond_inf(U, s), m)
@@ -27,11 +28,12 @@ def test_plain_solve_matches_oracle(m, n, nb):
     assert int(st.item()) == 0
 
 
-@pytest.mark.parametrize("m,n,nb", [(256, 64, 32), (37, 9, 16), (100, 20, 64), (1, 2, 32)])
-def test_conj_trans_solve_matches_oracle(m, n, nb):
+@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("m,n,nb", [(256, 64, 32), (37, 9, 16), (100, 20, 64), (1, 2, 32), (500, 77, 32)])
+def test_conj_trans_solve_matches_oracle(m, n, nb, tensor):
     U, s, B = W.plain_problem(m, n, seed=2000 + m)
     X = to_dev(B)
-    msts.msts_solve(to_dev(U), to_dev(s), X, conj_trans=True, nb=nb)
+    msts.msts_solve(to_dev(U), to_dev(s), X, conj_trans=True, nb=nb, tensor=tensor)
     Xg = to_np(X)
     Xo = oracle.solve(U, s, B, conj_trans=True)
     err, tol = forward_close(Xg, Xo, cond_inf(U, s), m)
@@ -65,9 +67,10 @@ def test_safe_solve_equals_oracle_when_nothing_scales(m, n, nb):
     assert (err <= tol).all()
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("p", [0, 1, 3])
 @pytest.mark.parametrize("nb", [16, 32])
-def test_safe_pow2_closed_form_bitwise(p, nb):
+def test_safe_pow2_closed_form_bitwise(p, nb, tensor):
     """Bidiagonal powers-of-two case: every value is exact, so GPU, oracle and
     closed form agree bit for bit (x(i) 2^e = 2^(40 + (p+40)(m-1-i)))."""
     m = 32 if nb == 32 else 40
@@ -78,7 +81,7 @@ def test_safe_pow2_closed_form_bitwise(p, nb):
     B[m - 1, 0] = 1.0
     s = np.zeros(1, dtype=np.complex128)
     X = to_dev(B)
-    _, sc, se, st = msts.msts_solve(to_dev(U), to_dev(s), X, safe=True, nb=nb)
+    _, sc, se, st = msts.msts_solve(to_dev(U), to_dev(s), X, safe=True, nb=nb, tensor=tensor)
     Xo, eo = oracle.safe_solve(U, s, B, nb)
     e = int(to_np(se)[0])
     assert e == int(eo[0]) and e > 0
@@ -89,8 +92,9 @@ def test_safe_pow2_closed_form_bitwise(p, nb):
     assert int(st.item()) & 8                       # MSTS_STATUS_SCALED
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("m,nb", [(256, 32), (300, 16), (257, 64)])
-def test_safe_solve_with_scaling_matches_oracle(m, nb):
+def test_safe_solve_with_scaling_matches_oracle(m, nb, tensor):
     """Eigenvalue-like shifts on a TREVC-style matrix: overflow scaling fires;
     scale exponents match the oracle and X agrees up to rounding."""
     T = W.trevc_problem(m, seed=44, cluster_frac=0.1, offdiag_scale=30.0)
@@ -98,7 +102,7 @@ def test_safe_solve_with_scaling_matches_oracle(m, nb):
     B = W.cn(g, (m, 24))
     shifts = np.diag(T)[g.permutation(m)[:24]] + 1e-9
     X = to_dev(B)
-    _, sc, se, st = msts.msts_solve(to_dev(T), to_dev(shifts), X, safe=True, nb=nb)
+    _, sc, se, st = msts.msts_solve(to_dev(T), to_dev(shifts), X, safe=True, nb=nb, tensor=tensor)
     Xo, eo = oracle.safe_solve(T, shifts, B, nb)
     eg = to_np(se)
     assert eo.max() > 0

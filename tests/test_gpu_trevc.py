@@ -21,11 +21,12 @@ def residuals_dev(Td, Z):
     return (torch.linalg.norm(R, dim=0) / (torch.linalg.norm(Tu) * torch.linalg.norm(zs, dim=0)))
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("m,nb", [(1, 32), (2, 16), (97, 16), (300, 32), (640, 64), (1000, 32)])
-def test_trevc_matches_oracle(m, nb):
+def test_trevc_matches_oracle(m, nb, tensor):
     T = W.trevc_problem(m, seed=m + 1)
     Td = to_dev(T)
-    Z, sc, se, st = msts.msts_trevc(Td, nb=nb)
+    Z, sc, se, st = msts.msts_trevc(Td, nb=nb, tensor=tensor)
     Zo, eo, sco = oracle.trevc(T, nb)
     eg = to_np(se)
     assert np.array_equal(eg, eo)
@@ -40,12 +41,14 @@ def test_trevc_matches_oracle(m, nb):
         assert eo.max() > 0 and int(st.item()) & 8
 
 
-def test_trevc_full_size_sampled_columns_and_residual():
-    """Workload 2 at full size (4096 x 4096, clustered eigenvalues): every column's
-    eigen-residual on the GPU, and 12 sampled columns against the oracle."""
+@pytest.mark.parametrize("tensor", [False, True])
+def test_trevc_full_size_sampled_columns_and_residual(tensor):
+    """Workload 2 at full size (4096 x 4096, clustered eigenvalues), in the launch
+    configuration bench.py times: every column's eigen-residual on the GPU, and 12
+    sampled columns against the oracle."""
     T = W.trevc_problem()
     Td = to_dev(T)
-    Z, sc, se, st = msts.msts_trevc(Td, nb=32)
+    Z, sc, se, st = msts.msts_trevc(Td, nb=32, tensor=tensor)
     rho = residuals_dev(Td, Z)
     assert rho.max().item() <= 2 * 4096 * EPS
     cols = [0, 1, 31, 32, 33, 1000, 2047, 2048, 3000, 4063, 4064, 4095]
