@@ -231,6 +231,8 @@ def run_native(args):
         config = {"workload": "safe TREVC (Alg. 6 on Alg. 5), T 4096x4096 complex128, 5% eigenvalues "
                               "in clusters of 4 at spacing 1e-10, strictly-upper 10*CN(0,1), all 4096 "
                               "eigenvectors", "m": m, "n_b": nb, "eigenvectors": m,
+                  "substitution_gemm": ("tensor cores, FP64-accurate BF16 digit planes" if args.tensor
+                                        else "FP64 FMA"),
                   "flops_per_step": "(4/3) m^3 algorithmic",
                   "l2": "no flush: T (268 MB) and Z (268 MB) exceed the 129 MB L2",
                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
@@ -272,27 +274,43 @@ def run_native(args):
     total_flops = sum_over_ranks(flops_per_step, dist, dev)
     value = total_flops / (ms_max * 1e-3) / 1e12
 
-    tms = ctypes.c_double()
-    tn = ctypes.c_int64()
-    tf = ctypes.c_double()
-    tb = ctypes.c_double()
-    lib.msts_trace_query(0, ctypes.byref(tms), ctypes.byref(tn), ctypes.byref(tf), ctypes.byref(tb))
-    gemm_ms, gemm_n, gemm_flops, gemm_bytes = tms.value, tn.value, tf.value, tb.value
-    lib.msts_trace_query(1, ctypes.byref(tms), ctypes.byref(tn), ctypes.byref(tf), ctypes.byref(tb))
-    diag_ms, diag_n, diag_flops = tms.value, tn.value, tf.value
-    peak = fp64_peak()
-    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
-    traffic = profiled_traffic("k_gemm", wl)
-    roofline = {"bound": "alu", "kernel": "k_gemm<32,SAFE> (FP64 DFMA substitution GEMM)",
-                "achieved": achieved, "peak": peak["peak"], "unit": "TFLOP/s",
-                "frac": achieved / peak["peak"] if achieved else None, "traffic": traffic,
-                "peak_source": peak["source"],
-                "algorithmic_flops_per_launch": gemm_flops / max(gemm_n, 1),
-                "avg_launch_ms": gemm_ms / max(gemm_n, 1),
-                "share_of_step": gemm_ms / (ms * args.steps) if ms > 0 else None,
-                "diag_kernel": {"avg_launch_ms": diag_ms / max(diag_n, 1),
-                                "tflops": diag_flops / (diag_ms * 1e-3) / 1e12 if diag_ms else None,
-                                "share_of_step": diag_ms / (ms * args.steps) if ms > 0 else None}}
+    def query(kid):
+        tms, tn, tf, tb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        lib.msts_trace_query(kid, ctypes.byref(tms), ctypes.byref(tn), ctypes.byref(tf), ctypes.byref(tb))
+        return {"ms": tms.value, "n": tn.value, "flops": tf.value, "bytes": tb.value}
+
+    kg, kd, ko = query(0), query(1), query(2)
+    step_ms_total = ms * args.steps
+    kernels = {
+        "k_gemm (FP64 FMA substitution GEMM)": kg,
+        "k_diag (diagonal-block step)": kd,
+        "k_oz_gemm<update> (tensor-core substitution GEMM)": ko,
+    }
+    shares = {k: (v["ms"] / step_ms_total if step_ms_total > 0 else None) for k, v in kernels.items()}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    kv = kernels[dom]
+    if kv is ko:
+        peak_v, src, bound, unit_r = (measured_peak("bf16_tflops_sustained"),
+                                      "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                                      "tensor", "TFLOP/s")
+    else:
+        pk = fp64_peak()
+        peak_v, src, bound, unit_r = pk["peak"], pk["source"], "alu", "TFLOP/s"
+    achieved = kv["flops"] / (kv["ms"] * 1e-3) / 1e12 if kv["ms"] > 0 else None
+    traffic = profiled_traffic("k_gemm", wl) if kv is kg else None
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak_v, "unit": unit_r,
+                "frac": achieved / peak_v if (achieved and peak_v) else None, "traffic": traffic,
+                "peak_source": src,
+                "algorithmic_flops_per_launch": kv["flops"] / max(kv["n"], 1),
+                "avg_launch_ms": kv["ms"] / max(kv["n"], 1),
+                "kernel_shares_of_step": shares,
+                "diag_kernel": {"avg_launch_ms": kd["ms"] / max(kd["n"], 1),
+                                "fp64_tflops": kd["flops"] / (kd["ms"] * 1e-3) / 1e12 if kd["ms"] else None}}
+    if ko["ms"] > 0:
+        roofline["tensor_update_kernel"] = {
+            "bf16_mma_tflops": ko["flops"] / (ko["ms"] * 1e-3) / 1e12,
+            "fp64_equivalent_tflops": (flops_per_step * args.steps - kd["flops"]) / (ko["ms"] * 1e-3) / 1e12,
+            "avg_launch_ms": ko["ms"] / max(ko["n"], 1)}
 
     # end to end through the public API with host buffers
     for _ in range(1):
@@ -331,51 +349,58 @@ def run_native(args):
 
 
 def extra_measurements(dev, nb):
-    """Secondary lines of the metric on the other workloads (one GPU)."""
+    """Secondary lines of the metric on the other workloads (one GPU), each with
+    the FP64-FMA and the tensor-core substitution GEMM."""
     import torch
     import paper_1607_01477_gb300 as msts
     from paper_1607_01477_gb300 import workloads as W
     res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # workload 1: plain 256 x 256, 64 shifts (latency-bound)
     U, s, B = W.plain_problem()
     Ud, sd, Bd = (msts.colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
                   msts.colmajor(torch.from_numpy(B).to(dev)))
-    X = Bd.clone()
-    for _ in range(5):
-        X.copy_(Bd)
-        msts.msts_solve(Ud, sd, X, nb=nb)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 50
-    e0.record()
-    for _ in range(reps):
-        msts.msts_solve(Ud, sd, X, nb=nb)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    res["plain_256x64"] = {"us_per_solve": ms * 1e3, "tflops": 4 * 256 ** 2 * 64 / (ms * 1e-3) / 1e12}
+    res["plain_256x64"] = {}
+    for tag, tensor in (("fp64_gemm", False), ("tensor_gemm", True)):
+        X = Bd.clone()
+        for _ in range(5):
+            msts.msts_solve(Ud, sd, X, nb=nb, tensor=tensor)
+        torch.cuda.synchronize()
+        reps = 50
+        e0.record()
+        for _ in range(reps):
+            msts.msts_solve(Ud, sd, X, nb=nb, tensor=tensor)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res["plain_256x64"][tag] = {"us_per_solve": ms * 1e3, "tflops": 4 * 256 ** 2 * 64 / (ms * 1e-3) / 1e12}
     # workload 4: pseudospectra 2000 x 2000, 100 x 100 grid, 20 Lanczos steps
     T, z, V0 = W.pseudo_problem()
     Td, zd, Vd = (msts.colmajor(torch.from_numpy(T).to(dev)), torch.from_numpy(z).to(dev),
                   msts.colmajor(torch.from_numpy(V0).to(dev)))
-    msts.msts_pseudospectra(Td, zd[:256], msts.colmajor(Vd[:, :256]), 20, nb=nb)
-    torch.cuda.synchronize()
-    e0.record()
-    sig, *_ = msts.msts_pseudospectra(Td, zd, Vd, 20, nb=nb)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
     N = z.size
-    res["pseudospectra_2000_grid100x100"] = {
-        "shifts_per_s": N / (ms * 1e-3), "ms": ms,
-        "tflops": 20 * 2 * 4 * 2000 ** 2 * N / (ms * 1e-3) / 1e12}
-    # the same 20-iteration pseudospectra call captured once in a CUDA graph and replayed
+    ps = {}
+    sigs = {}
+    for tag, tensor in (("fp64_gemm", False), ("tensor_gemm", True)):
+        msts.msts_pseudospectra(Td, zd[:256], msts.colmajor(Vd[:, :256]), 20, nb=nb, tensor=tensor)
+        torch.cuda.synchronize()
+        e0.record()
+        sig, *_ = msts.msts_pseudospectra(Td, zd, Vd, 20, nb=nb, tensor=tensor)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sigs[tag] = sig
+        ps[tag] = {"shifts_per_s": N / (ms * 1e-3), "ms": ms,
+                   "tflops": 20 * 2 * 4 * 2000 ** 2 * N / (ms * 1e-3) / 1e12}
+    ps["max_rel_diff_sigma_tensor_vs_fp64"] = float(((sigs["tensor_gemm"] - sigs["fp64_gemm"]).abs()
+                                                     / sigs["fp64_gemm"]).max())
+    # the tensor-core call captured once in a CUDA graph and replayed
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.stream(side):
         with torch.cuda.graph(graph, stream=side):
-            sig_g, *_ = msts.msts_pseudospectra(Td, zd, Vd, 20, nb=nb)
+            sig_g, *_ = msts.msts_pseudospectra(Td, zd, Vd, 20, nb=nb, tensor=True)
     torch.cuda.current_stream(dev).wait_stream(side)
     graph.replay()
     torch.cuda.synchronize()
@@ -384,10 +409,10 @@ def extra_measurements(dev, nb):
     e1.record()
     torch.cuda.synchronize()
     msg = e0.elapsed_time(e1)
-    res["pseudospectra_2000_grid100x100"]["cuda_graph"] = {
-        "ms": msg, "shifts_per_s": N / (msg * 1e-3),
-        "matches_eager": bool(torch.equal(sig_g, sig))}
-    del graph, sig_g
+    ps["tensor_gemm"]["cuda_graph"] = {"ms": msg, "shifts_per_s": N / (msg * 1e-3),
+                                       "matches_eager": bool(torch.equal(sig_g, sigs["tensor_gemm"]))}
+    res["pseudospectra_2000_grid100x100"] = ps
+    del graph, sig_g, sigs
     res["batched_adjoint_64x(256..2048)x32"] = batched_fwd_bwd(dev, nb)
     res["mixed_8192x2048"] = mixed_vs_fp64(dev, nb)
     return res

@@ -565,7 +565,14 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
   a.status = status ? status : abort_word();
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
-  void *h = trace_on() ? trace_start(0, flops, 0.0, st) : nullptr;
+  // Recorded as the tensor-core kernel: BF16 MMA FLOPs issued (36 digit pairs x
+  // 4 K-steps of 128 x 32 x 16 per tile and chunk) and the plane bytes it loads.
+  const double tiles = (double)((ncols + kOzBN - 1) / kOzBN) * ((row_hi - row_lo + kOzBM - 1) / kOzBM);
+  const double chunks = plan.KB / kOzKC;
+  const double mma_flops = tiles * chunks * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+  (void)flops;
+  void *h = trace_on() ? trace_start(2, mma_flops, tiles * chunks * (kOzS * kOzABytes + kOzBBytes), st)
+                       : nullptr;
   k_oz_gemm<kUpdate><<<dim3((ncols + kOzBN - 1) / kOzBN, (row_hi - row_lo + kOzBM - 1) / kOzBM), kOzThreads,
                        kOzSmem, st>>>(plan.tmA, tmB, a);
   trace_stop(h, st);
