@@ -544,6 +544,196 @@ cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, in
   return cudaGetLastError();
 }
 
+// W 2^ex rounded to the nearest double, assembled with integer operations
+// (exponent field and rounded 53-bit significand) so that the conversion and
+// the scaling cost no FP64 instruction; |W| < 2^62.  Outside the normal range
+// it falls back to FP64 scalbn.
+__device__ __forceinline__ double i64_ldexp(long long W, int ex) {
+  if (W == 0) return 0.0;
+  const unsigned long long a = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
+  const int lz = __clzll((long long)a);
+  const int E = 1023 + 63 - lz + ex;                   // biased exponent of the result
+  if (E <= 0 || E >= 2046) return scalbn((double)W, ex);
+  const unsigned long long nrm = a << lz;              // leading one at bit 63
+  unsigned long long sig = nrm >> 11;                  // 53 bits, leading one at bit 52
+  const unsigned long long rest = nrm & 0x7ffull;      // the 11 bits rounded away
+  sig += (rest > 0x400ull || (rest == 0x400ull && (sig & 1ull))) ? 1ull : 0ull;   // nearest, ties to even
+  // (E - 1) << 52 plus the significand with its leading one adds that one into
+  // the exponent field; a rounding carry to 2^53 moves it up one more.
+  const unsigned long long bits = ((unsigned long long)(E - 1) << 52) + sig;
+  return __longlong_as_double((long long)(bits | (W < 0 ? 0x8000000000000000ull : 0ull)));
+}
+
+// Persistent form of the substitution step for one 64-wide K chunk per block
+// (n_b <= 32): each CTA walks a contiguous run of output tiles in row-major
+// order, keeping the 8 A digit planes of its current row tile resident in
+// shared memory (reloaded only when the row tile changes) while the B planes of
+// successive column tiles stream through two buffers; TMEM accumulators are
+// double-buffered so the epilogue of one tile overlaps the MMAs of the next.
+// The epilogue folds the 8 diagonal sums into one int64
+// W = sum_d D_d 2^(42 - 7d) (exact for d <= 6, the last diagonal truncated
+// below 2^-56; |W| < 2^62 because every digit expansion is below 1) and applies
+// B = 2^-pend B - W 2^(e_r + f_j - 56) with a single FP64 subtraction.
+constexpr size_t kOzuSmem = (size_t)kOzS * kOzABytes + 2 * kOzBBytes + 1024;
+constexpr int kOzPersistentCtas = 152;             // one CTA per SM
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ OzArgs args, int tiles_n, int tiles_total) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  uint8_t *sA = base;                               // 8 resident A planes x 16 KB
+  uint8_t *sB = base + kOzS * kOzABytes;            // 2 buffers x 32 KB of B planes
+  __shared__ uint64_t afull, aempty, bfull[2], bempty[2], accfull[2], accempty[2], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (tiles_total + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * per, t1 = min(tiles_total, t0 + per);
+
+  if (warp == 0) tmem_alloc(&tmem_base, 512);
+  if (threadIdx.x == 0) {
+    mbar_init(&afull, 1);
+    mbar_init(&aempty, 1);
+    mbar_init(&mma_done, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bfull[i], 1);
+      mbar_init(&bempty[i], 1);
+      mbar_init(&accfull[i], 1);
+      mbar_init(&accempty[i], kOzBM);
+    }
+    fail = 0;
+    fence_barrier_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  auto wait = [&](uint64_t *bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity, args.status, MSTS_STATUS_TIMEOUT);
+    if (!ok) raise_status(args.status, MSTS_STATUS_TIMEOUT);
+    return ok;
+  };
+
+  if (warp == 4) {
+    if (lane == 0) {                                // ---------------- TMA producer
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      int prev_rt = -1, na = 0;
+      for (int t = t0, k = 0; t < t1; ++t, ++k) {
+        const int rt = t / tiles_n, ct = t - rt * tiles_n;
+        if (rt != prev_rt) {                        // new row tile: reload the A planes
+          if (na > 0 && !wait(&aempty, (na - 1) & 1)) { fail = 1; break; }
+          mbar_arrive_expect_tx(&afull, kOzS * kOzABytes);
+          for (int q = 0; q < kOzS; ++q)
+            tma_load_3d(sA + q * kOzABytes, &tmA, &afull, args.a_x0, args.row_lo + rt * kOzBM, q);
+          ++na;
+          prev_rt = rt;
+        }
+        const int bb = k & 1;
+        if (k >= 2 && !wait(&bempty[bb], ((k >> 1) - 1) & 1)) { fail = 1; break; }
+        mbar_arrive_expect_tx(&bfull[bb], kOzBBytes);
+        tma_load_3d(sB + bb * kOzBBytes, &tmB, &bfull[bb], 0, ct * kOzBN, 0);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {                                // ---------------- MMA issuer
+      int prev_rt = -1, na = 0;
+      for (int t = t0, k = 0; t < t1 && !fail; ++t, ++k) {
+        const int rt = t / tiles_n;
+        if (rt != prev_rt) {
+          if (na > 0) mma_commit(&aempty);          // old planes free once their MMAs finish
+          if (!wait(&afull, na & 1)) { fail = 1; break; }
+          ++na;
+          prev_rt = rt;
+        }
+        const int bb = k & 1, ab = k & 1;
+        if (k >= 2 && !wait(&accempty[ab], ((k >> 1) - 1) & 1)) { fail = 1; break; }
+        if (!wait(&bfull[bb], (k >> 1) & 1)) { fail = 1; break; }
+        tc_fence_after();
+        const uint32_t bbase = smem_u32(sB + bb * kOzBBytes);
+        const uint32_t dbase = tmem + ab * kOzAccCols;
+        for (int q = 0; q < kOzS; ++q) {
+          // A plane q+1 against B planes 1..8-q at once (N = 32 (8 - q) written
+          // at column 32 q), as in the chunked kernel above.
+          const uint32_t abase = smem_u32(sA + q * kOzABytes);
+          const uint32_t idesc_q = idesc_bf16(kOzBM, kOzBN * (kOzS - q));
+#pragma unroll
+          for (int kk = 0; kk < kOzKC / 16; ++kk)
+            mma_bf16(dbase + (uint32_t)(q * kOzBN), sdesc_k128(abase + 32 * kk), sdesc_k128(bbase + 32 * kk),
+                     idesc_q, (q > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(&bempty[bb]);
+        mma_commit(&accfull[ab]);
+      }
+      mma_commit(&mma_done);                        // drain before TMEM is freed
+      if (!wait(&mma_done, 0)) fail = 1;
+    }
+  } else {                                          // ---------------- epilogue, warps 0-3
+    const uint32_t lane_addr = (uint32_t)(32 * warp) << 16;
+    for (int t = t0, k = 0; t < t1; ++t, ++k) {
+      const int rt = t / tiles_n, ct = t - rt * tiles_n;
+      const int i = args.row_lo + rt * kOzBM + 32 * warp + lane;     // real row of A'
+      const bool row_ok = i < args.row_hi;
+      const int r = i >> 1, part = i & 1;
+      double bin[kOzBN];                            // B fetched before the accumulators are ready
+#pragma unroll
+      for (int j = 0; j < kOzBN; ++j) {
+        const int lc = ct * kOzBN + j;
+        bin[j] = (row_ok && lc < args.ncols)
+                     ? reinterpret_cast<const double *>(args.R + r + (long long)(args.col_base + lc) * args.ldr)[part]
+                     : 0.0;
+      }
+      const int er = row_ok ? args.rexp[r] : 0;
+      const int ab = k & 1;
+      if (!wait(&accfull[ab], (k >> 1) & 1)) { fail = 1; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {                 // two halves of 16 columns
+        long long W[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) W[j] = 0;
+#pragma unroll
+        for (int d = 0; d < kOzS; ++d) {            // diagonal s + t = d + 2
+          uint32_t v[16];
+          tmem_ld16(tmem + lane_addr + ab * kOzAccCols + d * kOzBN + 16 * h, v);
+          tmem_ld_wait();
+          const int sh = 42 - kOzBits * d;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long q = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact integer
+            W[j] += sh >= 0 ? (q << sh) : (q >> (-sh));
+          }
+        }
+        if (h == 1) {
+          tc_fence_before();
+          mbar_arrive(&accempty[ab]);
+        }
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int lc = ct * kOzBN + 16 * h + j;
+            if (lc >= args.ncols) continue;
+            const int col = args.col_base + lc;
+            double v = bin[16 * h + j];
+            if (args.pend) {
+              const int pe = args.pend[col];
+              if (pe) v = dshift(v, pe);
+            }
+            reinterpret_cast<double *>(args.R + r + (long long)col * args.ldr)[part] =
+                v - i64_ldexp(W[j], er + args.cexp[lc] - 56);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (fail && threadIdx.x == 0) raise_status(args.status, MSTS_STATUS_TIMEOUT);
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
                          cudaStream_t st) {
@@ -563,6 +753,19 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
   a.row_lo = row_lo; a.row_hi = row_hi;
   a.col_base = jstart; a.ncols = ncols;
   a.status = status ? status : abort_word();
+  if (plan.KB == kOzKC) {
+    const int tiles_n = (ncols + kOzBN - 1) / kOzBN, tiles_m = (row_hi - row_lo + kOzBM - 1) / kOzBM;
+    const int total = tiles_n * tiles_m;
+    cudaError_t e = cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzuSmem);
+    if (e != cudaSuccess) return e;
+    const double mma_flops = (double)total * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+    void *h = trace_on() ? trace_start(2, mma_flops, (double)total * kOzBBytes, st) : nullptr;
+    k_oz_update<<<std::min(total, kOzPersistentCtas), kOzThreads, kOzuSmem, st>>>(plan.tmA, tmB, a, tiles_n,
+                                                                                 total);
+    trace_stop(h, st);
+    count_launches(2);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
   // Recorded as the tensor-core kernel: BF16 MMA FLOPs issued (36 digit pairs x
