@@ -50,6 +50,29 @@ __device__ __forceinline__ long long gmax_ll(long long v) {
   return v;
 }
 
+// |z| with exactly the scaled operands and roundings of zabs_fast, the two
+// power-of-two scalings done on the exponent fields (integer operations) when
+// every operand stays a normal number; otherwise zabs_fast itself.
+__device__ __forceinline__ double zabs_exp(double2 z) {
+  const long long ax = absbits(z.x), ay = absbits(z.y);
+  const long long mx = max(ax, ay);
+  if (mx == 0) return 0.0;
+  const int e = (int)(mx >> 52) - 1023;
+  const bool ok = (mx >> 52) != 0 && e <= 1021 && (ax == 0 || (int)(ax >> 52) - e >= 1) &&
+                  (ay == 0 || (int)(ay >> 52) - e >= 1);
+  if (!ok) return zabs_fast(z);
+  const long long sh = (long long)e << 52;
+  const double a = ax == 0 ? 0.0 : __longlong_as_double(ax - sh);
+  const double b = ay == 0 ? 0.0 : __longlong_as_double(ay - sh);
+  const double r = sqrt(fma(a, a, b * b));              // in [1, 2 sqrt 2)
+  return __longlong_as_double(__double_as_longlong(r) + sh);
+}
+// x >= Omega for x >= 0 or NaN (false), on the bit pattern.
+__device__ __forceinline__ bool ge_omega(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0x7BF0000000000000LL && b <= 0x7FF0000000000000LL;   // [2^960, +inf]
+}
+
 // 1 / p with p scaled by a power of two first (one real division).
 __device__ __forceinline__ double2 zrecip(double2 p) { return zdiv_fast(make_double2(1.0, 0.0), p); }
 
@@ -100,6 +123,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   };
 
   double2 y[RPL], inv[RPL];
+  int pex[RPL];                          // biased exponent field of max(|Re p|, |Im p|)
   bool zero_piv = false;
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
@@ -109,7 +133,9 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     const double2 d = sU[r * LD + r];
     const double2 p0 = zsub(CONJ ? zconj(d) : d, lam);
     zero_piv |= v && zzero_bits(p0);
-    inv[q] = v ? zrecip(pivot(r)) : make_double2(0.0, 0.0);
+    const double2 p = pivot(r);
+    inv[q] = v ? zrecip(p) : make_double2(0.0, 0.0);
+    pex[q] = (int)(max(absbits(p.x), absbits(p.y)) >> 52);
   }
   if (zero_piv) raise_status(status, SAFE ? MSTS_STATUS_DELTA : MSTS_STATUS_ZERO_PIVOT);
 
@@ -119,10 +145,12 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       const int r = l + L * q;
+      // Row slots that lie wholly on the dead side of row i are skipped at
+      // compile time (i and q are constants of the unrolled loops).
       if (!CONJ) {
-        if (r < i) y[q] = zfms(y[q], xi, sU[i * LD + r]);
+        if (L * q < i && r < i) y[q] = zfms(y[q], xi, sU[i * LD + r]);
       } else {
-        if (r > i) y[q] = zfms(y[q], xi, zconj(sU[r * LD + i]));
+        if (L * q + L - 1 > i && r > i) y[q] = zfms(y[q], xi, zconj(sU[r * LD + i]));
       }
     }
   };
@@ -163,39 +191,81 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     return sqrt(gmax<L>(m2)) * pow2i(E);
   };
 
-  // A priori growth bounds (Sec. 3), conservative: 1/|p| <= sqrt(2) max(|Re|,
-  // |Im|) of 1/p and |y| <= sqrt(2) max(|Re y|, |Im y|).  They only choose
-  // between the plain and the safeguarded substitution, which give identical
-  // results whenever the plain one is chosen, so looser bounds only cost time.
-  long long gb = 0;
+  // Two ways to the same result.  Until its first rescale the safeguarded
+  // substitution (Alg. 4) computes exactly the plain one, so when a block starts
+  // far below Omega the plain substitution runs first and Alg. 4's two rescaling
+  // tests are checked afterwards in one pass over the rows, spread over the
+  // lanes; only if a test fires is the block redone with the safeguarded loop.
+  // Blocks that start near Omega, where a rescale is likely, take the
+  // safeguarded loop directly.
+  const double G0 = maxabs();                         // G before the first row (Alg. 4)
+  bool careful = __any_sync(0xffffffffu, active && !(G0 < 0x1p-64 * OM));
+  if (!careful) {
+    double2 ypre[RPL];                                // each row's value at its diagonal step
 #pragma unroll
-  for (int q = 0; q < RPL; ++q) gb = max(gb, max(absbits(y[q].x), absbits(y[q].y)));
-  double Gb = __longlong_as_double(gmax_ll<L>(gb)) * 1.4142135623730951, Mb = 0.0;
+    for (int q = 0; q < RPL; ++q) ypre[q] = make_double2(0.0, 0.0);
 #pragma unroll
-  for (int t = 0; t < NB; ++t) {
-    const int i = NB - 1 - t;
-    const int qi = i / L, li = i % L;
-    const double ia = gshfl<L>(__longlong_as_double(max(absbits(inv[qi].x), absbits(inv[qi].y))) *
-                                   1.4142135623730951, li);
-    if (i < nbe) {
-      Mb = fmax(Mb, Gb * ia);
-      Gb = Gb * fma(sC[i], ia, 1.0);
+    for (int t = 0; t < NB; ++t) {
+      const int i = NB - 1 - t;
+      const int qi = i / L, li = i % L;
+      const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);
+      if (l == li) {
+        ypre[qi] = y[qi];
+        y[qi] = xi;
+      }
+      axpy(i, xi);
+    }
+    bool fire = false;
+    double a[RPL];                                    // |x_r| C_r, rounded as in the serial loop
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = l + L * q;
+      a[q] = 0.0;
+      if (r < nbe) {
+        const double2 yp = ypre[q];
+        // |y|/|p| >= Omega is possible only if the exponents allow it (|y| <
+        // 2^(ey+1.5), |p| >= 2^ep for a normal pivot); decide exactly then.
+        const int ey = (int)(max(absbits(yp.x), absbits(yp.y)) >> 52);
+        if (!zzero_bits(yp) && (pex[q] == 0 || ey - pex[q] >= kOmegaExp - 1))
+          fire |= ratio_exp_fast(yp, pivot(r)) >= kOmegaExp;
+        a[q] = __dmul_rn(zabs_exp(y[q]), sC[r]);
+      }
+    }
+    double G = G0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int i = NB - 1 - t;
+      const double ai = gshfl<L>(a[i / L], i % L);
+      if (i < nbe) {
+        G = __dadd_rn(G, ai);
+        fire |= !(G < OM);                            // also catches a NaN from an overflow
+      }
+    }
+    careful = __any_sync(0xffffffffu, active && fire);
+    if (careful) {                                    // start again from the block's right-hand side
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int r = l + L * q;
+        y[q] = r < nbe ? col[r] : make_double2(0.0, 0.0);
+      }
     }
   }
-  const bool careful = __any_sync(0xffffffffu, active && !(Mb < OM && Gb < OM));
   int kexp = 0;
-  if (!careful) {
-    substitute();
-  } else {
+  if (careful) {
     // Safeguarded back substitution (Alg. 4, second branch), group-uniform.
-    double G = maxabs();
+    double G = G0;
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
       const int i = NB - 1 - t;
       const int qi = i / L, li = i % L;
       const double2 yi = gshfl_z<L>(y[qi], li);
+      const int epi = gshfl_i<L>(pex[qi], li);
+      // M = |y_i| / |p_i| >= Omega: exact test only where the exponent fields
+      // allow it (see above).
       int eM = -100000;
-      if (i < nbe && !zzero_bits(yi)) eM = ratio_exp_fast(yi, pivot(i));
+      const int ey = (int)(max(absbits(yi.x), absbits(yi.y)) >> 52);
+      if (i < nbe && !zzero_bits(yi) && (epi == 0 || ey - epi >= kOmegaExp - 1))
+        eM = ratio_exp_fast(yi, pivot(i));
       if (eM >= kOmegaExp) {                          // M >= Omega: rescale b first
         const int kk = eM - (kOmegaExp - 1);
 #pragma unroll
@@ -206,8 +276,8 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
       double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);   // diagonal step
       if (l == li) y[qi] = xi;
       if (i < nbe) {
-        G = __dadd_rn(G, __dmul_rn(zabs_fast(xi), sC[i]));
-        if (G >= OM) {                                   // protect the AXPY
+        G = __dadd_rn(G, __dmul_rn(zabs_exp(xi), sC[i]));
+        if (ge_omega(G)) {                               // protect the AXPY
           const int kk = choose_k(G);
 #pragma unroll
           for (int q = 0; q < RPL; ++q) y[q] = zshift(y[q], kk);
