@@ -548,20 +548,35 @@ cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, in
 // (exponent field and rounded 53-bit significand) so that the conversion and
 // the scaling cost no FP64 instruction; |W| < 2^62.  Outside the normal range
 // it falls back to FP64 scalbn.
+__device__ __forceinline__ double i64_ldexp_slow(long long W, int ex) { return scalbn((double)W, ex); }
 __device__ __forceinline__ double i64_ldexp(long long W, int ex) {
-  if (W == 0) return 0.0;
   const unsigned long long a = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
-  const int lz = __clzll((long long)a);
+  const int lz = __clzll((long long)a);                // 64 when W == 0
   const int E = 1023 + 63 - lz + ex;                   // biased exponent of the result
-  if (E <= 0 || E >= 2046) return scalbn((double)W, ex);
-  const unsigned long long nrm = a << lz;              // leading one at bit 63
+  if (a != 0 && (E <= 0 || E >= 2046)) return i64_ldexp_slow(W, ex);
+  const unsigned long long nrm = a << (lz & 63);       // leading one at bit 63
   unsigned long long sig = nrm >> 11;                  // 53 bits, leading one at bit 52
   const unsigned long long rest = nrm & 0x7ffull;      // the 11 bits rounded away
   sig += (rest > 0x400ull || (rest == 0x400ull && (sig & 1ull))) ? 1ull : 0ull;   // nearest, ties to even
   // (E - 1) << 52 plus the significand with its leading one adds that one into
   // the exponent field; a rounding carry to 2^53 moves it up one more.
   const unsigned long long bits = ((unsigned long long)(E - 1) << 52) + sig;
-  return __longlong_as_double((long long)(bits | (W < 0 ? 0x8000000000000000ull : 0ull)));
+  return a == 0 ? 0.0 : __longlong_as_double((long long)(bits | (W < 0 ? 0x8000000000000000ull : 0ull)));
+}
+
+// i64_ldexp without the out-of-range branch: sets *slow instead (the caller
+// then recomputes with i64_ldexp).
+__device__ __forceinline__ double i64_ldexp_fast(long long W, int ex, bool &slow) {
+  const unsigned long long a = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
+  const int lz = __clzll((long long)a);                // 64 when W == 0
+  const int E = 1023 + 63 - lz + ex;
+  slow |= a != 0 && (E <= 0 || E >= 2046);
+  const unsigned long long nrm = a << (lz & 63);
+  unsigned long long sig = nrm >> 11;
+  const unsigned long long rest = nrm & 0x7ffull;
+  sig += (rest > 0x400ull || (rest == 0x400ull && (sig & 1ull))) ? 1ull : 0ull;
+  const unsigned long long bits = ((unsigned long long)(E - 1) << 52) + sig;
+  return a == 0 ? 0.0 : __longlong_as_double((long long)(bits | (W < 0 ? 0x8000000000000000ull : 0ull)));
 }
 
 // Persistent form of the substitution step for one 64-wide K chunk per block
@@ -576,8 +591,9 @@ __device__ __forceinline__ double i64_ldexp(long long W, int ex) {
 // B = 2^-pend B - W 2^(e_r + f_j - 56) with a single FP64 subtraction.
 constexpr size_t kOzuSmem = (size_t)kOzS * kOzABytes + 2 * kOzBBytes + 1024;
 constexpr int kOzPersistentCtas = 152;             // one CTA per SM
+constexpr int kOzuThreads = 320;                   // 8 epilogue warps + producer + MMA
 
-__global__ void __launch_bounds__(kOzThreads, 1)
+__global__ void __launch_bounds__(kOzuThreads, 1)
 k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ OzArgs args, int tiles_n, int tiles_total) {
   using namespace tc;
@@ -601,7 +617,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       mbar_init(&bfull[i], 1);
       mbar_init(&bempty[i], 1);
       mbar_init(&accfull[i], 1);
-      mbar_init(&accempty[i], kOzBM);
+      mbar_init(&accempty[i], 2 * kOzBM);
     }
     fail = 0;
     fence_barrier_init();
@@ -616,7 +632,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     return ok;
   };
 
-  if (warp == 4) {
+  if (warp == 8) {
     if (lane == 0) {                                // ---------------- TMA producer
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
@@ -637,7 +653,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         tma_load_3d(sB + bb * kOzBBytes, &tmB, &bfull[bb], 0, ct * kOzBN, 0);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     if (lane == 0) {                                // ---------------- MMA issuer
       int prev_rt = -1, na = 0;
       for (int t = t0, k = 0; t < t1 && !fail; ++t, ++k) {
@@ -670,60 +686,102 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       mma_commit(&mma_done);                        // drain before TMEM is freed
       if (!wait(&mma_done, 0)) fail = 1;
     }
-  } else {                                          // ---------------- epilogue, warps 0-3
-    const uint32_t lane_addr = (uint32_t)(32 * warp) << 16;
+  } else {                                          // ---------------- epilogue, warps 0-7
+    // Warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows) and the columns
+    // 16 (w / 4) .. + 15 of every tile: two warps per sub-partition.
+    const int quarter = warp & 3, half = warp >> 2;
+    const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
+    const long long ldr2 = 2 * args.ldr;            // column stride in doubles
+    constexpr int kQ = 8, kPasses = kOzBN / 2 / kQ;
     for (int t = t0, k = 0; t < t1; ++t, ++k) {
       const int rt = t / tiles_n, ct = t - rt * tiles_n;
-      const int i = args.row_lo + rt * kOzBM + 32 * warp + lane;     // real row of A'
+      const int i = args.row_lo + rt * kOzBM + 32 * quarter + lane;   // real row of A'
       const bool row_ok = i < args.row_hi;
       const int r = i >> 1, part = i & 1;
-      double bin[kOzBN];                            // B fetched before the accumulators are ready
+      // Column data of the tile, lane j holding column j: the exponent f_j - 56
+      // and the pending exponent, shuffled to the rows below.
+      const int nval = min(kOzBN, args.ncols - ct * kOzBN);
+      const int cx_l = lane < nval ? args.cexp[ct * kOzBN + lane] - 56 : 0;
+      const int pe_l = (lane < nval && args.pend) ? args.pend[args.col_base + ct * kOzBN + lane] : 0;
+      const bool any_pe = __any_sync(0xffffffffu, pe_l != 0);
+      const int c0 = 16 * half;                     // first column of this warp
+      double *const base =
+          reinterpret_cast<double *>(args.R + r + (long long)(args.col_base + ct * kOzBN + c0) * args.ldr) + part;
+      double bq[kQ];                                // B of the first pass, fetched before the wait
+      {
+        const double *pj = base;
 #pragma unroll
-      for (int j = 0; j < kOzBN; ++j) {
-        const int lc = ct * kOzBN + j;
-        bin[j] = (row_ok && lc < args.ncols)
-                     ? reinterpret_cast<const double *>(args.R + r + (long long)(args.col_base + lc) * args.ldr)[part]
-                     : 0.0;
+        for (int j = 0; j < kQ; ++j, pj += ldr2) bq[j] = (row_ok && c0 + j < nval) ? *pj : 0.0;
       }
       const int er = row_ok ? args.rexp[r] : 0;
       const int ab = k & 1;
       if (!wait(&accfull[ab], (k >> 1) & 1)) { fail = 1; break; }
       tc_fence_after();
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {                 // two halves of 16 columns
-        long long W[16];
+      for (int h = 0; h < kPasses; ++h) {
+        const int cp = c0 + kQ * h;                 // first column of this pass
+        // W = sum_d D_d 2^(42 - 7d), the diagonals paired first in int32:
+        // |D_d| <= (d + 1) 64 127^2, so D_{2c} 2^7 + D_{2c+1} < 2^30 for d <= 7.
+        long long W[kQ];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) W[j] = 0;
-#pragma unroll
-        for (int d = 0; d < kOzS; ++d) {            // diagonal s + t = d + 2
-          uint32_t v[16];
-          tmem_ld16(tmem + lane_addr + ab * kOzAccCols + d * kOzBN + 16 * h, v);
+        for (int c = 0; c < kOzS / 2; ++c) {
+          uint32_t v0[kQ], v1[kQ];
+          tmem_ld8(tmem + lane_addr + ab * kOzAccCols + (2 * c) * kOzBN + cp, v0);
+          tmem_ld8(tmem + lane_addr + ab * kOzAccCols + (2 * c + 1) * kOzBN + cp, v1);
           tmem_ld_wait();
-          const int sh = 42 - kOzBits * d;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long q = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact integer
-            W[j] += sh >= 0 ? (q << sh) : (q >> (-sh));
+          for (int j = 0; j < kQ; ++j) {
+            const int pr = __float2int_rn(__uint_as_float(v0[j])) * (1 << kOzBits) +
+                           __float2int_rn(__uint_as_float(v1[j]));   // exact integers
+            const long long pw = c < 3 ? ((long long)pr << (35 - 14 * c)) : (long long)(pr >> kOzBits);
+            W[j] = c == 0 ? pw : W[j] + pw;
           }
         }
-        if (h == 1) {
+        if (h == kPasses - 1) {
           tc_fence_before();
           mbar_arrive(&accempty[ab]);
         }
-        if (row_ok) {
+        double bn[kQ];                              // next pass's B
+        if (h + 1 < kPasses) {
+          const double *pj = base + kQ * (h + 1) * ldr2;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int lc = ct * kOzBN + 16 * h + j;
-            if (lc >= args.ncols) continue;
-            const int col = args.col_base + lc;
-            double v = bin[16 * h + j];
-            if (args.pend) {
-              const int pe = args.pend[col];
-              if (pe) v = dshift(v, pe);
-            }
-            reinterpret_cast<double *>(args.R + r + (long long)col * args.ldr)[part] =
-                v - i64_ldexp(W[j], er + args.cexp[lc] - 56);
+          for (int j = 0; j < kQ; ++j, pj += ldr2) bn[j] = (row_ok && cp + kQ + j < nval) ? *pj : 0.0;
+        }
+        // Branch-free outputs: the pending scaling on the exponent field and
+        // the product by i64_ldexp_fast; a pass where either leaves the
+        // normal range is redone with the FP64 routines.
+        double out[kQ];
+        bool slow = false;
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+          const int ex = er + __shfl_sync(0xffffffffu, cx_l, cp + j);
+          const int pe = any_pe ? __shfl_sync(0xffffffffu, pe_l, cp + j) : 0;
+          long long vb = __double_as_longlong(bq[j]);
+          const int ev = (int)((vb >> 52) & 0x7ff);
+          const bool zero = (vb & 0x7fffffffffffffffLL) == 0;
+          // the scaled value must stay normal (zero stays zero); inf and NaN
+          // and everything else go the slow way
+          slow |= pe != 0 && !zero && (ev <= pe || ev == 0x7ff);
+          vb = (pe != 0 && !zero) ? vb - ((long long)pe << 52) : vb;
+          out[j] = __longlong_as_double(vb) - i64_ldexp_fast(W[j], ex, slow);
+        }
+        if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
+#pragma unroll
+          for (int j = 0; j < kQ; ++j) {
+            const int ex = er + __shfl_sync(0xffffffffu, cx_l, cp + j);
+            const int pe = __shfl_sync(0xffffffffu, pe_l, cp + j);
+            out[j] = (pe ? dshift(bq[j], pe) : bq[j]) - i64_ldexp(W[j], ex);
           }
+        }
+        {
+          double *pj = base + kQ * h * ldr2;
+#pragma unroll
+          for (int j = 0; j < kQ; ++j, pj += ldr2)
+            if (row_ok && cp + j < nval) *pj = out[j];
+        }
+        if (h + 1 < kPasses) {
+#pragma unroll
+          for (int j = 0; j < kQ; ++j) bq[j] = bn[j];
         }
       }
     }
@@ -760,7 +818,7 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
     if (e != cudaSuccess) return e;
     const double mma_flops = (double)total * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
     void *h = trace_on() ? trace_start(2, mma_flops, (double)total * kOzBBytes, st) : nullptr;
-    k_oz_update<<<std::min(total, kOzPersistentCtas), kOzThreads, kOzuSmem, st>>>(plan.tmA, tmB, a, tiles_n,
+    k_oz_update<<<std::min(total, kOzPersistentCtas), kOzuThreads, kOzuSmem, st>>>(plan.tmA, tmB, a, tiles_n,
                                                                                  total);
     trace_stop(h, st);
     count_launches(2);
