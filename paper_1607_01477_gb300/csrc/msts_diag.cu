@@ -67,6 +67,17 @@ __device__ __forceinline__ double zabs_exp(double2 z) {
   const double r = sqrt(fma(a, a, b * b));              // in [1, 2 sqrt 2)
   return __longlong_as_double(__double_as_longlong(r) + sh);
 }
+// x 2^s, exact unless the result is subnormal or overflows.
+__device__ __forceinline__ double dscale(double x, int s) {
+  if (s >= 0) {
+    if (s > 1023) {
+      x *= pow2i(1023);
+      s -= 1023;
+    }
+    return x * pow2i(min(s, 1023));
+  }
+  return dshift(x, -s);
+}
 // x >= Omega for x >= 0 or NaN (false), on the bit pattern.
 __device__ __forceinline__ bool ge_omega(double x) {
   const long long b = __double_as_longlong(x);
@@ -191,81 +202,117 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     return sqrt(gmax<L>(m2)) * pow2i(E);
   };
 
-  // Two ways to the same result.  Until its first rescale the safeguarded
-  // substitution (Alg. 4) computes exactly the plain one, so when a block starts
-  // far below Omega the plain substitution runs first and Alg. 4's two rescaling
-  // tests are checked afterwards in one pass over the rows, spread over the
-  // lanes; only if a test fires is the block redone with the safeguarded loop.
-  // Blocks that start near Omega, where a rescale is likely, take the
-  // safeguarded loop directly.
+  // Alg. 4 with its decisions taken after the fact.  A rescale by a power of
+  // two commutes exactly with every later operation of the substitution (as
+  // long as no value is subnormal), so the block is solved once in a scaling
+  // of its own, kept clear of overflow by integer bounds on the exponents and
+  // rare rescales (phase A).  Alg. 4's two tests are then replayed from per-row
+  // quantities computed in parallel over the lanes (phase B): the chain of G
+  // sums and rescales (phase C) costs one addition and one exact scaling per
+  // row.  The block is finally brought to Alg. 4's scaling (phase D); every
+  // value is then the one the serial safeguarded loop computes.
   const double G0 = maxabs();                         // G before the first row (Alg. 4)
-  bool careful = __any_sync(0xffffffffu, active && !(G0 < 0x1p-64 * OM));
-  if (!careful) {
-    double2 ypre[RPL];                                // each row's value at its diagonal step
+  // phase A: |y| < 2^Eb for every row; Kown = this block's own scaling
+  int Eb = G0 == 0.0 ? -1100 : (int)(__double_as_longlong(G0) >> 52) - 1022;
+  int Kown = 0;
+  bool patho = false;                                 // a rescale so large that small values would underflow
+  double2 ypre[RPL];                                  // each row's value at its diagonal step
+  int kpre[RPL];                                      // Kown at that step
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) ypre[q] = make_double2(0.0, 0.0);
+  for (int q = 0; q < RPL; ++q) {
+    ypre[q] = make_double2(0.0, 0.0);
+    kpre[q] = 0;
+  }
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const int i = NB - 1 - t;
-      const int qi = i / L, li = i % L;
-      const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);
-      if (l == li) {
-        ypre[qi] = y[qi];
-        y[qi] = xi;
-      }
-      axpy(i, xi);
+  for (int t = 0; t < NB; ++t) {
+    const int i = NB - 1 - t;
+    const int qi = i / L, li = i % L;
+    const int pi = gshfl_i<L>(pex[qi], li);
+    // |x_i| = |y_i| / |p_i| < 2^(Eb + 1024 - pi); the AXPY adds at most |x_i| C_i.
+    const int eC = (int)(__double_as_longlong(sC[i]) >> 52) - 1022;
+    const int xb = Eb + 1025 - pi;
+    int cand = i < nbe ? max(xb + max(eC, 0), Eb) + 1 : Eb;
+    if (cand > 1010) {                                // keep clear of overflow
+      const int kk = cand - 900;
+      patho |= kk > 600;                              // e.g. a subnormal pivot
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) y[q] = zshift(y[q], kk);
+      Kown += kk;
+      cand -= kk;
     }
-    bool fire = false;
-    double a[RPL];                                    // |x_r| C_r, rounded as in the serial loop
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const int r = l + L * q;
-      a[q] = 0.0;
-      if (r < nbe) {
-        const double2 yp = ypre[q];
-        // |y|/|p| >= Omega is possible only if the exponents allow it (|y| <
-        // 2^(ey+1.5), |p| >= 2^ep for a normal pivot); decide exactly then.
-        const int ey = (int)(max(absbits(yp.x), absbits(yp.y)) >> 52);
-        if (!zzero_bits(yp) && (pex[q] == 0 || ey - pex[q] >= kOmegaExp - 1))
-          fire |= ratio_exp_fast(yp, pivot(r)) >= kOmegaExp;
-        a[q] = __dmul_rn(zabs_exp(y[q]), sC[r]);
-      }
+    const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);
+    if (l == li) {
+      ypre[qi] = y[qi];
+      kpre[qi] = Kown;
+      y[qi] = xi;
     }
+    axpy(i, xi);
+    Eb = cand;
+  }
+  int kexp = 0;
+  if (!__any_sync(0xffffffffu, active && patho)) {
+  // phase B: per owned row, a_r = |x_r| C_r in the final own scaling and the
+  // exponent of M_r = |y_r| / |p_r| in the unscaled one
+  double a[RPL];
+  int em[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int r = l + L * q;
+    a[q] = 0.0;
+    em[q] = -(1 << 28);
+    if (r < nbe) {
+      a[q] = __dmul_rn(zabs_exp(y[q]), sC[r]);
+      if (!zzero_bits(ypre[q])) em[q] = ratio_exp_fast(ypre[q], pivot(r)) + kpre[q];
+    }
+  }
+  // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this block
+  int Ka = 0;
+  {
     double G = G0;
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
       const int i = NB - 1 - t;
-      const double ai = gshfl<L>(a[i / L], i % L);
+      const int qi = i / L, li = i % L;
+      const double ai = gshfl<L>(a[qi], li);
+      const int emi = gshfl_i<L>(em[qi], li);
       if (i < nbe) {
-        G = __dadd_rn(G, ai);
-        fire |= !(G < OM);                            // also catches a NaN from an overflow
-      }
-    }
-    careful = __any_sync(0xffffffffu, active && fire);
-    if (careful) {                                    // start again from the block's right-hand side
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        const int r = l + L * q;
-        y[q] = r < nbe ? col[r] : make_double2(0.0, 0.0);
+        const int eM = emi - Ka;
+        if (eM >= kOmegaExp) {                        // M >= Omega: rescale b first
+          const int kk = eM - (kOmegaExp - 1);
+          Ka += kk;
+          G = dshift(G, kk);
+        }
+        G = __dadd_rn(G, dscale(ai, Kown - Ka));
+        if (ge_omega(G)) {                            // protect the AXPY
+          const int kk = choose_k(G);
+          Ka += kk;
+          G = dshift(G, kk);
+        }
       }
     }
   }
-  int kexp = 0;
-  if (careful) {
-    // Safeguarded back substitution (Alg. 4, second branch), group-uniform.
+  // phase D: to Alg. 4's scaling
+  kexp = Ka;
+  if (Kown != Ka) {
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) y[q] = make_double2(dscale(y[q].x, Kown - Ka), dscale(y[q].y, Kown - Ka));
+  }
+  } else {
+    // The serial safeguarded back substitution (Alg. 4, second branch),
+    // group-uniform, from the block's right-hand side.
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = l + L * q;
+      y[q] = r < nbe ? col[r] : make_double2(0.0, 0.0);
+    }
     double G = G0;
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
       const int i = NB - 1 - t;
       const int qi = i / L, li = i % L;
       const double2 yi = gshfl_z<L>(y[qi], li);
-      const int epi = gshfl_i<L>(pex[qi], li);
-      // M = |y_i| / |p_i| >= Omega: exact test only where the exponent fields
-      // allow it (see above).
       int eM = -100000;
-      const int ey = (int)(max(absbits(yi.x), absbits(yi.y)) >> 52);
-      if (i < nbe && !zzero_bits(yi) && (epi == 0 || ey - epi >= kOmegaExp - 1))
-        eM = ratio_exp_fast(yi, pivot(i));
+      if (i < nbe && !zzero_bits(yi)) eM = ratio_exp_fast(yi, pivot(i));
       if (eM >= kOmegaExp) {                          // M >= Omega: rescale b first
         const int kk = eM - (kOmegaExp - 1);
 #pragma unroll
