@@ -564,19 +564,63 @@ __device__ __forceinline__ double i64_ldexp(long long W, int ex) {
   return a == 0 ? 0.0 : __longlong_as_double((long long)(bits | (W < 0 ? 0x8000000000000000ull : 0ull)));
 }
 
-// i64_ldexp without the out-of-range branch: sets *slow instead (the caller
-// then recomputes with i64_ldexp).
-__device__ __forceinline__ double i64_ldexp_fast(long long W, int ex, bool &slow) {
-  const unsigned long long a = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
-  const int lz = __clzll((long long)a);                // 64 when W == 0
-  const int E = 1023 + 63 - lz + ex;
-  slow |= a != 0 && (E <= 0 || E >= 2046);
-  const unsigned long long nrm = a << (lz & 63);
-  unsigned long long sig = nrm >> 11;
-  const unsigned long long rest = nrm & 0x7ffull;
-  sig += (rest > 0x400ull || (rest == 0x400ull && (sig & 1ull))) ? 1ull : 0ull;
-  const unsigned long long bits = ((unsigned long long)(E - 1) << 52) + sig;
-  return a == 0 ? 0.0 : __longlong_as_double((long long)(bits | (W < 0 ? 0x8000000000000000ull : 0ull)));
+// Exact integer value of an FP32 accumulator holding an integer of magnitude
+// below 2^22, without a conversion instruction: adding 1.5 2^23 puts it in the
+// low mantissa bits.
+__device__ __forceinline__ int f32_small_int(uint32_t f) {
+  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+}
+
+// W = P01 2^35 + P23 2^21 + P45 2^7 + floor(P67 / 2^7) as two 32-bit words
+// (h signed high word, l low word).
+__device__ __forceinline__ void fold_w(int P01, int P23, int P45, int P67, int &h, uint32_t &l) {
+  const uint32_t l2 = (uint32_t)P23 << 21, l3 = (uint32_t)P45 << 7, l4 = (uint32_t)(P67 >> 7);
+  int hh = (P01 << 3) + (P23 >> 11) + (P45 >> 25) + (P67 >> 31);
+  uint32_t ll;
+  asm("{\n\t"
+      "add.cc.u32 %0, %2, %3;\n\t"
+      "addc.u32 %1, %1, 0;\n\t"
+      "add.cc.u32 %0, %0, %4;\n\t"
+      "addc.u32 %1, %1, 0;\n\t"
+      "}"
+      : "=r"(ll), "+r"(hh)
+      : "r"(l2), "r"(l3), "r"(l4));
+  h = hh;
+  l = ll;
+}
+
+// (h, l) 2^ex rounded to the nearest double (ties to even), from 32-bit
+// integer operations only; |W| < 2^62.  Sets slow when the result leaves the
+// normal range: the caller then uses i64_ldexp.
+__device__ __forceinline__ double w_ldexp_fast(int h, uint32_t l, int ex, bool &slow) {
+  const bool neg = h < 0;
+  uint32_t nl, nh;                                      // -(h, l)
+  asm("{\n\t"
+      "sub.cc.u32 %0, 0, %2;\n\t"
+      "subc.u32 %1, 0, %3;\n\t"
+      "}"
+      : "=r"(nl), "=r"(nh)
+      : "r"(l), "r"((uint32_t)h));
+  const uint32_t ah = neg ? nh : (uint32_t)h, al = neg ? nl : l;
+  const bool big = ah != 0, zero = (ah | al) == 0;
+  const int lzh = __clz((int)ah), lzl = __clz((int)al);
+  const int lz = big ? lzh : 32 + lzl;                  // leading zeros of the 64-bit magnitude
+  const int E = 1023 + 63 - lz + ex;                    // biased exponent
+  slow |= !zero && (E <= 0 || E >= 2046);
+  const uint32_t th = big ? __funnelshift_l(al, ah, lzh) : al << (lzl & 31);   // normalised: bit 63 set
+  const uint32_t tl = big ? al << (lzh & 31) : 0u;
+  const uint32_t sh = th >> 11, sl = __funnelshift_r(tl, th, 11);          // 53-bit significand
+  const uint32_t rest = tl & 0x7ffu;
+  const uint32_t inc = (rest > 0x400u || (rest == 0x400u && (sl & 1u))) ? 1u : 0u;
+  uint32_t rh = ((uint32_t)(E - 1) << 20) + sh, rl;
+  asm("{\n\t"
+      "add.cc.u32 %0, %2, %3;\n\t"
+      "addc.u32 %1, %1, 0;\n\t"
+      "}"
+      : "=r"(rl), "+r"(rh)
+      : "r"(sl), "r"(inc));
+  rh |= neg ? 0x80000000u : 0u;
+  return zero ? 0.0 : __hiloint2double((int)rh, (int)rl);
 }
 
 // Persistent form of the substitution step for one 64-wide K chunk per block
@@ -722,7 +766,8 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int cp = c0 + kQ * h;                 // first column of this pass
         // W = sum_d D_d 2^(42 - 7d), the diagonals paired first in int32:
         // |D_d| <= (d + 1) 64 127^2, so D_{2c} 2^7 + D_{2c+1} < 2^30 for d <= 7.
-        long long W[kQ];
+        // (D_0..D_3 are below 2^22 and are read without a conversion.)
+        int P[kOzS / 2][kQ];
 #pragma unroll
         for (int c = 0; c < kOzS / 2; ++c) {
           uint32_t v0[kQ], v1[kQ];
@@ -730,13 +775,15 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tmem_ld8(tmem + lane_addr + ab * kOzAccCols + (2 * c + 1) * kOzBN + cp, v1);
           tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < kQ; ++j) {
-            const int pr = __float2int_rn(__uint_as_float(v0[j])) * (1 << kOzBits) +
-                           __float2int_rn(__uint_as_float(v1[j]));   // exact integers
-            const long long pw = c < 3 ? ((long long)pr << (35 - 14 * c)) : (long long)(pr >> kOzBits);
-            W[j] = c == 0 ? pw : W[j] + pw;
-          }
+          for (int j = 0; j < kQ; ++j)
+            P[c][j] = c < 2 ? f32_small_int(v0[j]) * (1 << kOzBits) + f32_small_int(v1[j])
+                            : __float2int_rn(__uint_as_float(v0[j])) * (1 << kOzBits) +
+                                  __float2int_rn(__uint_as_float(v1[j]));   // exact integers
         }
+        int Wh[kQ];
+        uint32_t Wl[kQ];
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) fold_w(P[0][j], P[1][j], P[2][j], P[3][j], Wh[j], Wl[j]);
         if (h == kPasses - 1) {
           tc_fence_before();
           mbar_arrive(&accempty[ab]);
@@ -763,14 +810,15 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           // and everything else go the slow way
           slow |= pe != 0 && !zero && (ev <= pe || ev == 0x7ff);
           vb = (pe != 0 && !zero) ? vb - ((long long)pe << 52) : vb;
-          out[j] = __longlong_as_double(vb) - i64_ldexp_fast(W[j], ex, slow);
+          out[j] = __longlong_as_double(vb) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
         }
         if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
 #pragma unroll
           for (int j = 0; j < kQ; ++j) {
             const int ex = er + __shfl_sync(0xffffffffu, cx_l, cp + j);
             const int pe = __shfl_sync(0xffffffffu, pe_l, cp + j);
-            out[j] = (pe ? dshift(bq[j], pe) : bq[j]) - i64_ldexp(W[j], ex);
+            const long long W = (long long)(((unsigned long long)(uint32_t)Wh[j] << 32) | Wl[j]);
+            out[j] = (pe ? dshift(bq[j], pe) : bq[j]) - i64_ldexp(W, ex);
           }
         }
         {
