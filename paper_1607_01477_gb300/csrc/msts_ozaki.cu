@@ -620,7 +620,15 @@ __device__ __forceinline__ double w_ldexp_fast(int h, uint32_t l, int ex, bool &
       : "=r"(rl), "+r"(rh)
       : "r"(sl), "r"(inc));
   rh |= neg ? 0x80000000u : 0u;
-  return zero ? 0.0 : __hiloint2double((int)rh, (int)rl);
+  return __hiloint2double(zero ? 0 : (int)rh, zero ? 0 : (int)rl);
+}
+
+// One output of the update through the FP64 routines (the rare cases that
+// leave the normal range); kept out of line so that the common path carries
+// none of its instructions.
+__device__ __noinline__ double update_out_slow(double v, int pe, int h, uint32_t l, int ex) {
+  const long long W = (long long)(((unsigned long long)(uint32_t)h << 32) | l);
+  return (pe ? dshift(v, pe) : v) - i64_ldexp(W, ex);
 }
 
 // Persistent form of the substitution step for one 64-wide K chunk per block
@@ -635,7 +643,8 @@ __device__ __forceinline__ double w_ldexp_fast(int h, uint32_t l, int ex, bool &
 // B = 2^-pend B - W 2^(e_r + f_j - 56) with a single FP64 subtraction.
 constexpr size_t kOzuSmem = (size_t)kOzS * kOzABytes + 2 * kOzBBytes + 1024;
 constexpr int kOzPersistentCtas = 152;             // one CTA per SM
-constexpr int kOzuThreads = 320;                   // 8 epilogue warps + producer + MMA
+constexpr int kOzuEpiWarps = 8;                    // epilogue warps (2 per sub-partition)
+constexpr int kOzuThreads = 32 * kOzuEpiWarps + 64; // + producer + MMA
 
 __global__ void __launch_bounds__(kOzuThreads, 1)
 k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -661,7 +670,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       mbar_init(&bfull[i], 1);
       mbar_init(&bempty[i], 1);
       mbar_init(&accfull[i], 1);
-      mbar_init(&accempty[i], 2 * kOzBM);
+      mbar_init(&accempty[i], 32 * kOzuEpiWarps);
     }
     fail = 0;
     fence_barrier_init();
@@ -676,7 +685,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     return ok;
   };
 
-  if (warp == 8) {
+  if (warp == kOzuEpiWarps) {
     if (lane == 0) {                                // ---------------- TMA producer
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
@@ -697,7 +706,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         tma_load_3d(sB + bb * kOzBBytes, &tmB, &bfull[bb], 0, ct * kOzBN, 0);
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == kOzuEpiWarps + 1) {
     if (lane == 0) {                                // ---------------- MMA issuer
       int prev_rt = -1, na = 0;
       for (int t = t0, k = 0; t < t1 && !fail; ++t, ++k) {
@@ -730,108 +739,106 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       mma_commit(&mma_done);                        // drain before TMEM is freed
       if (!wait(&mma_done, 0)) fail = 1;
     }
-  } else {                                          // ---------------- epilogue, warps 0-7
-    // Warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows) and the columns
-    // 16 (w / 4) .. + 15 of every tile: two warps per sub-partition.
-    const int quarter = warp & 3, half = warp >> 2;
+  } else {                                          // ---------------- epilogue warps
+    // Warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows) and kCW columns
+    // of every tile starting at kCW (w / 4).  Everything a tile reads from
+    // memory (its B values, column and row exponents) is fetched while the
+    // previous tile is processed, so no memory latency sits between tiles.
+    const int quarter = warp & 3, cgroup = warp >> 2;
     const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
     const long long ldr2 = 2 * args.ldr;            // column stride in doubles
-    constexpr int kQ = 8, kPasses = kOzBN / 2 / kQ;
-    for (int t = t0, k = 0; t < t1; ++t, ++k) {
+    constexpr int kCW = kOzBN * 4 / kOzuEpiWarps, kQ = 8, kPasses = kCW / kQ;
+    struct TileIn {
+      double b[kCW];                                // B(row, columns of this warp)
+      double *base;                                 // &B(row, first column of this warp)
+      int cx, pe;                                   // lane j: f_j - 56 and pend of column j
+      int er, nval;
+      bool row_ok;
+    };
+    auto fetch = [&](int t, TileIn &in) {
       const int rt = t / tiles_n, ct = t - rt * tiles_n;
       const int i = args.row_lo + rt * kOzBM + 32 * quarter + lane;   // real row of A'
-      const bool row_ok = i < args.row_hi;
       const int r = i >> 1, part = i & 1;
-      // Column data of the tile, lane j holding column j: the exponent f_j - 56
-      // and the pending exponent, shuffled to the rows below.
-      const int nval = min(kOzBN, args.ncols - ct * kOzBN);
-      const int cx_l = lane < nval ? args.cexp[ct * kOzBN + lane] - 56 : 0;
-      const int pe_l = (lane < nval && args.pend) ? args.pend[args.col_base + ct * kOzBN + lane] : 0;
-      const bool any_pe = __any_sync(0xffffffffu, pe_l != 0);
-      const int c0 = 16 * half;                     // first column of this warp
-      double *const base =
-          reinterpret_cast<double *>(args.R + r + (long long)(args.col_base + ct * kOzBN + c0) * args.ldr) + part;
-      double bq[kQ];                                // B of the first pass, fetched before the wait
-      {
-        const double *pj = base;
+      in.row_ok = i < args.row_hi;
+      in.nval = min(kOzBN, args.ncols - ct * kOzBN);
+      in.cx = lane < in.nval ? args.cexp[ct * kOzBN + lane] - 56 : 0;
+      in.pe = (lane < in.nval && args.pend) ? args.pend[args.col_base + ct * kOzBN + lane] : 0;
+      in.er = in.row_ok ? args.rexp[r] : 0;
+      const int c0 = kCW * cgroup;
+      in.base = reinterpret_cast<double *>(args.R + r + (long long)(args.col_base + ct * kOzBN + c0) * args.ldr) + part;
+      const double *pj = in.base;
 #pragma unroll
-        for (int j = 0; j < kQ; ++j, pj += ldr2) bq[j] = (row_ok && c0 + j < nval) ? *pj : 0.0;
-      }
-      const int er = row_ok ? args.rexp[r] : 0;
+      for (int j = 0; j < kCW; ++j, pj += ldr2) in.b[j] = (in.row_ok && c0 + j < in.nval) ? *pj : 0.0;
+    };
+    TileIn cur, nxt;
+    if (t0 < t1) fetch(t0, cur);
+    for (int t = t0, k = 0; t < t1; ++t, ++k) {
       const int ab = k & 1;
       if (!wait(&accfull[ab], (k >> 1) & 1)) { fail = 1; break; }
       tc_fence_after();
+      if (t + 1 < t1) fetch(t + 1, nxt);            // in flight during this tile
+      const bool any_pe = __any_sync(0xffffffffu, cur.pe != 0);
+      const int c0 = kCW * cgroup;
 #pragma unroll
       for (int h = 0; h < kPasses; ++h) {
         const int cp = c0 + kQ * h;                 // first column of this pass
         // W = sum_d D_d 2^(42 - 7d), the diagonals paired first in int32:
         // |D_d| <= (d + 1) 64 127^2, so D_{2c} 2^7 + D_{2c+1} < 2^30 for d <= 7.
         // (D_0..D_3 are below 2^22 and are read without a conversion.)
+        uint32_t v[kOzS][kQ];                       // all diagonals of the pass, one wait
+#pragma unroll
+        for (int d = 0; d < kOzS; ++d) tmem_ld8(tmem + lane_addr + ab * kOzAccCols + d * kOzBN + cp, v[d]);
+        tmem_ld_wait();
         int P[kOzS / 2][kQ];
 #pragma unroll
-        for (int c = 0; c < kOzS / 2; ++c) {
-          uint32_t v0[kQ], v1[kQ];
-          tmem_ld8(tmem + lane_addr + ab * kOzAccCols + (2 * c) * kOzBN + cp, v0);
-          tmem_ld8(tmem + lane_addr + ab * kOzAccCols + (2 * c + 1) * kOzBN + cp, v1);
-          tmem_ld_wait();
+        for (int c = 0; c < kOzS / 2; ++c)
 #pragma unroll
           for (int j = 0; j < kQ; ++j)
-            P[c][j] = c < 2 ? f32_small_int(v0[j]) * (1 << kOzBits) + f32_small_int(v1[j])
-                            : __float2int_rn(__uint_as_float(v0[j])) * (1 << kOzBits) +
-                                  __float2int_rn(__uint_as_float(v1[j]));   // exact integers
+            P[c][j] = c < 2 ? f32_small_int(v[2 * c][j]) * (1 << kOzBits) + f32_small_int(v[2 * c + 1][j])
+                            : __float2int_rn(__uint_as_float(v[2 * c][j])) * (1 << kOzBits) +
+                                  __float2int_rn(__uint_as_float(v[2 * c + 1][j]));   // exact integers
+        if (h == kPasses - 1) {
+          tc_fence_before();
+          mbar_arrive(&accempty[ab]);
         }
         int Wh[kQ];
         uint32_t Wl[kQ];
 #pragma unroll
         for (int j = 0; j < kQ; ++j) fold_w(P[0][j], P[1][j], P[2][j], P[3][j], Wh[j], Wl[j]);
-        if (h == kPasses - 1) {
-          tc_fence_before();
-          mbar_arrive(&accempty[ab]);
-        }
-        double bn[kQ];                              // next pass's B
-        if (h + 1 < kPasses) {
-          const double *pj = base + kQ * (h + 1) * ldr2;
-#pragma unroll
-          for (int j = 0; j < kQ; ++j, pj += ldr2) bn[j] = (row_ok && cp + kQ + j < nval) ? *pj : 0.0;
-        }
         // Branch-free outputs: the pending scaling on the exponent field and
-        // the product by i64_ldexp_fast; a pass where either leaves the
-        // normal range is redone with the FP64 routines.
+        // the product by w_ldexp_fast; a pass where either leaves the normal
+        // range is redone with the FP64 routines.
         double out[kQ];
         bool slow = false;
 #pragma unroll
         for (int j = 0; j < kQ; ++j) {
-          const int ex = er + __shfl_sync(0xffffffffu, cx_l, cp + j);
-          const int pe = any_pe ? __shfl_sync(0xffffffffu, pe_l, cp + j) : 0;
-          long long vb = __double_as_longlong(bq[j]);
+          const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
+          const int pe = any_pe ? __shfl_sync(0xffffffffu, cur.pe, cp + j) : 0;
+          long long vb = __double_as_longlong(cur.b[kQ * h + j]);
           const int ev = (int)((vb >> 52) & 0x7ff);
-          const bool zero = (vb & 0x7fffffffffffffffLL) == 0;
-          // the scaled value must stay normal (zero stays zero); inf and NaN
-          // and everything else go the slow way
-          slow |= pe != 0 && !zero && (ev <= pe || ev == 0x7ff);
-          vb = (pe != 0 && !zero) ? vb - ((long long)pe << 52) : vb;
+          // Only normal values are scaled on the exponent field (zero stays
+          // zero); subnormals, values that would become subnormal, inf and
+          // NaN go the slow way.  (The tests look at the exponent field and
+          // the mantissa bits separately: a test of all bits but the sign
+          // against zero may be compiled into an FP64 comparison.)
+          slow |= pe != 0 && ((ev == 0 && (vb & 0xfffffffffffffLL) != 0) || (ev != 0 && ev <= pe) || ev == 0x7ff);
+          vb = (pe != 0 && ev != 0) ? vb - ((long long)pe << 52) : vb;
           out[j] = __longlong_as_double(vb) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
         }
         if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
 #pragma unroll
           for (int j = 0; j < kQ; ++j) {
-            const int ex = er + __shfl_sync(0xffffffffu, cx_l, cp + j);
-            const int pe = __shfl_sync(0xffffffffu, pe_l, cp + j);
-            const long long W = (long long)(((unsigned long long)(uint32_t)Wh[j] << 32) | Wl[j]);
-            out[j] = (pe ? dshift(bq[j], pe) : bq[j]) - i64_ldexp(W, ex);
+            const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
+            const int pe = __shfl_sync(0xffffffffu, cur.pe, cp + j);
+            out[j] = update_out_slow(cur.b[kQ * h + j], pe, Wh[j], Wl[j], ex);
           }
         }
-        {
-          double *pj = base + kQ * h * ldr2;
+        double *pj = cur.base + kQ * h * ldr2;
 #pragma unroll
-          for (int j = 0; j < kQ; ++j, pj += ldr2)
-            if (row_ok && cp + j < nval) *pj = out[j];
-        }
-        if (h + 1 < kPasses) {
-#pragma unroll
-          for (int j = 0; j < kQ; ++j) bq[j] = bn[j];
-        }
+        for (int j = 0; j < kQ; ++j, pj += ldr2)
+          if (cur.row_ok && cp + j < cur.nval) *pj = out[j];
       }
+      cur = nxt;
     }
   }
   tc_fence_before();
