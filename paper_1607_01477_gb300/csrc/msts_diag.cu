@@ -54,18 +54,18 @@ __device__ __forceinline__ long long gmax_ll(long long v) {
 // power-of-two scalings done on the exponent fields (integer operations) when
 // every operand stays a normal number; otherwise zabs_fast itself.
 __device__ __forceinline__ double zabs_exp(double2 z) {
-  const long long ax = absbits(z.x), ay = absbits(z.y);
-  const long long mx = max(ax, ay);
-  if (mx == 0) return 0.0;
-  const int e = (int)(mx >> 52) - 1023;
-  const bool ok = (mx >> 52) != 0 && e <= 1021 && (ax == 0 || (int)(ax >> 52) - e >= 1) &&
-                  (ay == 0 || (int)(ay >> 52) - e >= 1);
+  const unsigned hx = (unsigned)__double2hiint(z.x) & 0x7fffffffu, lx = (unsigned)__double2loint(z.x);
+  const unsigned hy = (unsigned)__double2hiint(z.y) & 0x7fffffffu, ly = (unsigned)__double2loint(z.y);
+  const bool zx = (hx | lx) == 0u, zy = (hy | ly) == 0u;
+  if (zx && zy) return 0.0;
+  const int fx = (int)(hx >> 20), fy = (int)(hy >> 20);   // biased exponent fields
+  const int e = max(fx, fy) - 1023;
+  const bool ok = max(fx, fy) != 0 && e <= 1021 && (zx || fx - e >= 1) && (zy || fy - e >= 1);
   if (!ok) return zabs_fast(z);
-  const long long sh = (long long)e << 52;
-  const double a = ax == 0 ? 0.0 : __longlong_as_double(ax - sh);
-  const double b = ay == 0 ? 0.0 : __longlong_as_double(ay - sh);
+  const double a = zx ? 0.0 : __hiloint2double((int)(hx - ((unsigned)e << 20)), (int)lx);
+  const double b = zy ? 0.0 : __hiloint2double((int)(hy - ((unsigned)e << 20)), (int)ly);
   const double r = sqrt(fma(a, a, b * b));              // in [1, 2 sqrt 2)
-  return __longlong_as_double(__double_as_longlong(r) + sh);
+  return __hiloint2double(__double2hiint(r) + (e << 20), __double2loint(r));
 }
 // x 2^s, exact unless the result is subnormal or overflows.
 __device__ __forceinline__ double dscale(double x, int s) {
@@ -78,10 +78,27 @@ __device__ __forceinline__ double dscale(double x, int s) {
   }
   return dshift(x, -s);
 }
-// x >= Omega for x >= 0 or NaN (false), on the bit pattern.
+// x >= Omega for x >= 0 (false for NaN), on the exponent field.  (Range
+// tests on all bits of a double may be compiled into FP64 comparisons, which
+// cost as much as an FP64 multiply here.)
 __device__ __forceinline__ bool ge_omega(double x) {
-  const long long b = __double_as_longlong(x);
-  return b >= 0x7BF0000000000000LL && b <= 0x7FF0000000000000LL;   // [2^960, +inf]
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const bool nan = e == 0x7ffu && (((hi & 0xfffffu) | (unsigned)__double2loint(x)) != 0u);
+  return e >= 0x3ffu + kOmegaExp && !nan;
+}
+// x 2^s for x >= 0 on the exponent field when x and the result are normal,
+// else dscale.
+__device__ __forceinline__ double dscale_exp(double x, int s) {
+  const int hi = __double2hiint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  if (e == 0 || e == 0x7ff || e + s < 1 || e + s > 0x7fe) return dscale(x, s);
+  return __hiloint2double(hi + (s << 20), __double2loint(x));
+}
+// z == 0 on the bit patterns, word by word.
+__device__ __forceinline__ bool zzero_words(double2 z) {
+  return ((((unsigned)__double2hiint(z.x) | (unsigned)__double2hiint(z.y)) & 0x7fffffffu) |
+          (unsigned)__double2loint(z.x) | (unsigned)__double2loint(z.y)) == 0u;
 }
 
 // 1 / p with p scaled by a power of two first (one real division).
@@ -129,7 +146,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   auto pivot = [&](int i) {
     const double2 d = sU[i * LD + i];
     double2 p = zsub(CONJ ? zconj(d) : d, lam);
-    if (SAFE && zzero_bits(p)) p = make_double2(dlt, 0.0);   // U(i,i) = lambda -> delta (Sec. 3)
+    if (SAFE && zzero_words(p)) p = make_double2(dlt, 0.0);   // U(i,i) = lambda -> delta (Sec. 3)
     return p;
   };
 
@@ -143,7 +160,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     y[q] = v ? col[r] : make_double2(0.0, 0.0);
     const double2 d = sU[r * LD + r];
     const double2 p0 = zsub(CONJ ? zconj(d) : d, lam);
-    zero_piv |= v && zzero_bits(p0);
+    zero_piv |= v && zzero_words(p0);
     const double2 p = pivot(r);
     inv[q] = v ? zrecip(p) : make_double2(0.0, 0.0);
     pex[q] = (int)(max(absbits(p.x), absbits(p.y)) >> 52);
@@ -193,13 +210,13 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     for (int q = 0; q < RPL; ++q) E = max(E, zexp(y[q]));
     E = gmax_i<L>(E);
     const double sc = pow2i(-E);
-    double m2 = 0.0;
+    long long m2 = 0;                                  // max of the scaled squares, as bits (>= 0)
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       const double a = y[q].x * sc, bb = y[q].y * sc;
-      m2 = fmax(m2, fma(a, a, bb * bb));
+      m2 = max(m2, __double_as_longlong(fma(a, a, bb * bb)));
     }
-    return sqrt(gmax<L>(m2)) * pow2i(E);
+    return sqrt(__longlong_as_double(gmax_ll<L>(m2))) * pow2i(E);
   };
 
   // Alg. 4 with its decisions taken after the fact.  A rescale by a power of
@@ -262,7 +279,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     em[q] = -(1 << 28);
     if (r < nbe) {
       a[q] = __dmul_rn(zabs_exp(y[q]), sC[r]);
-      if (!zzero_bits(ypre[q])) em[q] = ratio_exp_fast(ypre[q], pivot(r)) + kpre[q];
+      if (!zzero_words(ypre[q])) em[q] = ratio_exp_fast(ypre[q], pivot(r)) + kpre[q];
     }
   }
   // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this block
@@ -282,7 +299,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
           Ka += kk;
           G = dshift(G, kk);
         }
-        G = __dadd_rn(G, dscale(ai, Kown - Ka));
+        G = __dadd_rn(G, dscale_exp(ai, Kown - Ka));
         if (ge_omega(G)) {                            // protect the AXPY
           const int kk = choose_k(G);
           Ka += kk;
@@ -312,7 +329,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
       const int qi = i / L, li = i % L;
       const double2 yi = gshfl_z<L>(y[qi], li);
       int eM = -100000;
-      if (i < nbe && !zzero_bits(yi)) eM = ratio_exp_fast(yi, pivot(i));
+      if (i < nbe && !zzero_words(yi)) eM = ratio_exp_fast(yi, pivot(i));
       if (eM >= kOmegaExp) {                          // M >= Omega: rescale b first
         const int kk = eM - (kOmegaExp - 1);
 #pragma unroll
