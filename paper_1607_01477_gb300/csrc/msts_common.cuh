@@ -137,13 +137,17 @@ __device__ __forceinline__ double zabs_fast(double2 z) {
 // floor(log2(|y| / |p|)) for y, p != 0 without a division or a square root:
 // |y| = sqrt(ny) 2^fy with ny in [1, 4), likewise p.
 __device__ __forceinline__ int ratio_exp_fast(double2 y, double2 p) {
+  // Subnormal operands are first brought into the normal range (exactly).
+  int adj = 0;
+  if ((max(absbits(p.x), absbits(p.y)) >> 52) == 0) { p = zscale(p, 0x1p64); adj += 64; }
+  if ((max(absbits(y.x), absbits(y.y)) >> 52) == 0) { y = zscale(y, 0x1p64); adj -= 64; }
   int fy = zexp(y), fp = zexp(p);
   const double sy = pow2i(-fy), sp = pow2i(-fp);
   const double ya = y.x * sy, yb = y.y * sy, pa = p.x * sp, pb = p.y * sp;
   double ny = fma(ya, ya, yb * yb), np = fma(pa, pa, pb * pb);
   if (ny >= 4.0) { fy += 1; ny *= 0.25; }
   if (np >= 4.0) { fp += 1; np *= 0.25; }
-  return fy - fp - (ny < np ? 1 : 0);
+  return fy - fp - (ny < np ? 1 : 0) + adj;
 }
 // z * 2^-k for k >= 0 (exact unless the result is subnormal).
 __device__ __forceinline__ double2 zshift(double2 z, int k) {

@@ -245,13 +245,14 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     const int i = NB - 1 - t;
     const int qi = i / L, li = i % L;
     const int pi = gshfl_i<L>(pex[qi], li);
+    patho |= i < nbe && pi == 0;                      // subnormal pivot: |p| >= 2^(pi - 1023) fails
     // |x_i| = |y_i| / |p_i| < 2^(Eb + 1024 - pi); the AXPY adds at most |x_i| C_i.
     const int eC = (int)(__double_as_longlong(sC[i]) >> 52) - 1022;
     const int xb = Eb + 1025 - pi;
     int cand = i < nbe ? max(xb + max(eC, 0), Eb) + 1 : Eb;
     if (cand > 1010) {                                // keep clear of overflow
       const int kk = cand - 900;
-      patho |= kk > 600;                              // e.g. a subnormal pivot
+      patho |= kk > 600;                              // e.g. a pivot near the bottom of the range
 #pragma unroll
       for (int q = 0; q < RPL; ++q) y[q] = zshift(y[q], kk);
       Kown += kk;
@@ -337,7 +338,9 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
         kexp += kk;
         G = dshift(G, kk);
       }
-      double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);   // diagonal step
+      // diagonal step by a division: in this path the reciprocal of a
+      // subnormal pivot may have overflowed
+      double2 xi = gshfl_z<L>(i < nbe ? zdiv_fast(y[qi], pivot(i)) : make_double2(0.0, 0.0), li);
       if (l == li) y[qi] = xi;
       if (i < nbe) {
         G = __dadd_rn(G, __dmul_rn(zabs_exp(xi), sC[i]));

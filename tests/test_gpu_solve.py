@@ -175,3 +175,43 @@ def test_graph_capture_replays_the_solve():
     Xo = oracle.solve(U, s, B)
     err, tol = forward_close(to_np(X), Xo, cond_inf(U, s), 128)
     assert (err <= tol).all()
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+def test_safe_subnormal_pivot_matches_oracle(tensor):
+    """A subnormal pivot (U(i,i) - s_j = 1e-310) sends its block through the
+    serial safeguarded loop; scale exponents and X still match the oracle."""
+    U, s, B = W.plain_problem(96, 6, seed=21)
+    U[40, 40] = 1e-310
+    s[2] = 0.0
+    X = to_dev(B)
+    _, sc, se, st = msts.msts_solve(to_dev(U), to_dev(s), X, safe=True, nb=32, tensor=tensor)
+    Xo, eo = oracle.safe_solve(U, s, B, 32)
+    assert eo[2] > 0
+    assert np.array_equal(to_np(se), eo)
+    Xg = to_np(X)
+    assert np.isfinite(Xg).all()
+    rel = np.abs(Xg - Xo).max(axis=0) / np.abs(Xo).max(axis=0)
+    assert rel.max() <= 1e-8
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+def test_safe_tiny_rows_with_scaling_match_oracle(tensor):
+    """Right-hand sides whose upper rows are ~1e-300 become subnormal when the
+    columns are rescaled: the exact slow paths of the lazy rescaling (and of the
+    tensor-core update's epilogue) keep X equal to the oracle's up to rounding."""
+    m = 256
+    T = W.trevc_problem(m, seed=44, cluster_frac=0.1, offdiag_scale=30.0)
+    g = W.rng(0, 10)
+    B = W.cn(g, (m, 24))
+    B[:64, :] *= 1e-300
+    shifts = np.diag(T)[g.permutation(m)[:24]] + 1e-9
+    X = to_dev(B)
+    _, sc, se, st = msts.msts_solve(to_dev(T), to_dev(shifts), X, safe=True, nb=32, tensor=tensor)
+    Xo, eo = oracle.safe_solve(T, shifts, B, 32)
+    eg = to_np(se)
+    assert eo.max() > 0
+    assert np.array_equal(eg, eo)
+    Xg = to_np(X)
+    rel = np.abs(Xg - Xo).max(axis=0) / np.abs(Xo).max(axis=0)
+    assert rel.max() <= 1e-8
