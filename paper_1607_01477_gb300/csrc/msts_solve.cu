@@ -37,47 +37,112 @@ constexpr int kNumSMs = 152;
 // Safe-variant preprocessing (Alg. 5 set-up, the column norms of Sec. 3).
 // ---------------------------------------------------------------------------
 
+// |Re z|, |Im z| bit patterns: the larger one (as a nonnegative int64, ordered
+// like the magnitudes) and whether both are finite.  max(|Re|, |Im|) <=
+// |z| <= sqrt 2 max(|Re|, |Im|), so an element whose larger component is
+// below half the largest seen cannot have the largest modulus: only the few
+// others need the FP64 square sum (FP64 arithmetic is slow on this part, the
+// integer tests are not).
+__device__ __forceinline__ long long zmaxbits(double2 z) {
+  return max(__double_as_longlong(z.x) & 0x7fffffffffffffffLL, __double_as_longlong(z.y) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool zfinite_bits(double2 z) {
+  return ((__double2hiint(z.x) & 0x7ff00000) != 0x7ff00000) && ((__double2hiint(z.y) & 0x7ff00000) != 0x7ff00000);
+}
+__device__ __forceinline__ long long half_bits(long long m) {   // bits of m / 2 (or 0)
+  return m >= (1LL << 53) ? m - (1LL << 52) : 0;
+}
+
 // One warp per column k: cin[k] = max_{lo(k) <= r < k} |U(r,k)| (within its own
 // block, diagonal excluded) and cup[k] = max_{r < lo(k)} |U(r,k)| (above it).
 __global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32_t *status) {
   const Prob &P = tab.p[blockIdx.z];
   if (P.n == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *P.delta = 0.0;   // the zero-pivot flag of k_zero_scan
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (k >= P.m) return;
   const int b = (P.m - 1 - k) / nb;
   int lo, hi;
   block_range(P, b, nb, lo, hi);
-  // Maxima of squared moduli, one square root per column at the end
-  // (|U(i,k)| < 2^48 is the documented range, so the squares cannot overflow).
-  double cin = 0.0, cup = 0.0, amax = 0.0;
+  // Maxima of squared moduli (as bits: nonnegative doubles order like their
+  // bits), one square root per column at the end (|U(i,k)| < 2^48 is the
+  // documented range, so the squares cannot overflow).
+  long long Min = 0, Mup = 0, Mall = 0, cin = 0, cup = 0, amax = 0;
   bool finite = true;
   const double2 *col = P.U + (long long)k * P.ldu;
-  for (int r = lane; r <= k; r += 32) {
-    const double2 u = col[r];
-    finite &= zfinite(u);
-    const double a2 = fma(u.x, u.x, u.y * u.y);
-    amax = fmax(amax, a2);
-    if (r < lo) cup = fmax(cup, a2);
-    else if (r < k) cin = fmax(cin, a2);
+  for (int r0 = 0; r0 <= k; r0 += 32) {                  // warp-uniform trip count
+    const int r = r0 + lane;
+    const double2 u = r <= k ? col[r] : make_double2(0.0, 0.0);
+    finite &= zfinite_bits(u);
+    const long long m = zmaxbits(u);
+    const bool in_in = r >= lo && r < k, in_up = r < lo;
+    Mall = max(Mall, m);
+    if (in_in) Min = max(Min, m);
+    if (in_up) Mup = max(Mup, m);
+    const bool cand = m != 0 && (m >= half_bits(Mall) || (in_in && m >= half_bits(Min)) ||
+                                 (in_up && m >= half_bits(Mup)));
+    if (__any_sync(0xffffffffu, cand)) {
+      const long long a2 = cand ? __double_as_longlong(fma(u.x, u.x, u.y * u.y)) : 0;
+      amax = max(amax, a2);
+      if (in_in) cin = max(cin, a2);
+      if (in_up) cup = max(cup, a2);
+    }
   }
-  cin = sqrt(warp_max(cin));
-  cup = sqrt(warp_max(cup));
-  amax = sqrt(warp_max(amax));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cin = max(cin, (long long)__shfl_xor_sync(0xffffffffu, cin, o));
+    cup = max(cup, (long long)__shfl_xor_sync(0xffffffffu, cup, o));
+    amax = max(amax, (long long)__shfl_xor_sync(0xffffffffu, amax, o));
+  }
   const bool all_finite = __all_sync(0xffffffffu, finite);
   if (lane == 0) {
-    P.cin[k] = cin;
-    P.cup[k] = cup;
+    P.cin[k] = sqrt(__longlong_as_double(cin));
+    P.cup[k] = sqrt(__longlong_as_double(cup));
     if (!all_finite) raise_status(status, MSTS_STATUS_NONFINITE);
-    if (amax >= kRangeLimitU) raise_status(status, MSTS_STATUS_RANGE);
+    if (sqrt(__longlong_as_double(amax)) >= kRangeLimitU) raise_status(status, MSTS_STATUS_RANGE);
   }
 }
 
+// a == b for doubles, on the bit patterns (+0 == -0; a NaN equals nothing).
+__device__ __forceinline__ bool deq_bits(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  if (((ia | ib) & 0x7fffffffffffffffLL) == 0) return true;
+  const bool nan = (((unsigned)__double2hiint(a) >> 20) & 0x7ffu) == 0x7ffu &&
+                   ((__double2hiint(a) & 0xfffff) | __double2loint(a)) != 0;
+  return !nan && ia == ib;
+}
+
+// delta (Sec. 3) replaces a pivot U(i,i) - lambda_j that is exactly zero, so
+// ||U||_inf is needed only if some shift equals a diagonal entry of a row it
+// visits (rows i < j for Alg. 6's right-hand sides, all rows otherwise).
+// One thread per shift and CTA per 256 diagonal entries (staged in shared
+// memory); *delta is
+// set nonzero (k_colnorms zeroed it) when such a pair exists.
+__global__ void k_zero_scan(const __grid_constant__ ProbTable tab, int shortcut) {
+  const Prob &P = tab.p[blockIdx.z];
+  __shared__ double2 dg[256];
+  if (P.m == 0 || P.n == 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = j < P.n;
+  const double2 lam = act ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
+  const int end = !act ? 0 : (shortcut ? min(j, P.m) : P.m);
+  const int i0 = 256 * blockIdx.y;                       // this CTA's 256 diagonal entries
+  if (i0 >= P.m) return;
+  if (i0 + (int)threadIdx.x < P.m) dg[threadIdx.x] = P.U[(long long)(i0 + threadIdx.x) * (P.ldu + 1)];
+  __syncthreads();
+  bool hit = false;
+  const int cnt = min(256, end - i0);
+  for (int t = 0; t < cnt; ++t) hit |= deq_bits(dg[t].x, lam.x) && deq_bits(dg[t].y, lam.y);
+  if (hit) *P.delta = 1.0;
+}
+
 // One warp per row: rowsum[r] = sum_{c >= r} |U(r,c)| (lanes stride over the
-// columns, then a fixed-order warp reduction: deterministic).
+// columns, then a fixed-order warp reduction: deterministic); only when a zero
+// pivot can occur (k_zero_scan).
 __global__ void k_rowsums(const __grid_constant__ ProbTable tab) {
   const Prob &P = tab.p[blockIdx.z];
-  if (P.n == 0) return;
+  if (P.n == 0 || *P.delta == 0.0) return;
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= P.m) return;
@@ -92,8 +157,8 @@ __global__ void k_rowsums(const __grid_constant__ ProbTable tab) {
   if (lane == 0) P.rowsum[r] = s;
 }
 
-// One CTA per problem: C_blk for every block (summed in column order) and
-// delta = max(eps * ||U||_inf, DBL_MIN).
+// C_blk per block (Alg. 5), and delta = max(eps ||U||_inf, DBL_MIN) when a
+// zero pivot can occur (otherwise delta is never read; DBL_MIN is stored).
 __global__ void k_safe_finish(const __grid_constant__ ProbTable tab, int nb) {
   const Prob &P = tab.p[blockIdx.z];
   __shared__ double red[32];
@@ -104,6 +169,12 @@ __global__ void k_safe_finish(const __grid_constant__ ProbTable tab, int nb) {
     double c = 0.0;
     for (int k = lo; k < hi; ++k) c += P.cup[k];
     P.cblk[b] = c;
+  }
+  const bool need = *P.delta != 0.0;                     // uniform
+  __syncthreads();
+  if (!need) {
+    if (threadIdx.x == 0) *P.delta = kDblMin;
+    return;
   }
   double mx = 0.0;
   for (int r = threadIdx.x; r < P.m; r += blockDim.x) mx = fmax(mx, P.rowsum[r]);
@@ -121,6 +192,8 @@ __global__ void k_safe_finish(const __grid_constant__ ProbTable tab, int nb) {
 }
 
 // One warp per column: G(j) = ||B(:,j)||_inf over the active rows, e_j = 0.
+// The scaled square sums are formed only for the candidates of the maximum
+// (see zmaxbits), with the same values as for all elements.
 __global__ void k_safe_init(const __grid_constant__ ProbTable tab, int shortcut, uint32_t *status) {
   const Prob &P = tab.p[blockIdx.z];
   const int lane = threadIdx.x & 31;
@@ -129,21 +202,30 @@ __global__ void k_safe_init(const __grid_constant__ ProbTable tab, int shortcut,
   const int end = shortcut ? min(j, P.m) : P.m;
   bool finite = true;
   const double2 *col = P.B + (long long)j * P.ldb;
-  int E = -1022;
+  long long M = 0;
   for (int r = lane; r < end; r += 32) {
     const double2 v = col[r];
-    finite &= zfinite(v);
-    E = max(E, zexp(v));
+    finite &= zfinite_bits(v);
+    M = max(M, zmaxbits(v));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+  for (int o = 16; o > 0; o >>= 1) M = max(M, (long long)__shfl_xor_sync(0xffffffffu, M, o));
+  const int E = min(max((int)(M >> 52) - 1023, -1022), 1022);   // zexp of the largest component
   const double sc = pow2i(-E);
-  double g2 = 0.0;
-  for (int r = lane; r < end; r += 32) {
-    const double a = col[r].x * sc, b = col[r].y * sc;
-    g2 = fmax(g2, fma(a, a, b * b));
+  const long long thr = half_bits(M);
+  long long g2 = 0;
+  for (int r0 = 0; r0 < end; r0 += 32) {                 // warp-uniform trip count
+    const int r = r0 + lane;
+    const double2 v = r < end ? col[r] : make_double2(0.0, 0.0);
+    const bool cand = r < end && M != 0 && zmaxbits(v) >= thr;
+    if (__any_sync(0xffffffffu, cand)) {
+      const double a = v.x * sc, bb = v.y * sc;
+      if (cand) g2 = max(g2, __double_as_longlong(fma(a, a, bb * bb)));
+    }
   }
-  const double g = sqrt(warp_max(g2)) * pow2i(E);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g2 = max(g2, (long long)__shfl_xor_sync(0xffffffffu, g2, o));
+  const double g = sqrt(__longlong_as_double(g2)) * pow2i(E);
   const bool all_finite = __all_sync(0xffffffffu, finite);
   if (lane == 0) {
     P.G[j] = g;
@@ -512,9 +594,10 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
     const int sc = shortcut ? 1 : 0;
     if (safe) {
       k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status);
+      k_zero_scan<<<dim3((maxn + 255) / 256, (maxm + 255) / 256, cnt), 256, 0, st>>>(tab, sc);
       k_rowsums<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab);
       k_safe_finish<<<dim3(1, 1, cnt), 256, 0, st>>>(tab, nb);
-      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);  count_launches(4);
+      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);  count_launches(5);
     }
     cudaError_t err;
     switch (nb) {
