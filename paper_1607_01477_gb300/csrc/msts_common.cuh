@@ -185,6 +185,12 @@ struct Prob {
   double *delta;            // 1: zero-pivot replacement
   int m, n, nblk;
   int diag_z;               // TREVC: write Z(j,j) = s_j in the fixup
+  // Tensor-core substitution: the diagonal-block step also writes the digit
+  // planes of X(I1, jstart..n) (BF16 pairs, plane t, column c at
+  // oz_bp[(t * (n - jstart) + c) * oz_kb / 2 + row]) and their exponents.
+  uint32_t *oz_bp;
+  int *oz_cexp;
+  int oz_kb;
 };
 
 struct ProbTable {

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "msts_common.cuh"
+#include "msts_digits.cuh"
 #include "msts_diag.h"
 
 namespace msts {
@@ -101,8 +102,30 @@ __device__ __forceinline__ bool zzero_words(double2 z) {
           (unsigned)__double2loint(z.x) | (unsigned)__double2loint(z.y)) == 0u;
 }
 
-// 1 / p with p scaled by a power of two first (one real division).
-__device__ __forceinline__ double2 zrecip(double2 p) { return zdiv_fast(make_double2(1.0, 0.0), p); }
+// 1 / p = conj(p') / |p'|^2 2^-e with p' = p 2^-e (one real division); the
+// scalings act on the exponent fields when every operand stays normal, with
+// the same values as zdiv_fast.
+__device__ __forceinline__ double2 zrecip(double2 p) {
+  const unsigned hx = (unsigned)__double2hiint(p.x) & 0x7fffffffu, hy = (unsigned)__double2hiint(p.y) & 0x7fffffffu;
+  const bool zx = (hx | (unsigned)__double2loint(p.x)) == 0u, zy = (hy | (unsigned)__double2loint(p.y)) == 0u;
+  const int fx = (int)(hx >> 20), fy = (int)(hy >> 20);
+  const int e = max(fx, fy) - 1023;                      // zexp(p) when unclamped
+  const bool ok = max(fx, fy) != 0 && e >= -1021 && e <= 1021 && (zx || fx - e >= 1) && (zy || fy - e >= 1);
+  if (!ok) return zdiv_fast(make_double2(1.0, 0.0), p);
+  const int sh = e << 20;
+  const double a = zx ? 0.0 : __hiloint2double(__double2hiint(p.x) - sh, __double2loint(p.x));
+  const double b = zy ? 0.0 : __hiloint2double(__double2hiint(p.y) - sh, __double2loint(p.y));
+  const double q = 1.0 / fma(a, a, b * b);               // |p'|^2 in [1, 8)
+  const double wr = a * q, wi = -(b * q);                // each zero or of magnitude in (2^-1077, 2]
+  // times 2^-e on the exponent fields where the result stays normal
+  auto scale = [&](double w) {
+    const int f = (__double2hiint(w) >> 20) & 0x7ff;
+    if (f == 0) return w * pow2i(-e);                    // zero or subnormal: exact as zdiv_fast
+    if (f - e < 1 || f - e > 2046) return w * pow2i(-e);
+    return __hiloint2double(__double2hiint(w) - sh, __double2loint(w));
+  };
+  return make_double2(scale(wr), scale(wi));
+}
 
 template <int NB, int L, bool SAFE, bool CONJ>
 __global__ void __launch_bounds__(kDiagThreads)
@@ -193,11 +216,38 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     }
   };
 
+  // The digit planes of the block's X and their column exponents, for the
+  // tensor-core substitution step that follows (integer work only; every lane
+  // takes part in the group reduction, inactive ones with zeros).
+  auto write_planes = [&](const double2 (&v)[RPL]) {
+    if (P.oz_bp == nullptr || (CONJ ? P.m - hi : lo) <= 0) return;   // uniform
+    int e = -(1 << 29);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) e = max(e, bound_exp(v[q]));
+    e = gmax_i<L>(e);
+    if (e < -(1 << 28)) e = 0;
+    if (!active) return;
+    const int jstart = shortcut ? lo + 1 : 0;
+    const int c = j - jstart, ncols = P.n - jstart, kw = P.oz_kb / 2;
+    if (l == 0) P.oz_cexp[c] = e;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      uint32_t w[kOzS];
+      digit_pairs(v[q], e, w);
+#pragma unroll
+      for (int t = 0; t < kOzS; ++t) P.oz_bp[(size_t)(t * ncols + c) * kw + l + L * q] = w[t];
+    }
+    for (int r = NB + l; r < kw; r += L)                 // K padding beyond n_b rows
+#pragma unroll
+      for (int t = 0; t < kOzS; ++t) P.oz_bp[(size_t)(t * ncols + c) * kw + r] = 0u;
+  };
+
   if (!SAFE) {
     substitute();
 #pragma unroll
     for (int q = 0; q < RPL; ++q)
       if (l + L * q < nbe) col[l + L * q] = y[q];
+    write_planes(y);
     return;
   }
 
@@ -280,7 +330,15 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     em[q] = -(1 << 28);
     if (r < nbe) {
       a[q] = __dmul_rn(zabs_exp(y[q]), sC[r]);
-      if (!zzero_words(ypre[q])) em[q] = ratio_exp_fast(ypre[q], pivot(r)) + kpre[q];
+      if (!zzero_words(ypre[q])) {
+        // floor(log2 M) <= ey - ep + 1 for normal operands; Alg. 4's test
+        // (M 2^(kpre - Ka) >= Omega with Ka >= 0) can only fire above it.
+        const int ey = (int)(((unsigned)max(__double2hiint(ypre[q].x) & 0x7fffffff,
+                                            __double2hiint(ypre[q].y) & 0x7fffffff)) >> 20);
+        const int up = ey - pex[q] + 1 + kpre[q];
+        em[q] = (ey != 0 && pex[q] != 0 && up < kOmegaExp) ? up
+                                                          : ratio_exp_fast(ypre[q], pivot(r)) + kpre[q];
+      }
     }
   }
   // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this block
@@ -361,23 +419,28 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   // GEMM applies it to I0 and the final fix-up to I2), then
   // G(j) += C_blk ||X(I1,j)||_inf with a whole-column rescale at Omega.
   const double N = maxabs();
-  if (!active) return;
-  int ej = P.e[j];
-  double Gj = P.G[j];
-  int pend = 0;
-  if (kexp > 0) { ej += kexp; Gj = dshift(Gj, kexp); pend = kexp; }
-  Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
-  int k2 = 0;
-  if (Gj >= OM) {
-    k2 = choose_k(Gj);
-    ej += k2;
-    Gj = dshift(Gj, k2);
-    pend += k2;
+  int ej = 0, pend = 0, k2 = 0;
+  double Gj = 0.0;
+  if (active) {
+    ej = P.e[j];
+    Gj = P.G[j];
+    if (kexp > 0) { ej += kexp; Gj = dshift(Gj, kexp); pend = kexp; }
+    Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
+    if (Gj >= OM) {
+      k2 = choose_k(Gj);
+      ej += k2;
+      Gj = dshift(Gj, k2);
+      pend += k2;
+    }
   }
+  double2 xo[RPL];
 #pragma unroll
-  for (int q = 0; q < RPL; ++q)
-    if (l + L * q < nbe) col[l + L * q] = k2 ? zshift(y[q], k2) : y[q];
-  if (l == 0) {
+  for (int q = 0; q < RPL; ++q) {
+    xo[q] = k2 ? zshift(y[q], k2) : y[q];
+    if (active && l + L * q < nbe) col[l + L * q] = xo[q];
+  }
+  write_planes(xo);
+  if (active && l == 0) {
     P.e[j] = ej;
     P.G[j] = Gj;
     P.pend[j] = pend;

@@ -40,14 +40,13 @@
 #include <mutex>
 
 #include "msts_common.cuh"
+#include "msts_digits.cuh"
 #include "msts_ozaki.h"
 #include "msts_tc.cuh"
 #include "msts_trace.h"
 
 namespace msts {
 
-constexpr int kOzS = 8;          // digit planes per operand
-constexpr int kOzBits = 7;       // bits per digit
 constexpr int kOzKC = 64;        // K' per chunk: one 128-byte swizzle row of BF16
 constexpr int kOzBM = 128;       // real rows per tile (= TMEM lanes)
 constexpr int kOzBN = 32;        // columns per tile
@@ -81,37 +80,6 @@ static OzakiBufs carve(void *ws, int m, int n) {
   o.rexp = reinterpret_cast<int *>(c); c += a256(4 * (size_t)m);
   o.cexp = reinterpret_cast<int *>(c);
   return o;
-}
-
-// floor(log2 max(|Re z|, |Im z|)) + 1, or INT_MIN/2 for z == 0, from the
-// exponent fields (ilogb of a subnormal from its leading zeros).  Integer
-// operations only: FP64 instructions and conversions are slow on this part.
-__device__ __forceinline__ int bound_exp(double2 z) {
-  const unsigned long long m = (unsigned long long)max(__double_as_longlong(z.x) & 0x7fffffffffffffffLL,
-                                                       __double_as_longlong(z.y) & 0x7fffffffffffffffLL);
-  if (m == 0ull) return -(1 << 29);
-  const int f = (int)(m >> 52);
-  return (f != 0 ? f - 1023 : (63 - __clzll((long long)m)) - 1074) + 1;
-}
-
-// The 8 signed 7-bit digits of a * 2^-e (|a| < 2^e), most significant first:
-// those of M = trunc(|a| 2^(56 - e)), read off the 53-bit significand by a
-// shift, each with the sign of a.  A digit c in [0, 127] becomes a float
-// exactly through the low mantissa bits of 2^23.
-__device__ __forceinline__ void digits8(double a, int e, float (&d)[kOzS]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
-  const unsigned long long ab = bits & 0x7fffffffffffffffull;
-  const int f = (int)(ab >> 52);
-  const unsigned long long sig = (ab & 0xfffffffffffffull) | (f != 0 ? (1ull << 52) : 0ull);
-  const int sh = max(f, 1) - 1075 + kOzS * kOzBits - e;      // |a| 2^(56 - e) = sig 2^sh
-  const unsigned long long M = sh >= 0 ? (sh < 64 ? sig << sh : 0ull) : (sh > -64 ? sig >> -sh : 0ull);
-  const bool neg = (bits >> 63) != 0ull;
-#pragma unroll
-  for (int s = 0; s < kOzS; ++s) {
-    const unsigned c = (unsigned)(M >> (kOzBits * (kOzS - 1 - s))) & 127u;
-    const float cf = __uint_as_float(0x4B000000u | c) - 8388608.0f;
-    d[s] = neg ? -cf : cf;
-  }
 }
 
 // e_r for every row of triu(U): one warp per row.
@@ -863,11 +831,14 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
 cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool planes_ready) {
   const int row_lo = plan.conj ? 2 * hi : 0, row_hi = plan.conj ? 2 * plan.m : 2 * lo;
   if (ncols <= 0 || row_hi <= row_lo) return cudaSuccess;
-  k_ozs_slice_X<<<(ncols + 7) / 8, 256, 0, st>>>(B, ldb, lo, hi - lo, jstart, ncols, plan.KB, plan.bp,
-                                                plan.cexp);
+  if (!planes_ready) {
+    k_ozs_slice_X<<<(ncols + 7) / 8, 256, 0, st>>>(B, ldb, lo, hi - lo, jstart, ncols, plan.KB, plan.bp,
+                                                  plan.cexp);
+    count_launches(1);
+  }
   CUtensorMap tmB;
   if (!make_map(&tmB, plan.bp, plan.KB, ncols, kOzBN, kOzS)) return cudaErrorNotSupported;
   OzArgs a{};
@@ -890,7 +861,7 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
     k_oz_update<<<std::min(total, kOzPersistentCtas), kOzuThreads, kOzuSmem, st>>>(plan.tmA, tmB, a, tiles_n,
                                                                                  total);
     trace_stop(h, st);
-    count_launches(2);
+    count_launches(1);
     return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
@@ -906,7 +877,7 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
   k_oz_gemm<kUpdate><<<dim3((ncols + kOzBN - 1) / kOzBN, (row_hi - row_lo + kOzBM - 1) / kOzBM), kOzThreads,
                        kOzSmem, st>>>(plan.tmA, tmB, a);
   trace_stop(h, st);
-  count_launches(2);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,9 @@ cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, in
                                bool conj, void *ws, cudaStream_t st);
 // B(rows, jstart..jstart+ncols) = 2^-pend B - U-panel(b) X(I1, .), rows above the
 // block (upper) or below it (conj); `flops` is recorded by the tracer.
+// planes_ready: the X digit planes and exponents of this block were written by
+// the diagonal-block step (otherwise they are sliced here first).
 cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
-                         cudaStream_t st);
+                         cudaStream_t st, bool planes_ready = false);
 }  // namespace msts

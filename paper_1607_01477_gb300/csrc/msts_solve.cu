@@ -534,7 +534,7 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       const int jstart = shortcut ? lo + 1 : 0;
       const cudaError_t e = ozaki_update(*probs[0].oz, b, lo, hi, probs[0].B, probs[0].ldb, jstart,
                                          probs[0].n - jstart, SAFE ? tab.p[0].pend : nullptr, status,
-                                         gflops, st);
+                                         gflops, st, tab.p[0].oz_bp != nullptr);
       if (e != cudaSuccess) return e;
     } else if (rows_max > 0) {
       // FP64 throughput per SM is low, so the tile is chosen to give the grid
@@ -591,6 +591,11 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
       maxn = std::max(maxn, q.n);
     }
     if (maxm == 0 || maxn == 0) continue;
+    if (cnt == 1 && probs[base].oz) {          // the diagonal step writes the X digit planes
+      tab.p[0].oz_bp = reinterpret_cast<uint32_t *>(probs[base].oz->bp);
+      tab.p[0].oz_cexp = probs[base].oz->cexp;
+      tab.p[0].oz_kb = probs[base].oz->KB;
+    }
     const int sc = shortcut ? 1 : 0;
     if (safe) {
       k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status);
