@@ -160,21 +160,24 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # roofline helpers
 # --------------------------------------------------------------------------
-def kernel_source_hash() -> str:
-    src = os.path.join(ROOT, "paper_1607_01477_gb300", "csrc", "msts_solve.cu")
+KERNEL_SOURCES = {"k_gemm": "msts_solve.cu", "k_diag": "msts_diag.cu", "k_oz_update": "msts_ozaki.cu"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    src = os.path.join(ROOT, "paper_1607_01477_gb300", "csrc", KERNEL_SOURCES[kernel])
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    if it was taken on a different version of the kernel source."""
+    if it was taken on a different version of the kernel's source file."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}4096.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not h or not t or h.group(1) != kernel_source_hash():
+    if not h or not t or h.group(1) != kernel_source_hash(kernel):
         return None
     return float(t.group(1))
 
@@ -297,7 +300,7 @@ def run_native(args):
         pk = fp64_peak()
         peak_v, src, bound, unit_r = pk["peak"], pk["source"], "alu", "TFLOP/s"
     achieved = kv["flops"] / (kv["ms"] * 1e-3) / 1e12 if kv["ms"] > 0 else None
-    traffic = profiled_traffic("k_gemm", wl) if kv is kg else None
+    traffic = profiled_traffic({id(kg): "k_gemm", id(kd): "k_diag", id(ko): "k_oz_update"}[id(kv)], wl)
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak_v, "unit": unit_r,
                 "frac": achieved / peak_v if (achieved and peak_v) else None, "traffic": traffic,
                 "peak_source": src,

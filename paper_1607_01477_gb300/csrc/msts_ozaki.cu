@@ -553,6 +553,14 @@ __device__ __forceinline__ int f32_small_int(uint32_t f) {
   return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
 }
 
+// a 2^7 + b for two such accumulators, the two offsets folded into one.
+__device__ __forceinline__ int f32_small_pair(uint32_t a, uint32_t b) {
+  const int ia = __float_as_int(__uint_as_float(a) + 12582912.0f);
+  const int ib = __float_as_int(__uint_as_float(b) + 12582912.0f);
+  // modulo 2^32 (the result fits an int32)
+  return (int)((uint32_t)ia * (1u << kOzBits) + (uint32_t)ib - 0x4B400000u * ((1u << kOzBits) + 1u));
+}
+
 // W = P01 2^35 + P23 2^21 + P45 2^7 + floor(P67 / 2^7) as two 32-bit words
 // (h signed high word, l low word).
 __device__ __forceinline__ void fold_w(int P01, int P23, int P45, int P67, int &h, uint32_t &l) {
@@ -759,7 +767,6 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       if (!wait(&accfull[ab], (k >> 1) & 1)) { fail = 1; break; }
       tc_fence_after();
       if (t + 1 < t1) fetch(t + 1, nxt);            // in flight during this tile
-      const bool any_pe = __any_sync(0xffffffffu, cur.pe != 0);
       const int c0 = kCW * cgroup;
 #pragma unroll
       for (int h = 0; h < kPasses; ++h) {
@@ -776,7 +783,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         for (int c = 0; c < kOzS / 2; ++c)
 #pragma unroll
           for (int j = 0; j < kQ; ++j)
-            P[c][j] = c < 2 ? f32_small_int(v[2 * c][j]) * (1 << kOzBits) + f32_small_int(v[2 * c + 1][j])
+            P[c][j] = c < 2 ? f32_small_pair(v[2 * c][j], v[2 * c + 1][j])
                             : __float2int_rn(__uint_as_float(v[2 * c][j])) * (1 << kOzBits) +
                                   __float2int_rn(__uint_as_float(v[2 * c + 1][j]));   // exact integers
         if (h == kPasses - 1) {
@@ -795,17 +802,18 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
         for (int j = 0; j < kQ; ++j) {
           const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
-          const int pe = any_pe ? __shfl_sync(0xffffffffu, cur.pe, cp + j) : 0;
-          long long vb = __double_as_longlong(cur.b[kQ * h + j]);
-          const int ev = (int)((vb >> 52) & 0x7ff);
+          const int pe = __shfl_sync(0xffffffffu, cur.pe, cp + j);
+          const double v = cur.b[kQ * h + j];
+          const int vh = __double2hiint(v), vl = __double2loint(v);
+          const int ev = (vh >> 20) & 0x7ff;
+          const bool nz = ((vh & 0x7fffffff) | vl) != 0;
           // Only normal values are scaled on the exponent field (zero stays
           // zero); subnormals, values that would become subnormal, inf and
-          // NaN go the slow way.  (The tests look at the exponent field and
-          // the mantissa bits separately: a test of all bits but the sign
-          // against zero may be compiled into an FP64 comparison.)
-          slow |= pe != 0 && ((ev == 0 && (vb & 0xfffffffffffffLL) != 0) || (ev != 0 && ev <= pe) || ev == 0x7ff);
-          vb = (pe != 0 && ev != 0) ? vb - ((long long)pe << 52) : vb;
-          out[j] = __longlong_as_double(vb) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
+          // NaN go the slow way.  (Word-wise tests: a test of all bits but
+          // the sign against zero may be compiled into an FP64 comparison.)
+          slow |= pe != 0 && nz && (ev <= pe || ev == 0x7ff);
+          const int vh2 = (pe != 0 && nz) ? vh - (pe << 20) : vh;
+          out[j] = __hiloint2double(vh2, vl) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
         }
         if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
 #pragma unroll
