@@ -192,27 +192,32 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
 
   // One row of the substitution: x_i = y_i / piv_i by the owner lane, broadcast
   // in the group, AXPY on the rows each lane owns.
-  auto axpy = [&](int i, double2 xi) {
+  // Row i = L qi + li of the substitution: AXPY on the rows each lane owns.
+  // The loops below unroll over the row slot qi only (so that qi is a
+  // compile-time constant and y[] stays in registers) and run over li at run
+  // time: the unrolled code stays small enough for the instruction cache, and
+  // slots wholly on the dead side of row i still drop out at compile time.
+  auto axpy = [&](int qi, int li, double2 xi) {
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
-      const int r = l + L * q;
-      // Row slots that lie wholly on the dead side of row i are skipped at
-      // compile time (i and q are constants of the unrolled loops).
-      if (!CONJ) {
-        if (L * q < i && r < i) y[q] = zfms(y[q], xi, sU[i * LD + r]);
-      } else {
-        if (L * q + L - 1 > i && r > i) y[q] = zfms(y[q], xi, zconj(sU[r * LD + i]));
+      if (!CONJ) {        // rows l + L q < i
+        if (q < qi || (q == qi && l < li)) y[q] = zfms(y[q], xi, sU[(L * qi + li) * LD + l + L * q]);
+      } else {            // rows l + L q > i
+        if (q > qi || (q == qi && l > li)) y[q] = zfms(y[q], xi, zconj(sU[(l + L * q) * LD + L * qi + li]));
       }
     }
   };
   auto substitute = [&]() {
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const int i = CONJ ? t : NB - 1 - t;
-      const int qi = i / L, li = i % L;
-      const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);   // zero for rows >= nbe
-      if (l == li) y[qi] = xi;
-      axpy(i, xi);
+    for (int s_ = 0; s_ < RPL; ++s_) {
+      const int qi = CONJ ? s_ : RPL - 1 - s_;
+#pragma unroll 1
+      for (int u_ = 0; u_ < L; ++u_) {
+        const int li = CONJ ? u_ : L - 1 - u_;
+        const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);   // zero for rows >= nbe
+        if (l == li) y[qi] = xi;
+        axpy(qi, li, xi);
+      }
     }
   };
 
@@ -291,9 +296,11 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     kpre[q] = 0;
   }
 #pragma unroll
-  for (int t = 0; t < NB; ++t) {
-    const int i = NB - 1 - t;
-    const int qi = i / L, li = i % L;
+  for (int s_ = 0; s_ < RPL; ++s_) {
+   const int qi = RPL - 1 - s_;
+#pragma unroll 1
+   for (int u_ = 0; u_ < L; ++u_) {
+    const int li = L - 1 - u_, i = L * qi + li;
     const int pi = gshfl_i<L>(pex[qi], li);
     patho |= i < nbe && pi == 0;                      // subnormal pivot: |p| >= 2^(pi - 1023) fails
     // |x_i| = |y_i| / |p_i| < 2^(Eb + 1024 - pi); the AXPY adds at most |x_i| C_i.
@@ -314,8 +321,9 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
       kpre[qi] = Kown;
       y[qi] = xi;
     }
-    axpy(i, xi);
+    axpy(qi, li, xi);
     Eb = cand;
+   }
   }
   int kexp = 0;
   if (!__any_sync(0xffffffffu, active && patho)) {
@@ -346,9 +354,11 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   {
     double G = G0;
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const int i = NB - 1 - t;
-      const int qi = i / L, li = i % L;
+    for (int s_ = 0; s_ < RPL; ++s_) {
+     const int qi = RPL - 1 - s_;
+#pragma unroll 1
+     for (int u_ = 0; u_ < L; ++u_) {
+      const int li = L - 1 - u_, i = L * qi + li;
       const double ai = gshfl<L>(a[qi], li);
       const int emi = gshfl_i<L>(em[qi], li);
       if (i < nbe) {
@@ -365,6 +375,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
           G = dshift(G, kk);
         }
       }
+     }
     }
   }
   // phase D: to Alg. 4's scaling
@@ -383,9 +394,11 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     }
     double G = G0;
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const int i = NB - 1 - t;
-      const int qi = i / L, li = i % L;
+    for (int s_ = 0; s_ < RPL; ++s_) {
+     const int qi = RPL - 1 - s_;
+#pragma unroll 1
+     for (int u_ = 0; u_ < L; ++u_) {
+      const int li = L - 1 - u_, i = L * qi + li;
       const double2 yi = gshfl_z<L>(y[qi], li);
       int eM = -100000;
       if (i < nbe && !zzero_words(yi)) eM = ratio_exp_fast(yi, pivot(i));
@@ -411,7 +424,8 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
           G = dshift(G, kk);
         }
       }
-      axpy(i, xi);
+      axpy(qi, li, xi);
+     }
     }
   }
 
