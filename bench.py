@@ -464,10 +464,11 @@ def eta_dev(Ud, sd, Bd, X):
 
 
 def mixed_vs_fp64(dev, nb):
-    """Workload 3 (8192 x 8192, 2048 shifts): the plain FP64 solve and the mixed
-    solve refined to eta <= 1e-12 with the FP64-FMA residual and with the
-    tensor-core residual; TFLOP/s at 4 m^2 n (refinement not credited), each
-    with its measured eta, and the tensor-core residual kernel's roofline."""
+    """Workload 3 (8192 x 8192, 2048 shifts): the plain FP64 solve (FP64-FMA
+    substitution and tensor-core substitution) and the mixed solve refined to
+    eta <= 1e-12 with the FP64-FMA residual and with the tensor-core residual;
+    TFLOP/s at 4 m^2 n (refinement not credited), each with its measured eta,
+    and the tensor-core residual kernel's roofline."""
     import ctypes
     import torch
     import paper_1607_01477_gb300 as msts
@@ -489,6 +490,18 @@ def mixed_vs_fp64(dev, nb):
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1)
     out = {"fp64": {"ms": ms64, "tflops": fl / (ms64 * 1e-3) / 1e12, "eta": eta_dev(Ud, sd, Bd, X)}}
+    # the same FP64-accurate solve with the substitution step on the tensor cores
+    X.copy_(Bd)
+    msts.msts_solve(Ud, sd, X, nb=nb, tensor=True)   # warm-up
+    X.copy_(Bd)
+    torch.cuda.synchronize()
+    e0.record()
+    msts.msts_solve(Ud, sd, X, nb=nb, tensor=True)
+    e1.record()
+    torch.cuda.synchronize()
+    mst = e0.elapsed_time(e1)
+    out["fp64_tensor_gemm"] = {"ms": mst, "tflops": fl / (mst * 1e-3) / 1e12, "eta": eta_dev(Ud, sd, Bd, X),
+                               "speedup_vs_fp64": ms64 / mst}
     del X
     for name, flags in (("mixed_fp64_residual", 0), ("mixed_tensor_core_residual", msts.MSTS_RESIDUAL_OZAKI)):
         msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, nb=nb, flags=flags)   # warm-up

@@ -456,8 +456,12 @@ __global__ void k_ozs_prepare(const double2 *U, long long ldu, int m, int nb, in
   const int nblk = gridDim.x;
   const int hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb, w = hi - lo;
   const bool used = CONJ ? r >= hi : r < lo;
+  // Rows that the substitution of this block never updates are left unwritten:
+  // the update reads only used rows (others at most fill a tile whose outputs
+  // are masked, and an MMA row depends on its own A row only).
+  if (!used) return;                                   // warp-uniform (one warp per row)
   auto entry = [&](int k) {   // the complex entry of A' row r at column k of the block
-    if (!used || k >= w) return make_double2(0.0, 0.0);
+    if (k >= w) return make_double2(0.0, 0.0);
     return CONJ ? zconj(U[(lo + k) + (long long)r * ldu]) : U[r + (long long)(lo + k) * ldu];
   };
   int e = -(1 << 29);
@@ -815,6 +819,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           const int vh2 = (pe != 0 && nz) ? vh - (pe << 20) : vh;
           out[j] = __hiloint2double(vh2, vl) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
         }
+        slow = slow && cur.row_ok;                  // rows past the range hold no planes
         if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
 #pragma unroll
           for (int j = 0; j < kQ; ++j) {

@@ -71,6 +71,7 @@ __global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32
   long long Min = 0, Mup = 0, Mall = 0, cin = 0, cup = 0, amax = 0;
   bool finite = true;
   const double2 *col = P.U + (long long)k * P.ldu;
+#pragma unroll 4
   for (int r0 = 0; r0 <= k; r0 += 32) {                  // warp-uniform trip count
     const int r = r0 + lane;
     const double2 u = r <= k ? col[r] : make_double2(0.0, 0.0);
@@ -203,6 +204,7 @@ __global__ void k_safe_init(const __grid_constant__ ProbTable tab, int shortcut,
   bool finite = true;
   const double2 *col = P.B + (long long)j * P.ldb;
   long long M = 0;
+#pragma unroll 4
   for (int r = lane; r < end; r += 32) {
     const double2 v = col[r];
     finite &= zfinite_bits(v);
@@ -214,6 +216,7 @@ __global__ void k_safe_init(const __grid_constant__ ProbTable tab, int shortcut,
   const double sc = pow2i(-E);
   const long long thr = half_bits(M);
   long long g2 = 0;
+#pragma unroll 4
   for (int r0 = 0; r0 < end; r0 += 32) {                 // warp-uniform trip count
     const int r = r0 + lane;
     const double2 v = r < end ? col[r] : make_double2(0.0, 0.0);
