@@ -59,7 +59,9 @@ typedef struct { double re, im; } msts_z;
                                   BF16 tensor cores (error-free digit splitting) instead of FP64 FMA */
 #define MSTS_TENSOR_GEMM 8u    /* msts_solve / msts_trevc / msts_pseudospectra: the substitution GEMM
                                   of every block step as the same FP64-accurate digit-plane product
-                                  on the BF16 tensor cores instead of FP64 FMA (single problem) */
+                                  on the BF16 tensor cores instead of FP64 FMA (single problem);
+                                  msts_back_transform: the product X = Q Z likewise */
+#define MSTS_NORMALIZE_COLUMNS 16u /* msts_back_transform: scale every column of X to unit 2-norm */
 
 /* status bits */
 #define MSTS_STATUS_ZERO_PIVOT  1u  /* plain solve: some U(i,i) - s_j == 0 exactly (X is undefined) */
@@ -137,6 +139,30 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m,
                double *scales, int32_t *scale_exp,
                int32_t nb, void *workspace, size_t workspace_bytes,
                uint32_t *status, uint32_t flags, void *stream);   /* flags: 0 or MSTS_TENSOR_GEMM */
+
+/* ---------------------------------------------------------------------------
+ * Back-transformation (Sec. 4, Alg. 6 "Eig", second half): the eigenvectors
+ * of A = Q T Q^H are the columns of X = Q Z, with Z the upper triangular
+ * eigenvectors of T from msts_trevc.
+ * Q   m x m (leading dimension ldq), typically the unitary Schur vectors.
+ * Z   m x m upper triangular (ldz); only the upper triangle is read.
+ * X   m x m output (ldx); must not overlap Q or Z.
+ * flags: MSTS_TENSOR_GEMM runs the product on the tensor cores through the
+ *   exact digit splitting (FP64-accurate: the error is below 2^-46 m times
+ *   max|Q(i,:)| max|Z(:,j)| per entry), else FP64 FMA; MSTS_NORMALIZE_COLUMNS
+ *   then scales every column to unit 2-norm (zero columns stay zero).
+ * workspace: msts_back_transform_workspace_size(m, flags) bytes (0 without
+ *   MSTS_TENSOR_GEMM), device memory owned by the caller.
+ * status: device word, only MSTS_STATUS_TIMEOUT can be set.
+ * Returns 0, or -k for an invalid argument k (nothing launched; -8/-9 for a
+ * missing / too small workspace), or MSTS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+size_t msts_back_transform_workspace_size(int64_t m, uint32_t flags);
+int msts_back_transform(const msts_z *Q, int64_t ldq, int64_t m,
+                        const msts_z *Z, int64_t ldz,
+                        msts_z *X, int64_t ldx,
+                        void *workspace, size_t workspace_bytes,
+                        uint32_t *status, uint32_t flags, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Pseudospectra (Sec. 5, Alg. 7, Van Loan / Lui): for each grid point z[p],

@@ -166,6 +166,17 @@ def trevc(T, nb):
     return Z, e, sc
 
 
+def back_transform(Q, Z):
+    """X = Q triu(Z) (the eigenvectors of A = Q T Q^H from those of T, Alg. 6)."""
+    Q = _cz(Q, "Q")
+    Z = _cz(Z, "Z")
+    m = Q.shape[0]
+    X = np.zeros((m, m), dtype=np.complex128, order="F")
+    _load().or_back_transform(_c_int64(m), _p(Q), _c_int64(_ld(Q)), _p(Z), _c_int64(_ld(Z)), _p(X),
+                              _c_int64(_ld(X)))
+    return X
+
+
 def pseudospectra(T, z, V0, iters):
     """Alg. 7 (Van Loan / Lui): sigma_min(T - z_p I) for every grid point z_p.
 

@@ -537,6 +537,22 @@ void or_adjoint(int64_t m, const oz *U, int64_t ldu, int64_t n, const oz *shifts
 }
 
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+/* ------------------------------------------------------------------------
+ * Back-transformation (Sec. 4, Alg. 6 "Eig"): the eigenvectors of
+ * A = Q T Q^H are X = Q Z, Z upper triangular (only its upper triangle is
+ * read).  Plain definition: X(i,j) = sum_{k <= j} Q(i,k) Z(k,j), summed in
+ * increasing k.
+ * ---------------------------------------------------------------------- */
+void or_back_transform(int64_t m, const oz *Q, int64_t ldq, const oz *Z, int64_t ldz, oz *X, int64_t ldx) {
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < m; ++j)
+    for (int64_t i = 0; i < m; ++i) {
+      oz s = oz_make(0.0, 0.0);
+      for (int64_t k = 0; k <= j; ++k) s = oz_add(s, oz_mul(AT(Q, ldq, i, k), AT(Z, ldz, k, j)));
+      AT(X, ldx, i, j) = s;
+    }
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -26,7 +26,7 @@ __all__ = [
     "MSTS_SAFE", "MSTS_CONJ_TRANS", "STATUS_BITS", "colmajor", "load_library", "library_path",
     "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
     "msts_adjoint_batched", "msts_solve_mixed", "msts_residual", "MSTS_RESIDUAL_OZAKI",
-    "MSTS_TENSOR_GEMM",
+    "MSTS_TENSOR_GEMM", "MSTS_NORMALIZE_COLUMNS", "msts_back_transform", "eig",
     "MultiShiftSolve", "multishift_solve",
     "decode_status",
 ]
@@ -35,6 +35,7 @@ MSTS_SAFE = 1
 MSTS_CONJ_TRANS = 2
 MSTS_RESIDUAL_OZAKI = 4
 MSTS_TENSOR_GEMM = 8
+MSTS_NORMALIZE_COLUMNS = 16
 STATUS_BITS = {
     1: "ZERO_PIVOT", 2: "NONFINITE", 4: "RANGE", 8: "SCALED", 16: "DELTA", 32: "NOT_CONVERGED",
     64: "TIMEOUT",
@@ -115,6 +116,10 @@ def load_library():
         lib.msts_residual.restype = ctypes.c_int
         lib.msts_residual.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                                       _vp, _sz, _vp, _u32, _vp]
+        lib.msts_back_transform_workspace_size.restype = _sz
+        lib.msts_back_transform_workspace_size.argtypes = [_i64, _u32]
+        lib.msts_back_transform.restype = ctypes.c_int
+        lib.msts_back_transform.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp, _u32, _vp]
         _lib = lib
         return lib
 
@@ -262,6 +267,45 @@ def msts_trevc(T, *, nb=32, tensor=False, status=None):
                         _ptr(status), flags, _stream(dev))
     _check(rc, "msts_trevc")
     return Z, sc, se, status
+
+
+def msts_back_transform(Q, Z, *, tensor=False, normalize=False, status=None):
+    """X = Q Z (the eigenvectors of A = Q T Q^H from those of T, Alg. 6 "Eig");
+    only the upper triangle of Z is read. normalize=True scales every column of
+    X to unit 2-norm. Returns (X, status)."""
+    lib = load_library()
+    m = Q.shape[0]
+    ldq = _mat(Q, "Q", m)
+    ldz = _mat(Z, "Z", m)
+    dev = Q.device
+    X = colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
+    flags = (MSTS_TENSOR_GEMM if tensor else 0) | (MSTS_NORMALIZE_COLUMNS if normalize else 0)
+    ws = _workspace(lib.msts_back_transform_workspace_size(m, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_back_transform(_ptr(Q), ldq, m, _ptr(Z), ldz, _ptr(X), max(1, m), wp, wb, _ptr(status),
+                                 flags, _stream(dev))
+    _check(rc, "msts_back_transform")
+    return X, status
+
+
+def eig(A, *, nb=32, tensor=True, device=None):
+    """Eigenvalues and unit-norm eigenvectors of a general complex matrix A
+    (Alg. 6 "Eig"): the Schur factorisation A = Q T Q^H comes from the host
+    library (as in the paper, which takes it from LAPACK); the triangular
+    eigenvectors (msts_trevc) and the back-transformation X = Q Z
+    (msts_back_transform) run on the GPU. Returns (w, X, status) with w =
+    diag(T) and A X(:,j) = w[j] X(:,j)."""
+    import numpy as np
+    import scipy.linalg
+    A = np.asarray(A.detach().cpu().numpy() if isinstance(A, torch.Tensor) else A, dtype=np.complex128)
+    T, Q = scipy.linalg.schur(A, output="complex")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    Td = colmajor(torch.from_numpy(np.asfortranarray(T)).to(dev))
+    Qd = colmajor(torch.from_numpy(np.asfortranarray(Q)).to(dev))
+    Z, _, _, status = msts_trevc(Td, nb=nb, tensor=tensor)
+    X, status = msts_back_transform(Qd, Z, tensor=tensor, normalize=True, status=status)
+    return torch.diagonal(Td).clone(), X, status
 
 
 def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, tensor=False, status=None, workspace=None):

@@ -82,13 +82,13 @@ static OzakiBufs carve(void *ws, int m, int n) {
   return o;
 }
 
-// e_r for every row of triu(U): one warp per row.
-__global__ void k_oz_rowexp(const double2 *U, long long ldu, int m, int *rexp) {
+// e_r for every row of triu(U) (or of the whole matrix with full): one warp per row.
+__global__ void k_oz_rowexp(const double2 *U, long long ldu, int m, int *rexp, int full) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= m) return;
   int e = -(1 << 29);
-  for (int k = r + lane; k < m; k += 32) e = max(e, bound_exp(U[r + (long long)k * ldu]));
+  for (int k = (full ? 0 : r) + lane; k < m; k += 32) e = max(e, bound_exp(U[r + (long long)k * ldu]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if (lane == 0) rexp[r] = e < -(1 << 28) ? 0 : e;
@@ -96,14 +96,14 @@ __global__ void k_oz_rowexp(const double2 *U, long long ldu, int m, int *rexp) {
 
 // Digit planes of A': plane s, row i, column k' at Ap[(s * 2m + i) * K + k'].
 // Thread (k, r) writes rows 2r, 2r+1 at columns 2k, 2k+1 of every plane
-// (zero outside the upper triangle and in the padding).
+// (zero outside the upper triangle unless full, and in the padding).
 __global__ void k_oz_slice_A(const double2 *U, long long ldu, int m, const int *rexp,
-                             __nv_bfloat16 *Ap, int K) {
+                             __nv_bfloat16 *Ap, int K, int full) {
   const int r = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * k >= K) return;
   float dr[kOzS], di[kOzS];
-  if (k >= r && k < m) {
+  if ((full || k >= r) && k < m) {
     const double2 u = U[r + (long long)k * ldu];
     digits8(u.x, rexp[r], dr);
     digits8(u.y, rexp[r], di);
@@ -122,14 +122,16 @@ __global__ void k_oz_slice_A(const double2 *U, long long ldu, int m, const int *
 }
 
 // Digit planes of B' = X (as real): plane t, column j, k' at Bp[(t * n + j) * K + k'],
-// with the column exponent f_j; one CTA per column.
+// with the column exponent f_j (triu: X upper triangular, rows k > j read as
+// zero); one CTA per column.
 __global__ void k_oz_slice_B(const double2 *X, long long ldx, int m, int n, int *cexp,
-                             __nv_bfloat16 *Bp, int K) {
+                             __nv_bfloat16 *Bp, int K, int triu) {
   __shared__ int red[32];
   const int j = blockIdx.x;
   const double2 *col = X + (long long)j * ldx;
+  const int mend = triu ? min(m, j + 1) : m;         // rows read (upper triangle only with triu)
   int e = -(1 << 29);
-  for (int k = threadIdx.x; k < m; k += blockDim.x) e = max(e, bound_exp(col[k]));
+  for (int k = threadIdx.x; k < mend; k += blockDim.x) e = max(e, bound_exp(col[k]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
@@ -140,7 +142,7 @@ __global__ void k_oz_slice_B(const double2 *X, long long ldx, int m, int n, int 
   if (threadIdx.x == 0) cexp[j] = e;
   for (int k = threadIdx.x; 2 * k < K; k += blockDim.x) {
     float dr[kOzS], di[kOzS];
-    if (k < m) {
+    if (k < mend) {
       const double2 x = col[k];
       digits8(x.x, e, dr);
       digits8(x.y, e, di);
@@ -162,7 +164,10 @@ __global__ void k_oz_slice_B(const double2 *X, long long ldx, int m, int n, int 
 //             B(r, col) = 2^-pend(col) B(r, col) - P(r, col) over real rows
 //             [row_lo, row_hi) of A' and `ncols` columns starting at col_base,
 //             K' = the chunks of this block (a_x0 = its first column in the
-//             block-layout planes).
+//             block-layout planes);
+//  kProduct:  R = P over rows [0, 2m) (A dense; with triu_b the K' chunks
+//             below the column tile's last diagonal entry are skipped, B being
+//             upper triangular).
 struct OzArgs {
   const double2 *B; long long ldb;    // residual: right-hand side; update: matrix updated in place
   const double2 *X; long long ldx;    // residual only
@@ -175,10 +180,11 @@ struct OzArgs {
   int a_x0;                           // update: first K' column of this block in the A planes
   int row_lo, row_hi;                 // update: real rows of A' updated
   int col_base, ncols;                // update: global column of local column 0, local columns
+  int triu_b;                         // product: B upper triangular
   uint32_t *status;
 };
 
-enum { kResidual = 0, kUpdate = 1 };
+enum { kResidual = 0, kUpdate = 1, kProduct = 2 };
 
 template <int MODE>
 __global__ void __launch_bounds__(kOzThreads, 1)
@@ -197,9 +203,12 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = (MODE == kUpdate ? args.row_lo : 0) + blockIdx.y * kOzBM;   // first real row
   const int j0 = blockIdx.x * kOzBN;                                         // first local column
-  // Residual: U is upper, so K' columns below the tile's first row vanish.
+  // Residual: U is upper, so K' columns below the tile's first row vanish;
+  // product with an upper-triangular B: K' rows past the tile's last column do.
   const int c_begin = MODE == kResidual ? i0 / kOzKC : 0;
-  const int nch = args.K / kOzKC - c_begin;
+  const int nch = MODE == kProduct && args.triu_b
+                      ? min(args.K / kOzKC, (2 * (j0 + kOzBN) + kOzKC - 1) / kOzKC)
+                      : args.K / kOzKC - c_begin;
   const int ax0 = MODE == kUpdate ? args.a_x0 : 0;
 
   if (warp == 0) tmem_alloc(&tmem_base, 512);
@@ -309,16 +318,18 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (!ok) fail = 1;
     // P = 2^(e_r + f_j) (hi 2^-28 + lo 2^-63)
     const int i = i0 + 32 * warp + lane;                     // real row of A'
-    const bool row_ok = MODE == kResidual ? i < 2 * args.m : i < args.row_hi;
+    const bool row_ok = MODE != kUpdate ? i < 2 * args.m : i < args.row_hi;
     if (ok && row_ok) {
       const int r = i >> 1, part = i & 1;
       const int er = args.rexp[r];
 #pragma unroll
       for (int j = 0; j < kOzBN; ++j) {
         const int lc = j0 + j;
-        if (lc >= (MODE == kResidual ? args.n : args.ncols)) continue;
+        if (lc >= (MODE != kUpdate ? args.n : args.ncols)) continue;
         const double p = scalbn(fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-63), er + args.cexp[lc]);
-        if (MODE == kResidual) {
+        if (MODE == kProduct) {
+          reinterpret_cast<double *>(args.R + r + (long long)lc * args.ldr)[part] = p;
+        } else if (MODE == kResidual) {
           const double2 x = args.X[r + (long long)lc * args.ldx];
           const double2 sj = args.s[lc];
           const double2 b = args.B[r + (long long)lc * args.ldb];
@@ -387,8 +398,8 @@ static bool make_map(CUtensorMap *map, void *ptr, int K, int rows, int box_rows,
 
 cudaError_t ozaki_prepare(const double2 *U, long long ldu, int m, int n, void *ws, cudaStream_t st) {
   OzakiBufs o = carve(ws, m, n);
-  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(U, ldu, m, o.rexp);
-  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(U, ldu, m, o.rexp, o.Ap, o.K);
+  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(U, ldu, m, o.rexp, 0);
+  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(U, ldu, m, o.rexp, o.Ap, o.K, 0);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -398,7 +409,7 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
                            double2 *R, long long ldr, void *ws, uint32_t *status, cudaStream_t st) {
   (void)U; (void)ldu;
   OzakiBufs o = carve(ws, m, n);
-  k_oz_slice_B<<<n, 256, 0, st>>>(X, ldx, m, n, o.cexp, o.Bp, o.K);
+  k_oz_slice_B<<<n, 256, 0, st>>>(X, ldx, m, n, o.cexp, o.Bp, o.K, 0);
   count_launches(1);
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, o.Ap, o.K, 2 * m, kOzBM, 1) || !make_map(&tmB, o.Bp, o.K, n, kOzBN, kOzS))
@@ -422,6 +433,38 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
   void *h = trace_on() ? trace_start(2, mma_flops, (double)kOzS * (2.0 * m * o.K + (double)n * o.K), st)
                        : nullptr;
   k_oz_gemm<kResidual><<<dim3((n + kOzBN - 1) / kOzBN, (2 * m + kOzBM - 1) / kOzBM), kOzThreads, kOzSmem, st>>>(tmA, tmB, a);
+  trace_stop(h, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_product(const double2 *A, long long lda, int m, const double2 *Bm, long long ldbm, int n,
+                          bool triu_b, double2 *C, long long ldc, void *ws, uint32_t *status, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  OzakiBufs o = carve(ws, m, n);
+  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(A, lda, m, o.rexp, 1);
+  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(A, lda, m, o.rexp, o.Ap, o.K, 1);
+  k_oz_slice_B<<<n, 256, 0, st>>>(Bm, ldbm, m, n, o.cexp, o.Bp, o.K, triu_b ? 1 : 0);
+  count_launches(3);
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, o.Ap, o.K, 2 * m, kOzBM, 1) || !make_map(&tmB, o.Bp, o.K, n, kOzBN, kOzS))
+    return cudaErrorNotSupported;
+  OzArgs a{};
+  a.R = C; a.ldr = ldc;
+  a.rexp = o.rexp; a.cexp = o.cexp; a.m = m; a.n = n; a.K = o.K; a.triu_b = triu_b ? 1 : 0;
+  a.status = status ? status : abort_word();
+  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kProduct>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  if (e != cudaSuccess) return e;
+  // BF16 MMA FLOPs issued: per tile, its K' chunks of 36 digit pairs x 4
+  // K-steps of 128 x 32 x 16.
+  double chunks = 0.0;
+  const int tiles_n = (n + kOzBN - 1) / kOzBN, tiles_m = (2 * m + kOzBM - 1) / kOzBM;
+  for (int x = 0; x < tiles_n; ++x)
+    chunks += triu_b ? std::min(o.K / kOzKC, (2 * (x * kOzBN + kOzBN) + kOzKC - 1) / kOzKC) : o.K / kOzKC;
+  const double mma_flops = chunks * tiles_m * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+  void *h = trace_on() ? trace_start(2, mma_flops, (double)kOzS * (2.0 * m * o.K + (double)n * o.K), st)
+                       : nullptr;
+  k_oz_gemm<kProduct><<<dim3(tiles_n, tiles_m), kOzThreads, kOzSmem, st>>>(tmA, tmB, a);
   trace_stop(h, st);
   count_launches(1);
   return cudaGetLastError();

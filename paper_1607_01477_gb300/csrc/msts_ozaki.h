@@ -16,6 +16,10 @@ cudaError_t ozaki_prepare(const double2 *U, long long ldu, int m, int n, void *w
 cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2 *s, int n,
                            const double2 *B, long long ldb, const double2 *X, long long ldx,
                            double2 *R, long long ldr, void *ws, uint32_t *status, cudaStream_t st);
+// C = A B (m x m dense A, m x n B; B upper triangular when triu_b), FP64-accurate
+// on the tensor cores; workspace ozaki_workspace_bytes(m, n).
+cudaError_t ozaki_product(const double2 *A, long long lda, int m, const double2 *Bm, long long ldbm, int n,
+                          bool triu_b, double2 *C, long long ldc, void *ws, uint32_t *status, cudaStream_t st);
 // Tensor-core substitution step of the blocked solve: the block-layout digit
 // planes of U (upper, or conjugate-transposed for forward substitution) and
 // a per-step buffer for the planes of the solved block X(I1,:).

@@ -31,7 +31,7 @@ def declared_functions():
 def test_header_declares_entry_points():
     names = declared_functions()
     for n in ["msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra",
-              "msts_adjoint", "msts_adjoint_batched", "msts_version"]:
+              "msts_adjoint", "msts_adjoint_batched", "msts_back_transform", "msts_version"]:
         assert n in names
 
 
@@ -73,3 +73,19 @@ def test_workspace_sizes(lib):
     assert lib.msts_trevc_workspace_size(64, 32, 0) == lib.msts_solve_workspace_size(64, 64, 32, 1)
     assert lib.msts_trevc_workspace_size(64, 32, 8) > lib.msts_trevc_workspace_size(64, 32, 0)
     assert lib.msts_pseudospectra_workspace_size(50, 7, 20, 32, 0) >= 21 * 50 * 7 * 16
+
+
+def test_back_transform_arguments_and_workspace(lib):
+    P = ctypes.c_void_p(16)
+    assert lib.msts_back_transform_workspace_size(64, 0) == 0
+    assert lib.msts_back_transform_workspace_size(64, 8) > 8 * 2 * 64 * 64 * 2
+    assert lib.msts_back_transform_workspace_size(-1, 8) == 0
+    # negative m, ldq < m, ldz < m, ldx < m, unknown flags, missing / small workspace
+    assert lib.msts_back_transform(P, 4, -1, P, 4, P, 4, None, 0, None, 0, None) == -3
+    assert lib.msts_back_transform(P, 3, 4, P, 4, P, 4, None, 0, None, 0, None) == -2
+    assert lib.msts_back_transform(P, 4, 4, P, 3, P, 4, None, 0, None, 0, None) == -5
+    assert lib.msts_back_transform(P, 4, 4, P, 4, P, 3, None, 0, None, 0, None) == -7
+    assert lib.msts_back_transform(P, 4, 4, P, 4, P, 4, None, 0, None, 32, None) == -11
+    assert lib.msts_back_transform(P, 4, 4, P, 4, P, 4, None, 0, None, 8, None) == -8
+    assert lib.msts_back_transform(P, 4, 4, P, 4, P, 4, P, 16, None, 8, None) == -9
+    assert lib.msts_back_transform(None, 1, 0, None, 1, None, 1, None, 0, None, 0, None) == 0
