@@ -418,7 +418,60 @@ def extra_measurements(dev, nb):
     del graph, sig_g, sigs
     res["batched_adjoint_64x(256..2048)x32"] = batched_fwd_bwd(dev, nb)
     res["mixed_8192x2048"] = mixed_vs_fp64(dev, nb)
+    res["eig_back_transform_4096"] = back_transform_extra(dev, nb)
     return res
+
+
+def back_transform_extra(dev, nb):
+    """Alg. 6's second half at the TREVC workload's size: X = Q Z for the 4096
+    triangular eigenvectors Z and a random unitary Q (FLOPs 4 m^3: Z upper
+    triangular), both product paths, with the eigen-residual of A = Q T Q^H;
+    and the whole Eig driver (host Schur + GPU TREVC + GPU back-transformation)
+    on a random 1000 x 1000 matrix, with the host Schur time split out."""
+    import torch
+    import scipy.linalg
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    m = 4096
+    T = W.trevc_problem()
+    Td = msts.colmajor(torch.from_numpy(T).to(dev))
+    Z, *_ = msts.msts_trevc(Td, nb=nb, tensor=True)
+    g = torch.Generator(device=dev).manual_seed(1607)
+    Qd, _ = torch.linalg.qr(torch.randn((m, m), dtype=torch.complex128, device=dev, generator=g))
+    Qd = msts.colmajor(Qd)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for tag, tensor in (("fp64_gemm", False), ("tensor_gemm", True)):
+        X, _ = msts.msts_back_transform(Qd, Z, tensor=tensor, normalize=True)   # warm-up
+        torch.cuda.synchronize()
+        e0.record()
+        X, _ = msts.msts_back_transform(Qd, Z, tensor=tensor, normalize=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[tag] = {"ms": ms, "tflops": 4.0 * m ** 3 / (ms * 1e-3) / 1e12}
+    A = Qd @ torch.triu(Td) @ Qd.conj().T
+    lam = torch.diagonal(Td)
+    out["eigen_residual"] = (torch.linalg.norm(A @ X - X * lam[None, :]) / torch.linalg.norm(A)).item()
+    del A, X, Qd, Z
+    # the whole driver on a general matrix
+    me = 1000
+    Ah = W.cn(W.rng(0, 1000), (me, me))
+    t0 = time.perf_counter()
+    scipy.linalg.schur(Ah, output="complex")
+    schur_s = time.perf_counter() - t0
+    msts.eig(Ah, nb=nb, tensor=True)              # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w, X, _ = msts.eig(Ah, nb=nb, tensor=True)
+    torch.cuda.synchronize()
+    total_s = time.perf_counter() - t0
+    Ad = torch.from_numpy(Ah).to(dev)
+    out["eig_driver_1000"] = {"total_ms": total_s * 1e3, "host_schur_ms": schur_s * 1e3,
+                              "gpu_and_copies_ms": (total_s - schur_s) * 1e3,
+                              "eigen_residual": (torch.linalg.norm(Ad @ X - X * w[None, :])
+                                                 / torch.linalg.norm(Ad)).item()}
+    return out
 
 
 def batched_fwd_bwd(dev, nb):
