@@ -166,6 +166,47 @@ def trevc(T, nb):
     return Z, e, sc
 
 
+def gsolve(U, V, shifts, B):
+    """Alg. 8 per shift (plain definition): x_j = (U - s_j V)^{-1} b_j."""
+    U = _cz(U, "U")
+    V = _cz(V, "V")
+    s = np.ascontiguousarray(shifts, dtype=np.complex128)
+    X = np.array(B, dtype=np.complex128, order="F", copy=True)
+    m, n = X.shape
+    _load().or_gmultishift_solve(_c_int64(m), _p(U), _c_int64(_ld(U)), _p(V), _c_int64(_ld(V)), _c_int64(n),
+                                 _p(s), _p(X), _c_int64(_ld(X)))
+    return X
+
+
+def safe_gsolve(U, V, shifts, B, nb, shortcut=False):
+    """Alg. 9 (SafeGeneralizedMultiShiftTrsm): (U - s_j V) x_j = 2^-e_j b_j; returns (X, e)."""
+    U = _cz(U, "U")
+    V = _cz(V, "V")
+    s = np.ascontiguousarray(shifts, dtype=np.complex128)
+    X = np.array(B, dtype=np.complex128, order="F", copy=True)
+    m, n = X.shape
+    e = np.zeros(n, dtype=np.int32)
+    _load().or_safe_gmultishift_solve(_c_int64(m), _p(U), _c_int64(_ld(U)), _p(V), _c_int64(_ld(V)),
+                                      _c_int64(n), _p(s), _p(X), _c_int64(_ld(X)), _c_int64(nb),
+                                      ctypes.c_int(1 if shortcut else 0), _p(e))
+    return X, e
+
+
+def gtrevc(T, S, nb):
+    """Alg. 10 (GeneralizedTriangEig): returns (Z, lam, e, scales) with
+    lam = diag(T) ./ diag(S), T Z(:,j) = lam_j S Z(:,j), diag(Z) = 2^-e."""
+    T = _cz(T, "T")
+    S = _cz(S, "S")
+    m = T.shape[0]
+    Z = np.zeros((m, m), dtype=np.complex128, order="F")
+    lam = np.zeros(m, dtype=np.complex128)
+    e = np.zeros(m, dtype=np.int32)
+    sc = np.zeros(m, dtype=np.float64)
+    _load().or_gtrevc(_c_int64(m), _p(T), _c_int64(_ld(T)), _p(S), _c_int64(_ld(S)), _p(Z), _c_int64(_ld(Z)),
+                      _p(lam), _c_int64(nb), _p(e), _p(sc))
+    return Z, lam, e, sc
+
+
 def back_transform(Q, Z):
     """X = Q triu(Z) (the eigenvectors of A = Q T Q^H from those of T, Alg. 6)."""
     Q = _cz(Q, "Q")

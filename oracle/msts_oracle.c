@@ -538,6 +538,206 @@ void or_adjoint(int64_t m, const oz *U, int64_t ldu, int64_t n, const oz *shifts
 
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 /* ------------------------------------------------------------------------
+ * Generalized multi-shift triangular solve (appendix, Alg. 8):
+ * (U - lambda_j V) x_j = b_j with U, V upper triangular.  Plain definition,
+ * per shift: unblocked back substitution on U - lambda V, whose entries are
+ * formed as U(r,i) - lambda V(r,i).
+ * ---------------------------------------------------------------------- */
+static inline oz gentry(const oz *U, int64_t ldu, const oz *V, int64_t ldv, oz lambda, int64_t r, int64_t c) {
+  return oz_sub(AT(U, ldu, r, c), oz_mul(lambda, AT(V, ldv, r, c)));
+}
+
+static void trsv_gshift(int64_t m, const oz *U, int64_t ldu, const oz *V, int64_t ldv, oz lambda, oz *b) {
+  for (int64_t i = m - 1; i >= 0; --i) {
+    b[i] = oz_div(b[i], gentry(U, ldu, V, ldv, lambda, i, i));   /* diagonal step */
+    oz xi = b[i];
+    for (int64_t r = 0; r < i; ++r)                               /* AXPY */
+      b[r] = oz_sub(b[r], oz_mul(xi, gentry(U, ldu, V, ldv, lambda, r, i)));
+  }
+}
+
+void or_gmultishift_solve(int64_t m, const oz *U, int64_t ldu, const oz *V, int64_t ldv, int64_t n,
+                          const oz *shifts, oz *B, int64_t ldb) {
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) trsv_gshift(m, U, ldu, V, ldv, shifts[j], &AT(B, ldb, 0, j));
+}
+
+/* Alg. 4 on the k x k block U' = A - lambda W (A, W the diagonal blocks of U
+ * and V): as safe_trsv, with the pivots and AXPY entries of U' and the column
+ * bounds cnorm[i] = cnU[i] + |lambda| cnV[i] >= max_{r<i} |U'(r,i)|. */
+static int safe_gtrsv(int64_t k, const oz *A, int64_t lda, const oz *Wv, int64_t ldw, oz lambda,
+                      double delta, const double *cnU, const double *cnV, oz *b) {
+  const double OM = omega();
+  if (k <= 0) return 0;
+  const double al = oz_abs(lambda);
+  oz *piv = (oz *)malloc(sizeof(oz) * (size_t)k);
+  double *cnorm = (double *)malloc(sizeof(double) * (size_t)k);
+  for (int64_t i = 0; i < k; ++i) {
+    piv[i] = gentry(A, lda, Wv, ldw, lambda, i, i);
+    if (oz_is_zero(piv[i])) piv[i] = oz_make(delta, 0.0);   /* U'(i,i)=0 -> delta */
+    cnorm[i] = cnU[i] + al * cnV[i];
+  }
+  double M = 0.0, G = 0.0;
+  for (int64_t i = 0; i < k; ++i) { double a = oz_abs(b[i]); if (a > G) G = a; }
+  for (int64_t i = k - 1; i >= 0; --i) {
+    double ap = oz_abs(piv[i]);
+    double q = G / ap;
+    if (q > M) M = q;
+    G = G * (1.0 + cnorm[i] / ap);
+  }
+  int kexp = 0;
+  if (M < OM && G < OM) {
+    for (int64_t i = k - 1; i >= 0; --i) {
+      b[i] = oz_div(b[i], piv[i]);
+      oz xi = b[i];
+      for (int64_t r = 0; r < i; ++r) b[r] = oz_sub(b[r], oz_mul(xi, gentry(A, lda, Wv, ldw, lambda, r, i)));
+    }
+    free(piv); free(cnorm);
+    return 0;
+  }
+  G = 0.0;
+  for (int64_t i = 0; i < k; ++i) { double a = oz_abs(b[i]); if (a > G) G = a; }
+  for (int64_t i = k - 1; i >= 0; --i) {
+    double Mi;
+    int eM = split_ratio(oz_abs(b[i]), oz_abs(piv[i]), 0, &Mi);
+    if (eM >= OR_OMEGA_EXP) {
+      int kk = eM - (OR_OMEGA_EXP - 1);
+      if (kk < 1) kk = 1;
+      for (int64_t r = 0; r < k; ++r) b[r] = oz_ldexp(b[r], -kk);
+      kexp += kk;
+      G = ldexp(G, -kk);
+    }
+    b[i] = oz_div(b[i], piv[i]);
+    M = oz_abs(b[i]);
+    G = G + M * cnorm[i];
+    if (G >= OM) {
+      int kk = choose_k(G);
+      for (int64_t r = 0; r < k; ++r) b[r] = oz_ldexp(b[r], -kk);
+      kexp += kk;
+      M = ldexp(M, -kk);
+      G = ldexp(G, -kk);
+    }
+    oz xi = b[i];
+    for (int64_t r = 0; r < i; ++r) b[r] = oz_sub(b[r], oz_mul(xi, gentry(A, lda, Wv, ldw, lambda, r, i)));
+  }
+  free(piv); free(cnorm);
+  return kexp;
+}
+
+/* Shift-independent data of Alg. 9: within-block column norms and the block
+ * sums C_blk of U and of V, and ||U||_inf, ||V||_inf for delta. */
+typedef struct { double *cinU, *cinV, *cblkU, *cblkV; double nU, nV; int64_t nblk; } gsafe_prep;
+
+static void colnorm_blocks(int64_t m, const oz *U, int64_t ldu, int64_t nb, int64_t nblk, double *cin,
+                           double *cblk) {
+  for (int64_t b = 0; b < nblk; ++b) {
+    int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
+    double C = 0.0;
+    for (int64_t k = lo; k < hi; ++k) {
+      double c = 0.0, cu = 0.0;
+      for (int64_t r = lo; r < k; ++r) { double a = oz_abs(AT(U, ldu, r, k)); if (a > c) c = a; }
+      for (int64_t r = 0; r < lo; ++r) { double a = oz_abs(AT(U, ldu, r, k)); if (a > cu) cu = a; }
+      cin[k] = c;
+      C += cu;
+    }
+    cblk[b] = C;
+  }
+}
+
+static gsafe_prep gsafe_prepare(int64_t m, const oz *U, int64_t ldu, const oz *V, int64_t ldv, int64_t nb) {
+  gsafe_prep P;
+  P.nblk = (m + nb - 1) / nb;
+  size_t mm = (size_t)(m > 0 ? m : 1), nn = (size_t)(P.nblk > 0 ? P.nblk : 1);
+  P.cinU = (double *)malloc(sizeof(double) * mm);
+  P.cinV = (double *)malloc(sizeof(double) * mm);
+  P.cblkU = (double *)malloc(sizeof(double) * nn);
+  P.cblkV = (double *)malloc(sizeof(double) * nn);
+  colnorm_blocks(m, U, ldu, nb, P.nblk, P.cinU, P.cblkU);
+  colnorm_blocks(m, V, ldv, nb, P.nblk, P.cinV, P.cblkV);
+  P.nU = or_norm_inf_upper(m, U, ldu);
+  P.nV = or_norm_inf_upper(m, V, ldv);
+  return P;
+}
+
+static void gsafe_release(gsafe_prep *P) { free(P->cinU); free(P->cinV); free(P->cblkU); free(P->cblkV); }
+
+/* Alg. 9 for one column x with shift lambda; rows >= end are zero and never
+ * visited.  Readings: the within-block SafeTrsv uses the column bounds of
+ * safe_gtrsv; delta_j = max(eps (||U||_inf + |lambda| ||V||_inf), DBL_MIN); the
+ * block bound is (C_blk(U) + |lambda| C_blk(V)) ||B(I1,j)||_inf, and the
+ * update subtracts U(I0,I1) X(I1,j) and then adds V(I0,I1) (lambda X(I1,j)). */
+static int gsafe_column(int64_t m, const oz *U, int64_t ldu, const oz *V, int64_t ldv, int64_t nb,
+                        const gsafe_prep *P, oz lambda, oz *x, int64_t end) {
+  const double OM = omega();
+  const double al = oz_abs(lambda);
+  double delta = DBL_EPSILON * (P->nU + al * P->nV);
+  if (delta < DBL_MIN) delta = DBL_MIN;
+  int e = 0;
+  double G = 0.0;
+  for (int64_t r = 0; r < end; ++r) { double a = oz_abs(x[r]); if (a > G) G = a; }
+  for (int64_t b = 0; b < P->nblk; ++b) {
+    int64_t hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb;
+    if (lo >= end) continue;
+    int64_t hie = hi < end ? hi : end;
+    int kk = safe_gtrsv(hie - lo, &AT(U, ldu, lo, lo), ldu, &AT(V, ldv, lo, lo), ldv, lambda, delta,
+                        &P->cinU[lo], &P->cinV[lo], &x[lo]);
+    if (kk > 0) {
+      for (int64_t r = 0; r < lo; ++r) x[r] = oz_ldexp(x[r], -kk);
+      for (int64_t r = hie; r < end; ++r) x[r] = oz_ldexp(x[r], -kk);
+      e += kk;
+      G = ldexp(G, -kk);
+    }
+    double N = 0.0;
+    for (int64_t r = lo; r < hie; ++r) { double a = oz_abs(x[r]); if (a > N) N = a; }
+    G = G + (P->cblkU[b] + al * P->cblkV[b]) * N;
+    if (G >= OM) {
+      int k2 = choose_k(G);
+      for (int64_t r = 0; r < end; ++r) x[r] = oz_ldexp(x[r], -k2);
+      e += k2;
+      G = ldexp(G, -k2);
+    }
+    for (int64_t k = lo; k < hie; ++k) {                     /* B(I0,j) -= U(I0,I1) X(I1,j) */
+      oz xk = x[k];
+      for (int64_t r = 0; r < lo; ++r) x[r] = oz_sub(x[r], oz_mul(AT(U, ldu, r, k), xk));
+    }
+    for (int64_t k = lo; k < hie; ++k) {                     /* B(I0,j) += V(I0,I1) C(:,j) */
+      oz ck = oz_mul(lambda, x[k]);
+      for (int64_t r = 0; r < lo; ++r) x[r] = oz_add(x[r], oz_mul(AT(V, ldv, r, k), ck));
+    }
+  }
+  return e;
+}
+
+void or_safe_gmultishift_solve(int64_t m, const oz *U, int64_t ldu, const oz *V, int64_t ldv, int64_t n,
+                               const oz *shifts, oz *B, int64_t ldb, int64_t nb, int shortcut,
+                               int32_t *scale_exp) {
+  gsafe_prep P = gsafe_prepare(m, U, ldu, V, ldv, nb);
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t end = shortcut ? (j < m ? j : m) : m;
+    scale_exp[j] = gsafe_column(m, U, ldu, V, ldv, nb, &P, shifts[j], &AT(B, ldb, 0, j), end);
+  }
+  gsafe_release(&P);
+}
+
+/* Alg. 10 (GeneralizedTriangEig): lambda = diag(T) ./ diag(S) (S(j,j) != 0);
+ * Z = -T + S diag(lambda) strictly above the diagonal, zero elsewhere;
+ * SafeGeneralizedMultiShiftTrsm with the strictly-upper shortcut; diag(Z) = s. */
+void or_gtrevc(int64_t m, const oz *T, int64_t ldt, const oz *S, int64_t lds, oz *Z, int64_t ldz,
+               oz *lam, int64_t nb, int32_t *scale_exp, double *scales) {
+  for (int64_t j = 0; j < m; ++j) {
+    lam[j] = oz_div(AT(T, ldt, j, j), AT(S, lds, j, j));
+    for (int64_t r = 0; r < m; ++r)
+      AT(Z, ldz, r, j) = r < j ? oz_sub(oz_mul(lam[j], AT(S, lds, r, j)), AT(T, ldt, r, j)) : oz_make(0.0, 0.0);
+  }
+  or_safe_gmultishift_solve(m, T, ldt, S, lds, m, lam, Z, ldz, nb, 1, scale_exp);
+  for (int64_t j = 0; j < m; ++j) {
+    scales[j] = ldexp(1.0, -scale_exp[j]);
+    AT(Z, ldz, j, j) = oz_make(scales[j], 0.0);
+  }
+}
+
+/* ------------------------------------------------------------------------
  * Back-transformation (Sec. 4, Alg. 6 "Eig"): the eigenvectors of
  * A = Q T Q^H are X = Q Z, Z upper triangular (only its upper triangle is
  * read).  Plain definition: X(i,j) = sum_{k <= j} Q(i,k) Z(k,j), summed in
