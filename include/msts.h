@@ -141,6 +141,45 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m,
                uint32_t *status, uint32_t flags, void *stream);   /* flags: 0 or MSTS_TENSOR_GEMM */
 
 /* ---------------------------------------------------------------------------
+ * Generalized multi-shift triangular solve (appendix, Alg. 8; safe form
+ * Alg. 9): for U, V upper triangular (m x m; only their upper triangles are
+ * read),
+ *   (U - shifts[j] V) X(:,j) = scale_j B(:,j),
+ * B (m x n, ldb) overwritten with X. flags: 0 (Alg. 8, scale_j = 1) or
+ * MSTS_SAFE (Alg. 9 with Alg. 4 on each shifted diagonal block; scales and
+ * scale_exp as for msts_solve). Readings: the column bounds of U - s_j V are
+ * ||U(.,k)|| + |s_j| ||V(.,k)|| (rigorous upper bounds), and an exactly zero
+ * pivot U(i,i) - s_j V(i,i) becomes delta_j = max(2^-52 (||U||_inf +
+ * |s_j| ||V||_inf), DBL_MIN). FP64 FMA throughout (no MSTS_TENSOR_GEMM).
+ * workspace: msts_gsolve_workspace_size(m, n, nb, flags) bytes.
+ * Returns 0, -k for invalid argument k (nothing launched; -13/-14 for a
+ * missing / too small workspace, -16 for unsupported flags), MSTS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+size_t msts_gsolve_workspace_size(int64_t m, int64_t n, int32_t nb, uint32_t flags);
+int msts_gsolve(const msts_z *U, int64_t ldu, const msts_z *V, int64_t ldv, int64_t m,
+                const msts_z *shifts, int64_t n,
+                msts_z *B, int64_t ldb,
+                double *scales, int32_t *scale_exp,
+                int32_t nb, void *workspace, size_t workspace_bytes,
+                uint32_t *status, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Generalized triangular eigenvectors (appendix, Alg. 10
+ * "GeneralizedTriangEig"): for the generalized Schur pair (T, S), both upper
+ * triangular with S(j,j) != 0, writes lambda[j] = T(j,j) / S(j,j) and the upper
+ * triangular Z with T Z(:,j) = lambda[j] S Z(:,j), Z(j,j) = scales[j] =
+ * 2^-scale_exp[j] (right-hand sides -T(0:j-1,j) + lambda[j] S(0:j-1,j), the
+ * strictly-upper shortcut as in msts_trevc). flags must be 0.
+ * workspace: msts_gtrevc_workspace_size(m, nb, 0) bytes.
+ * ------------------------------------------------------------------------- */
+size_t msts_gtrevc_workspace_size(int64_t m, int32_t nb, uint32_t flags);
+int msts_gtrevc(const msts_z *T, int64_t ldt, const msts_z *S, int64_t lds, int64_t m,
+                msts_z *Z, int64_t ldz, msts_z *lambda,
+                double *scales, int32_t *scale_exp,
+                int32_t nb, void *workspace, size_t workspace_bytes,
+                uint32_t *status, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Back-transformation (Sec. 4, Alg. 6 "Eig", second half): the eigenvectors
  * of A = Q T Q^H are the columns of X = Q Z, with Z the upper triangular
  * eigenvectors of T from msts_trevc.

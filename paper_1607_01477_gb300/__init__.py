@@ -27,6 +27,7 @@ __all__ = [
     "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
     "msts_adjoint_batched", "msts_solve_mixed", "msts_residual", "MSTS_RESIDUAL_OZAKI",
     "MSTS_TENSOR_GEMM", "MSTS_NORMALIZE_COLUMNS", "msts_back_transform", "eig",
+    "msts_gsolve", "msts_gtrevc", "geig",
     "MultiShiftSolve", "multishift_solve",
     "decode_status",
 ]
@@ -116,6 +117,16 @@ def load_library():
         lib.msts_residual.restype = ctypes.c_int
         lib.msts_residual.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                                       _vp, _sz, _vp, _u32, _vp]
+        lib.msts_gsolve_workspace_size.restype = _sz
+        lib.msts_gsolve_workspace_size.argtypes = [_i64, _i64, _i32, _u32]
+        lib.msts_gsolve.restype = ctypes.c_int
+        lib.msts_gsolve.argtypes = [_vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i32, _vp, _sz,
+                                    _vp, _u32, _vp]
+        lib.msts_gtrevc_workspace_size.restype = _sz
+        lib.msts_gtrevc_workspace_size.argtypes = [_i64, _i32, _u32]
+        lib.msts_gtrevc.restype = ctypes.c_int
+        lib.msts_gtrevc.argtypes = [_vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp, _sz, _vp,
+                                    _u32, _vp]
         lib.msts_back_transform_workspace_size.restype = _sz
         lib.msts_back_transform_workspace_size.argtypes = [_i64, _u32]
         lib.msts_back_transform.restype = ctypes.c_int
@@ -267,6 +278,70 @@ def msts_trevc(T, *, nb=32, tensor=False, status=None):
                         _ptr(status), flags, _stream(dev))
     _check(rc, "msts_trevc")
     return Z, sc, se, status
+
+
+def msts_gsolve(U, V, shifts, B, *, safe=False, nb=32, status=None):
+    """Generalized multi-shift solve (Alg. 8; Alg. 9 with safe=True): B is
+    overwritten with X, (U - s_j V) X(:,j) = scale_j B(:,j).
+    Returns (B, scales, scale_exp, status); scales/scale_exp are None unless safe."""
+    lib = load_library()
+    m, n = B.shape
+    ldu = _mat(U, "U", m)
+    ldv = _mat(V, "V", m)
+    ldb = _mat(B, "B", m)
+    dev = B.device
+    s = shifts.contiguous()
+    sc = torch.empty(n, dtype=torch.float64, device=dev) if safe else None
+    se = torch.empty(n, dtype=torch.int32, device=dev) if safe else None
+    flags = MSTS_SAFE if safe else 0
+    ws = _workspace(lib.msts_gsolve_workspace_size(m, n, nb, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_gsolve(_ptr(U), ldu, _ptr(V), ldv, m, _ptr(s), n, _ptr(B), ldb, _ptr(sc), _ptr(se), nb, wp, wb,
+                         _ptr(status), flags, _stream(dev))
+    _check(rc, "msts_gsolve")
+    return B, sc, se, status
+
+
+def msts_gtrevc(T, S, *, nb=32, status=None):
+    """Generalized triangular eigenvectors (Alg. 10): returns (Z, lam, scales,
+    scale_exp, status) with lam = diag(T) / diag(S), T Z = S Z diag(lam)."""
+    lib = load_library()
+    m = T.shape[0]
+    ldt = _mat(T, "T", m)
+    lds = _mat(S, "S", m)
+    dev = T.device
+    Z = colmajor(torch.empty((m, m), dtype=torch.complex128, device=dev))
+    lam = torch.empty(m, dtype=torch.complex128, device=dev)
+    sc = torch.empty(m, dtype=torch.float64, device=dev)
+    se = torch.empty(m, dtype=torch.int32, device=dev)
+    ws = _workspace(lib.msts_gtrevc_workspace_size(m, nb, 0), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_gtrevc(_ptr(T), ldt, _ptr(S), lds, m, _ptr(Z), max(1, m), _ptr(lam), _ptr(sc), _ptr(se), nb,
+                         wp, wb, _ptr(status), 0, _stream(dev))
+    _check(rc, "msts_gtrevc")
+    return Z, lam, sc, se, status
+
+
+def geig(A, B, *, nb=32, tensor=True, device=None):
+    """Generalized eigenvalues and unit-norm eigenvectors of the pencil (A, B)
+    (Alg. 10 "GeneralizedEig"): the generalized Schur (QZ) factorisation
+    A = Q T P^H, B = Q S P^H comes from the host library; GeneralizedTriangEig
+    (msts_gtrevc) and X = P Z (msts_back_transform) run on the GPU.
+    Returns (lam, X, status) with A X(:,j) = lam[j] B X(:,j)."""
+    import numpy as np
+    import scipy.linalg
+    A = np.asarray(A.detach().cpu().numpy() if isinstance(A, torch.Tensor) else A, dtype=np.complex128)
+    B = np.asarray(B.detach().cpu().numpy() if isinstance(B, torch.Tensor) else B, dtype=np.complex128)
+    T, S, _, P = scipy.linalg.qz(A, B, output="complex")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    Td = colmajor(torch.from_numpy(np.asfortranarray(T)).to(dev))
+    Sd = colmajor(torch.from_numpy(np.asfortranarray(S)).to(dev))
+    Pd = colmajor(torch.from_numpy(np.asfortranarray(P)).to(dev))
+    Z, lam, _, _, status = msts_gtrevc(Td, Sd, nb=nb)
+    X, status = msts_back_transform(Pd, Z, tensor=tensor, normalize=True, status=status)
+    return lam, X, status
 
 
 def msts_back_transform(Q, Z, *, tensor=False, normalize=False, status=None):

@@ -152,4 +152,73 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m, msts_z *Z, int64_t ldz, 
   return cuda_rc(msts::engine_run(&p, 1, nb, true, false, true, workspace, status, st));
 }
 
+// ----- generalized problems (appendix, Alg. 8-10) ----------------------------
+size_t msts_gsolve_workspace_size(int64_t m, int64_t n, int32_t nb, uint32_t flags) {
+  if (m < 0 || n < 0 || !nb_ok(nb)) return 0;
+  msts::EngineProblem p = make_problem(nullptr, 1, m, nullptr, 1, n, nullptr, 1, nullptr, nullptr, 0);
+  p.V = reinterpret_cast<const double2 *>(16);     // sizes of the generalized form (never read)
+  return align256(msts::engine_workspace_bytes(&p, 1, nb, (flags & MSTS_SAFE) != 0));
+}
+
+int msts_gsolve(const msts_z *U, int64_t ldu, const msts_z *V, int64_t ldv, int64_t m, const msts_z *shifts,
+                int64_t n, msts_z *B, int64_t ldb, double *scales, int32_t *scale_exp, int32_t nb,
+                void *workspace, size_t workspace_bytes, uint32_t *status, uint32_t flags, void *stream) {
+  const bool safe = (flags & MSTS_SAFE) != 0;
+  if (m < 0 || m > kMaxDim) return -5;
+  if (m > 0 && !U) return -1;
+  if (ldu < std::max<int64_t>(1, m)) return -2;
+  if (m > 0 && !V) return -3;
+  if (ldv < std::max<int64_t>(1, m)) return -4;
+  if (n < 0 || n > kMaxDim) return -7;
+  if (n > 0 && !shifts) return -6;
+  if (m > 0 && n > 0 && !B) return -8;
+  if (ldb < std::max<int64_t>(1, m)) return -9;
+  if (safe && n > 0 && (!scales || !scale_exp)) return scales ? -11 : -10;
+  if (!nb_ok(nb)) return -12;
+  if ((flags & ~(uint32_t)MSTS_SAFE) != 0) return -16;
+  const size_t need = msts_gsolve_workspace_size(m, n, nb, flags);
+  if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -14 : -13;
+  if (m == 0 || n == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  msts::EngineProblem p = make_problem(U, ldu, m, shifts, 1, n, B, ldb, scales, scale_exp, 0);
+  p.V = reinterpret_cast<const double2 *>(V);
+  p.ldv = ldv;
+  return cuda_rc(msts::engine_run(&p, 1, nb, safe, false, false, workspace, status, st));
+}
+
+size_t msts_gtrevc_workspace_size(int64_t m, int32_t nb, uint32_t flags) {
+  if (m < 0 || !nb_ok(nb) || flags != 0) return 0;
+  return msts_gsolve_workspace_size(m, m, nb, MSTS_SAFE);
+}
+
+int msts_gtrevc(const msts_z *T, int64_t ldt, const msts_z *S, int64_t lds, int64_t m, msts_z *Z, int64_t ldz,
+                msts_z *lambda, double *scales, int32_t *scale_exp, int32_t nb, void *workspace,
+                size_t workspace_bytes, uint32_t *status, uint32_t flags, void *stream) {
+  if (m < 0 || m > kMaxDim) return -5;
+  if (m > 0 && !T) return -1;
+  if (ldt < std::max<int64_t>(1, m)) return -2;
+  if (m > 0 && !S) return -3;
+  if (lds < std::max<int64_t>(1, m)) return -4;
+  if (m > 0 && !Z) return -6;
+  if (ldz < std::max<int64_t>(1, m)) return -7;
+  if (m > 0 && !lambda) return -8;
+  if (m > 0 && !scales) return -9;
+  if (m > 0 && !scale_exp) return -10;
+  if (!nb_ok(nb)) return -11;
+  if (flags != 0) return -15;
+  const size_t need = msts_gtrevc_workspace_size(m, nb, flags);
+  if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -13 : -12;
+  if (m == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double2 *lam = reinterpret_cast<double2 *>(lambda);
+  cudaError_t e = msts::engine_gtrevc_setup(reinterpret_cast<const double2 *>(T), ldt,
+                                            reinterpret_cast<const double2 *>(S), lds, (int)m,
+                                            reinterpret_cast<double2 *>(Z), ldz, lam, st);
+  if (e != cudaSuccess) return MSTS_ERR_CUDA;
+  msts::EngineProblem p = make_problem(T, ldt, m, lambda, 1, m, Z, ldz, scales, scale_exp, 1);
+  p.V = reinterpret_cast<const double2 *>(S);
+  p.ldv = lds;
+  return cuda_rc(msts::engine_run(&p, 1, nb, true, false, true, workspace, status, st));
+}
+
 }  // extern "C"

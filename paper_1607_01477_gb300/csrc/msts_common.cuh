@@ -30,6 +30,26 @@ __device__ __forceinline__ double2 zscale(double2 a, double s) { return make_dou
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
+// a * b and Smith's a / b with every operation rounded on its own (no fused
+// multiply-add): the arithmetic of the generalized pivots U(i,i) - s V(i,i)
+// and of lambda = T(j,j) / S(j,j), so that exact zeros and the shifts come out
+// the same whatever the compiler contracts elsewhere.
+__device__ __forceinline__ double2 zmul_rn(double2 a, double2 b) {
+  return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
+                      __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ double2 zdiv_rn(double2 a, double2 b) {
+  if (fabs(b.x) >= fabs(b.y)) {
+    const double r = __ddiv_rn(b.y, b.x);
+    const double d = __dadd_rn(b.x, __dmul_rn(b.y, r));
+    return make_double2(__ddiv_rn(__dadd_rn(a.x, __dmul_rn(a.y, r)), d),
+                        __ddiv_rn(__dsub_rn(a.y, __dmul_rn(a.x, r)), d));
+  }
+  const double r = __ddiv_rn(b.x, b.y);
+  const double d = __dadd_rn(__dmul_rn(b.x, r), b.y);
+  return make_double2(__ddiv_rn(__dadd_rn(__dmul_rn(a.x, r), a.y), d),
+                      __ddiv_rn(__dsub_rn(__dmul_rn(a.y, r), a.x), d));
+}
 // acc - a * b, fused.
 __device__ __forceinline__ double2 zfms(double2 acc, double2 a, double2 b) {
   acc.x = fma(-a.x, b.x, acc.x);
@@ -183,6 +203,12 @@ struct Prob {
   double *cblk;             // nblk: C_blk = sum_k cup[k] over the block
   double *rowsum;           // m: row sums of |U| (for ||U||_inf)
   double *delta;            // 1: zero-pivot replacement
+  // generalized problem (appendix): V upper triangular, or null
+  const double2 *V;
+  long long ldv;
+  double *cinV, *cupV, *cblkV;  // as cin, cup, cblk for V (safe)
+  double *rowsumV;              // m: row sums of |V| (for ||V||_inf)
+  double *deltaV;               // 1: eps ||V||_inf (delta_j = max(delta + |s_j| deltaV, DBL_MIN))
   int m, n, nblk;
   int diag_z;               // TREVC: write Z(j,j) = s_j in the fixup
   // Tensor-core substitution: the diagonal-block step also writes the digit

@@ -127,16 +127,24 @@ __device__ __forceinline__ double2 zrecip(double2 p) {
   return make_double2(scale(wr), scale(wi));
 }
 
-template <int NB, int L, bool SAFE, bool CONJ>
+// GEN: the generalized problem (appendix, Alg. 8/9), U' = U(I1,I1) - s_j V(I1,I1):
+// pivots U(i,i) - s_j V(i,i), AXPY entries U(r,i) - s_j V(r,i) (applied as
+// x_i U(r,i) - (s_j x_i) V(r,i)), and in the safe form the column bounds
+// cin_U + |s_j| cin_V, C_blk(U) + |s_j| C_blk(V) and
+// delta_j = max(eps (||U||_inf + |s_j| ||V||_inf), DBL_MIN).
+template <int NB, int L, bool SAFE, bool CONJ, bool GEN>
 __global__ void __launch_bounds__(kDiagThreads)
 k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *status) {
   constexpr int RPL = NB / L;            // rows per lane
   constexpr int SPW = 32 / L;            // shifts per warp
   constexpr int SPC = (kDiagThreads / 32) * SPW;
   constexpr int LD = NB + 1;
+  static_assert(!(GEN && CONJ), "generalized solves are upper only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *sU = reinterpret_cast<double2 *>(smem_raw);   // U(I1,I1) column-major, LD
-  double *sC = reinterpret_cast<double *>(sU + NB * LD);  // within-block column norms
+  double2 *sV = sU + NB * LD;                            // V(I1,I1) (GEN)
+  double *sC = reinterpret_cast<double *>(sU + (GEN ? 2 : 1) * NB * LD);   // within-block column norms
+  double *sCV = sC + NB;                                 // those of V (GEN)
 
   const Prob &P = tab.p[blockIdx.z];
   if (step >= P.nblk) return;
@@ -151,9 +159,13 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     double2 v = make_double2(0.0, 0.0);
     if (r <= c && c < nbf) v = P.U[(lo + r) + (long long)(lo + c) * P.ldu];
     sU[c * LD + r] = v;
+    if (GEN) sV[c * LD + r] = (r <= c && c < nbf) ? P.V[(lo + r) + (long long)(lo + c) * P.ldv] : make_double2(0.0, 0.0);
   }
   if (SAFE)
-    for (int k = threadIdx.x; k < NB; k += kDiagThreads) sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
+    for (int k = threadIdx.x; k < NB; k += kDiagThreads) {
+      sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
+      if (GEN) sCV[k] = k < nbf ? P.cinV[lo + k] : 0.0;
+    }
   __syncthreads();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -164,14 +176,20 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   double2 lam = active ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
   if (CONJ) lam = zconj(lam);
   double2 *col = P.B + (long long)(active ? j : 0) * P.ldb + lo;
-  const double dlt = SAFE ? *P.delta : 0.0;
-
-  auto pivot = [&](int i) {
+  const double al = GEN ? zabs_exp(lam) : 0.0;           // |s_j|
+  const double dlt = !SAFE ? 0.0 : !GEN ? *P.delta : fmax(__dadd_rn(*P.delta, __dmul_rn(al, *P.deltaV)), kDblMin);
+  // the unperturbed pivot: U(i,i) - lambda (or - lambda V(i,i))
+  auto pivot0 = [&](int i) {
     const double2 d = sU[i * LD + i];
-    double2 p = zsub(CONJ ? zconj(d) : d, lam);
+    return GEN ? zsub(d, zmul_rn(lam, sV[i * LD + i])) : zsub(CONJ ? zconj(d) : d, lam);
+  };
+  auto pivot = [&](int i) {
+    double2 p = pivot0(i);
     if (SAFE && zzero_words(p)) p = make_double2(dlt, 0.0);   // U(i,i) = lambda -> delta (Sec. 3)
     return p;
   };
+  // bound on the off-diagonal column norm of row i's column of U'
+  auto ccol = [&](int i) { return GEN ? __dadd_rn(sC[i], __dmul_rn(al, sCV[i])) : sC[i]; };
 
   double2 y[RPL], inv[RPL];
   int pex[RPL];                          // biased exponent field of max(|Re p|, |Im p|)
@@ -181,8 +199,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     const int r = l + L * q;
     const bool v = r < nbe;
     y[q] = v ? col[r] : make_double2(0.0, 0.0);
-    const double2 d = sU[r * LD + r];
-    const double2 p0 = zsub(CONJ ? zconj(d) : d, lam);
+    const double2 p0 = pivot0(r);
     zero_piv |= v && zzero_words(p0);
     const double2 p = pivot(r);
     inv[q] = v ? zrecip(p) : make_double2(0.0, 0.0);
@@ -198,10 +215,14 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   // time: the unrolled code stays small enough for the instruction cache, and
   // slots wholly on the dead side of row i still drop out at compile time.
   auto axpy = [&](int qi, int li, double2 xi) {
+    const double2 cx = GEN ? zmul(lam, xi) : xi;          // s_j x_i for the V part
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       if (!CONJ) {        // rows l + L q < i
-        if (q < qi || (q == qi && l < li)) y[q] = zfms(y[q], xi, sU[(L * qi + li) * LD + l + L * q]);
+        if (q < qi || (q == qi && l < li)) {
+          y[q] = zfms(y[q], xi, sU[(L * qi + li) * LD + l + L * q]);
+          if (GEN) y[q] = zfma(y[q], cx, sV[(L * qi + li) * LD + l + L * q]);
+        }
       } else {            // rows l + L q > i
         if (q > qi || (q == qi && l > li)) y[q] = zfms(y[q], xi, zconj(sU[(l + L * q) * LD + L * qi + li]));
       }
@@ -304,7 +325,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     const int pi = gshfl_i<L>(pex[qi], li);
     patho |= i < nbe && pi == 0;                      // subnormal pivot: |p| >= 2^(pi - 1023) fails
     // |x_i| = |y_i| / |p_i| < 2^(Eb + 1024 - pi); the AXPY adds at most |x_i| C_i.
-    const int eC = (int)(__double_as_longlong(sC[i]) >> 52) - 1022;
+    const int eC = (int)(__double_as_longlong(ccol(i)) >> 52) - 1022;
     const int xb = Eb + 1025 - pi;
     int cand = i < nbe ? max(xb + max(eC, 0), Eb) + 1 : Eb;
     if (cand > 1010) {                                // keep clear of overflow
@@ -337,7 +358,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     a[q] = 0.0;
     em[q] = -(1 << 28);
     if (r < nbe) {
-      a[q] = __dmul_rn(zabs_exp(y[q]), sC[r]);
+      a[q] = __dmul_rn(zabs_exp(y[q]), ccol(r));
       if (!zzero_words(ypre[q])) {
         // floor(log2 M) <= ey - ep + 1 for normal operands; Alg. 4's test
         // (M 2^(kpre - Ka) >= Omega with Ka >= 0) can only fire above it.
@@ -414,7 +435,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
       double2 xi = gshfl_z<L>(i < nbe ? zdiv_fast(y[qi], pivot(i)) : make_double2(0.0, 0.0), li);
       if (l == li) y[qi] = xi;
       if (i < nbe) {
-        G = __dadd_rn(G, __dmul_rn(zabs_exp(xi), sC[i]));
+        G = __dadd_rn(G, __dmul_rn(zabs_exp(xi), ccol(i)));
         if (ge_omega(G)) {                               // protect the AXPY
           const int kk = choose_k(G);
 #pragma unroll
@@ -439,7 +460,8 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     ej = P.e[j];
     Gj = P.G[j];
     if (kexp > 0) { ej += kexp; Gj = dshift(Gj, kexp); pend = kexp; }
-    Gj = __dadd_rn(Gj, __dmul_rn(P.cblk[b], N));
+    const double cb = GEN ? __dadd_rn(P.cblk[b], __dmul_rn(al, P.cblkV[b])) : P.cblk[b];
+    Gj = __dadd_rn(Gj, __dmul_rn(cb, N));
     if (Gj >= OM) {
       k2 = choose_k(Gj);
       ej += k2;
@@ -463,34 +485,34 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   }
 }
 
-template <int NB, int L, bool SAFE, bool CONJ>
+template <int NB, int L, bool SAFE, bool CONJ, bool GEN>
 static cudaError_t launch(const ProbTable &tab, int step, int shortcut, int ncols_max,
                           uint32_t *status, cudaStream_t st) {
-  constexpr size_t smem = (size_t)NB * (NB + 1) * sizeof(double2) + NB * sizeof(double);
+  constexpr size_t smem = (GEN ? 2 : 1) * ((size_t)NB * (NB + 1) * sizeof(double2) + NB * sizeof(double));
   constexpr int SPC = (kDiagThreads / 32) * (32 / L);
-  cudaError_t e = cudaFuncSetAttribute(k_diag<NB, L, SAFE, CONJ>,
+  cudaError_t e = cudaFuncSetAttribute(k_diag<NB, L, SAFE, CONJ, GEN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_diag<NB, L, SAFE, CONJ><<<dim3((ncols_max + SPC - 1) / SPC, 1, tab.count), kDiagThreads, smem, st>>>(
+  k_diag<NB, L, SAFE, CONJ, GEN><<<dim3((ncols_max + SPC - 1) / SPC, 1, tab.count), kDiagThreads, smem, st>>>(
       tab, step, shortcut, status);
   return cudaSuccess;
 }
 
-template <int NB, bool SAFE, bool CONJ>
+template <int NB, bool SAFE, bool CONJ, bool GEN>
 static cudaError_t launch_nb(int L, const ProbTable &tab, int step, int shortcut, int ncols_max,
                              uint32_t *status, cudaStream_t st) {
   if constexpr (NB == 64) {
-    if (L <= 16) return launch<64, 16, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
-    return launch<64, 32, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    if (L <= 16) return launch<64, 16, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
+    return launch<64, 32, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
   } else if constexpr (NB == 32) {
-    if (L <= 4) return launch<32, 4, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
-    if (L == 8) return launch<32, 8, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
-    if (L == 16) return launch<32, 16, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
-    return launch<32, 32, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    if (L <= 4) return launch<32, 4, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
+    if (L == 8) return launch<32, 8, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
+    if (L == 16) return launch<32, 16, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
+    return launch<32, 32, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
   } else {
-    if (L <= 4) return launch<16, 4, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
-    if (L == 8) return launch<16, 8, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
-    return launch<16, 16, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+    if (L <= 4) return launch<16, 4, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
+    if (L == 8) return launch<16, 8, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
+    return launch<16, 16, SAFE, CONJ, GEN>(tab, step, shortcut, ncols_max, status, st);
   }
 }
 
@@ -504,13 +526,15 @@ int diag_lanes(int nb, long long total_cols) {
 }
 
 cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int step, int shortcut,
-                        int ncols_max, long long total_cols, uint32_t *status, cudaStream_t st) {
+                        int ncols_max, long long total_cols, uint32_t *status, cudaStream_t st, bool gen) {
   const int L = diag_lanes(nb, total_cols);
-#define MSTS_DIAG_CASE(NBV)                                                                   \
-  case NBV:                                                                                   \
-    if (safe) return launch_nb<NBV, true, false>(L, tab, step, shortcut, ncols_max, status, st); \
-    if (conj) return launch_nb<NBV, false, true>(L, tab, step, shortcut, ncols_max, status, st); \
-    return launch_nb<NBV, false, false>(L, tab, step, shortcut, ncols_max, status, st);
+#define MSTS_DIAG_CASE(NBV)                                                                          \
+  case NBV:                                                                                          \
+    if (gen && safe) return launch_nb<NBV, true, false, true>(L, tab, step, shortcut, ncols_max, status, st); \
+    if (gen) return launch_nb<NBV, false, false, true>(L, tab, step, shortcut, ncols_max, status, st);    \
+    if (safe) return launch_nb<NBV, true, false, false>(L, tab, step, shortcut, ncols_max, status, st);  \
+    if (conj) return launch_nb<NBV, false, true, false>(L, tab, step, shortcut, ncols_max, status, st);  \
+    return launch_nb<NBV, false, false, false>(L, tab, step, shortcut, ncols_max, status, st);
   switch (nb) {
     MSTS_DIAG_CASE(16)
     MSTS_DIAG_CASE(32)

@@ -23,6 +23,10 @@ struct EngineProblem {
   int *scale_exp;
   int diag_z;  // write Z(j,j) = s_j at the end (TREVC)
   const struct OzPlan *oz;  // non-null: substitution GEMM on the tensor cores (single problem)
+  // Generalized problem (appendix, Alg. 8/9): (U - s_j V) x_j = b_j with V
+  // upper triangular; null for the standard one.
+  const double2 *V = nullptr;
+  long long ldv = 1;
 };
 
 size_t engine_workspace_bytes(const EngineProblem *probs, int count, int nb, bool safe);
@@ -36,5 +40,9 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
 
 cudaError_t engine_trevc_setup(const double2 *T, long long ldt, int m, double2 *Z, long long ldz,
                                cudaStream_t st);
+// Alg. 10's set-up: lam[j] = T(j,j) / S(j,j); Z = -T + S diag(lam) strictly
+// above the diagonal, zero elsewhere.
+cudaError_t engine_gtrevc_setup(const double2 *T, long long ldt, const double2 *S, long long lds, int m,
+                                double2 *Z, long long ldz, double2 *lam, cudaStream_t st);
 
 }  // namespace msts

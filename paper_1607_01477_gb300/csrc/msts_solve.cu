@@ -54,11 +54,12 @@ __device__ __forceinline__ long long half_bits(long long m) {   // bits of m / 2
 }
 
 // One warp per column k: cin[k] = max_{lo(k) <= r < k} |U(r,k)| (within its own
-// block, diagonal excluded) and cup[k] = max_{r < lo(k)} |U(r,k)| (above it).
-__global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32_t *status) {
+// block, diagonal excluded) and cup[k] = max_{r < lo(k)} |U(r,k)| (above it);
+// with useV the same for V into cinV, cupV (generalized problem).
+__global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32_t *status, int useV) {
   const Prob &P = tab.p[blockIdx.z];
-  if (P.n == 0) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *P.delta = 0.0;   // the zero-pivot flag of k_zero_scan
+  if (P.n == 0 || (useV && !P.V)) return;
+  if (!useV && blockIdx.x == 0 && threadIdx.x == 0) *P.delta = 0.0;   // the zero-pivot flag of k_zero_scan
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (k >= P.m) return;
@@ -70,7 +71,7 @@ __global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32
   // documented range, so the squares cannot overflow).
   long long Min = 0, Mup = 0, Mall = 0, cin = 0, cup = 0, amax = 0;
   bool finite = true;
-  const double2 *col = P.U + (long long)k * P.ldu;
+  const double2 *col = useV ? P.V + (long long)k * P.ldv : P.U + (long long)k * P.ldu;
 #pragma unroll 4
   for (int r0 = 0; r0 <= k; r0 += 32) {                  // warp-uniform trip count
     const int r = r0 + lane;
@@ -98,8 +99,8 @@ __global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32
   }
   const bool all_finite = __all_sync(0xffffffffu, finite);
   if (lane == 0) {
-    P.cin[k] = sqrt(__longlong_as_double(cin));
-    P.cup[k] = sqrt(__longlong_as_double(cup));
+    (useV ? P.cinV : P.cin)[k] = sqrt(__longlong_as_double(cin));
+    (useV ? P.cupV : P.cup)[k] = sqrt(__longlong_as_double(cup));
     if (!all_finite) raise_status(status, MSTS_STATUS_NONFINITE);
     if (sqrt(__longlong_as_double(amax)) >= kRangeLimitU) raise_status(status, MSTS_STATUS_RANGE);
   }
@@ -122,7 +123,7 @@ __device__ __forceinline__ bool deq_bits(double a, double b) {
 // set nonzero (k_colnorms zeroed it) when such a pair exists.
 __global__ void k_zero_scan(const __grid_constant__ ProbTable tab, int shortcut) {
   const Prob &P = tab.p[blockIdx.z];
-  __shared__ double2 dg[256];
+  __shared__ double2 dg[256], dv[256];
   if (P.m == 0 || P.n == 0) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = j < P.n;
@@ -131,35 +132,46 @@ __global__ void k_zero_scan(const __grid_constant__ ProbTable tab, int shortcut)
   const int i0 = 256 * blockIdx.y;                       // this CTA's 256 diagonal entries
   if (i0 >= P.m) return;
   if (i0 + (int)threadIdx.x < P.m) dg[threadIdx.x] = P.U[(long long)(i0 + threadIdx.x) * (P.ldu + 1)];
+  if (P.V && i0 + (int)threadIdx.x < P.m) dv[threadIdx.x] = P.V[(long long)(i0 + threadIdx.x) * (P.ldv + 1)];
   __syncthreads();
   bool hit = false;
   const int cnt = min(256, end - i0);
-  for (int t = 0; t < cnt; ++t) hit |= deq_bits(dg[t].x, lam.x) && deq_bits(dg[t].y, lam.y);
+  if (!P.V) {
+    for (int t = 0; t < cnt; ++t) hit |= deq_bits(dg[t].x, lam.x) && deq_bits(dg[t].y, lam.y);
+  } else {                                               // U(i,i) - lambda V(i,i), as the diagonal step forms it
+    for (int t = 0; t < cnt; ++t) {
+      const double2 p = zsub(dg[t], zmul_rn(lam, dv[t]));
+      hit |= deq_bits(p.x, 0.0) && deq_bits(p.y, 0.0);
+    }
+  }
   if (hit) *P.delta = 1.0;
 }
 
 // One warp per row: rowsum[r] = sum_{c >= r} |U(r,c)| (lanes stride over the
 // columns, then a fixed-order warp reduction: deterministic); only when a zero
 // pivot can occur (k_zero_scan).
-__global__ void k_rowsums(const __grid_constant__ ProbTable tab) {
+__global__ void k_rowsums(const __grid_constant__ ProbTable tab, int useV) {
   const Prob &P = tab.p[blockIdx.z];
-  if (P.n == 0 || *P.delta == 0.0) return;
+  if (P.n == 0 || *P.delta == 0.0 || (useV && !P.V)) return;
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= P.m) return;
   double s = 0.0;
-  const double2 *row = P.U + r;
+  const double2 *row = useV ? P.V + r : P.U + r;
+  const long long ld = useV ? P.ldv : P.ldu;
   for (int c = r + lane; c < P.m; c += 32) {
-    const double2 u = row[(long long)c * P.ldu];
+    const double2 u = row[(long long)c * ld];
     s += sqrt(fma(u.x, u.x, u.y * u.y));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) P.rowsum[r] = s;
+  if (lane == 0) (useV ? P.rowsumV : P.rowsum)[r] = s;
 }
 
-// C_blk per block (Alg. 5), and delta = max(eps ||U||_inf, DBL_MIN) when a
-// zero pivot can occur (otherwise delta is never read; DBL_MIN is stored).
+// C_blk per block (Alg. 5; and of V, Alg. 9), and delta = max(eps ||U||_inf,
+// DBL_MIN) when a zero pivot can occur (otherwise delta is never read; DBL_MIN
+// is stored).  Generalized: delta = eps ||U||_inf and deltaV = eps ||V||_inf,
+// delta_j = max(delta + |s_j| deltaV, DBL_MIN) being formed per shift.
 __global__ void k_safe_finish(const __grid_constant__ ProbTable tab, int nb) {
   const Prob &P = tab.p[blockIdx.z];
   __shared__ double red[32];
@@ -167,28 +179,41 @@ __global__ void k_safe_finish(const __grid_constant__ ProbTable tab, int nb) {
   for (int b = threadIdx.x; b < P.nblk; b += blockDim.x) {
     int lo, hi;
     block_range(P, b, nb, lo, hi);
-    double c = 0.0;
+    double c = 0.0, cv = 0.0;
     for (int k = lo; k < hi; ++k) c += P.cup[k];
     P.cblk[b] = c;
+    if (P.V) {
+      for (int k = lo; k < hi; ++k) cv += P.cupV[k];
+      P.cblkV[b] = cv;
+    }
   }
   const bool need = *P.delta != 0.0;                     // uniform
   __syncthreads();
   if (!need) {
-    if (threadIdx.x == 0) *P.delta = kDblMin;
+    if (threadIdx.x == 0) {
+      *P.delta = kDblMin;
+      if (P.V) *P.deltaV = 0.0;
+    }
     return;
   }
-  double mx = 0.0;
-  for (int r = threadIdx.x; r < P.m; r += blockDim.x) mx = fmax(mx, P.rowsum[r]);
-  mx = warp_max(mx);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    v = warp_max(v);
-    if (threadIdx.x == 0) {
-      const double d = kEps * v;
-      *P.delta = d < kDblMin ? kDblMin : d;
+  // max row sum of U (and of V): eps ||U||_inf, eps ||V||_inf
+  for (int w = 0; w < (P.V ? 2 : 1); ++w) {
+    const double *rs = w ? P.rowsumV : P.rowsum;
+    double mx = 0.0;
+    for (int r = threadIdx.x; r < P.m; r += blockDim.x) mx = fmax(mx, rs[r]);
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      v = warp_max(v);
+      if (threadIdx.x == 0) {
+        const double d = kEps * v;
+        if (w) *P.deltaV = d;
+        else *P.delta = P.V ? d : (d < kDblMin ? kDblMin : d);   // generalized: capped per shift
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -261,7 +286,7 @@ struct GemmCfg {
   static constexpr size_t smem() { return (size_t)NB * (LDA + LDX) * sizeof(double2); }
 };
 
-template <int NB, int BM, int BN, bool SAFE, bool CONJ>
+template <int NB, int BM, int BN, bool SAFE, bool CONJ, bool GEN = false>
 __global__ void __launch_bounds__(256)
 k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
   using C = GemmCfg<BM, BN>;
@@ -298,6 +323,15 @@ k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
     if (k < K && c0 + c < P.n) v = P.B[(lo + k) + (long long)(c0 + c) * P.ldb];
     sX[k * LDX + c] = v;
   }
+  // Generalized problem (Alg. 8/9): also V(I0,I1), for B(I0,:) += V(I0,I1) (s X(I1,:)).
+  constexpr bool gen = GEN && !CONJ;
+  double2 *sV = sX + NB * LDX;                           // [NB][LDA]
+  if constexpr (gen)
+    for (int idx = tid; idx < NB * BM; idx += NT) {
+      const int kk = idx / BM, r = idx - kk * BM;
+      sV[kk * LDA + r] = (kk < K && r0 + r < rend) ? P.V[(r0 + r) + (long long)(lo + kk) * P.ldv]
+                                                   : make_double2(0.0, 0.0);
+    }
   __syncthreads();
 
   const int tr = tid & 31, tc = tid >> 5;
@@ -306,16 +340,42 @@ k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int c = 0; c < TN; ++c) acc[i][c] = make_double2(0.0, 0.0);
+  double2 accv[TM][TN];                                  // V(I0,I1) X(I1,:) (generalized)
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) accv[i][c] = make_double2(0.0, 0.0);
+  if constexpr (!gen) {
 #pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    double2 a[TM];
+    for (int k = 0; k < K; ++k) {
+      double2 a[TM];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) a[i] = sA[k * LDA + tr + 32 * i];
+      for (int i = 0; i < TM; ++i) a[i] = sA[k * LDA + tr + 32 * i];
 #pragma unroll
-    for (int c = 0; c < TN; ++c) {
-      const double2 x = sX[k * LDX + tc + 8 * c];
+      for (int c = 0; c < TN; ++c) {
+        const double2 x = sX[k * LDX + tc + 8 * c];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) acc[i][c] = zfma(acc[i][c], a[i], x);
+        for (int i = 0; i < TM; ++i) acc[i][c] = zfma(acc[i][c], a[i], x);
+      }
+    }
+  } else {
+#pragma unroll 2
+    for (int k = 0; k < K; ++k) {
+      double2 a[TM], w[TM];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        a[i] = sA[k * LDA + tr + 32 * i];
+        w[i] = sV[k * LDA + tr + 32 * i];
+      }
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        const double2 x = sX[k * LDX + tc + 8 * c];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          acc[i][c] = zfma(acc[i][c], a[i], x);
+          accv[i][c] = zfma(accv[i][c], w[i], x);
+        }
+      }
     }
   }
 #pragma unroll
@@ -323,6 +383,7 @@ k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
     const int col = c0 + tc + 8 * c;
     if (col >= P.n) continue;
     const int pend = SAFE ? P.pend[col] : 0;
+    const double2 lam = gen ? P.shifts[(long long)col * P.shift_stride] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
       const int row = r0 + tr + 32 * i;
@@ -330,7 +391,9 @@ k_gemm(const __grid_constant__ ProbTable tab, int step, int shortcut) {
       double2 *p = P.B + row + (long long)col * P.ldb;
       double2 v = *p;
       if (SAFE && pend) v = zshift(v, pend);
-      *p = zsub(v, acc[i][c]);
+      v = zsub(v, acc[i][c]);
+      if (gen) v = zfma(v, lam, accv[i][c]);             // + s_j V(I0,I1) X(I1,j)
+      *p = v;
     }
   }
 }
@@ -447,10 +510,15 @@ __global__ void k_fixup(const __grid_constant__ ProbTable tab, int nb, int short
 // ---------------------------------------------------------------------------
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static size_t prob_ws_bytes(int m, int n, int nb, bool safe) {
+static size_t prob_ws_bytes(int m, int n, int nb, bool safe, bool gen) {
   if (!safe || m == 0 || n == 0) return 0;
   const size_t nblk = (size_t)(m + nb - 1) / nb;
   size_t s = 0;
+  if (gen) {
+    s += align256(sizeof(double) * m) * 3;      // cinV, cupV, rowsumV
+    s += align256(sizeof(double) * nblk);       // cblkV
+    s += align256(sizeof(double));              // deltaV
+  }
   s += align256(sizeof(double) * n);            // G
   s += align256(sizeof(int) * n) * 2;           // e, pend
   s += align256(sizeof(int) * nblk * n);        // E
@@ -462,7 +530,7 @@ static size_t prob_ws_bytes(int m, int n, int nb, bool safe) {
 
 size_t engine_workspace_bytes(const EngineProblem *probs, int count, int nb, bool safe) {
   size_t s = 0;
-  for (int p = 0; p < count; ++p) s += prob_ws_bytes(probs[p].m, probs[p].n, nb, safe);
+  for (int p = 0; p < count; ++p) s += prob_ws_bytes(probs[p].m, probs[p].n, nb, safe, probs[p].V != nullptr);
   return s;
 }
 
@@ -475,13 +543,23 @@ static T *carve(char *&cur, size_t count) {
 
 template <int NB, int BM, int BN, bool SAFE, bool CONJ>
 static void launch_gemm(const ProbTable &tab, int gx, int gy, int s, bool shortcut, bool lp,
-                        cudaStream_t st) {
-  constexpr size_t smem = GemmCfg<BM, BN>::template smem<NB>();
+                        cudaStream_t st, bool gen = false) {
+  // the generalized form also stages V(I0,I1) (NB x LDA)
+  const size_t smem = GemmCfg<BM, BN>::template smem<NB>() +
+                      (gen ? (size_t)NB * GemmCfg<BM, BN>::LDA * sizeof(double2) : 0);
   if (lp && !SAFE && !CONJ) {
     cudaFuncSetAttribute(k_gemm_f32<NB, BM, BN, SAFE, CONJ>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gemm_f32<NB, BM, BN, SAFE, CONJ><<<dim3(gx, gy, tab.count), 256, smem, st>>>(tab, s, shortcut ? 1 : 0);
     return;
+  }
+  if constexpr (!CONJ) {
+    if (gen) {
+      cudaFuncSetAttribute(k_gemm<NB, BM, BN, SAFE, CONJ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      k_gemm<NB, BM, BN, SAFE, CONJ, true><<<dim3(gx, gy, tab.count), 256, smem, st>>>(tab, s, shortcut ? 1 : 0);
+      return;
+    }
   }
   cudaFuncSetAttribute(k_gemm<NB, BM, BN, SAFE, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
@@ -494,6 +572,7 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
   int maxblk = 0;
   for (int p = 0; p < count; ++p) maxblk = std::max(maxblk, (probs[p].m + NB - 1) / NB);
   const bool tracing = trace_on();
+  const bool gen = count > 0 && probs[0].V != nullptr;   // a table is all generalized or none
   for (int s = 0; s < maxblk; ++s) {
     int dx = 0, rows_max = 0, cols_max = 0;
     long long tiles_big = 0, tiles_mid = 0, total_cols = 0;
@@ -510,21 +589,21 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       dx = std::max(dx, ncols);
       total_cols += ncols;
       // algorithmic work: 8 real FLOPs per complex multiply-add
-      dflops += 4.0 * K * K * ncols;
+      dflops += (gen ? 8.0 : 4.0) * K * K * ncols;
       dbytes += 16.0 * K * K / 2 + 32.0 * K * ncols;
       if (rows > 0) {
         rows_max = std::max(rows_max, rows);
         cols_max = std::max(cols_max, ncols);
         tiles_big += (long long)((rows + 63) / 64) * ((ncols + 31) / 32);
         tiles_mid += (long long)((rows + 31) / 32) * ((ncols + 15) / 16);
-        gflops += 8.0 * rows * K * ncols;
+        gflops += (gen ? 16.0 : 8.0) * rows * K * ncols;
         gbytes += 16.0 * rows * K + 16.0 * K * ncols + 32.0 * (double)rows * ncols;
       }
     }
     if (dx > 0) {
       void *h = tracing ? trace_start(1, dflops, dbytes, st) : nullptr;
       const cudaError_t e = launch_diag(tab, NB, SAFE, CONJ, s, shortcut ? 1 : 0, dx, total_cols,
-                                        status, st);
+                                        status, st, gen);
       if (e != cudaSuccess) return e;
       trace_stop(h, st);
       count_launches(1);
@@ -544,11 +623,11 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       // at least two waves of CTAs over the 152 SMs when the problem allows.
       void *h = tracing ? trace_start(0, gflops, gbytes, st) : nullptr;
       if (tiles_big >= 2 * kNumSMs)
-        launch_gemm<NB, 64, 32, SAFE, CONJ>(tab, (cols_max + 31) / 32, (rows_max + 63) / 64, s, shortcut, lp, st);
+        launch_gemm<NB, 64, 32, SAFE, CONJ>(tab, (cols_max + 31) / 32, (rows_max + 63) / 64, s, shortcut, lp, st, gen);
       else if (tiles_mid >= kNumSMs)
-        launch_gemm<NB, 32, 16, SAFE, CONJ>(tab, (cols_max + 15) / 16, (rows_max + 31) / 32, s, shortcut, lp, st);
+        launch_gemm<NB, 32, 16, SAFE, CONJ>(tab, (cols_max + 15) / 16, (rows_max + 31) / 32, s, shortcut, lp, st, gen);
       else
-        launch_gemm<NB, 32, 8, SAFE, CONJ>(tab, (cols_max + 7) / 8, (rows_max + 31) / 32, s, shortcut, lp, st);
+        launch_gemm<NB, 32, 8, SAFE, CONJ>(tab, (cols_max + 7) / 8, (rows_max + 31) / 32, s, shortcut, lp, st, gen);
       trace_stop(h, st);
       count_launches(1);
     }
@@ -579,6 +658,7 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
       P.U = q.U; P.ldu = q.ldu; P.shifts = q.shifts; P.shift_stride = q.shift_stride;
       P.B = q.B; P.ldb = q.ldb; P.scales = q.scales; P.scale_exp = q.scale_exp;
       P.m = q.m; P.n = q.n; P.nblk = (q.m + nb - 1) / nb; P.diag_z = q.diag_z;
+      P.V = q.V; P.ldv = q.ldv;
       if (safe && q.m > 0 && q.n > 0) {
         P.G = carve<double>(cur, q.n);
         P.e = carve<int>(cur, q.n);
@@ -589,6 +669,13 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
         P.rowsum = carve<double>(cur, q.m);
         P.cblk = carve<double>(cur, P.nblk);
         P.delta = carve<double>(cur, 1);
+        if (q.V) {
+          P.cinV = carve<double>(cur, q.m);
+          P.cupV = carve<double>(cur, q.m);
+          P.rowsumV = carve<double>(cur, q.m);
+          P.cblkV = carve<double>(cur, P.nblk);
+          P.deltaV = carve<double>(cur, 1);
+        }
       }
       maxm = std::max(maxm, q.m);
       maxn = std::max(maxn, q.n);
@@ -601,11 +688,15 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
     }
     const int sc = shortcut ? 1 : 0;
     if (safe) {
-      k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status);
+      const bool gen = probs[base].V != nullptr;
+      k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status, 0);
+      if (gen) k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status, 1);
       k_zero_scan<<<dim3((maxn + 255) / 256, (maxm + 255) / 256, cnt), 256, 0, st>>>(tab, sc);
-      k_rowsums<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab);
+      k_rowsums<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, 0);
+      if (gen) k_rowsums<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, 1);
       k_safe_finish<<<dim3(1, 1, cnt), 256, 0, st>>>(tab, nb);
-      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);  count_launches(5);
+      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);
+      count_launches(gen ? 7 : 5);
     }
     cudaError_t err;
     switch (nb) {
@@ -629,6 +720,28 @@ cudaError_t engine_trevc_setup(const double2 *T, long long ldt, int m, double2 *
                                cudaStream_t st) {
   if (m > 0) {
     k_trevc_setup<<<m, 256, 0, st>>>(T, ldt, m, Z, ldz);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+// Alg. 10's set-up: lam[j] = T(j,j) / S(j,j), Z(r,j) = lam[j] S(r,j) - T(r,j)
+// for r < j and zero elsewhere (the oracle's rounding: no fused operations).
+__global__ void k_gtrevc_setup(const double2 *T, long long ldt, const double2 *S, long long lds, int m,
+                               double2 *Z, long long ldz, double2 *lam) {
+  const int j = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const double2 lj = zdiv_rn(T[(long long)j * (ldt + 1)], S[(long long)j * (lds + 1)]);
+  if (r == 0) lam[j] = lj;
+  Z[r + (long long)j * ldz] = r < j ? zsub(zmul_rn(lj, S[r + (long long)j * lds]), T[r + (long long)j * ldt])
+                                    : make_double2(0.0, 0.0);
+}
+
+cudaError_t engine_gtrevc_setup(const double2 *T, long long ldt, const double2 *S, long long lds, int m,
+                                double2 *Z, long long ldz, double2 *lam, cudaStream_t st) {
+  if (m > 0) {
+    k_gtrevc_setup<<<dim3((m + 255) / 256, m), 256, 0, st>>>(T, ldt, S, lds, m, Z, ldz, lam);
     count_launches(1);
   }
   return cudaGetLastError();
