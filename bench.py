@@ -419,7 +419,39 @@ def extra_measurements(dev, nb):
     res["batched_adjoint_64x(256..2048)x32"] = batched_fwd_bwd(dev, nb)
     res["mixed_8192x2048"] = mixed_vs_fp64(dev, nb)
     res["eig_back_transform_4096"] = back_transform_extra(dev, nb)
+    res["gtrevc_4096"] = gtrevc_extra(dev, nb)
     return res
+
+
+def gtrevc_extra(dev, nb):
+    """GeneralizedTriangEig (Alg. 10) of the 4096 x 4096 synthetic triangular
+    pencil: all 4096 generalized eigenvectors with the safe generalized solve
+    (FP64 substitution GEMM, U and V products), FLOPs (8/3) m^3 (twice the
+    standard TREVC's: the V term doubles every multiply-add), with the largest
+    scale exponent and the generalized eigen-residual of sampled columns."""
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    m = 4096
+    T, S = W.pencil_problem(m)
+    Td = msts.colmajor(torch.from_numpy(T).to(dev))
+    Sd = msts.colmajor(torch.from_numpy(S).to(dev))
+    msts.msts_gtrevc(Td, Sd, nb=nb)                  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    Z, lam, sc, se, st = msts.msts_gtrevc(Td, Sd, nb=nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cols = torch.arange(0, m, 64, device=dev)
+    zs = Z[:, cols] / Z[:, cols].abs().amax(dim=0, keepdim=True)
+    R = Td @ zs - (Sd @ zs) * lam[cols][None, :]
+    rho = torch.linalg.norm(R, dim=0) / ((torch.linalg.norm(Td) + lam[cols].abs() * torch.linalg.norm(Sd))
+                                         * torch.linalg.norm(zs, dim=0))
+    return {"ms": ms, "tflops": (8.0 / 3.0) * m ** 3 / (ms * 1e-3) / 1e12, "gemm": "fp64",
+            "max_scale_exp": int(se.max().item()), "max_residual_sampled": rho.max().item(),
+            "status": int(st.item())}
 
 
 def back_transform_extra(dev, nb):

@@ -151,3 +151,37 @@ def batch_problem(batch: int = 64, m_lo: int = 256, m_hi: int = 2048, n: int = 3
         B = cn(g, (mb, n))
         probs.append((U, s, B))
     return probs
+
+
+# --------------------------------------------------------------------------
+# Generalized eigenvectors of a triangular pencil (appendix, Alg. 10)
+# --------------------------------------------------------------------------
+def pencil_problem(m: int = 4096, seed: int | None = None, k: int = 6):
+    """A triangular pencil (T, S): T as the TREVC workload (clustered unit-disk
+    diagonal, strictly-upper 10 CN), S with diagonal 1 + 0.1 disk and
+    strictly-upper 0.1 CN -- the shape of the factors QZ returns."""
+    g = rng(k, seed)
+    T = trevc_problem(m, seed=int(g.integers(1 << 30)))
+    S = upper(g, m, 1.0 + disk(g, m, 0.1), 0.1)
+    return T, S
+
+
+# --------------------------------------------------------------------------
+# Scaling study of the multi-shift solve (Sec. 6): U is the upper triangle of
+# a Hermitian matrix with eigenvalues uniform in [1, 2]; shifts uniform in the
+# disk of centre 1.5 and radius 0.5.
+# --------------------------------------------------------------------------
+def hermitian_upper(g: np.random.Generator, m: int, lo: float = 1.0, hi: float = 2.0) -> np.ndarray:
+    q, r = np.linalg.qr(cn(g, (m, m)))
+    q = q * (np.diagonal(r) / np.abs(np.diagonal(r)))[None, :]       # Haar-distributed unitary
+    lam = lo + (hi - lo) * g.random(m)
+    H = (q * lam[None, :]) @ q.conj().T
+    return np.asfortranarray(np.triu(H))
+
+
+def scaling_problem(m: int, n: int, seed: int | None = None, k: int = 7):
+    g = rng(k, seed)
+    U = hermitian_upper(g, m)
+    s = 1.5 + disk(g, n, 0.5)
+    B = np.asfortranarray(cn(g, (m, n)))
+    return U, s, B
