@@ -139,6 +139,48 @@ def safe_solve(U, shifts, B, nb, shortcut=False):
     return X, e
 
 
+_SIDE = {"left": 0, "right": 1}
+_UPLO = {"upper": 0, "lower": 1}
+_TRANS = {"N": 0, "T": 1, "C": 2}
+
+
+def _variant_args(A, side, uplo, trans, B):
+    A = _cz(A, "A")
+    if side not in _SIDE or uplo not in _UPLO or trans not in _TRANS:
+        raise ValueError("side in {left,right}, uplo in {upper,lower}, trans in {N,T,C}")
+    X = np.array(B, dtype=np.complex128, order="F", copy=True)
+    m = A.shape[0]
+    n = X.shape[1] if side == "left" else X.shape[0]
+    if (X.shape[0] if side == "left" else X.shape[1]) != m:
+        raise ValueError("B does not match A")
+    return A, X, m, n
+
+
+def solve_variant(A, shifts, B, side="left", uplo="upper", trans="N"):
+    """The triangular variants of the footnote to Sec. 2: M_j = op(A) - s_j I
+    with op(A) in {A, A^T, A^H}, A upper or lower triangular; left side
+    M_j x_j = b_j (columns of the m x n B), right side x_j^T M_j = b_j^T (rows
+    of the n x m B).  Plain substitution per shift.  Returns a new array."""
+    A, X, m, n = _variant_args(A, side, uplo, trans, B)
+    s = np.ascontiguousarray(shifts, dtype=np.complex128)
+    _load().or_solve_variant(ctypes.c_int(_SIDE[side]), ctypes.c_int(_UPLO[uplo]), ctypes.c_int(_TRANS[trans]),
+                             _c_int64(m), _c_int64(n), _p(A), _c_int64(_ld(A)), _p(s), _p(X), _c_int64(_ld(X)))
+    return X
+
+
+def safe_solve_variant(A, shifts, B, nb, side="left", uplo="upper", trans="N"):
+    """Alg. 5 for every variant, run in the variant's substitution order (the
+    operator written as an upper-triangular matrix in that order).  Returns
+    (X, e): M_j x_j = 2^-e_j b_j (left) or x_j^T M_j = 2^-e_j b_j^T (right)."""
+    A, X, m, n = _variant_args(A, side, uplo, trans, B)
+    s = np.ascontiguousarray(shifts, dtype=np.complex128)
+    e = np.zeros(n, dtype=np.int32)
+    _load().or_safe_solve_variant(ctypes.c_int(_SIDE[side]), ctypes.c_int(_UPLO[uplo]),
+                                  ctypes.c_int(_TRANS[trans]), _c_int64(m), _c_int64(n), _p(A),
+                                  _c_int64(_ld(A)), _p(s), _p(X), _c_int64(_ld(X)), _c_int64(nb), _p(e))
+    return X, e
+
+
 def safe_trsv_unblocked(U, shifts, B):
     """Alg. 4 (SafeTrsv) on the whole U - s_j I, column by column.  Returns (X, e)."""
     U = _cz(U, "U")

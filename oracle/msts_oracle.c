@@ -753,6 +753,97 @@ void or_back_transform(int64_t m, const oz *Q, int64_t ldq, const oz *Z, int64_t
     }
 }
 
+/* ------------------------------------------------------------------------
+ * The other triangular variants (footnote to Sec. 2: the lower-triangular
+ * and right-hand cases).  The operator is M_j = op(A) - s_j I, op(A) = A, A^T
+ * or A^H (trans = 0, 1, 2), A upper (uplo = 0) or lower (uplo = 1)
+ * triangular; only that triangle of A is read.
+ *   left  (side = 0): M_j x_j = b_j,       x_j, b_j column j of the m x n B;
+ *   right (side = 1): x_j^T M_j = b_j^T,   x_j, b_j row j of the n x m B.
+ * A right-side system is the left-side system with the transposed operator
+ * M_j^T = op'(A) - s_j I, where op' maps A -> A^T, A^T -> A and A^H -> conj(A)
+ * (internal code 3).  Plain definition per shift: unblocked substitution in
+ * the order the triangle of M_j fixes -- back substitution when M_j is upper
+ * triangular, forward substitution when it is lower triangular.
+ * ---------------------------------------------------------------------- */
+static inline oz op_entry(const oz *A, int64_t lda, int op, int64_t r, int64_t c) {
+  if (op == 0) return AT(A, lda, r, c);
+  if (op == 3) return oz_conj(AT(A, lda, r, c));
+  oz a = AT(A, lda, c, r);
+  return op == 2 ? oz_conj(a) : a;
+}
+
+/* op(A) is upper triangular when A is upper and op keeps the triangle
+ * (op = A or conj(A)), or A is lower and op transposes. */
+static inline int op_is_upper(int uplo, int op) { return (uplo == 0) == (op == 0 || op == 3); }
+
+static int right_op(int trans) { return trans == 0 ? 1 : (trans == 1 ? 0 : 3); }
+
+static void trsv_op_shift(int64_t m, const oz *A, int64_t lda, int uplo, int op, oz s, oz *x) {
+  if (op_is_upper(uplo, op)) {
+    for (int64_t i = m - 1; i >= 0; --i) {
+      x[i] = oz_div(x[i], oz_sub(op_entry(A, lda, op, i, i), s));
+      oz xi = x[i];
+      for (int64_t r = 0; r < i; ++r) x[r] = oz_sub(x[r], oz_mul(xi, op_entry(A, lda, op, r, i)));
+    }
+  } else {
+    for (int64_t i = 0; i < m; ++i) {
+      x[i] = oz_div(x[i], oz_sub(op_entry(A, lda, op, i, i), s));
+      oz xi = x[i];
+      for (int64_t r = i + 1; r < m; ++r) x[r] = oz_sub(x[r], oz_mul(xi, op_entry(A, lda, op, r, i)));
+    }
+  }
+}
+
+void or_solve_variant(int side, int uplo, int trans, int64_t m, int64_t n, const oz *A, int64_t lda,
+                      const oz *shifts, oz *B, int64_t ldb) {
+  const int op = side == 0 ? trans : right_op(trans);
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < n; ++j) {
+    if (side == 0) {
+      trsv_op_shift(m, A, lda, uplo, op, shifts[j], &AT(B, ldb, 0, j));
+    } else {
+      oz *x = (oz *)malloc(sizeof(oz) * (size_t)(m > 0 ? m : 1));
+      for (int64_t c = 0; c < m; ++c) x[c] = AT(B, ldb, j, c);
+      trsv_op_shift(m, A, lda, uplo, op, shifts[j], x);
+      for (int64_t c = 0; c < m; ++c) AT(B, ldb, j, c) = x[c];
+      free(x);
+    }
+  }
+}
+
+/* Safe form of every variant: Alg. 5 run in the variant's own substitution
+ * order.  The operator is first written as an upper-triangular matrix U in
+ * that order -- U = op'(A) when it is upper triangular, else the reversal
+ * U(r,c) = op'(A)(m-1-r, m-1-c) with the right-hand side reversed alike --
+ * so the blocks are cut from the end where the substitution starts (the
+ * ragged block is the last one visited), and SafeMultiShiftTrsm runs on it. */
+void or_safe_solve_variant(int side, int uplo, int trans, int64_t m, int64_t n, const oz *A, int64_t lda,
+                           const oz *shifts, oz *B, int64_t ldb, int64_t nb, int32_t *scale_exp) {
+  const int op = side == 0 ? trans : right_op(trans);
+  const int rev = !op_is_upper(uplo, op);
+  size_t mm = (size_t)(m > 0 ? m : 1), nn = (size_t)(n > 0 ? n : 1);
+  oz *U = (oz *)calloc(mm * mm, sizeof(oz));
+  oz *X = (oz *)malloc(sizeof(oz) * mm * nn);
+  for (int64_t c = 0; c < m; ++c)
+    for (int64_t r = 0; r <= c; ++r)
+      U[r + c * (int64_t)mm] = rev ? op_entry(A, lda, op, m - 1 - r, m - 1 - c) : op_entry(A, lda, op, r, c);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t r = 0; r < m; ++r) {
+      int64_t q = rev ? m - 1 - r : r;
+      X[r + j * (int64_t)mm] = side == 0 ? AT(B, ldb, q, j) : AT(B, ldb, j, q);
+    }
+  or_safe_multishift_solve(m, U, (int64_t)mm, n, shifts, X, (int64_t)mm, nb, 0, scale_exp);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t r = 0; r < m; ++r) {
+      int64_t q = rev ? m - 1 - r : r;
+      if (side == 0) AT(B, ldb, q, j) = X[r + j * (int64_t)mm];
+      else AT(B, ldb, j, q) = X[r + j * (int64_t)mm];
+    }
+  free(U);
+  free(X);
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
