@@ -420,7 +420,60 @@ def extra_measurements(dev, nb):
     res["mixed_8192x2048"] = mixed_vs_fp64(dev, nb)
     res["eig_back_transform_4096"] = back_transform_extra(dev, nb)
     res["gtrevc_4096"] = gtrevc_extra(dev, nb)
+    res["scaling_study_4096"] = scaling_study_extra(dev, nb)
     return res
+
+
+def scaling_study_extra(dev, nb):
+    """The paper's scaling-study comparison (Sec. 6) on the GPU: U the upper
+    triangle of a 4096 x 4096 Hermitian matrix with eigenvalues in [1, 2],
+    shifts uniform in the disk B(1.5, 0.5), n = 256, 1024, 4096 right-hand
+    sides.  Times the library triangular solve with one matrix (cuBLAS ZTRSM
+    through torch, no shifts) beside the multi-shift solve (plain, FP64 and
+    tensor-core substitution; safe, tensor-core) and the left lower variant
+    on U^H (the same work through the remapped engine).  FLOPs 4 m^2 n; every
+    multi-shift call restores B first (a 16 m n-byte copy, inside the time)."""
+    import numpy as np
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    m = 4096
+    U, s_all, _ = W.scaling_problem(m, 4096)
+    Ud = msts.colmajor(torch.from_numpy(U).to(dev))
+    Ld = msts.colmajor(torch.from_numpy(np.asfortranarray(U.conj().T)).to(dev))
+    Ut = torch.triu(Ud).contiguous()
+    g = torch.Generator(device=dev).manual_seed(1607)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {}
+    for n in (256, 1024, 4096):
+        sd = torch.from_numpy(s_all[:n]).to(dev)
+        B = msts.colmajor(torch.randn((m, n), dtype=torch.complex128, device=dev, generator=g))
+        row = {}
+        Bt = B.clone()
+        row["ztrsm_library_no_shifts"] = timed(lambda: torch.linalg.solve_triangular(Ut, Bt, upper=True))
+        for tag, kw in (("multishift_fp64", {}), ("multishift_tensor", {"tensor": True}),
+                        ("safe_multishift_tensor", {"tensor": True, "safe": True})):
+            X = B.clone()
+            row[tag] = timed(lambda: msts.msts_solve(Ud, sd, X.copy_(B), nb=nb, **kw))
+        X = B.clone()
+        row["safe_left_lower_variant_tensor"] = timed(
+            lambda: msts.msts_solve_variant(Ld, sd, X.copy_(B), side="left", uplo="lower", trans="N", nb=nb,
+                                            safe=True, tensor=True))
+        out[f"n{n}"] = {k: {"ms": v, "tflops": 4.0 * m * m * n / (v * 1e-3) / 1e12} for k, v in row.items()}
+    return out
 
 
 def gtrevc_extra(dev, nb):

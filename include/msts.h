@@ -105,6 +105,46 @@ int msts_solve(const msts_z *U, int64_t ldu, int64_t m,
                uint32_t *status, uint32_t flags, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * The other triangular variants (footnote to Sec. 2: the lower-triangular and
+ * right-hand cases of the multi-shift solve).  With op(A) = A, A^T or A^H
+ * (trans = MSTS_OP_N, MSTS_OP_T, MSTS_OP_C) and A upper or lower triangular
+ * (uplo = MSTS_UPLO_UPPER / MSTS_UPLO_LOWER; only that triangle is read):
+ *
+ *   side = MSTS_SIDE_LEFT:  (op(A) - shifts[j] I) X(:,j) = scale_j B(:,j)
+ *                           B is m x n (ldb >= m), one column per shift;
+ *   side = MSTS_SIDE_RIGHT: X(j,:) (op(A) - shifts[j] I) = scale_j B(j,:)
+ *                           B is n x m (ldb >= n), one row per shift;
+ *
+ * scale_j = 1 for the plain solve; with MSTS_SAFE, scale_j = scales[j] =
+ * 2^-scale_exp[j] from Alg. 5 run in the variant's own substitution order
+ * (the operator written as an upper-triangular matrix in that order, blocks
+ * of n_b cut from where the substitution starts).  The shifts are not
+ * conjugated for MSTS_OP_C.  Left/upper/N is msts_solve itself; every other
+ * variant is mapped onto it by exact permutations (and conjugation) of A and
+ * B in the workspace: msts_solve_variant_workspace_size(side, uplo, trans, m,
+ * n, nb, flags) bytes, up to 16 m^2 + 16 m n bytes more than msts_solve.
+ * flags: MSTS_SAFE, MSTS_TENSOR_GEMM.  B is overwritten with X.  Returns 0,
+ * -15 for an unknown side/uplo/trans, the other codes of msts_solve (ldb
+ * checked against the row count of B), or MSTS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+#define MSTS_SIDE_LEFT  0
+#define MSTS_SIDE_RIGHT 1
+#define MSTS_UPLO_UPPER 0
+#define MSTS_UPLO_LOWER 1
+#define MSTS_OP_N 0
+#define MSTS_OP_T 1
+#define MSTS_OP_C 2
+size_t msts_solve_variant_workspace_size(int32_t side, int32_t uplo, int32_t trans, int64_t m, int64_t n,
+                                         int32_t nb, uint32_t flags);
+int msts_solve_variant(int32_t side, int32_t uplo, int32_t trans,
+                       const msts_z *A, int64_t lda, int64_t m,
+                       const msts_z *shifts, int64_t n,
+                       msts_z *B, int64_t ldb,
+                       double *scales, int32_t *scale_exp,
+                       int32_t nb, void *workspace, size_t workspace_bytes,
+                       uint32_t *status, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched multi-shift solves of uneven sizes: problem p is solved exactly as
  * msts_solve would with the fields of probs[p] (host array of `batch`
  * descriptors; the pointers inside are device pointers).  All problems share

@@ -27,7 +27,7 @@ __all__ = [
     "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
     "msts_adjoint_batched", "msts_solve_mixed", "msts_residual", "MSTS_RESIDUAL_OZAKI",
     "MSTS_TENSOR_GEMM", "MSTS_NORMALIZE_COLUMNS", "msts_back_transform", "eig",
-    "msts_gsolve", "msts_gtrevc", "geig",
+    "msts_gsolve", "msts_gtrevc", "geig", "msts_solve_variant",
     "MultiShiftSolve", "multishift_solve",
     "decode_status",
 ]
@@ -131,6 +131,11 @@ def load_library():
         lib.msts_back_transform_workspace_size.argtypes = [_i64, _u32]
         lib.msts_back_transform.restype = ctypes.c_int
         lib.msts_back_transform.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp, _u32, _vp]
+        lib.msts_solve_variant_workspace_size.restype = _sz
+        lib.msts_solve_variant_workspace_size.argtypes = [_i32, _i32, _i32, _i64, _i64, _i32, _u32]
+        lib.msts_solve_variant.restype = ctypes.c_int
+        lib.msts_solve_variant.argtypes = [_i32, _i32, _i32, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp,
+                                           _i32, _vp, _sz, _vp, _u32, _vp]
         _lib = lib
         return lib
 
@@ -225,6 +230,46 @@ def msts_solve(U, shifts, B, *, safe=False, conj_trans=False, nb=32, tensor=Fals
     rc = lib.msts_solve(_ptr(U), ldu, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(scales), _ptr(sexp),
                         nb, wp, wb, _ptr(status), flags, _stream(dev))
     _check(rc, "msts_solve")
+    return B, scales, sexp, status
+
+
+_SIDES = {"left": 0, "right": 1}
+_UPLOS = {"upper": 0, "lower": 1}
+_OPS = {"N": 0, "T": 1, "C": 2}
+
+
+def msts_solve_variant(A, shifts, B, *, side="left", uplo="upper", trans="N", safe=False, nb=32,
+                       tensor=False, status=None):
+    """The lower-triangular and right-hand variants (footnote to Sec. 2), in
+    place on B: left (op(A) - s_j I) X(:,j) = scale_j B(:,j) with B m x n;
+    right X(j,:) (op(A) - s_j I) = scale_j B(j,:) with B n x m; op(A) = A, A^T
+    or A^H (trans "N", "T", "C"), A upper or lower (only that triangle read).
+    Returns (B, scales, scale_exp, status); scales/scale_exp are None unless safe."""
+    if side not in _SIDES or uplo not in _UPLOS or trans not in _OPS:
+        raise ValueError("side in {left,right}, uplo in {upper,lower}, trans in {N,T,C}")
+    lib = load_library()
+    m = A.shape[0]
+    lda = _mat(A, "A", m)
+    if side == "left":
+        n = B.shape[1]
+        ldb = _mat(B, "B", m)
+    else:
+        n = B.shape[0]
+        ldb = _mat(B, "B", n)
+        if B.shape[1] != m:
+            raise ValueError("B must be n x m for the right side")
+    _vec(shifts, "shifts")
+    dev = B.device
+    flags = (MSTS_SAFE if safe else 0) | (MSTS_TENSOR_GEMM if tensor else 0)
+    scales = torch.empty(n, dtype=torch.float64, device=dev) if safe else None
+    sexp = torch.empty(n, dtype=torch.int32, device=dev) if safe else None
+    args = (_SIDES[side], _UPLOS[uplo], _OPS[trans])
+    ws = _workspace(lib.msts_solve_variant_workspace_size(*args, m, n, nb, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_solve_variant(*args, _ptr(A), lda, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(scales), _ptr(sexp),
+                                nb, wp, wb, _ptr(status), flags, _stream(dev))
+    _check(rc, "msts_solve_variant")
     return B, scales, sexp, status
 
 

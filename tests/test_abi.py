@@ -113,3 +113,29 @@ def test_generalized_arguments_and_workspace(lib):
     assert t(P, 4, P, 4, 4, P, 4, None, P, P, 32, P, 1 << 20, None, 0, None) == -8
     assert t(P, 4, P, 4, 4, P, 4, P, P, P, 32, P, 1 << 20, None, 8, None) == -15
     assert t(None, 1, None, 1, 0, None, 1, None, None, None, 32, None, 0, None, 0, None) == 0
+
+
+def test_variant_arguments_and_workspace(lib):
+    P = ctypes.c_void_p(16)
+    ws = lib.msts_solve_variant_workspace_size
+    sw = lib.msts_solve_workspace_size
+    a256 = lambda x: (x + 255) // 256 * 256
+    m, n = 100, 12
+    for flags in (0, 1, 8, 9):
+        assert ws(0, 0, 0, m, n, 32, flags) == sw(m, n, 32, flags)                         # left/upper/N
+        assert ws(1, 0, 1, m, n, 32, flags) == a256(16 * m * n) + sw(m, n, 32, flags)       # right/upper/T
+        assert ws(0, 1, 0, m, n, 32, flags) == a256(16 * m * m) + a256(16 * m * n) + sw(m, n, 32, flags)
+        assert ws(1, 1, 2, m, n, 32, flags) == a256(16 * m * m) + a256(16 * m * n) + sw(m, n, 32, flags)
+    assert ws(0, 0, 2, m, n, 32, 0) == a256(16 * n) + sw(m, n, 32, 2)                       # conjugate-transposed engine
+    assert ws(0, 0, 2, m, n, 32, 1) == a256(16 * m * m) + a256(16 * m * n) + sw(m, n, 32, 1)   # safe: reversed
+    assert ws(2, 0, 0, m, n, 32, 0) == 0 and ws(0, 2, 0, m, n, 32, 0) == 0 and ws(0, 0, 3, m, n, 32, 0) == 0
+    assert ws(0, 0, 0, m, n, 32, 2) == 0 and ws(0, 0, 0, m, n, 48, 0) == 0
+    v = lib.msts_solve_variant
+    assert v(0, 0, 5, P, 4, 4, P, 2, P, 4, None, None, 32, None, 0, None, 0, None) == -15
+    assert v(0, 1, 0, P, 3, 4, P, 2, P, 4, None, None, 32, None, 0, None, 0, None) == -2
+    assert v(1, 1, 0, P, 4, 4, P, 6, P, 5, None, None, 32, None, 0, None, 0, None) == -7   # right: ldb >= n
+    assert v(0, 1, 0, P, 4, 4, P, 2, P, 3, None, None, 32, None, 0, None, 0, None) == -7   # left: ldb >= m
+    assert v(0, 1, 0, P, 4, 4, P, 2, P, 4, None, None, 32, None, 0, None, 2, None) == -14  # no conj-trans flag
+    assert v(0, 1, 0, P, 4, 4, P, 2, P, 4, None, None, 32, None, 0, None, 1, None) == -8   # safe needs scales
+    assert v(0, 1, 0, P, 4, 4, P, 2, P, 4, None, None, 32, None, 0, None, 0, None) == -11  # workspace missing
+    assert v(1, 1, 1, None, 1, 0, None, 0, None, 1, None, None, 32, None, 0, None, 0, None) == 0
