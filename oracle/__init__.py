@@ -281,6 +281,36 @@ def pseudospectra(T, z, V0, iters):
     return sig, al, be, st
 
 
+def pseudospectra_1norm(T, z, Q=None):
+    """1-norm pseudospectra (footnote to Sec. 5): Hager/Higham estimates of
+    ||Q (T - z_p I)^{-1} Q^H||_1 for every grid point (Q = I when None).
+    Returns (est, kind, steps): kind = j when est = ||R e_j||_1, -1 for the
+    start vector e/m, -2 for the alternative vector; steps = R^H applications."""
+    T = _cz(T, "T")
+    zz = np.ascontiguousarray(z, dtype=np.complex128)
+    m, N = T.shape[0], zz.shape[0]
+    Qa = None if Q is None else _cz(Q, "Q")
+    est = np.zeros(N, dtype=np.float64)
+    kind = np.zeros(N, dtype=np.int32)
+    steps = np.zeros(N, dtype=np.int32)
+    _load().or_pseudospectra_1norm(_c_int64(m), _p(T), _c_int64(_ld(T)), None if Qa is None else _p(Qa),
+                                   _c_int64(1 if Qa is None else _ld(Qa)), _c_int64(N), _p(zz), _p(est),
+                                   _p(kind), _p(steps))
+    return est, kind, steps
+
+
+def portrait_grid(T, nx, ny):
+    """Automatic grid of the spectral portrait: the eigenvalue bounding box
+    widened by a quarter of its larger side, nx x ny points (point k + l nx).
+    Returns (z, box) with box = (xmin, xmax, ymin, ymax)."""
+    T = _cz(T, "T")
+    z = np.zeros(nx * ny, dtype=np.complex128)
+    box = np.zeros(4, dtype=np.float64)
+    _load().or_portrait_grid(_c_int64(T.shape[0]), _p(T), _c_int64(_ld(T)), _c_int64(nx), _c_int64(ny),
+                             _p(z), _p(box))
+    return z, box
+
+
 def tridiag_max_eig(a, b):
     """Largest eigenvalue of tridiag(b, a, b) by Sturm bisection."""
     a = np.ascontiguousarray(a, dtype=np.float64)

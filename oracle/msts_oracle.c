@@ -844,6 +844,140 @@ void or_safe_solve_variant(int side, int uplo, int trans, int64_t m, int64_t n, 
   free(X);
 }
 
+/* ------------------------------------------------------------------------
+ * 1-norm pseudospectra (the footnote to Sec. 5: Hager's estimator as refined
+ * by Higham, driven by shifted triangular solves with the grid points as
+ * shifts).  For each grid point z, an estimate of ||R||_1 with
+ * R = Q (T - zI)^{-1} Q^H, i.e. the resolvent norm ||(zI - A)^{-1}||_1 of
+ * A = Q T Q^H (Q = I when Q is NULL; the sign of the resolvent does not
+ * change any norm).
+ *
+ * Estimator (t = 1 column, at most 5 gradient steps), with y = R x,
+ * g = ||y||_1 and sign(y)_i = y_i/|y_i| (1 where y_i = 0):
+ *   x = (1/m) e;  y = R x;  est = g;  kind = -1
+ *   repeat up to 5 times:
+ *     w = R^H sign(y);  j = the first index of max_i |w_i|
+ *     stop if |w_j| <= g                 (x is a local maximum of ||R x||_1:
+ *                                          w^H x = ||R x||_1 for every x)
+ *     x = e_j;  y = R x;  g = ||y||_1
+ *     stop if g <= est                   (no increase)
+ *     est = g;  kind = j
+ *   alternative vector x_i = (-1)^i (1 + i/(m-1)), i = 0..m-1 (m >= 2):
+ *     est = max(est, 2 ||R x||_1 / (3m)), kind = -2 when it wins.
+ * steps[p] = the number of R^H applications.  ||y||_1 sums the moduli in
+ * increasing row order.
+ * ---------------------------------------------------------------------- */
+static void apply_resolvent(int64_t m, const oz *T, int64_t ldt, const oz *Q, int64_t ldq, oz z, int adj,
+                            oz *x, oz *tmp) {
+  if (Q) {
+    for (int64_t i = 0; i < m; ++i) {                 /* tmp = Q^H x */
+      oz s = oz_make(0.0, 0.0);
+      for (int64_t r = 0; r < m; ++r) s = oz_add(s, oz_mul(oz_conj(AT(Q, ldq, r, i)), x[r]));
+      tmp[i] = s;
+    }
+  } else {
+    memcpy(tmp, x, sizeof(oz) * (size_t)m);
+  }
+  if (adj) trsv_shift_conj_trans(m, T, ldt, z, tmp);  /* (T - zI)^{-H}: (T^H - conj(z) I)^{-1} */
+  else trsv_shift(m, T, ldt, z, tmp);
+  if (Q) {
+    for (int64_t r = 0; r < m; ++r) {                 /* x = Q tmp */
+      oz s = oz_make(0.0, 0.0);
+      for (int64_t i = 0; i < m; ++i) s = oz_add(s, oz_mul(AT(Q, ldq, r, i), tmp[i]));
+      x[r] = s;
+    }
+  } else {
+    memcpy(x, tmp, sizeof(oz) * (size_t)m);
+  }
+}
+
+static double norm1_vec(int64_t m, const oz *y) {
+  double s = 0.0;
+  for (int64_t i = 0; i < m; ++i) s += oz_abs(y[i]);
+  return s;
+}
+
+static void sign_vec(int64_t m, oz *y) {
+  for (int64_t i = 0; i < m; ++i) {
+    double a = oz_abs(y[i]);
+    y[i] = a == 0.0 ? oz_make(1.0, 0.0) : oz_make(y[i].re / a, y[i].im / a);
+  }
+}
+
+void or_pseudospectra_1norm(int64_t m, const oz *T, int64_t ldt, const oz *Q, int64_t ldq, int64_t N,
+                            const oz *z, double *est_out, int32_t *kind_out, int32_t *steps_out) {
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t p = 0; p < N; ++p) {
+    oz *y = (oz *)malloc(sizeof(oz) * (size_t)(m > 0 ? m : 1));
+    oz *tmp = (oz *)malloc(sizeof(oz) * (size_t)(m > 0 ? m : 1));
+    for (int64_t i = 0; i < m; ++i) y[i] = oz_make(1.0 / (double)m, 0.0);
+    apply_resolvent(m, T, ldt, Q, ldq, z[p], 0, y, tmp);
+    double g = norm1_vec(m, y), est = g;
+    int kind = -1, steps = 0;
+    for (int it = 0; it < 5 && m > 1; ++it) {
+      sign_vec(m, y);
+      apply_resolvent(m, T, ldt, Q, ldq, z[p], 1, y, tmp);       /* w = R^H sign(y) */
+      ++steps;
+      int64_t j = 0;
+      double wj = -1.0;
+      for (int64_t i = 0; i < m; ++i) { double a = oz_abs(y[i]); if (a > wj) { wj = a; j = i; } }
+      if (wj <= g) break;
+      for (int64_t i = 0; i < m; ++i) y[i] = oz_make(i == j ? 1.0 : 0.0, 0.0);
+      apply_resolvent(m, T, ldt, Q, ldq, z[p], 0, y, tmp);
+      g = norm1_vec(m, y);
+      if (g <= est) break;
+      est = g;
+      kind = (int)j;
+    }
+    if (m > 1) {
+      for (int64_t i = 0; i < m; ++i) {
+        double v = 1.0 + (double)i / (double)(m - 1);
+        y[i] = oz_make((i & 1) ? -v : v, 0.0);
+      }
+      apply_resolvent(m, T, ldt, Q, ldq, z[p], 0, y, tmp);
+      double alt = 2.0 * norm1_vec(m, y) / (3.0 * (double)m);
+      if (alt > est) { est = alt; kind = -2; }
+    }
+    est_out[p] = est;
+    kind_out[p] = kind;
+    steps_out[p] = steps;
+    free(y);
+    free(tmp);
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * Automatic grid of a spectral portrait (the SpectralPortrait driver of
+ * Sec. 5, whose grid the paper leaves to the software): the bounding box
+ * [a, b] x [c, d] of the eigenvalues diag(T), widened on every side by
+ * h = max(0.25 max(b - a, d - c), 2^-20 max(1, max |T(i,i)|)), sampled with
+ * nx x ny points: z(k, l) = (a - h + k dx) + i (c - h + l dy), k < nx, l < ny,
+ * dx = (b - a + 2h)/(nx - 1) (0 when nx == 1), likewise dy; point k + l nx.
+ * Every operation is a single rounding in the order written.
+ * ---------------------------------------------------------------------- */
+void or_portrait_grid(int64_t m, const oz *T, int64_t ldt, int64_t nx, int64_t ny, oz *zout, double *box) {
+  double a = 0.0, b = 0.0, c = 0.0, d = 0.0, big = 1.0;
+  for (int64_t i = 0; i < m; ++i) {
+    oz t = AT(T, ldt, i, i);
+    if (i == 0 || t.re < a) a = t.re;
+    if (i == 0 || t.re > b) b = t.re;
+    if (i == 0 || t.im < c) c = t.im;
+    if (i == 0 || t.im > d) d = t.im;
+    double mod = oz_abs(t);
+    if (mod > big) big = mod;
+  }
+  double w = b - a, hgt = d - c;
+  double h = 0.25 * (w > hgt ? w : hgt);
+  double hmin = ldexp(big, -20);
+  if (h < hmin) h = hmin;
+  double x0 = a - h, y0 = c - h;
+  double dx = nx > 1 ? ((b + h) - x0) / (double)(nx - 1) : 0.0;
+  double dy = ny > 1 ? ((d + h) - y0) / (double)(ny - 1) : 0.0;
+  for (int64_t l = 0; l < ny; ++l)
+    for (int64_t k = 0; k < nx; ++k) zout[k + l * nx] = oz_make(x0 + (double)k * dx, y0 + (double)l * dy);
+  box[0] = x0; box[1] = b + h; box[2] = y0; box[3] = d + h;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
