@@ -950,10 +950,11 @@ void or_pseudospectra_1norm(int64_t m, const oz *T, int64_t ldt, const oz *Q, in
  * Automatic grid of a spectral portrait (the SpectralPortrait driver of
  * Sec. 5, whose grid the paper leaves to the software): the bounding box
  * [a, b] x [c, d] of the eigenvalues diag(T), widened on every side by
- * h = max(0.25 max(b - a, d - c), 2^-20 max(1, max |T(i,i)|)), sampled with
- * nx x ny points: z(k, l) = (a - h + k dx) + i (c - h + l dy), k < nx, l < ny,
- * dx = (b - a + 2h)/(nx - 1) (0 when nx == 1), likewise dy; point k + l nx.
- * Every operation is a single rounding in the order written.
+ * h = max(0.25 max(b - a, d - c), 2^-20 max(1, max_i max(|Re T(i,i)|, |Im T(i,i)|)))
+ * (no square roots: the grid is exact up to the roundings written here), and
+ * sampled with nx x ny points: x0 = a - h, x1 = b + h, dx = (x1 - x0)/(nx - 1)
+ * (0 when nx == 1), z(k, l) = (x0 + k dx) + i (y0 + l dy), likewise in y;
+ * point k + l nx.  Every operation is a single rounding in the order written.
  * ---------------------------------------------------------------------- */
 void or_portrait_grid(int64_t m, const oz *T, int64_t ldt, int64_t nx, int64_t ny, oz *zout, double *box) {
   double a = 0.0, b = 0.0, c = 0.0, d = 0.0, big = 1.0;
@@ -963,8 +964,8 @@ void or_portrait_grid(int64_t m, const oz *T, int64_t ldt, int64_t nx, int64_t n
     if (i == 0 || t.re > b) b = t.re;
     if (i == 0 || t.im < c) c = t.im;
     if (i == 0 || t.im > d) d = t.im;
-    double mod = oz_abs(t);
-    if (mod > big) big = mod;
+    if (fabs(t.re) > big) big = fabs(t.re);
+    if (fabs(t.im) > big) big = fabs(t.im);
   }
   double w = b - a, hgt = d - c;
   double h = 0.25 * (w > hgt ? w : hgt);

@@ -130,6 +130,6 @@ def test_portrait_grid_properties():
 def test_portrait_grid_degenerate_spectrum():
     T = np.asfortranarray(np.eye(4, dtype=np.complex128) * (3.0 - 4.0j))
     z, box = oracle.portrait_grid(T, 3, 3)
-    h = 5.0 * 2.0 ** -20
+    h = 4.0 * 2.0 ** -20                               # 2^-20 max(|Re|, |Im|)
     assert np.array_equal(box, [3.0 - h, 3.0 + h, -4.0 - h, -4.0 + h])
     assert z[4] == 3.0 - 4.0j                          # the centre point of a 3 x 3 grid
