@@ -421,7 +421,59 @@ def extra_measurements(dev, nb):
     res["eig_back_transform_4096"] = back_transform_extra(dev, nb)
     res["gtrevc_4096"] = gtrevc_extra(dev, nb)
     res["scaling_study_4096"] = scaling_study_extra(dev, nb)
+    res["pseudospectra_extras"] = pseudo_extras(dev, nb)
     return res
+
+
+def pseudo_extras(dev, nb):
+    """Pseudospectra beyond the 2-norm workload: the 1-norm estimator on the
+    pseudospectra workload (2000 x 2000, 10^4 points; without Q, and with a
+    random unitary Q as for a general A = Q T Q^H), and spectral portraits of
+    the Fox-Li matrix (F = 10; Schur factor from the host library, timed
+    apart) on the automatic grid: n = 100 at 100 x 100 points in both norms,
+    n = 3200 at 100 x 100 points in the 2-norm (20 Lanczos steps)."""
+    import numpy as np
+    import scipy.linalg
+    import torch
+    import paper_1607_01477_gb300 as msts
+    from paper_1607_01477_gb300 import workloads as W
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    out = {}
+    T, z, _ = W.pseudo_problem()
+    Td, zd = msts.colmajor(torch.from_numpy(T).to(dev)), torch.from_numpy(z).to(dev)
+    g = torch.Generator(device=dev).manual_seed(1607)
+    Qd = msts.colmajor(torch.linalg.qr(torch.randn((2000, 2000), dtype=torch.complex128, device=dev,
+                                                   generator=g))[0])
+    for tag, Q in (("no_q", None), ("with_q", Qd)):
+        ms, (est, kind, steps, _) = timed(lambda: msts.msts_pseudospectra_1norm(Td, zd, Q, nb=nb, tensor=True))
+        out[f"norm1_2000_grid100x100_{tag}"] = {"ms": ms, "points_per_s": z.size / (ms * 1e-3),
+                                                "mean_steps": steps.double().mean().item(),
+                                                "max_steps": int(steps.max().item())}
+    del Qd
+    for n, norms in ((100, (2, 1)), (3200, (2,))):
+        A = W.fox_li(n, 10.0)
+        t0 = time.perf_counter()
+        Tf, Qf = scipy.linalg.schur(A, output="complex")
+        schur_ms = (time.perf_counter() - t0) * 1e3
+        Tfd = msts.colmajor(torch.from_numpy(np.asfortranarray(Tf)).to(dev))
+        Qfd = msts.colmajor(torch.from_numpy(np.asfortranarray(Qf)).to(dev))
+        row = {"host_schur_ms": schur_ms}
+        for nrm in norms:
+            ms, _ = timed(lambda: msts.spectral_portrait(Tfd, 100, 100, norm=nrm, Q=Qfd, iters=20, nb=nb))
+            row[f"norm{nrm}_ms"] = ms
+            row[f"norm{nrm}_points_per_s"] = 1e4 / (ms * 1e-3)
+        out[f"fox_li_F10_n{n}_portrait100x100"] = row
+    return out
 
 
 def scaling_study_extra(dev, nb):

@@ -247,7 +247,7 @@ int msts_back_transform(const msts_z *Q, int64_t ldq, int64_t m,
  * Pseudospectra (Sec. 5, Alg. 7, Van Loan / Lui): for each grid point z[p],
  *   sigma_min[p] = sigma_min(T - z[p] I) = 1 / ||(z[p] I - A)^{-1}||_2
  * for A = Q T Q^H, from the largest eigenvalue of (T - zI)^{-H} (T - zI)^{-1}
- * estimated by `iters` Lanczos steps; every operator application is a pair of
+ * estimated by `iters` (1..64) Lanczos steps; every operator application is a pair of
  * multi-shift solves over all N grid points at once (upper with T - zI, then
  * lower with its conjugate transpose).
  * V0       m x N start vectors (leading dimension ldv), normalised inside.
@@ -264,6 +264,47 @@ int msts_pseudospectra(const msts_z *T, int64_t ldt, int64_t m,
                        double *sigma_min, double *alpha, double *beta, int32_t *steps,
                        int32_t nb, void *workspace, size_t workspace_bytes,
                        uint32_t *status, uint32_t flags, void *stream);   /* flags: 0 or MSTS_TENSOR_GEMM */
+
+/* ---------------------------------------------------------------------------
+ * 1-norm pseudospectra (footnote to Sec. 5: Hager's estimator with Higham's
+ * refinements, driven by multi-shift solves with the grid points as shifts):
+ *   est[p] <= ||(z[p] I - A)^{-1}||_1,  A = Q T Q^H (Q may be NULL: A = T),
+ * a lower-bound estimate of the resolvent 1-norm from the start vector e/m,
+ * at most five gradient steps (each one solve with (T - zI)^H and one with
+ * T - zI, between products with Q^H and Q), and the alternative vector
+ * x(i) = (-1)^i (1 + i/(m-1)) scaled by 2/(3m).  Points leave the iteration
+ * as they converge; each step solves only the points still iterating.
+ * kind[p] = j >= 0 when est[p] = ||R e_j||_1, -1 for the start vector, -2 for
+ * the alternative vector; steps[p] = the number of (T - zI)^H solves.
+ * T        m x m upper triangular (ldt), Q m x m unitary (ldq) or NULL.
+ * z, est, kind, steps: N grid points and the three outputs (device).
+ * flags    0 or MSTS_TENSOR_GEMM (the substitution and the Q products on the
+ *          tensor cores, FP64-accurate).
+ * workspace: msts_pseudospectra_1norm_workspace_size(m, N, nb, Q != NULL,
+ * flags) bytes.  The call synchronises the stream once per step (the number
+ * of live points decides the next launch).  A grid point equal to a
+ * diagonal entry of T raises MSTS_STATUS_ZERO_PIVOT.  Returns 0, -k for an
+ * invalid argument k (-9/-10 missing / small workspace), or MSTS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+size_t msts_pseudospectra_1norm_workspace_size(int64_t m, int64_t N, int32_t nb, int32_t with_q, uint32_t flags);
+int msts_pseudospectra_1norm(const msts_z *T, int64_t ldt, int64_t m,
+                             const msts_z *Q, int64_t ldq,
+                             const msts_z *z, int64_t N,
+                             double *est, int32_t *kind, int32_t *steps,
+                             int32_t nb, void *workspace, size_t workspace_bytes,
+                             uint32_t *status, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Automatic grid of a spectral portrait (the SpectralPortrait driver of
+ * Sec. 5): box = (x0, x1, y0, y1) is the bounding box of diag(T) widened on
+ * every side by h = max(max(x-side, y-side)/4, 2^-20 max(1, max_i max(|Re
+ * T(i,i)|, |Im T(i,i)|))); z[k + l nx] = (x0 + k dx) + i (y0 + l dy) with
+ * dx = (x1 - x0)/(nx - 1) (0 for nx == 1), likewise dy, each operation one
+ * rounding.  T (device, ldt >= m >= 1); z: nx*ny points, box: 4 doubles
+ * (device).  Returns 0, -k for an invalid argument k, or MSTS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+int msts_portrait_grid(const msts_z *T, int64_t ldt, int64_t m, int64_t nx, int64_t ny,
+                       msts_z *z, double *box, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Adjoint of X = (U - s_j I)^{-1} B(:,j) (not in the paper): given

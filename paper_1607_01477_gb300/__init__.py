@@ -28,6 +28,7 @@ __all__ = [
     "msts_adjoint_batched", "msts_solve_mixed", "msts_residual", "MSTS_RESIDUAL_OZAKI",
     "MSTS_TENSOR_GEMM", "MSTS_NORMALIZE_COLUMNS", "msts_back_transform", "eig",
     "msts_gsolve", "msts_gtrevc", "geig", "msts_solve_variant",
+    "msts_pseudospectra_1norm", "msts_portrait_grid", "spectral_portrait",
     "MultiShiftSolve", "multishift_solve",
     "decode_status",
 ]
@@ -136,6 +137,13 @@ def load_library():
         lib.msts_solve_variant.restype = ctypes.c_int
         lib.msts_solve_variant.argtypes = [_i32, _i32, _i32, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp,
                                            _i32, _vp, _sz, _vp, _u32, _vp]
+        lib.msts_pseudospectra_1norm_workspace_size.restype = _sz
+        lib.msts_pseudospectra_1norm_workspace_size.argtypes = [_i64, _i64, _i32, _i32, _u32]
+        lib.msts_pseudospectra_1norm.restype = ctypes.c_int
+        lib.msts_pseudospectra_1norm.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i32, _vp,
+                                                 _sz, _vp, _u32, _vp]
+        lib.msts_portrait_grid.restype = ctypes.c_int
+        lib.msts_portrait_grid.argtypes = [_vp, _i64, _i64, _i64, _i64, _vp, _vp, _vp]
         _lib = lib
         return lib
 
@@ -454,6 +462,66 @@ def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, tensor=False, status=None, 
                                 _stream(dev))
     _check(rc, "msts_pseudospectra")
     return sig, al, be, st, status
+
+
+def msts_pseudospectra_1norm(T, z, Q=None, *, nb=32, tensor=True, status=None):
+    """1-norm pseudospectra (footnote to Sec. 5): Hager/Higham lower-bound
+    estimates of ||(z_p I - A)^{-1}||_1, A = Q T Q^H (A = T without Q).
+
+    Returns (est, kind, steps, status): kind[p] = j when est = ||R e_j||_1,
+    -1 for the start vector, -2 for the alternative vector."""
+    lib = load_library()
+    m = T.shape[0]
+    ldt = _mat(T, "T", m)
+    ldq = _mat(Q, "Q", m) if Q is not None else 1
+    _vec(z, "z")
+    N = z.shape[0]
+    dev = T.device
+    est = torch.empty(N, dtype=torch.float64, device=dev)
+    kind = torch.empty(N, dtype=torch.int32, device=dev)
+    steps = torch.empty(N, dtype=torch.int32, device=dev)
+    flags = MSTS_TENSOR_GEMM if tensor else 0
+    ws = _workspace(lib.msts_pseudospectra_1norm_workspace_size(m, N, nb, 0 if Q is None else 1, flags), dev)
+    wp, wb = _ws_ptr(ws)
+    status = _status(dev, status)
+    rc = lib.msts_pseudospectra_1norm(_ptr(T), ldt, m, _ptr(Q), ldq, _ptr(z), N, _ptr(est), _ptr(kind),
+                                      _ptr(steps), nb, wp, wb, _ptr(status), flags, _stream(dev))
+    _check(rc, "msts_pseudospectra_1norm")
+    return est, kind, steps, status
+
+
+def msts_portrait_grid(T, nx, ny):
+    """The automatic grid of a spectral portrait: (z, box), z of nx*ny points
+    (point k + l nx), box = (xmin, xmax, ymin, ymax) on the device."""
+    lib = load_library()
+    m = T.shape[0]
+    ldt = _mat(T, "T", m)
+    dev = T.device
+    z = torch.empty(nx * ny, dtype=torch.complex128, device=dev)
+    box = torch.empty(4, dtype=torch.float64, device=dev)
+    rc = lib.msts_portrait_grid(_ptr(T), ldt, m, nx, ny, _ptr(z), _ptr(box), _stream(dev))
+    _check(rc, "msts_portrait_grid")
+    return z, box
+
+
+def spectral_portrait(T, nx=100, ny=100, *, norm=2, Q=None, iters=20, nb=32, tensor=True, seed=0):
+    """SpectralPortrait (Sec. 5): resolvent norms of A = Q T Q^H over the
+    automatic grid.  norm=2: 1/sigma_min(T - zI) by inverse Lanczos (Q does
+    not change the 2-norm; iters <= 64; start vectors CN(0,1) from `seed`); norm=1: the
+    Hager/Higham estimate of ||(zI - A)^{-1}||_1.  Returns (resolvent norms
+    as an ny x nx array, box, status)."""
+    z, box = msts_portrait_grid(T, nx, ny)
+    m = T.shape[0]
+    if norm == 2:
+        g = torch.Generator(device=T.device).manual_seed(seed)
+        V0 = colmajor(torch.randn((m, nx * ny), dtype=torch.complex128, device=T.device, generator=g))
+        sig, _, _, _, status = msts_pseudospectra(T, z, V0, iters, nb=nb, tensor=tensor)
+        res = 1.0 / sig
+    elif norm == 1:
+        res, _, _, status = msts_pseudospectra_1norm(T, z, Q, nb=nb, tensor=tensor)
+    else:
+        raise ValueError("norm must be 1 or 2")
+    return res.reshape(ny, nx), box, status
 
 
 def msts_adjoint(U, shifts, B, GX, *, nb=32, status=None):

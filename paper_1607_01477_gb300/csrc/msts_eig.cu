@@ -10,6 +10,7 @@
 #include "../../include/msts.h"
 #include "msts_common.cuh"
 #include "msts_ozaki.h"
+#include "msts_eig.h"
 #include "msts_trace.h"
 
 namespace msts {
@@ -18,31 +19,34 @@ namespace {
 constexpr int kT = 32;         // FP64 path: 32 x 32 output tile, 8 x 32 threads, 4 outputs each
 constexpr int kKT = 16;        // K step staged in shared memory
 
-// X(i, j) = sum_{k <= j} Q(i, k) Z(k, j) in FP64 (Z upper triangular).
-__global__ void __launch_bounds__(256) k_zgemm_triu(const double2 *Q, long long ldq, const double2 *Z,
-                                                    long long ldz, double2 *X, long long ldx, int m) {
-  __shared__ double2 sQ[kKT][kT + 1];
-  __shared__ double2 sZ[kKT][kT + 1];
+// C(i, j) = sum_k A(i, k) B(k, j) in FP64, A m x m, B m x n; with TRIU, B is
+// upper triangular (k <= j only: K stops at the tile's last column).
+template <bool TRIU>
+__global__ void __launch_bounds__(256) k_zgemm(const double2 *A, long long lda, const double2 *B,
+                                               long long ldb, double2 *C, long long ldc, int m, int n) {
+  __shared__ double2 sA[kKT][kT + 1];
+  __shared__ double2 sB[kKT][kT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // ty in [0, 8)
   const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
   double2 acc[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
-  const int kend = min(m, j0 + kT);               // rows of Z below the tile's last column are zero
+  const int kend = TRIU ? min(m, j0 + kT) : m;   // rows of B below the tile's last column are zero
   for (int k0 = 0; k0 < kend; k0 += kKT) {
     for (int idx = threadIdx.x; idx < kKT * kT; idx += 256) {
       const int kk = idx / kT, c = idx % kT;
       const int k = k0 + kk;
-      // Q(i0 + c, k) and Z(k, j0 + c)
-      sQ[kk][c] = (k < m && i0 + c < m) ? Q[(i0 + c) + (long long)k * ldq] : make_double2(0.0, 0.0);
-      sZ[kk][c] = (k < m && j0 + c < m && k <= j0 + c) ? Z[k + (long long)(j0 + c) * ldz] : make_double2(0.0, 0.0);
+      // A(i0 + c, k) and B(k, j0 + c)
+      sA[kk][c] = (k < m && i0 + c < m) ? A[(i0 + c) + (long long)k * lda] : make_double2(0.0, 0.0);
+      sB[kk][c] = (k < m && j0 + c < n && (!TRIU || k <= j0 + c)) ? B[k + (long long)(j0 + c) * ldb]
+                                                                    : make_double2(0.0, 0.0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kKT; ++kk) {
-      const double2 q = sQ[kk][tx];
+      const double2 q = sA[kk][tx];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = zfma(acc[u], q, sZ[kk][ty + 8 * u]);
+      for (int u = 0; u < 4; ++u) acc[u] = zfma(acc[u], q, sB[kk][ty + 8 * u]);
     }
     __syncthreads();
   }
@@ -51,7 +55,7 @@ __global__ void __launch_bounds__(256) k_zgemm_triu(const double2 *Q, long long 
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int j = j0 + ty + 8 * u;
-    if (j < m) X[i + (long long)j * ldx] = acc[u];
+    if (j < n) C[i + (long long)j * ldc] = acc[u];
   }
 }
 
@@ -84,6 +88,21 @@ __global__ void k_normalize_cols(double2 *X, long long ldx, int m, int n) {
 }
 
 }  // namespace
+
+cudaError_t zgemm_fp64(const double2 *A, long long lda, const double2 *B, long long ldb, double2 *C, long long ldc,
+                       int m, int n, bool triu_b, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((n + kT - 1) / kT), (unsigned)((m + kT - 1) / kT));
+  // Recorded as the FP64 GEMM: 8 FLOPs per complex multiply-add.
+  const double macs = triu_b ? 0.5 * (double)m * n * (double)std::min(m, n) : (double)m * m * (double)n;
+  void *h = trace_on() ? trace_start(0, 8.0 * macs, 16.0 * ((double)m * m + 2.0 * (double)m * n), st) : nullptr;
+  if (triu_b) k_zgemm<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, m, n);
+  else k_zgemm<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, m, n);
+  trace_stop(h, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace msts
 
 extern "C" {
@@ -116,13 +135,7 @@ int msts_back_transform(const msts_z *Q, int64_t ldq, int64_t m, const msts_z *Z
   if (flags & MSTS_TENSOR_GEMM) {
     e = msts::ozaki_product(q, ldq, (int)m, z, ldz, (int)m, true, x, ldx, workspace, status, st);
   } else {
-    const int t = (int)((m + msts::kT - 1) / msts::kT);
-    // Recorded as the FP64 GEMM: 8 FLOPs per complex multiply-add, m^3 / 2 of them.
-    void *h = msts::trace_on() ? msts::trace_start(0, 4.0 * (double)m * m * m, 48.0 * (double)m * m, st) : nullptr;
-    msts::k_zgemm_triu<<<dim3(t, t), 256, 0, st>>>(q, ldq, z, ldz, x, ldx, (int)m);
-    msts::trace_stop(h, st);
-    msts::count_launches(1);
-    e = cudaGetLastError();
+    e = msts::zgemm_fp64(q, ldq, z, ldz, x, ldx, (int)m, (int)m, true, st);
   }
   if (e != cudaSuccess) return MSTS_ERR_CUDA;
   if (flags & MSTS_NORMALIZE_COLUMNS) {

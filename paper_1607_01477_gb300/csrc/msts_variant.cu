@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "../../include/msts.h"
+#include "msts_remap.h"
 #include "msts_trace.h"
 
 namespace msts {
@@ -100,18 +101,6 @@ __global__ void k_conj_vec(const double2 *__restrict__ s, double2 *__restrict__ 
   if (i < n) t[i] = make_double2(s[i].x, -s[i].y);
 }
 
-cudaError_t remap(const double2 *src, long long lds, double2 *dst, long long ldd, int rows, int cols,
-                  bool tr, bool rev_r, bool rev_c, bool conj, bool upper, cudaStream_t st) {
-  if (rows == 0 || cols == 0) return cudaSuccess;
-  const dim3 grid((unsigned)((rows + kRT - 1) / kRT), (unsigned)std::min((cols + kRT - 1) / kRT, 65535));
-  if (tr)
-    k_remap<true><<<grid, 256, 0, st>>>(src, lds, dst, ldd, rows, cols, rev_r, rev_c, conj, upper);
-  else
-    k_remap<false><<<grid, 256, 0, st>>>(src, lds, dst, ldd, rows, cols, rev_r, rev_c, conj, upper);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
 // Code of op' for the effective left operator: 0 = A, 1 = A^T, 2 = A^H,
 // 3 = conj(A).
 int effective_op(int32_t side, int32_t trans) {
@@ -163,6 +152,19 @@ bool args_ok(int32_t side, int32_t uplo, int32_t trans) {
 constexpr int64_t kMaxDim = (int64_t)1 << 30;
 
 }  // namespace
+
+cudaError_t remap(const double2 *src, long long lds, double2 *dst, long long ldd, int rows, int cols,
+                  bool tr, bool rev_r, bool rev_c, bool conj, bool upper, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((rows + kRT - 1) / kRT), (unsigned)std::min((cols + kRT - 1) / kRT, 65535));
+  if (tr)
+    k_remap<true><<<grid, 256, 0, st>>>(src, lds, dst, ldd, rows, cols, rev_r, rev_c, conj, upper);
+  else
+    k_remap<false><<<grid, 256, 0, st>>>(src, lds, dst, ldd, rows, cols, rev_r, rev_c, conj, upper);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace msts
 
 extern "C" {

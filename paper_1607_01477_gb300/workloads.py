@@ -185,3 +185,18 @@ def scaling_problem(m: int, n: int, seed: int | None = None, k: int = 7):
     s = 1.5 + disk(g, n, 0.5)
     B = np.asfortranarray(cn(g, (m, n)))
     return U, s, B
+
+
+# --------------------------------------------------------------------------
+# The Fox-Li operator (Sec. 7's pseudospectra test matrix), written from its
+# definition: (A f)(x) = sqrt(iF/pi) int_{-1}^{1} exp(-iF (x - y)^2) f(y) dy,
+# discretised by n-point Gauss-Legendre quadrature (nodes x_k, weights w_k)
+# and symmetrised by the quadrature weights:
+#   A_jk = sqrt(iF/pi) sqrt(w_j) exp(-iF (x_j - x_k)^2) sqrt(w_k).
+# --------------------------------------------------------------------------
+def fox_li(n: int = 100, F: float = 10.0) -> np.ndarray:
+    x, w = np.polynomial.legendre.leggauss(n)
+    sw = np.sqrt(w)
+    c = np.sqrt(1j * F / np.pi)
+    d = x[:, None] - x[None, :]
+    return np.asfortranarray(c * (np.exp(-1j * F * d * d) * (sw[:, None] * sw[None, :])))

@@ -139,3 +139,25 @@ def test_variant_arguments_and_workspace(lib):
     assert v(0, 1, 0, P, 4, 4, P, 2, P, 4, None, None, 32, None, 0, None, 1, None) == -8   # safe needs scales
     assert v(0, 1, 0, P, 4, 4, P, 2, P, 4, None, None, 32, None, 0, None, 0, None) == -11  # workspace missing
     assert v(1, 1, 1, None, 1, 0, None, 0, None, 1, None, None, 32, None, 0, None, 0, None) == 0
+
+
+def test_pseudospectra_1norm_and_grid_arguments(lib):
+    P = ctypes.c_void_p(16)
+    ws = lib.msts_pseudospectra_1norm_workspace_size
+    assert ws(100, 50, 32, 0, 0) > 0 and ws(100, 50, 32, 1, 0) > ws(100, 50, 32, 0, 0)
+    assert ws(100, 50, 32, 1, 8) > ws(100, 50, 32, 1, 0)                 # digit planes for the Q products
+    assert ws(100, 50, 32, 0, 2) == 0 and ws(100, 50, 48, 0, 0) == 0 and ws(0, 50, 32, 0, 0) == 0
+    f = lib.msts_pseudospectra_1norm
+    assert f(P, 3, 4, None, 1, P, 2, P, P, P, 32, None, 0, None, 0, None) == -2
+    assert f(P, 4, 4, P, 3, P, 2, P, P, P, 32, None, 0, None, 0, None) == -4      # ldq < m with Q
+    assert f(P, 4, 4, None, 1, P, 2, None, P, P, 32, None, 0, None, 0, None) == -7
+    assert f(P, 4, 4, None, 1, P, 2, P, P, P, 48, None, 0, None, 0, None) == -8
+    assert f(P, 4, 4, None, 1, P, 2, P, P, P, 32, None, 0, None, 2, None) == -11
+    assert f(P, 4, 4, None, 1, P, 2, P, P, P, 32, None, 0, None, 0, None) == -9
+    assert f(None, 1, 0, None, 1, None, 0, None, None, None, 32, None, 0, None, 0, None) == 0
+    g = lib.msts_portrait_grid
+    assert g(P, 4, 0, 3, 3, P, P, None) == -3
+    assert g(P, 3, 4, 3, 3, P, P, None) == -2
+    assert g(P, 4, 4, 0, 3, P, P, None) == -4
+    assert g(P, 4, 4, 3, 3, None, P, None) == -5
+    assert g(P, 4, 4, 3, 3, P, None, None) == -6
