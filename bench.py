@@ -477,7 +477,7 @@ def pseudo_extras(dev, nb):
 
 
 def scaling_study_extra(dev, nb):
-    """The paper's scaling-study comparison (Sec. 6) on the GPU: U the upper
+    """The paper's scaling-study comparison (Sec. 7.1) on the GPU: U the upper
     triangle of a 4096 x 4096 Hermitian matrix with eigenvalues in [1, 2],
     shifts uniform in the disk B(1.5, 0.5), n = 256, 1024, 4096 right-hand
     sides.  Times the library triangular solve with one matrix (cuBLAS ZTRSM

@@ -295,8 +295,8 @@ int msts_pseudospectra_1norm(const msts_z *T, int64_t ldt, int64_t m,
                              uint32_t *status, uint32_t flags, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Automatic grid of a spectral portrait (the SpectralPortrait driver of
- * Sec. 5): box = (x0, x1, y0, y1) is the bounding box of diag(T) widened on
+ * Automatic grid of a spectral portrait (the SpectralPortrait driver listed in
+ * Sec. 6): box = (x0, x1, y0, y1) is the bounding box of diag(T) widened on
  * every side by h = max(max(x-side, y-side)/4, 2^-20 max(1, max_i max(|Re
  * T(i,i)|, |Im T(i,i)|))); z[k + l nx] = (x0 + k dx) + i (y0 + l dy) with
  * dx = (x1 - x0)/(nx - 1) (0 for nx == 1), likewise dy, each operation one

@@ -947,8 +947,8 @@ void or_pseudospectra_1norm(int64_t m, const oz *T, int64_t ldt, const oz *Q, in
 }
 
 /* ------------------------------------------------------------------------
- * Automatic grid of a spectral portrait (the SpectralPortrait driver of
- * Sec. 5, whose grid the paper leaves to the software): the bounding box
+ * Automatic grid of a spectral portrait (the SpectralPortrait driver listed in
+ * Sec. 6, whose grid the paper leaves to the software): the bounding box
  * [a, b] x [c, d] of the eigenvalues diag(T), widened on every side by
  * h = max(0.25 max(b - a, d - c), 2^-20 max(1, max_i max(|Re T(i,i)|, |Im T(i,i)|)))
  * (no square roots: the grid is exact up to the roundings written here), and

@@ -505,7 +505,7 @@ def msts_portrait_grid(T, nx, ny):
 
 
 def spectral_portrait(T, nx=100, ny=100, *, norm=2, Q=None, iters=20, nb=32, tensor=True, seed=0):
-    """SpectralPortrait (Sec. 5): resolvent norms of A = Q T Q^H over the
+    """SpectralPortrait (Sec. 6): resolvent norms of A = Q T Q^H over the
     automatic grid.  norm=2: 1/sigma_min(T - zI) by inverse Lanczos (Q does
     not change the 2-norm; iters <= 64; start vectors CN(0,1) from `seed`); norm=1: the
     Hager/Higham estimate of ||(zI - A)^{-1}||_1.  Returns (resolvent norms

@@ -21,7 +21,7 @@
 //   alternative: s = ||R x_alt||_1, x_alt(i) = (-1)^i (1 + i/(m-1));
 //                           est = max(est, 2 s / (3m)) (kind = -2 if it wins).
 //
-// Portrait grid (the SpectralPortrait driver of Sec. 5; the paper leaves the
+// Portrait grid (the SpectralPortrait driver listed in Sec. 6; the paper leaves the
 // grid to the software): the bounding box of diag(T) widened on every side by
 // h = max(box side / 4, 2^-20 max(1, max |Re|, |Im| of the diagonal)), nx x ny
 // equispaced points, every value a fixed sequence of single roundings.

@@ -167,7 +167,7 @@ def pencil_problem(m: int = 4096, seed: int | None = None, k: int = 6):
 
 
 # --------------------------------------------------------------------------
-# Scaling study of the multi-shift solve (Sec. 6): U is the upper triangle of
+# Scaling study of the multi-shift solve (Sec. 7.1): U is the upper triangle of
 # a Hermitian matrix with eigenvalues uniform in [1, 2]; shifts uniform in the
 # disk of centre 1.5 and radius 0.5.
 # --------------------------------------------------------------------------
@@ -188,7 +188,7 @@ def scaling_problem(m: int, n: int, seed: int | None = None, k: int = 7):
 
 
 # --------------------------------------------------------------------------
-# The Fox-Li operator (Sec. 7's pseudospectra test matrix), written from its
+# The Fox-Li operator (the pseudospectra test matrix of Sec. 7.3), from its
 # definition: (A f)(x) = sqrt(iF/pi) int_{-1}^{1} exp(-iF (x - y)^2) f(y) dy,
 # discretised by n-point Gauss-Legendre quadrature (nodes x_k, weights w_k)
 # and symmetrised by the quadrature weights:
