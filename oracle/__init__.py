@@ -249,6 +249,21 @@ def gtrevc(T, S, nb):
     return Z, lam, e, sc
 
 
+def gtrevc_columns(T, S, cols, nb):
+    """Alg. 10 for the listed columns only: returns (Zc, lam, e) with Zc[:, c]
+    the generalized eigenvector cols[c] exactly as ``gtrevc`` computes it."""
+    T = _cz(T, "T")
+    S = _cz(S, "S")
+    m = T.shape[0]
+    cc = np.ascontiguousarray(cols, dtype=np.int64)
+    Zc = np.zeros((m, cc.size), dtype=np.complex128, order="F")
+    lam = np.zeros(cc.size, dtype=np.complex128)
+    e = np.zeros(cc.size, dtype=np.int32)
+    _load().or_gtrevc_columns(_c_int64(m), _p(T), _c_int64(_ld(T)), _p(S), _c_int64(_ld(S)), _c_int64(cc.size),
+                              _p(cc), _p(Zc), _c_int64(_ld(Zc)), _p(lam), _c_int64(nb), _p(e))
+    return Zc, lam, e
+
+
 def back_transform(Q, Z):
     """X = Q triu(Z) (the eigenvectors of A = Q T Q^H from those of T, Alg. 6)."""
     Q = _cz(Q, "Q")

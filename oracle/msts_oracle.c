@@ -737,6 +737,25 @@ void or_gtrevc(int64_t m, const oz *T, int64_t ldt, const oz *S, int64_t lds, oz
   }
 }
 
+/* Alg. 10 for the listed columns only, each exactly as or_gtrevc computes it
+ * (the same block partition and bounds): Zc(:, c) is eigenvector cols[c]. */
+void or_gtrevc_columns(int64_t m, const oz *T, int64_t ldt, const oz *S, int64_t lds, int64_t ncols,
+                       const int64_t *cols, oz *Zc, int64_t ldzc, oz *lam, int64_t nb, int32_t *scale_exp) {
+  gsafe_prep P = gsafe_prepare(m, T, ldt, S, lds, nb);
+  #pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < ncols; ++c) {
+    int64_t j = cols[c];
+    oz l = oz_div(AT(T, ldt, j, j), AT(S, lds, j, j));
+    oz *x = &AT(Zc, ldzc, 0, c);
+    for (int64_t r = 0; r < m; ++r)
+      x[r] = r < j ? oz_sub(oz_mul(l, AT(S, lds, r, j)), AT(T, ldt, r, j)) : oz_make(0.0, 0.0);
+    scale_exp[c] = gsafe_column(m, T, ldt, S, lds, nb, &P, l, x, j);
+    x[j] = oz_make(ldexp(1.0, -scale_exp[c]), 0.0);
+    lam[c] = l;
+  }
+  gsafe_release(&P);
+}
+
 /* ------------------------------------------------------------------------
  * Back-transformation (Sec. 4, Alg. 6 "Eig"): the eigenvectors of
  * A = Q T Q^H are X = Q Z, Z upper triangular (only its upper triangle is

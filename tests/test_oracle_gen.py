@@ -121,3 +121,14 @@ def test_gtrevc_residual_and_directions(m):
         k = int(np.argmin(np.abs(w - lam[j])))
         c = abs(np.vdot(Vs[:, k], X[:, j])) / np.linalg.norm(Vs[:, k])
         assert c >= 1 - 1e-8
+
+
+def test_gtrevc_columns_entry_point_is_bit_identical():
+    g = W.rng(0, 360)
+    m = 150
+    T = np.asfortranarray(np.triu(W.cn(g, (m, m))) * 3 + np.diag(W.disk(g, m, 1.0)))
+    S = np.asfortranarray(np.triu(W.cn(g, (m, m))) * 0.1 + np.diag(1.0 + 0.1 * W.disk(g, m, 1.0)))
+    Z, lam, e, _ = oracle.gtrevc(T, S, 32)
+    cols = np.array([0, 1, 37, 64, 100, 149])
+    Zc, lc, ec = oracle.gtrevc_columns(T, S, cols, 32)
+    assert np.array_equal(Zc, Z[:, cols]) and np.array_equal(lc, lam[cols]) and np.array_equal(ec, e[cols])
