@@ -531,7 +531,7 @@ def scaling_study_extra(dev, nb):
 def gtrevc_extra(dev, nb):
     """GeneralizedTriangEig (Alg. 10) of the 4096 x 4096 synthetic triangular
     pencil: all 4096 generalized eigenvectors with the safe generalized solve
-    (FP64 substitution GEMM, U and V products), FLOPs (8/3) m^3 (twice the
+    (FP64 and tensor-core substitution, U and V products), FLOPs (8/3) m^3 (twice the
     standard TREVC's: the V term doubles every multiply-add), with the largest
     scale exponent and the generalized eigen-residual of sampled columns."""
     import torch
@@ -541,22 +541,26 @@ def gtrevc_extra(dev, nb):
     T, S = W.pencil_problem(m)
     Td = msts.colmajor(torch.from_numpy(T).to(dev))
     Sd = msts.colmajor(torch.from_numpy(S).to(dev))
-    msts.msts_gtrevc(Td, Sd, nb=nb)                  # warm-up
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    Z, lam, sc, se, st = msts.msts_gtrevc(Td, Sd, nb=nb)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    cols = torch.arange(0, m, 64, device=dev)
-    zs = Z[:, cols] / Z[:, cols].abs().amax(dim=0, keepdim=True)
-    R = Td @ zs - (Sd @ zs) * lam[cols][None, :]
-    rho = torch.linalg.norm(R, dim=0) / ((torch.linalg.norm(Td) + lam[cols].abs() * torch.linalg.norm(Sd))
-                                         * torch.linalg.norm(zs, dim=0))
-    return {"ms": ms, "tflops": (8.0 / 3.0) * m ** 3 / (ms * 1e-3) / 1e12, "gemm": "fp64",
-            "max_scale_exp": int(se.max().item()), "max_residual_sampled": rho.max().item(),
-            "status": int(st.item())}
+    out = {}
+    for tag, tensor in (("fp64_gemm", False), ("tensor_gemm", True)):
+        msts.msts_gtrevc(Td, Sd, nb=nb, tensor=tensor)                  # warm-up
+        torch.cuda.synchronize()
+        e0.record()
+        Z, lam, sc, se, st = msts.msts_gtrevc(Td, Sd, nb=nb, tensor=tensor)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        cols = torch.arange(0, m, 64, device=dev)
+        zs = Z[:, cols] / Z[:, cols].abs().amax(dim=0, keepdim=True)
+        R = torch.triu(Td) @ zs - (torch.triu(Sd) @ zs) * lam[cols][None, :]
+        rho = torch.linalg.norm(R, dim=0) / ((torch.linalg.norm(Td) + lam[cols].abs() * torch.linalg.norm(Sd))
+                                             * torch.linalg.norm(zs, dim=0))
+        out[tag] = {"ms": ms, "tflops": (8.0 / 3.0) * m ** 3 / (ms * 1e-3) / 1e12,
+                    "max_scale_exp": int(se.max().item()), "max_residual_sampled": rho.max().item(),
+                    "status": int(st.item())}
+        del Z
+    return out
 
 
 def back_transform_extra(dev, nb):

@@ -190,7 +190,10 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m,
  * scale_exp as for msts_solve). Readings: the column bounds of U - s_j V are
  * ||U(.,k)|| + |s_j| ||V(.,k)|| (rigorous upper bounds), and an exactly zero
  * pivot U(i,i) - s_j V(i,i) becomes delta_j = max(2^-52 (||U||_inf +
- * |s_j| ||V||_inf), DBL_MIN). FP64 FMA throughout (no MSTS_TENSOR_GEMM).
+ * |s_j| ||V||_inf), DBL_MIN). MSTS_TENSOR_GEMM runs the substitution step
+ * B(I0,:) -= U(I0,I1) X(I1,:) - V(I0,I1) (s X(I1,:)) on the tensor cores as one
+ * FP64-accurate digit-plane product of [U | V] and [X; -s X] (s X rounded once
+ * in FP64); otherwise FP64 FMA.
  * workspace: msts_gsolve_workspace_size(m, n, nb, flags) bytes.
  * Returns 0, -k for invalid argument k (nothing launched; -13/-14 for a
  * missing / too small workspace, -16 for unsupported flags), MSTS_ERR_CUDA.
@@ -209,8 +212,9 @@ int msts_gsolve(const msts_z *U, int64_t ldu, const msts_z *V, int64_t ldv, int6
  * triangular with S(j,j) != 0, writes lambda[j] = T(j,j) / S(j,j) and the upper
  * triangular Z with T Z(:,j) = lambda[j] S Z(:,j), Z(j,j) = scales[j] =
  * 2^-scale_exp[j] (right-hand sides -T(0:j-1,j) + lambda[j] S(0:j-1,j), the
- * strictly-upper shortcut as in msts_trevc). flags must be 0.
- * workspace: msts_gtrevc_workspace_size(m, nb, 0) bytes.
+ * strictly-upper shortcut as in msts_trevc). flags: 0 or MSTS_TENSOR_GEMM
+ * (the substitution step as in msts_gsolve).
+ * workspace: msts_gtrevc_workspace_size(m, nb, flags) bytes.
  * ------------------------------------------------------------------------- */
 size_t msts_gtrevc_workspace_size(int64_t m, int32_t nb, uint32_t flags);
 int msts_gtrevc(const msts_z *T, int64_t ldt, const msts_z *S, int64_t lds, int64_t m,

@@ -333,9 +333,10 @@ def msts_trevc(T, *, nb=32, tensor=False, status=None):
     return Z, sc, se, status
 
 
-def msts_gsolve(U, V, shifts, B, *, safe=False, nb=32, status=None):
+def msts_gsolve(U, V, shifts, B, *, safe=False, nb=32, tensor=False, status=None):
     """Generalized multi-shift solve (Alg. 8; Alg. 9 with safe=True): B is
-    overwritten with X, (U - s_j V) X(:,j) = scale_j B(:,j).
+    overwritten with X, (U - s_j V) X(:,j) = scale_j B(:,j).  tensor=True runs
+    the substitution step on the tensor cores ([U | V] against [X; -s X]).
     Returns (B, scales, scale_exp, status); scales/scale_exp are None unless safe."""
     lib = load_library()
     m, n = B.shape
@@ -346,7 +347,7 @@ def msts_gsolve(U, V, shifts, B, *, safe=False, nb=32, status=None):
     s = shifts.contiguous()
     sc = torch.empty(n, dtype=torch.float64, device=dev) if safe else None
     se = torch.empty(n, dtype=torch.int32, device=dev) if safe else None
-    flags = MSTS_SAFE if safe else 0
+    flags = (MSTS_SAFE if safe else 0) | (MSTS_TENSOR_GEMM if tensor else 0)
     ws = _workspace(lib.msts_gsolve_workspace_size(m, n, nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
@@ -356,9 +357,10 @@ def msts_gsolve(U, V, shifts, B, *, safe=False, nb=32, status=None):
     return B, sc, se, status
 
 
-def msts_gtrevc(T, S, *, nb=32, status=None):
+def msts_gtrevc(T, S, *, nb=32, tensor=False, status=None):
     """Generalized triangular eigenvectors (Alg. 10): returns (Z, lam, scales,
-    scale_exp, status) with lam = diag(T) / diag(S), T Z = S Z diag(lam)."""
+    scale_exp, status) with lam = diag(T) / diag(S), T Z = S Z diag(lam).
+    tensor=True runs the substitution step on the tensor cores."""
     lib = load_library()
     m = T.shape[0]
     ldt = _mat(T, "T", m)
@@ -368,11 +370,12 @@ def msts_gtrevc(T, S, *, nb=32, status=None):
     lam = torch.empty(m, dtype=torch.complex128, device=dev)
     sc = torch.empty(m, dtype=torch.float64, device=dev)
     se = torch.empty(m, dtype=torch.int32, device=dev)
-    ws = _workspace(lib.msts_gtrevc_workspace_size(m, nb, 0), dev)
+    flags = MSTS_TENSOR_GEMM if tensor else 0
+    ws = _workspace(lib.msts_gtrevc_workspace_size(m, nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
     rc = lib.msts_gtrevc(_ptr(T), ldt, _ptr(S), lds, m, _ptr(Z), max(1, m), _ptr(lam), _ptr(sc), _ptr(se), nb,
-                         wp, wb, _ptr(status), 0, _stream(dev))
+                         wp, wb, _ptr(status), flags, _stream(dev))
     _check(rc, "msts_gtrevc")
     return Z, lam, sc, se, status
 
@@ -392,7 +395,7 @@ def geig(A, B, *, nb=32, tensor=True, device=None):
     Td = colmajor(torch.from_numpy(np.asfortranarray(T)).to(dev))
     Sd = colmajor(torch.from_numpy(np.asfortranarray(S)).to(dev))
     Pd = colmajor(torch.from_numpy(np.asfortranarray(P)).to(dev))
-    Z, lam, _, _, status = msts_gtrevc(Td, Sd, nb=nb)
+    Z, lam, _, _, status = msts_gtrevc(Td, Sd, nb=nb, tensor=tensor)
     X, status = msts_back_transform(Pd, Z, tensor=tensor, normalize=True, status=status)
     return lam, X, status
 

@@ -157,7 +157,9 @@ size_t msts_gsolve_workspace_size(int64_t m, int64_t n, int32_t nb, uint32_t fla
   if (m < 0 || n < 0 || !nb_ok(nb)) return 0;
   msts::EngineProblem p = make_problem(nullptr, 1, m, nullptr, 1, n, nullptr, 1, nullptr, nullptr, 0);
   p.V = reinterpret_cast<const double2 *>(16);     // sizes of the generalized form (never read)
-  return align256(msts::engine_workspace_bytes(&p, 1, nb, (flags & MSTS_SAFE) != 0));
+  size_t s = align256(msts::engine_workspace_bytes(&p, 1, nb, (flags & MSTS_SAFE) != 0));
+  if ((flags & MSTS_TENSOR_GEMM) && m > 0 && n > 0) s += msts::ozaki_plan_bytes((int)m, (int)n, nb, true);
+  return s;
 }
 
 int msts_gsolve(const msts_z *U, int64_t ldu, const msts_z *V, int64_t ldv, int64_t m, const msts_z *shifts,
@@ -175,7 +177,7 @@ int msts_gsolve(const msts_z *U, int64_t ldu, const msts_z *V, int64_t ldv, int6
   if (ldb < std::max<int64_t>(1, m)) return -9;
   if (safe && n > 0 && (!scales || !scale_exp)) return scales ? -11 : -10;
   if (!nb_ok(nb)) return -12;
-  if ((flags & ~(uint32_t)MSTS_SAFE) != 0) return -16;
+  if ((flags & ~(uint32_t)(MSTS_SAFE | MSTS_TENSOR_GEMM)) != 0) return -16;
   const size_t need = msts_gsolve_workspace_size(m, n, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -14 : -13;
   if (m == 0 || n == 0) return 0;
@@ -183,12 +185,20 @@ int msts_gsolve(const msts_z *U, int64_t ldu, const msts_z *V, int64_t ldv, int6
   msts::EngineProblem p = make_problem(U, ldu, m, shifts, 1, n, B, ldb, scales, scale_exp, 0);
   p.V = reinterpret_cast<const double2 *>(V);
   p.ldv = ldv;
+  msts::OzPlan plan;
+  if (flags & MSTS_TENSOR_GEMM) {
+    const size_t eng = align256(msts::engine_workspace_bytes(&p, 1, nb, safe));
+    if (msts::ozaki_plan_prepare(&plan, p.U, ldu, (int)m, (int)n, nb, false, static_cast<char *>(workspace) + eng,
+                                 st, p.V, ldv) != cudaSuccess)
+      return MSTS_ERR_CUDA;
+    p.oz = &plan;
+  }
   return cuda_rc(msts::engine_run(&p, 1, nb, safe, false, false, workspace, status, st));
 }
 
 size_t msts_gtrevc_workspace_size(int64_t m, int32_t nb, uint32_t flags) {
-  if (m < 0 || !nb_ok(nb) || flags != 0) return 0;
-  return msts_gsolve_workspace_size(m, m, nb, MSTS_SAFE);
+  if (m < 0 || !nb_ok(nb) || (flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return 0;
+  return msts_gsolve_workspace_size(m, m, nb, MSTS_SAFE | flags);
 }
 
 int msts_gtrevc(const msts_z *T, int64_t ldt, const msts_z *S, int64_t lds, int64_t m, msts_z *Z, int64_t ldz,
@@ -205,7 +215,7 @@ int msts_gtrevc(const msts_z *T, int64_t ldt, const msts_z *S, int64_t lds, int6
   if (m > 0 && !scales) return -9;
   if (m > 0 && !scale_exp) return -10;
   if (!nb_ok(nb)) return -11;
-  if (flags != 0) return -15;
+  if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -15;
   const size_t need = msts_gtrevc_workspace_size(m, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -13 : -12;
   if (m == 0) return 0;
@@ -218,6 +228,14 @@ int msts_gtrevc(const msts_z *T, int64_t ldt, const msts_z *S, int64_t lds, int6
   msts::EngineProblem p = make_problem(T, ldt, m, lambda, 1, m, Z, ldz, scales, scale_exp, 1);
   p.V = reinterpret_cast<const double2 *>(S);
   p.ldv = lds;
+  msts::OzPlan plan;
+  if (flags & MSTS_TENSOR_GEMM) {
+    const size_t eng = align256(msts::engine_workspace_bytes(&p, 1, nb, true));
+    if (msts::ozaki_plan_prepare(&plan, p.U, ldt, (int)m, (int)m, nb, false, static_cast<char *>(workspace) + eng,
+                                 st, p.V, lds) != cudaSuccess)
+      return MSTS_ERR_CUDA;
+    p.oz = &plan;
+  }
   return cuda_rc(msts::engine_run(&p, 1, nb, true, false, true, workspace, status, st));
 }
 

@@ -481,17 +481,21 @@ cudaError_t ozaki_product(const double2 *A, long long lda, int m, const double2 
 // Row exponents are per (block, row): rexp[b m + r] over the block's columns,
 // which keeps the digits of each panel as fine as the panel itself allows.
 // ===========================================================================
-static int kb_of(int nb) { return ((2 * nb + kOzKC - 1) / kOzKC) * kOzKC; }
+// Panel width in K' of one block: 2 real columns per complex column, twice as
+// many for a generalized problem ([U | V] against [X; -lambda X]).
+static int kb_of(int nb, bool gen) { return (((gen ? 4 : 2) * nb + kOzKC - 1) / kOzKC) * kOzKC; }
 
-size_t ozaki_plan_bytes(int m, int n, int nb) {
-  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb);
+size_t ozaki_plan_bytes(int m, int n, int nb, bool gen) {
+  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb, gen);
   return a256((size_t)kOzS * 2 * m * (size_t)nblk * KB * 2) + a256(4 * (size_t)nblk * m) +
          a256((size_t)kOzS * n * KB * 2) + a256(4 * (size_t)n);
 }
 
+// With V (generalized problem, upper only) the panel row is
+// [U(r, lo:hi) | V(r, lo:hi)], one exponent for both halves.
 template <bool CONJ>
-__global__ void k_ozs_prepare(const double2 *U, long long ldu, int m, int nb, int KB,
-                              __nv_bfloat16 *planes, int *rexp) {
+__global__ void k_ozs_prepare(const double2 *U, long long ldu, const double2 *V, long long ldv, int m, int nb,
+                              int KB, __nv_bfloat16 *planes, int *rexp) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int b = blockIdx.x;
@@ -503,12 +507,14 @@ __global__ void k_ozs_prepare(const double2 *U, long long ldu, int m, int nb, in
   // the update reads only used rows (others at most fill a tile whose outputs
   // are masked, and an MMA row depends on its own A row only).
   if (!used) return;                                   // warp-uniform (one warp per row)
+  const int wt = V ? 2 * w : w;                        // complex columns of the panel
   auto entry = [&](int k) {   // the complex entry of A' row r at column k of the block
-    if (k >= w) return make_double2(0.0, 0.0);
+    if (k >= wt) return make_double2(0.0, 0.0);
+    if (k >= w) return V[r + (long long)(lo + k - w) * ldv];
     return CONJ ? zconj(U[(lo + k) + (long long)r * ldu]) : U[r + (long long)(lo + k) * ldu];
   };
   int e = -(1 << 29);
-  for (int k = lane; k < w; k += 32) e = max(e, bound_exp(entry(k)));
+  for (int k = lane; k < wt; k += 32) e = max(e, bound_exp(entry(k)));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if (e < -(1 << 28)) e = 0;
@@ -531,22 +537,31 @@ __global__ void k_ozs_prepare(const double2 *U, long long ldu, int m, int nb, in
 }
 
 // Digit planes of X(lo:hi, jstart + c) for this block step: plane t, local
-// column c, K' = 2 (k - lo) + {0,1}; one warp per column.
+// column c, K' = 2 (k - lo) + {0,1}; one warp per column.  With lam
+// (generalized problem) the column is [X(lo:hi, j); -lam_j X(lo:hi, j)],
+// lam_j = lam[j lam_stride], the products rounded once in FP64.
 __global__ void k_ozs_slice_X(const double2 *B, long long ldb, int lo, int w, int jstart, int ncols,
-                              int KB, __nv_bfloat16 *bp, int *cexp) {
+                              int KB, __nv_bfloat16 *bp, int *cexp, const double2 *lam, long long lam_stride) {
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= ncols) return;
   const double2 *col = B + (long long)(jstart + c) * ldb + lo;
+  const double2 nl = lam ? lam[(long long)(jstart + c) * lam_stride] : make_double2(0.0, 0.0);
+  const double2 mlam = make_double2(-nl.x, -nl.y);
+  const int wt = lam ? 2 * w : w;
+  auto entry = [&](int k) {
+    if (k >= wt) return make_double2(0.0, 0.0);
+    return k < w ? col[k] : zmul_rn(mlam, col[k - w]);
+  };
   int e = -(1 << 29);
-  for (int k = lane; k < w; k += 32) e = max(e, bound_exp(col[k]));
+  for (int k = lane; k < wt; k += 32) e = max(e, bound_exp(entry(k)));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if (e < -(1 << 28)) e = 0;
   if (lane == 0) cexp[c] = e;
   for (int k = lane; 2 * k < KB; k += 32) {
     float dr[kOzS], di[kOzS];
-    const double2 x = k < w ? col[k] : make_double2(0.0, 0.0);
+    const double2 x = entry(k);
     digits8(x.x, e, dr);
     digits8(x.y, e, di);
 #pragma unroll
@@ -557,8 +572,9 @@ __global__ void k_ozs_slice_X(const double2 *B, long long ldb, int lo, int w, in
 }
 
 cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, int m, int n, int nb,
-                               bool conj, void *ws, cudaStream_t st) {
-  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb);
+                               bool conj, void *ws, cudaStream_t st, const double2 *V, long long ldv) {
+  if (V && conj) return cudaErrorInvalidValue;
+  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb, V != nullptr);
   char *c = static_cast<char *>(ws);
   plan->planes = reinterpret_cast<__nv_bfloat16 *>(c); c += a256((size_t)kOzS * 2 * m * (size_t)nblk * KB * 2);
   plan->rexp = reinterpret_cast<int *>(c); c += a256(4 * (size_t)nblk * m);
@@ -567,8 +583,8 @@ cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, in
   plan->m = m; plan->nb = nb; plan->nblk = nblk; plan->KB = KB; plan->nmax = n; plan->conj = conj;
   if (!make_map(&plan->tmA, plan->planes, nblk * KB, 2 * m, kOzBM, 1)) return cudaErrorNotSupported;
   const dim3 grid(nblk, (m + 7) / 8);
-  if (conj) k_ozs_prepare<true><<<grid, 256, 0, st>>>(U, ldu, m, nb, KB, plan->planes, plan->rexp);
-  else k_ozs_prepare<false><<<grid, 256, 0, st>>>(U, ldu, m, nb, KB, plan->planes, plan->rexp);
+  if (conj) k_ozs_prepare<true><<<grid, 256, 0, st>>>(U, ldu, nullptr, 0, m, nb, KB, plan->planes, plan->rexp);
+  else k_ozs_prepare<false><<<grid, 256, 0, st>>>(U, ldu, V, ldv, m, nb, KB, plan->planes, plan->rexp);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -887,12 +903,12 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
 cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
-                         cudaStream_t st, bool planes_ready) {
+                         cudaStream_t st, bool planes_ready, const double2 *lam, long long lam_stride) {
   const int row_lo = plan.conj ? 2 * hi : 0, row_hi = plan.conj ? 2 * plan.m : 2 * lo;
   if (ncols <= 0 || row_hi <= row_lo) return cudaSuccess;
   if (!planes_ready) {
     k_ozs_slice_X<<<(ncols + 7) / 8, 256, 0, st>>>(B, ldb, lo, hi - lo, jstart, ncols, plan.KB, plan.bp,
-                                                  plan.cexp);
+                                                  plan.cexp, lam, lam_stride);
     count_launches(1);
   }
   CUtensorMap tmB;

@@ -32,14 +32,19 @@ struct OzPlan {
   bool conj;
   CUtensorMap tmA;
 };
-size_t ozaki_plan_bytes(int m, int n, int nb);
+// gen: a generalized problem (U - lambda_j V), whose panels are [U | V].
+size_t ozaki_plan_bytes(int m, int n, int nb, bool gen = false);
 cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, int m, int n, int nb,
-                               bool conj, void *ws, cudaStream_t st);
+                               bool conj, void *ws, cudaStream_t st, const double2 *V = nullptr,
+                               long long ldv = 0);
 // B(rows, jstart..jstart+ncols) = 2^-pend B - U-panel(b) X(I1, .), rows above the
 // block (upper) or below it (conj); `flops` is recorded by the tracer.
 // planes_ready: the X digit planes and exponents of this block were written by
-// the diagonal-block step (otherwise they are sliced here first).
+// the diagonal-block step (otherwise they are sliced here first).  lam (a
+// generalized plan): the shifts, column j's at lam[j lam_stride]; the update
+// is then B(I0,:) -= U(I0,I1) X(I1,:) - V(I0,I1) (lam X(I1,:)).
 cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
-                         cudaStream_t st, bool planes_ready = false);
+                         cudaStream_t st, bool planes_ready = false, const double2 *lam = nullptr,
+                         long long lam_stride = 0);
 }  // namespace msts

@@ -614,9 +614,11 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       const int b = CONJ ? nblk - 1 - s : s;
       const int hi = m - b * NB, lo = std::max(0, hi - NB);
       const int jstart = shortcut ? lo + 1 : 0;
+      // (generalized: the X planes carry [X; -lambda X] and are sliced here)
       const cudaError_t e = ozaki_update(*probs[0].oz, b, lo, hi, probs[0].B, probs[0].ldb, jstart,
                                          probs[0].n - jstart, SAFE ? tab.p[0].pend : nullptr, status,
-                                         gflops, st, tab.p[0].oz_bp != nullptr);
+                                         gflops, st, tab.p[0].oz_bp != nullptr, gen ? probs[0].shifts : nullptr,
+                                         probs[0].shift_stride);
       if (e != cudaSuccess) return e;
     } else if (rows_max > 0) {
       // FP64 throughput per SM is low, so the tile is chosen to give the grid
@@ -681,7 +683,7 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
       maxn = std::max(maxn, q.n);
     }
     if (maxm == 0 || maxn == 0) continue;
-    if (cnt == 1 && probs[base].oz) {          // the diagonal step writes the X digit planes
+    if (cnt == 1 && probs[base].oz && !probs[base].V) {   // the diagonal step writes the X digit planes
       tab.p[0].oz_bp = reinterpret_cast<uint32_t *>(probs[base].oz->bp);
       tab.p[0].oz_cexp = probs[base].oz->cexp;
       tab.p[0].oz_kb = probs[base].oz->KB;

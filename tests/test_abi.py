@@ -96,7 +96,9 @@ def test_generalized_arguments_and_workspace(lib):
     assert lib.msts_gsolve_workspace_size(64, 8, 32, 0) == 0
     assert lib.msts_gsolve_workspace_size(64, 8, 32, 1) > lib.msts_solve_workspace_size(64, 8, 32, 1)
     assert lib.msts_gtrevc_workspace_size(64, 32, 0) == lib.msts_gsolve_workspace_size(64, 64, 32, 1)
-    assert lib.msts_gtrevc_workspace_size(64, 32, 8) == 0
+    assert lib.msts_gtrevc_workspace_size(64, 32, 8) > lib.msts_gtrevc_workspace_size(64, 32, 0)
+    assert lib.msts_gtrevc_workspace_size(64, 32, 2) == 0
+    assert lib.msts_gsolve_workspace_size(64, 8, 32, 9) > lib.msts_gsolve_workspace_size(64, 8, 32, 1)
     g = lib.msts_gsolve
     # negative m, ldu < m, V missing, ldv < m, bad nb, unsupported flags, missing / small workspace
     assert g(P, 4, P, 4, -1, P, 1, P, 4, None, None, 32, None, 0, None, 0, None) == -5
@@ -104,14 +106,14 @@ def test_generalized_arguments_and_workspace(lib):
     assert g(P, 4, None, 4, 4, P, 1, P, 4, None, None, 32, None, 0, None, 0, None) == -3
     assert g(P, 4, P, 3, 4, P, 1, P, 4, None, None, 32, None, 0, None, 0, None) == -4
     assert g(P, 4, P, 4, 4, P, 1, P, 4, None, None, 48, None, 0, None, 0, None) == -12
-    assert g(P, 4, P, 4, 4, P, 1, P, 4, None, None, 32, None, 0, None, 8, None) == -16
+    assert g(P, 4, P, 4, 4, P, 1, P, 4, None, None, 32, None, 0, None, 2, None) == -16
     assert g(P, 4, P, 4, 4, P, 1, P, 4, P, P, 32, None, 0, None, 1, None) == -13
     assert g(P, 4, P, 4, 4, P, 1, P, 4, P, P, 32, P, 8, None, 1, None) == -14
     assert g(None, 1, None, 1, 0, None, 0, None, 1, None, None, 32, None, 0, None, 0, None) == 0
     t = lib.msts_gtrevc
     assert t(P, 4, None, 4, 4, P, 4, P, P, P, 32, P, 1 << 20, None, 0, None) == -3
     assert t(P, 4, P, 4, 4, P, 4, None, P, P, 32, P, 1 << 20, None, 0, None) == -8
-    assert t(P, 4, P, 4, 4, P, 4, P, P, P, 32, P, 1 << 20, None, 8, None) == -15
+    assert t(P, 4, P, 4, 4, P, 4, P, P, P, 32, P, 1 << 20, None, 2, None) == -15
     assert t(None, 1, None, 1, 0, None, 1, None, None, None, 32, None, 0, None, 0, None) == 0
 
 
