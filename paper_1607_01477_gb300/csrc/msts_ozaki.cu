@@ -696,7 +696,7 @@ __device__ __noinline__ double update_out_slow(double v, int pe, int h, uint32_t
 // B = 2^-pend B - W 2^(e_r + f_j - 56) with a single FP64 subtraction.
 constexpr size_t kOzuSmem = (size_t)kOzS * kOzABytes + 2 * kOzBBytes + 1024;
 constexpr int kOzPersistentCtas = 152;             // one CTA per SM
-constexpr int kOzuEpiWarps = 8;                    // epilogue warps (2 per sub-partition)
+constexpr int kOzuEpiWarps = 16;                   // epilogue warps (4 per sub-partition)
 constexpr int kOzuThreads = 32 * kOzuEpiWarps + 64; // + producer + MMA
 
 __global__ void __launch_bounds__(kOzuThreads, 1)
@@ -800,7 +800,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int quarter = warp & 3, cgroup = warp >> 2;
     const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
     const long long ldr2 = 2 * args.ldr;            // column stride in doubles
-    constexpr int kCW = kOzBN * 4 / kOzuEpiWarps, kQ = 8, kPasses = kCW / kQ;
+    constexpr int kCW = kOzBN * 4 / kOzuEpiWarps, kQ = 4, kPasses = kCW / kQ;
     struct TileIn {
       double b[kCW];                                // B(row, columns of this warp)
       double *base;                                 // &B(row, first column of this warp)
@@ -839,7 +839,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         // (D_0..D_3 are below 2^22 and are read without a conversion.)
         uint32_t v[kOzS][kQ];                       // all diagonals of the pass, one wait
 #pragma unroll
-        for (int d = 0; d < kOzS; ++d) tmem_ld8(tmem + lane_addr + ab * kOzAccCols + d * kOzBN + cp, v[d]);
+        for (int d = 0; d < kOzS; ++d) tmem_ld4(tmem + lane_addr + ab * kOzAccCols + d * kOzBN + cp, v[d]);
         tmem_ld_wait();
         int P[kOzS / 2][kQ];
 #pragma unroll
