@@ -96,6 +96,23 @@ __device__ __forceinline__ double dscale_exp(double x, int s) {
   if (e == 0 || e == 0x7ff || e + s < 1 || e + s > 0x7fe) return dscale(x, s);
   return __hiloint2double(hi + (s << 20), __double2loint(x));
 }
+// x 2^s on the exponent field, zero kept as it is (its sign too); otherwise
+// as dscale_exp.
+__device__ __forceinline__ double dscale_exp0(double x, int s) {
+  const int hi = __double2hiint(x);
+  if (((hi & 0x7fffffff) | __double2loint(x)) == 0) return x;
+  return dscale_exp(x, s);
+}
+__device__ __forceinline__ double2 zscale_exp(double2 z, int s) {
+  return make_double2(dscale_exp0(z.x, s), dscale_exp0(z.y, s));
+}
+// choose_k for a finite x >= Omega, from the exponent field (the same value as
+// ilogb there).
+__device__ __forceinline__ int choose_k_exp(double x) {
+  const int k = ((__double2hiint(x) >> 20) & 0x7ff) - 1023 - (kOmegaExp - 1);
+  return k < 1 ? 1 : k;
+}
+
 // z == 0 on the bit patterns, word by word.
 __device__ __forceinline__ bool zzero_words(double2 z) {
   return ((((unsigned)__double2hiint(z.x) | (unsigned)__double2hiint(z.y)) & 0x7fffffffu) |
@@ -332,7 +349,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
       const int kk = cand - 900;
       patho |= kk > 600;                              // e.g. a pivot near the bottom of the range
 #pragma unroll
-      for (int q = 0; q < RPL; ++q) y[q] = zshift(y[q], kk);
+      for (int q = 0; q < RPL; ++q) y[q] = zscale_exp(y[q], -kk);
       Kown += kk;
       cand -= kk;
     }
@@ -387,13 +404,13 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
         if (eM >= kOmegaExp) {                        // M >= Omega: rescale b first
           const int kk = eM - (kOmegaExp - 1);
           Ka += kk;
-          G = dshift(G, kk);
+          G = dscale_exp(G, -kk);
         }
         G = __dadd_rn(G, dscale_exp(ai, Kown - Ka));
         if (ge_omega(G)) {                            // protect the AXPY
-          const int kk = choose_k(G);
+          const int kk = choose_k_exp(G);
           Ka += kk;
-          G = dshift(G, kk);
+          G = dscale_exp(G, -kk);
         }
       }
      }
@@ -403,7 +420,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   kexp = Ka;
   if (Kown != Ka) {
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) y[q] = make_double2(dscale(y[q].x, Kown - Ka), dscale(y[q].y, Kown - Ka));
+    for (int q = 0; q < RPL; ++q) y[q] = zscale_exp(y[q], Kown - Ka);
   }
   } else {
     // The serial safeguarded back substitution (Alg. 4, second branch),
@@ -459,20 +476,20 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   if (active) {
     ej = P.e[j];
     Gj = P.G[j];
-    if (kexp > 0) { ej += kexp; Gj = dshift(Gj, kexp); pend = kexp; }
+    if (kexp > 0) { ej += kexp; Gj = dscale_exp0(Gj, -kexp); pend = kexp; }
     const double cb = GEN ? __dadd_rn(P.cblk[b], __dmul_rn(al, P.cblkV[b])) : P.cblk[b];
     Gj = __dadd_rn(Gj, __dmul_rn(cb, N));
     if (Gj >= OM) {
-      k2 = choose_k(Gj);
+      k2 = choose_k_exp(Gj);
       ej += k2;
-      Gj = dshift(Gj, k2);
+      Gj = dscale_exp(Gj, -k2);
       pend += k2;
     }
   }
   double2 xo[RPL];
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
-    xo[q] = k2 ? zshift(y[q], k2) : y[q];
+    xo[q] = k2 ? zscale_exp(y[q], -k2) : y[q];
     if (active && l + L * q < nbe) col[l + L * q] = xo[q];
   }
   write_planes(xo);

@@ -21,6 +21,7 @@ bool g_on = false;
 long long g_cap = 0;
 struct Rec { int kernel; cudaEvent_t a, b; double flops, bytes; };
 std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;   // 2 x capacity events, created by msts_trace_begin
 struct Tot { double ms = 0, flops = 0, bytes = 0; long long n = 0; };
 Tot g_tot[kTraceKernels];
 }  // namespace
@@ -32,9 +33,8 @@ bool trace_on() { return g_on; }
 void *trace_start(int kernel, double flops, double bytes, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on || (long long)g_recs.size() >= g_cap) return nullptr;
-  Rec r{kernel, nullptr, nullptr, flops, bytes};
-  cudaEventCreate(&r.a);
-  cudaEventCreate(&r.b);
+  const size_t k = g_recs.size();
+  Rec r{kernel, g_pool[2 * k], g_pool[2 * k + 1], flops, bytes};
   cudaEventRecord(r.a, st);
   g_recs.push_back(r);
   return &g_recs.back();
@@ -54,10 +54,15 @@ uint64_t msts_launch_count(void) { return msts::g_launches.load(); }
 
 int msts_trace_begin(int64_t capacity) {
   std::lock_guard<std::mutex> lk(msts::g_mu);
-  if (capacity < 0) return -1;
-  for (auto &r : msts::g_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  if (capacity < 0 || capacity > (1 << 22)) return -1;
   msts::g_recs.clear();
   msts::g_recs.reserve((size_t)capacity);   // pointers handed out stay valid
+  // the events are created here, outside the traced region
+  while (msts::g_pool.size() < 2 * (size_t)capacity) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return MSTS_ERR_CUDA;
+    msts::g_pool.push_back(e);
+  }
   for (auto &t : msts::g_tot) t = msts::Tot{};
   msts::g_cap = capacity;
   msts::g_on = true;
@@ -74,8 +79,6 @@ int msts_trace_end(void) {
     if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) rc = MSTS_ERR_CUDA;
     auto &t = msts::g_tot[r.kernel];
     t.ms += ms; t.flops += r.flops; t.bytes += r.bytes; t.n += 1;
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
   }
   msts::g_recs.clear();
   return rc;
