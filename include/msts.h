@@ -404,9 +404,9 @@ int msts_residual(const msts_z *U, int64_t ldu, int64_t m,
  *   tensor-core residual) with CUDA events on its stream, for at most
  *   `capacity` launches, recording the algorithmic FLOPs (8 per complex
  *   multiply-add) and algorithmic bytes of each launch.  The 2 x capacity
- *   events are created by this call (kept for later calls), so the traced
- *   region only records them; capacity <= 2^22.  Host-side; not for use
- *   inside stream capture.
+ *   events are created by this call and destroyed by msts_trace_end, so the
+ *   traced region only records them; capacity <= 2^22.  Host-side; not for
+ *   use inside stream capture.
  * msts_trace_end: waits for the recorded events, accumulates per-kernel
  *   totals and stops recording.  msts_trace_query reads the totals.
  * ------------------------------------------------------------------------- */

@@ -81,6 +81,8 @@ int msts_trace_end(void) {
     t.ms += ms; t.flops += r.flops; t.bytes += r.bytes; t.n += 1;
   }
   msts::g_recs.clear();
+  for (cudaEvent_t e : msts::g_pool) cudaEventDestroy(e);   // outside the traced region too
+  msts::g_pool.clear();
   return rc;
 }
 
