@@ -239,13 +239,20 @@ def run_native(args):
                   "flops_per_step": "(4/3) m^3 algorithmic",
                   "l2": "no flush: T (268 MB) and Z (268 MB) exceed the 129 MB L2",
                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
-        h2d_host = torch.from_numpy(T).pin_memory()
-        Zh = torch.empty((m, m), dtype=torch.complex128).pin_memory()
+        # pinned host buffers with the device tensors' column-major strides, so
+        # each transfer is one contiguous copy
+        h2d_host = torch.empty_strided((m, m), (1, m), dtype=torch.complex128, pin_memory=True)
+        h2d_host.copy_(torch.from_numpy(T))
+        Zh = torch.empty_strided((m, m), (1, m), dtype=torch.complex128, pin_memory=True)
+        sch = torch.empty(m, dtype=torch.float64, pin_memory=True)
+        seh = torch.empty(m, dtype=torch.int32, pin_memory=True)
 
         def e2e_step():
-            Td.copy_(h2d_host, non_blocking=True)      # same column-major strides: one H2D copy
+            Td.copy_(h2d_host, non_blocking=True)
             step()
             Zh.copy_(Z, non_blocking=True)
+            sch.copy_(sc, non_blocking=True)
+            seh.copy_(se, non_blocking=True)
 
         e2e_bytes = (T.nbytes, T.nbytes + m * 12)
     else:

@@ -118,6 +118,31 @@ __device__ __forceinline__ void raise_status(uint32_t *status, uint32_t bits) {
   if (status) atomicOr(reinterpret_cast<unsigned int *>(status), bits);
 }
 
+// ----- programmatic dependent launch ------------------------------------------
+// A kernel launched by launch_pdl may start while the previous kernel of its
+// stream is finishing.  pdl_wait() blocks until that kernel has completed and
+// its writes are visible, so it must come before any read of data an earlier
+// kernel wrote; pdl_trigger() lets the next launch_pdl kernel start once every
+// CTA of this one has called it (or exited).  Plain launches are unaffected.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ----- cheap exact helpers: power-of-two scaling through the exponent field,
 // so that the per-row work of the diagonal step stays off the (slow) FP64 pipe
 // wherever possible.

@@ -163,6 +163,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   double *sC = reinterpret_cast<double *>(sU + (GEN ? 2 : 1) * NB * LD);   // within-block column norms
   double *sCV = sC + NB;                                 // those of V (GEN)
 
+  pdl_wait();                            // B, the safe state and U' may come from the kernel before
   const Prob &P = tab.p[blockIdx.z];
   if (step >= P.nblk) return;
   const int b = CONJ ? P.nblk - 1 - step : step;
@@ -510,9 +511,8 @@ static cudaError_t launch(const ProbTable &tab, int step, int shortcut, int ncol
   cudaError_t e = cudaFuncSetAttribute(k_diag<NB, L, SAFE, CONJ, GEN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_diag<NB, L, SAFE, CONJ, GEN><<<dim3((ncols_max + SPC - 1) / SPC, 1, tab.count), kDiagThreads, smem, st>>>(
-      tab, step, shortcut, status);
-  return cudaSuccess;
+  return launch_pdl(k_diag<NB, L, SAFE, CONJ, GEN>, dim3((ncols_max + SPC - 1) / SPC, 1, tab.count),
+                    dim3(kDiagThreads), smem, st, tab, step, shortcut, status);
 }
 
 template <int NB, bool SAFE, bool CONJ, bool GEN>

@@ -742,6 +742,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (lane == 0) {                                // ---------------- TMA producer
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
+      pdl_wait();                                   // the X planes come from the diagonal step
       int prev_rt = -1, na = 0;
       for (int t = t0, k = 0; t < t1; ++t, ++k) {
         const int rt = t / tiles_n, ct = t - rt * tiles_n;
@@ -761,6 +762,9 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
   } else if (warp == kOzuEpiWarps + 1) {
     if (lane == 0) {                                // ---------------- MMA issuer
+      // wait in hardware for the diagonal step rather than spinning on the
+      // first barrier beside its CTAs
+      pdl_wait();
       int prev_rt = -1, na = 0;
       for (int t = t0, k = 0; t < t1 && !fail; ++t, ++k) {
         const int rt = t / tiles_n;
@@ -824,6 +828,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       for (int j = 0; j < kCW; ++j, pj += ldr2) in.b[j] = (in.row_ok && c0 + j < in.nval) ? *pj : 0.0;
     };
     TileIn cur, nxt;
+    pdl_wait();                                     // B, exponents and pending scalings of the diagonal step
     if (t0 < t1) fetch(t0, cur);
     for (int t = t0, k = 0; t < t1; ++t, ++k) {
       const int ab = k & 1;
@@ -930,11 +935,11 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
     if (e != cudaSuccess) return e;
     const double mma_flops = (double)total * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
     void *h = trace_on() ? trace_start(2, mma_flops, (double)total * kOzBBytes, st) : nullptr;
-    k_oz_update<<<std::min(total, kOzPersistentCtas), kOzuThreads, kOzuSmem, st>>>(plan.tmA, tmB, a, tiles_n,
-                                                                                 total);
+    e = launch_pdl(k_oz_update, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads), kOzuSmem, st,
+                   plan.tmA, tmB, a, tiles_n, total);
     trace_stop(h, st);
     count_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
