@@ -23,13 +23,14 @@
 //    is rounded until the final conversion to FP64.
 // The result is accurate to about 2^-50 relative to K' max|U(r,:)| max|X(:,j)|.
 //
-// Kernel layout (one CTA per 128 x 32 output tile of A' B'; 6 warps):
-//  warp 4  : TMA producer (B digit planes per chunk, A planes through a ring);
-//  warp 5  : one thread issues the MMAs of each chunk: for every A plane one
+// Kernel layout (one CTA per 128 x 32 output tile of A' B'; 10 warps):
+//  warp 8  : TMA producer (B digit planes per chunk, A planes through a ring);
+//  warp 9  : one thread issues the MMAs of each chunk: for every A plane one
 //            MMA per 16-wide K step against all the B planes it pairs with
 //            (N = 32 x (9 - s)), into 8 TMEM accumulators laid out by diagonal
 //            (double-buffered: 2 x 8 x 32 = 512 columns);
-//  warps 0-3: epilogue, one thread per TMEM lane (= output row).
+//  warps 0-7: epilogue, one thread per TMEM lane (= output row) and half
+//            of the tile's columns.
 // Every mbarrier wait is bounded; a timeout raises MSTS_STATUS_TIMEOUT in the
 // status word (which also makes the waits of all other CTAs give up) and the
 // kernel drains without hanging.
@@ -51,7 +52,8 @@ constexpr int kOzKC = 64;        // K' per chunk: one 128-byte swizzle row of BF
 constexpr int kOzBM = 128;       // real rows per tile (= TMEM lanes)
 constexpr int kOzBN = 32;        // columns per tile
 constexpr int kOzRing = 6;       // A-plane ring depth
-constexpr int kOzThreads = 192;  // 4 epilogue warps + producer + MMA
+constexpr int kOzEpi = 8;         // epilogue warps: two per TMEM lane quarter, 16 columns each
+constexpr int kOzThreads = 32 * kOzEpi + 64;  // + producer + MMA
 constexpr int kOzAccCols = kOzS * kOzBN;   // 8 diagonals x 32 columns per buffer
 constexpr uint32_t kOzABytes = kOzBM * kOzKC * 2;          // 16 KB per A plane
 constexpr uint32_t kOzBBytes = kOzS * kOzBN * kOzKC * 2;   // 32 KB for all B planes
@@ -215,7 +217,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1);
-      mbar_init(&accfull[i], 1); mbar_init(&accempty[i], kOzBM);
+      mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 32 * kOzEpi);
     }
     for (int i = 0; i < kOzRing; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 1); }
     mbar_init(&mma_done, 1);
@@ -232,7 +234,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     return ok;
   };
 
-  if (warp == 4) {
+  if (warp == kOzEpi) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       prefetch_tmap(&tmA);
@@ -253,7 +255,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (fail) break;
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == kOzEpi + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       int ia = 0;
@@ -290,11 +292,14 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       if (!wait(&mma_done, 0)) fail = 1;
     }
   } else {
-    // ---------------- epilogue: warps 0-3, one thread per output row -------
-    long long hi[kOzBN], lo[kOzBN];
+    // ---------------- epilogue: warp w reads TMEM lanes 32 (w mod 4).. (its
+    // rows) and the kEC columns starting at kEC (w / 4) -------------------
+    constexpr int kEC = kOzBN * 4 / kOzEpi;
+    const int quarter = warp & 3, cg = warp >> 2;
+    long long hi[kEC], lo[kEC];
 #pragma unroll
-    for (int j = 0; j < kOzBN; ++j) hi[j] = lo[j] = 0;
-    const uint32_t lane_addr = (uint32_t)(32 * warp) << 16;
+    for (int j = 0; j < kEC; ++j) hi[j] = lo[j] = 0;
+    const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       const int ab = c & 1;
@@ -302,11 +307,11 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       tc_fence_after();
 #pragma unroll
       for (int d = 0; d < kOzS; ++d) {                       // diagonal s + t = d + 2
-        uint32_t v[32];
-        tmem_ld32(tmem + lane_addr + ab * kOzAccCols + d * kOzBN, v);
+        uint32_t v[kEC];
+        tmem_ld16(tmem + lane_addr + ab * kOzAccCols + d * kOzBN + kEC * cg, v);
         tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < kOzBN; ++j) {
+        for (int j = 0; j < kEC; ++j) {
           const long long q = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact integer
           if (d <= 2) hi[j] += q << (kOzBits * (2 - d));
           else lo[j] += q << (kOzBits * (7 - d));
@@ -317,14 +322,14 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     if (!ok) fail = 1;
     // P = 2^(e_r + f_j) (hi 2^-28 + lo 2^-63)
-    const int i = i0 + 32 * warp + lane;                     // real row of A'
+    const int i = i0 + 32 * quarter + lane;                  // real row of A'
     const bool row_ok = MODE != kUpdate ? i < 2 * args.m : i < args.row_hi;
     if (ok && row_ok) {
       const int r = i >> 1, part = i & 1;
       const int er = args.rexp[r];
 #pragma unroll
-      for (int j = 0; j < kOzBN; ++j) {
-        const int lc = j0 + j;
+      for (int j = 0; j < kEC; ++j) {
+        const int lc = j0 + kEC * cg + j;
         if (lc >= (MODE != kUpdate ? args.n : args.ncols)) continue;
         const double p = scalbn(fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-63), er + args.cexp[lc]);
         if (MODE == kProduct) {
