@@ -1,0 +1,88 @@
+"""GPU edge cases of every entry point: empty problems (m = 0 or n = 0) are
+no-ops that launch nothing and leave the outputs alone, zero right-hand
+sides solve to zero with unit scales, and exact zero pivots are flagged (plain)
+or replaced by delta (safe), as the oracle does."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1607_01477_gb300 as msts
+from paper_1607_01477_gb300 import workloads as W
+from gpu_util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def zeros(rows, cols):
+    return msts.colmajor(torch.zeros((rows, cols), dtype=torch.complex128, device="cuda"))
+
+
+def cvec(n):
+    return torch.zeros(n, dtype=torch.complex128, device="cuda")
+
+
+@pytest.mark.parametrize("safe", [False, True])
+@pytest.mark.parametrize("tensor", [False, True])
+def test_empty_solves_launch_nothing(safe, tensor):
+    lib = msts.load_library()
+    U = to_dev(W.plain_problem(40, 3, seed=1)[0])
+    before = lib.msts_launch_count()
+    B = zeros(40, 0)
+    _, sc, se, st = msts.msts_solve(U, cvec(0), B, safe=safe, tensor=tensor)
+    B0 = zeros(0, 5)
+    msts.msts_solve(zeros(0, 0), cvec(5), B0, safe=safe, tensor=tensor)
+    msts.msts_gsolve(U, U, cvec(0), zeros(40, 0), safe=safe, tensor=tensor)
+    msts.msts_solve_variant(U, cvec(0), zeros(0, 40), side="right", uplo="lower", trans="C", safe=safe,
+                            tensor=tensor)
+    msts.msts_solve_variant(zeros(0, 0), cvec(3), zeros(0, 3), side="left", uplo="lower", safe=safe,
+                            tensor=tensor)
+    est, kind, steps, _ = msts.msts_pseudospectra_1norm(U, cvec(0), tensor=tensor)
+    torch.cuda.synchronize()
+    assert lib.msts_launch_count() == before
+    assert est.numel() == 0 and int(st.item()) == 0
+
+
+def test_empty_trevc_and_back_transform():
+    lib = msts.load_library()
+    before = lib.msts_launch_count()
+    Z, sc, se, st = msts.msts_trevc(zeros(0, 0))
+    X, st2 = msts.msts_back_transform(zeros(0, 0), zeros(0, 0))
+    torch.cuda.synchronize()
+    assert Z.numel() == 0 and X.numel() == 0 and lib.msts_launch_count() == before
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+def test_zero_right_hand_sides(tensor):
+    U, s, B = W.plain_problem(100, 7, seed=5)
+    Bz = np.zeros_like(B)
+    X = to_dev(Bz)
+    _, sc, se, st = msts.msts_solve(to_dev(U), to_dev(s), X, safe=True, nb=32, tensor=tensor)
+    assert (to_np(X) == 0).all() and (to_np(se) == 0).all() and (to_np(sc) == 1.0).all()
+    assert int(st.item()) == 0
+
+
+def test_plain_zero_pivot_is_flagged():
+    U, s, B = W.plain_problem(64, 4, seed=6)
+    s = s.copy()
+    s[2] = U[10, 10]                                    # U(10,10) - s_2 = 0 exactly
+    X = to_dev(B)
+    _, _, _, st = msts.msts_solve(to_dev(U), to_dev(s), X, nb=32)
+    assert int(st.item()) & 1                           # MSTS_STATUS_ZERO_PIVOT
+    Xg = to_np(X)
+    assert np.isfinite(Xg[:, [0, 1, 3]]).all()          # the other shifts are unaffected
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+def test_safe_zero_pivot_uses_delta_like_the_oracle(tensor):
+    U, s, B = W.plain_problem(64, 4, seed=7)
+    s = s.copy()
+    s[1] = U[20, 20]
+    X = to_dev(B)
+    _, sc, se, st = msts.msts_solve(to_dev(U), to_dev(s), X, safe=True, nb=32, tensor=tensor)
+    Xo, eo = oracle.safe_solve(U, s, B, 32)
+    assert int(st.item()) & 16                          # MSTS_STATUS_DELTA
+    assert np.array_equal(to_np(se), eo)
+    Xg = to_np(X)
+    rel = np.abs(Xg - Xo).max(axis=0) / np.abs(Xo).max(axis=0)
+    assert rel.max() <= 1e-8
