@@ -795,12 +795,14 @@ def run_reference(args):
     import oracle
     T = W.trevc_problem(4096)
     m = 4096
-    stride = 16
-    cols_all = np.arange(0, m, stride)
+    # each step: every 2nd eigenvector column (rotating offset), the sample the
+    # main line's cpu_baseline uses (~0.8 s on 16 cores), so the oracle's O(m^2)
+    # set-up of Alg. 5 is amortised as in a full run
+    cols_all = np.arange(0, m)
     oracle.trevc_columns(T, cols_all[:4], 32)
     times = []
     for k in range(args.warmup + args.steps):
-        cols = cols_all[(k % 4)::4]                 # a bounded sample per step
+        cols = cols_all[(k % 2)::2]                 # a bounded sample per step
         t0 = time.perf_counter()
         oracle.trevc_columns(T, cols, 32)
         dt = time.perf_counter() - t0
@@ -818,8 +820,8 @@ def run_reference(args):
                                   "10*CN(0,1)", "m": m, "n_b": 32},
            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.num_threads(),
                             "kind": "oracle",
-                            "sample": f"{cols_all.size // 4} eigenvector columns per step "
-                                      f"(every {4 * stride}th column, rotating offset)"},
+                            "sample": f"{cols_all.size // 2} eigenvector columns per step "
+                                      f"(every 2nd column, rotating offset)"},
            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
