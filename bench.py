@@ -32,6 +32,7 @@ import os
 import re
 import signal
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -109,7 +110,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples go to a scratch directory (MSTS_CLOCKS_DIR, else the system temp dir)
+        out_dir = os.environ.get("MSTS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
