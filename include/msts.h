@@ -255,8 +255,9 @@ int msts_back_transform(const msts_z *Q, int64_t ldq, int64_t m,
  * multi-shift solves over all N grid points at once (upper with T - zI, then
  * lower with its conjugate transpose).
  * V0       m x N start vectors (leading dimension ldv), normalised inside.
- * Lanczos readings: full reorthogonalisation (classical Gram-Schmidt, twice);
- * exactly min(iters, m) steps unless beta_k <= 1e-14 max_i |alpha_i|.
+ * Lanczos readings: full reorthogonalisation by classical Gram-Schmidt, run a
+ * second time when the first pass removed more than half of ||w||^2 ("twice
+ * is enough"); exactly min(iters, m) steps unless beta_k <= 1e-14 max_i |alpha_i|.
  * alpha, beta (optional, may be NULL): N x iters tridiagonal entries, point p
  * at [p*iters, (p+1)*iters); steps (optional): the tridiagonal order per point.
  * ------------------------------------------------------------------------- */

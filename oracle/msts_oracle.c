@@ -427,9 +427,10 @@ double or_tridiag_max_eig(int k, const double *a, const double *b) {
  * two triangular solves: upper with T - z I, then lower with (T - z I)^H.
  *
  * Readings: the start vector of point p is column p of V0, normalised; the
- * Lanczos vectors are fully reorthogonalised by classical Gram-Schmidt run
- * twice; exactly min(iters, m) steps are taken, stopping earlier only when
- * beta_k <= 1e-14 * max_{i<=k} |alpha_i|.  alpha/beta (iters x N, column p
+ * Lanczos vectors are fully reorthogonalised by classical Gram-Schmidt, run a
+ * second time only when the first pass removed more than half of ||w||^2
+ * (Kahan-Parlett "twice is enough"); exactly min(iters, m) steps are taken,
+ * stopping earlier only when beta_k <= 1e-14 * max_{i<=k} |alpha_i|.  alpha/beta (iters x N, column p
  * for point p; may be NULL) receive the tridiagonal, steps[p] its order.
  * ---------------------------------------------------------------------- */
 void or_pseudospectra(int64_t m, const oz *T, int64_t ldt, int64_t N, const oz *z,
@@ -462,7 +463,11 @@ void or_pseudospectra(int64_t m, const oz *T, int64_t ldt, int64_t N, const oz *
         oz *vp = &V[(size_t)(k - 1) * m];
         for (int64_t r = 0; r < m; ++r) w[r] = oz_sub(w[r], oz_scale(vp[r], be[k - 1]));
       }
-      for (int pass = 0; pass < 2; ++pass) {       /* CGS2 against v_0..v_k   */
+      /* classical Gram-Schmidt against v_0..v_k, repeated once when the first
+       * pass removed more than half of ||w||^2 ("twice is enough") */
+      double n0 = 0.0;
+      for (int64_t r = 0; r < m; ++r) n0 += w[r].re * w[r].re + w[r].im * w[r].im;
+      for (int pass = 0; pass < 2; ++pass) {
         oz h[64];
         oz *hh = (k + 1 <= 64) ? h : (oz *)malloc(sizeof(oz) * (size_t)(k + 1));
         for (int i = 0; i <= k; ++i) {
@@ -476,6 +481,11 @@ void or_pseudospectra(int64_t m, const oz *T, int64_t ldt, int64_t N, const oz *
           for (int64_t r = 0; r < m; ++r) w[r] = oz_sub(w[r], oz_mul(vi[r], hh[i]));
         }
         if (hh != h) free(hh);
+        if (pass == 0) {
+          double n1 = 0.0;
+          for (int64_t r = 0; r < m; ++r) n1 += w[r].re * w[r].re + w[r].im * w[r].im;
+          if (!(n1 < 0.5 * n0)) break;
+        }
       }
       double bn = 0.0;
       for (int64_t r = 0; r < m; ++r) bn += w[r].re * w[r].re + w[r].im * w[r].im;

@@ -7,7 +7,8 @@
 // two engine solves (upper T - zI, then the conjugate-transposed lower solve),
 // followed by one fused per-point kernel for the Lanczos recurrence (alpha,
 // the three-term update, full reorthogonalisation by classical Gram-Schmidt
-// run twice, beta and the next Lanczos vector).  The tridiagonal's largest
+// with a second pass when the first removed more than half of ||w||^2, beta and
+// the next Lanczos vector).  The tridiagonal's largest
 // eigenvalue is then found per point by Sturm-count bisection.
 #include <math_constants.h>
 
@@ -98,8 +99,12 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_step(LanczosState S, int
     w[r] = x;
   }
   __syncthreads();
-  // Full reorthogonalisation against v_0..v_k, classical Gram-Schmidt twice.
+  // Full reorthogonalisation against v_0..v_k by classical Gram-Schmidt, run
+  // a second time only when the first pass removed more than half of ||w||^2.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double n0 = 0.0;
+  for (int r = threadIdx.x; r < m; r += kLzThreads) n0 += w[r].x * w[r].x + w[r].y * w[r].y;
+  n0 = block_sum(n0, red);
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = 0; i <= k; ++i) {
       const double2 *vi = S.V + (long long)i * S.vstride + (long long)p * m;
@@ -120,13 +125,16 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_step(LanczosState S, int
       h[i] = s;
     }
     __syncthreads();
+    double n1 = 0.0;
     for (int r = threadIdx.x; r < m; r += kLzThreads) {
       double2 x = w[r];
       for (int i = 0; i <= k; ++i)
         x = zfms(x, S.V[(long long)i * S.vstride + (long long)p * m + r], h[i]);
       w[r] = x;
+      n1 += x.x * x.x + x.y * x.y;
     }
     __syncthreads();
+    if (pass == 0 && !(block_sum(n1, red) < 0.5 * n0)) break;   // CTA-uniform
   }
   double bb = 0.0;
   for (int r = threadIdx.x; r < m; r += kLzThreads) bb += w[r].x * w[r].x + w[r].y * w[r].y;
@@ -146,6 +154,124 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_step(LanczosState S, int
     S.steps[p] = k + 1;
     if (stop) S.active[p] = 0;
   }
+}
+
+// The same step with w held in registers (element r = threadIdx.x + 256 q of
+// this point, q < RW): the reorthogonalisation then reads only the Lanczos
+// vectors from memory, not w again for every dot product and update.  The
+// sums run over the same elements in the same order as k_lanczos_step.
+template <int RW>
+__global__ void __launch_bounds__(kLzThreads) k_lanczos_step_r(LanczosState S, int k) {
+  __shared__ double red[kLzWarps];
+  __shared__ double2 part[kMaxIters + 1][kLzWarps];
+  __shared__ double2 h[kMaxIters + 1];
+  const int p = blockIdx.x;
+  if (!S.active[p]) return;
+  const int m = S.m;
+  const double2 *wsrc = S.W + (long long)p * m;
+  const double2 *vk = S.V + (long long)k * S.vstride + (long long)p * m;
+  double2 w[RW];
+#pragma unroll
+  for (int q = 0; q < RW; ++q) {
+    const int r = threadIdx.x + kLzThreads * q;
+    w[q] = r < m ? wsrc[r] : make_double2(0.0, 0.0);
+  }
+  // alpha_k = Re(v_k^H w)
+  double a = 0.0;
+#pragma unroll
+  for (int q = 0; q < RW; ++q) {
+    const int r = threadIdx.x + kLzThreads * q;
+    if (r < m) a += vk[r].x * w[q].x + vk[r].y * w[q].y;
+  }
+  a = block_sum(a, red);
+  const double bprev = k > 0 ? S.beta[(long long)p * S.iters + k - 1] : 0.0;
+  const double2 *vp = k > 0 ? S.V + (long long)(k - 1) * S.vstride + (long long)p * m : nullptr;
+#pragma unroll
+  for (int q = 0; q < RW; ++q) {
+    const int r = threadIdx.x + kLzThreads * q;
+    if (r < m) {
+      double2 x = zsub(w[q], zscale(vk[r], a));
+      if (k > 0) x = zsub(x, zscale(vp[r], bprev));
+      w[q] = x;
+    }
+  }
+  // Full reorthogonalisation against v_0..v_k by classical Gram-Schmidt, run
+  // a second time only when the first pass removed more than half of ||w||^2.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double n0 = 0.0;
+#pragma unroll
+  for (int q = 0; q < RW; ++q) n0 += w[q].x * w[q].x + w[q].y * w[q].y;
+  n0 = block_sum(n0, red);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i <= k; ++i) {
+      const double2 *vi = S.V + (long long)i * S.vstride + (long long)p * m;
+      double2 sacc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < RW; ++q) {
+        const int r = threadIdx.x + kLzThreads * q;
+        if (r < m) sacc = zfma_cj(sacc, vi[r], w[q]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+        sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+      }
+      if (lane == 0) part[i][warp] = sacc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= k; i += kLzThreads) {
+      double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int ww = 0; ww < kLzWarps; ++ww) t = zadd(t, part[i][ww]);
+      h[i] = t;
+    }
+    __syncthreads();
+    double n1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const int r = threadIdx.x + kLzThreads * q;
+      if (r < m) {
+        double2 x = w[q];
+        for (int i = 0; i <= k; ++i) x = zfms(x, S.V[(long long)i * S.vstride + (long long)p * m + r], h[i]);
+        w[q] = x;
+        n1 += x.x * x.x + x.y * x.y;
+      }
+    }
+    __syncthreads();
+    if (pass == 0 && !(block_sum(n1, red) < 0.5 * n0)) break;   // CTA-uniform
+  }
+  double bb = 0.0;
+#pragma unroll
+  for (int q = 0; q < RW; ++q) bb += w[q].x * w[q].x + w[q].y * w[q].y;
+  const double beta = sqrt(block_sum(bb, red));
+  const double amax = fmax(S.amax[p], fabs(a));
+  const bool stop = (k == S.K - 1) || (beta <= 1e-14 * amax);
+  {  // v_{k+1} = w / beta_k (zero once the recurrence has stopped)
+    double2 *vn = S.V + (long long)(k + 1) * S.vstride + (long long)p * m;
+    const double inv = stop ? 0.0 : 1.0 / beta;
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const int r = threadIdx.x + kLzThreads * q;
+      if (r < m) vn[r] = stop ? make_double2(0.0, 0.0) : zscale(w[q], inv);
+    }
+  }
+  if (threadIdx.x == 0) {
+    S.alpha[(long long)p * S.iters + k] = a;
+    S.beta[(long long)p * S.iters + k] = beta;
+    S.amax[p] = amax;
+    S.steps[p] = k + 1;
+    if (stop) S.active[p] = 0;
+  }
+}
+
+static void launch_lanczos_step(const LanczosState &S, int k, cudaStream_t st) {
+  const int m = S.m;
+  if (m <= kLzThreads) k_lanczos_step_r<1><<<S.N, kLzThreads, 0, st>>>(S, k);
+  else if (m <= 2 * kLzThreads) k_lanczos_step_r<2><<<S.N, kLzThreads, 0, st>>>(S, k);
+  else if (m <= 4 * kLzThreads) k_lanczos_step_r<4><<<S.N, kLzThreads, 0, st>>>(S, k);
+  else if (m <= 8 * kLzThreads) k_lanczos_step_r<8><<<S.N, kLzThreads, 0, st>>>(S, k);
+  else if (m <= 16 * kLzThreads) k_lanczos_step_r<16><<<S.N, kLzThreads, 0, st>>>(S, k);
+  else k_lanczos_step<<<S.N, kLzThreads, 0, st>>>(S, k);
 }
 
 // Number of eigenvalues of tridiag(b, a, b) below x (negative LDL^T pivots).
@@ -252,7 +378,7 @@ cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z,
     if (e != cudaSuccess) return e;
     e = engine_run(&Pc, 1, nb, false, true, false, engine_ws, status, st);              // (T - zI)^{-H}
     if (e != cudaSuccess) return e;
-    k_lanczos_step<<<N, kLzThreads, 0, st>>>(S, k);
+    launch_lanczos_step(S, k, st);
     count_launches(2);
   }
   k_ritz<<<(N + 127) / 128, 128, 0, st>>>(S, sigma_min);
