@@ -669,23 +669,25 @@ def batched_fwd_bwd(dev, nb):
     Xs = [B.clone() for _, _, B in dp]
     fwd_fl = sum(4.0 * B.shape[0] ** 2 * B.shape[1] for _, _, B in probs)
 
-    def forward():
-        for X, (_, _, B) in zip(Xs, dp):
-            X.copy_(B)
-        msts.msts_solve_batched([(U, s, X) for (U, s, _), X in zip(dp, Xs)], nb=nb)
+    out = {"note": "forward 4 m^2 n, backward 12 m^2 n FLOPs (X recomputed, adjoint solve, triu(Lambda X^H))"}
+    for tag, tensor in (("fp64_gemm", False), ("tensor_gemm", True)):
+        def forward():
+            for X, (_, _, B) in zip(Xs, dp):
+                X.copy_(B)
+            msts.msts_solve_batched([(U, s, X) for (U, s, _), X in zip(dp, Xs)], nb=nb, tensor=tensor)
 
-    def backward():
-        return msts.msts_adjoint_batched([(U, s, B, 2 * X) for (U, s, B), X in zip(dp, Xs)], nb=nb)
+        def backward():
+            return msts.msts_adjoint_batched([(U, s, B, 2 * X) for (U, s, B), X in zip(dp, Xs)], nb=nb,
+                                             tensor=tensor)
 
-    forward(); backward()
-    torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    e[0].record(); forward(); e[1].record(); backward(); e[2].record()
-    torch.cuda.synchronize()
-    fms, bms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-    return {"forward_ms": fms, "backward_ms": bms,
-            "tflops": 4 * fwd_fl / ((fms + bms) * 1e-3) / 1e12,
-            "note": "forward 4 m^2 n, backward 12 m^2 n FLOPs (X recomputed, adjoint solve, triu(Lambda X^H))"}
+        forward(); backward()
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(); forward(); e[1].record(); backward(); e[2].record()
+        torch.cuda.synchronize()
+        fms, bms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        out[tag] = {"forward_ms": fms, "backward_ms": bms, "tflops": 4 * fwd_fl / ((fms + bms) * 1e-3) / 1e12}
+    return out
 
 
 def eta_dev(Ud, sd, Bd, X):

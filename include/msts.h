@@ -149,7 +149,9 @@ int msts_solve_variant(int32_t side, int32_t uplo, int32_t trans,
  * msts_solve would with the fields of probs[p] (host array of `batch`
  * descriptors; the pointers inside are device pointers).  All problems share
  * n_b, flags and stream; their block steps run together, one launch per step
- * for all problems.
+ * for all problems.  flags: MSTS_SAFE, MSTS_CONJ_TRANS (plain only) and
+ * MSTS_TENSOR_GEMM (each problem's U split into digit planes in the workspace,
+ * every problem's substitution step in one tensor-core launch per block step).
  * ------------------------------------------------------------------------- */
 typedef struct {
   const msts_z *U; int64_t ldu; int64_t m;
@@ -349,6 +351,15 @@ size_t msts_adjoint_batched_workspace_size(const msts_adjoint_problem *probs, in
 int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32_t nb,
                          void *workspace, size_t workspace_bytes,
                          uint32_t *status, void *stream);
+/* The same with flags: MSTS_TENSOR_GEMM runs the substitution steps of both
+ * internal solves (X recomputed, and Lambda) on the tensor cores, all problems
+ * of a block step in one launch; workspace from the _flags size query (it adds
+ * the digit planes of U and U^H per problem).  Returns -8 for unknown flags. */
+size_t msts_adjoint_batched_flags_workspace_size(const msts_adjoint_problem *probs, int64_t batch,
+                                                 int32_t nb, uint32_t flags);
+int msts_adjoint_batched_flags(const msts_adjoint_problem *probs, int64_t batch, int32_t nb,
+                               void *workspace, size_t workspace_bytes,
+                               uint32_t *status, uint32_t flags, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Mixed-precision multi-shift solve with FP64 iterative refinement (not in the

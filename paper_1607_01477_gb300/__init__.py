@@ -107,6 +107,10 @@ def load_library():
         lib.msts_adjoint_batched_workspace_size.argtypes = [_vp, _i64, _i32]
         lib.msts_adjoint_batched.restype = ctypes.c_int
         lib.msts_adjoint_batched.argtypes = [_vp, _i64, _i32, _vp, _sz, _vp, _vp]
+        lib.msts_adjoint_batched_flags_workspace_size.restype = _sz
+        lib.msts_adjoint_batched_flags_workspace_size.argtypes = [_vp, _i64, _i32, _u32]
+        lib.msts_adjoint_batched_flags.restype = ctypes.c_int
+        lib.msts_adjoint_batched_flags.argtypes = [_vp, _i64, _i32, _vp, _sz, _vp, _u32, _vp]
         lib.msts_solve_mixed_workspace_size.restype = _sz
         lib.msts_solve_mixed_workspace_size.argtypes = [_i64, _i64, _i32, _u32]
         lib.msts_solve_mixed.restype = ctypes.c_int
@@ -281,8 +285,10 @@ def msts_solve_variant(A, shifts, B, *, side="left", uplo="upper", trans="N", sa
     return B, scales, sexp, status
 
 
-def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, status=None):
+def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, tensor=False, status=None):
     """Solves every (U, shifts, B) of `problems` in shared launches, in place on each B.
+    tensor=True runs every problem's substitution step on the tensor cores, all
+    problems of a block step in one launch.
 
     Returns (list of (scales, scale_exp) or None, status).
     """
@@ -303,7 +309,7 @@ def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, status=
                           sc.data_ptr() if safe else None, se.data_ptr() if safe else None)
     if not problems:
         return [], status
-    flags = (MSTS_SAFE if safe else 0) | (MSTS_CONJ_TRANS if conj_trans else 0)
+    flags = (MSTS_SAFE if safe else 0) | (MSTS_CONJ_TRANS if conj_trans else 0) | (MSTS_TENSOR_GEMM if tensor else 0)
     ws = _workspace(lib.msts_solve_batched_workspace_size(arr, len(problems), nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
@@ -547,8 +553,9 @@ def msts_adjoint(U, shifts, B, GX, *, nb=32, status=None):
     return dU, dB, ds, status
 
 
-def msts_adjoint_batched(problems, *, nb=32, status=None):
-    """problems: list of (U, shifts, B, GX).  Returns (list of (dU, dB, ds), status)."""
+def msts_adjoint_batched(problems, *, nb=32, tensor=False, status=None):
+    """problems: list of (U, shifts, B, GX).  Returns (list of (dU, dB, ds), status).
+    tensor=True runs the substitution steps of both internal solves on the tensor cores."""
     lib = load_library()
     arr = (_AdjProblem * len(problems))()
     outs = []
@@ -566,11 +573,12 @@ def msts_adjoint_batched(problems, *, nb=32, status=None):
                              ldg, dU.data_ptr(), max(1, m), dB.data_ptr(), max(1, m), ds.data_ptr())
     if not problems:
         return [], status
-    ws = _workspace(lib.msts_adjoint_batched_workspace_size(arr, len(problems), nb), dev)
+    flags = MSTS_TENSOR_GEMM if tensor else 0
+    ws = _workspace(lib.msts_adjoint_batched_flags_workspace_size(arr, len(problems), nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
-    rc = lib.msts_adjoint_batched(arr, len(problems), nb, wp, wb, _ptr(status), _stream(dev))
-    _check(rc, "msts_adjoint_batched")
+    rc = lib.msts_adjoint_batched_flags(arr, len(problems), nb, wp, wb, _ptr(status), flags, _stream(dev))
+    _check(rc, "msts_adjoint_batched_flags")
     return outs, status
 
 

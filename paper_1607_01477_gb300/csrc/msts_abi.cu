@@ -81,6 +81,15 @@ int msts_solve(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shifts, in
   return cuda_rc(msts::engine_run(&p, 1, nb, safe, conj, false, workspace, status, st));
 }
 
+// Tensor-core plans of a batch: one per problem with work, after the engine's
+// own workspace.
+static size_t batched_plan_bytes(const msts_problem *probs, int64_t batch, int32_t nb) {
+  size_t s = 0;
+  for (int64_t i = 0; i < batch; ++i)
+    if (probs[i].m > 0 && probs[i].n > 0) s += align256(msts::ozaki_plan_bytes((int)probs[i].m, (int)probs[i].n, nb));
+  return s;
+}
+
 size_t msts_solve_batched_workspace_size(const msts_problem *probs, int64_t batch, int32_t nb,
                                          uint32_t flags) {
   if (!probs || batch < 0 || !nb_ok(nb)) return 0;
@@ -88,7 +97,9 @@ size_t msts_solve_batched_workspace_size(const msts_problem *probs, int64_t batc
   for (int64_t i = 0; i < batch; ++i)
     v.push_back(make_problem(nullptr, 1, probs[i].m, nullptr, 1, probs[i].n, nullptr, 1, nullptr,
                              nullptr, 0));
-  return msts::engine_workspace_bytes(v.data(), (int)batch, nb, (flags & MSTS_SAFE) != 0);
+  size_t s = msts::engine_workspace_bytes(v.data(), (int)batch, nb, (flags & MSTS_SAFE) != 0);
+  if (flags & MSTS_TENSOR_GEMM) s = align256(s) + batched_plan_bytes(probs, batch, nb);
+  return s;
 }
 
 int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb, void *workspace,
@@ -97,7 +108,7 @@ int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb, voi
   if (batch < 0 || batch > kMaxDim) return -2;
   if (batch > 0 && !probs) return -1;
   if (!nb_ok(nb)) return -3;
-  if ((flags & ~(MSTS_SAFE | MSTS_CONJ_TRANS)) != 0 || (safe && conj)) return -7;
+  if ((flags & ~(MSTS_SAFE | MSTS_CONJ_TRANS | MSTS_TENSOR_GEMM)) != 0 || (safe && conj)) return -7;
   std::vector<msts::EngineProblem> v;
   for (int64_t i = 0; i < batch; ++i) {
     const msts_problem &q = probs[i];
@@ -108,11 +119,24 @@ int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb, voi
     v.push_back(make_problem(q.U, q.ldu, q.m, q.shifts, 1, q.n, q.B, q.ldb, q.scales,
                              q.scale_exp, 0));
   }
-  const size_t need = msts::engine_workspace_bytes(v.data(), (int)batch, nb, safe);
+  const size_t need = msts_solve_batched_workspace_size(probs, batch, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -5 : -4;
   if (batch == 0) return 0;
-  return cuda_rc(msts::engine_run(v.data(), (int)batch, nb, safe, conj, false, workspace, status,
-                                  static_cast<cudaStream_t>(stream)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<msts::OzPlan> plans;
+  if (flags & MSTS_TENSOR_GEMM) {
+    plans.resize((size_t)batch);
+    char *cur = static_cast<char *>(workspace) + align256(msts::engine_workspace_bytes(v.data(), (int)batch, nb, safe));
+    for (int64_t i = 0; i < batch; ++i) {
+      if (probs[i].m == 0 || probs[i].n == 0) continue;
+      if (msts::ozaki_plan_prepare(&plans[(size_t)i], v[(size_t)i].U, probs[i].ldu, (int)probs[i].m, (int)probs[i].n,
+                                   nb, conj, cur, st) != cudaSuccess)
+        return MSTS_ERR_CUDA;
+      cur += align256(msts::ozaki_plan_bytes((int)probs[i].m, (int)probs[i].n, nb));
+      v[(size_t)i].oz = &plans[(size_t)i];
+    }
+  }
+  return cuda_rc(msts::engine_run(v.data(), (int)batch, nb, safe, conj, false, workspace, status, st));
 }
 
 size_t msts_trevc_workspace_size(int64_t m, int32_t nb, uint32_t flags) {

@@ -11,6 +11,7 @@
 
 #include "msts_common.cuh"
 #include "msts_engine.h"
+#include "msts_ozaki.h"
 #include "msts_trace.h"
 
 namespace msts {
@@ -114,16 +115,21 @@ __global__ void k_ds(const __grid_constant__ AdjTable tab) {
 
 static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t adjoint_workspace_bytes(const msts_adjoint_problem *probs, int64_t batch, int nb) {
+// X per problem, then (tensor) the digit-plane plans of U for the forward
+// solve and of U^H for the adjoint solve.
+size_t adjoint_workspace_bytes(const msts_adjoint_problem *probs, int64_t batch, int nb, bool tensor) {
   size_t s = 0;
-  for (int64_t i = 0; i < batch; ++i) s += a256(sizeof(double2) * (size_t)probs[i].m * probs[i].n);
-  (void)nb;
+  for (int64_t i = 0; i < batch; ++i) {
+    s += a256(sizeof(double2) * (size_t)probs[i].m * probs[i].n);
+    if (tensor && probs[i].m > 0 && probs[i].n > 0) s += 2 * a256(ozaki_plan_bytes((int)probs[i].m, (int)probs[i].n, nb));
+  }
   return s;
 }
 
 cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb, void *ws,
-                        uint32_t *status, cudaStream_t st) {
+                        uint32_t *status, cudaStream_t st, bool tensor) {
   char *cur = static_cast<char *>(ws);
+  std::vector<OzPlan> plans(tensor ? 2 * (size_t)std::min<int64_t>(batch, kMaxProbs) : 0);
   for (int64_t base = 0; base < batch; base += kMaxProbs) {
     const int cnt = (int)std::min<int64_t>(kMaxProbs, batch - base);
     std::vector<EngineProblem> fwd(cnt), adj(cnt);
@@ -150,6 +156,17 @@ cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb
       at.p[i] = AdjProb{reinterpret_cast<const double2 *>(q.dB), q.lddb, X, ldx,
                         reinterpret_cast<double2 *>(q.dU), q.lddu, reinterpret_cast<double2 *>(q.ds),
                         (int)q.m, (int)q.n};
+      if (tensor && q.m > 0 && q.n > 0) {
+        const size_t pb = a256(ozaki_plan_bytes((int)q.m, (int)q.n, nb));
+        cudaError_t e = ozaki_plan_prepare(&plans[2 * i], fwd[i].U, q.ldu, (int)q.m, (int)q.n, nb, false, cur, st);
+        if (e != cudaSuccess) return e;
+        cur += pb;
+        e = ozaki_plan_prepare(&plans[2 * i + 1], fwd[i].U, q.ldu, (int)q.m, (int)q.n, nb, true, cur, st);
+        if (e != cudaSuccess) return e;
+        cur += pb;
+        fwd[i].oz = &plans[2 * i];
+        adj[i].oz = &plans[2 * i + 1];
+      }
       maxm = std::max<int>(maxm, (int)q.m);
       maxn = std::max<int>(maxn, (int)q.n);
     }
@@ -175,18 +192,31 @@ cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb
 
 extern "C" {
 
+size_t msts_adjoint_batched_flags_workspace_size(const msts_adjoint_problem *probs, int64_t batch,
+                                                 int32_t nb, uint32_t flags) {
+  if (!probs || batch < 0 || (nb != 16 && nb != 32 && nb != 64)) return 0;
+  if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return 0;
+  return msts::adjoint_workspace_bytes(probs, batch, nb, (flags & MSTS_TENSOR_GEMM) != 0);
+}
+
 size_t msts_adjoint_batched_workspace_size(const msts_adjoint_problem *probs, int64_t batch,
                                            int32_t nb) {
-  if (!probs || batch < 0 || (nb != 16 && nb != 32 && nb != 64)) return 0;
-  return msts::adjoint_workspace_bytes(probs, batch, nb);
+  return msts_adjoint_batched_flags_workspace_size(probs, batch, nb, 0);
 }
 
 int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32_t nb,
                          void *workspace, size_t workspace_bytes, uint32_t *status, void *stream) {
+  return msts_adjoint_batched_flags(probs, batch, nb, workspace, workspace_bytes, status, 0, stream);
+}
+
+int msts_adjoint_batched_flags(const msts_adjoint_problem *probs, int64_t batch, int32_t nb,
+                               void *workspace, size_t workspace_bytes, uint32_t *status, uint32_t flags,
+                               void *stream) {
   const int64_t kMax = (int64_t)1 << 30;
   if (batch < 0 || batch > kMax) return -2;
   if (batch > 0 && !probs) return -1;
   if (nb != 16 && nb != 32 && nb != 64) return -3;
+  if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -8;
   for (int64_t i = 0; i < batch; ++i) {
     const msts_adjoint_problem &q = probs[i];
     const int64_t mm = q.m > 1 ? q.m : 1;
@@ -196,11 +226,12 @@ int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32
     if (q.n > 0 && (!q.shifts || !q.ds)) return -1;
     if (q.m > 0 && q.n > 0 && (!q.B || !q.GX || !q.dB)) return -1;
   }
-  const size_t need = msts::adjoint_workspace_bytes(probs, batch, nb);
+  const bool tensor = (flags & MSTS_TENSOR_GEMM) != 0;
+  const size_t need = msts::adjoint_workspace_bytes(probs, batch, nb, tensor);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -5 : -4;
   if (batch == 0) return 0;
   const cudaError_t e = msts::adjoint_run(probs, batch, nb, workspace, status,
-                                          static_cast<cudaStream_t>(stream));
+                                          static_cast<cudaStream_t>(stream), tensor);
   return e == cudaSuccess ? 0 : MSTS_ERR_CUDA;
 }
 

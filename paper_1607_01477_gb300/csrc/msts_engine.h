@@ -22,7 +22,7 @@ struct EngineProblem {
   double *scales;
   int *scale_exp;
   int diag_z;  // write Z(j,j) = s_j at the end (TREVC)
-  const struct OzPlan *oz;  // non-null: substitution GEMM on the tensor cores (single problem)
+  const struct OzPlan *oz;  // non-null: substitution GEMM on the tensor cores (one plan per problem)
   // Generalized problem (appendix, Alg. 8/9): (U - s_j V) x_j = b_j with V
   // upper triangular; null for the standard one.
   const double2 *V = nullptr;

@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <memory>
 #include <mutex>
 
 #include "msts_common.cuh"
@@ -188,10 +189,11 @@ struct OzArgs {
 
 enum { kResidual = 0, kUpdate = 1, kProduct = 2 };
 
+// One output tile (bx, by) of the product; pA, pB and args point into the
+// kernel's parameter space (a plain launch, or one problem of a batch).
 template <int MODE>
-__global__ void __launch_bounds__(kOzThreads, 1)
-k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          const __grid_constant__ OzArgs args) {
+__device__ __forceinline__ void oz_gemm_tile(const CUtensorMap *pA, const CUtensorMap *pB, const OzArgs &args,
+                                             int bx, int by) {
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -203,8 +205,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __shared__ int fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = (MODE == kUpdate ? args.row_lo : 0) + blockIdx.y * kOzBM;   // first real row
-  const int j0 = blockIdx.x * kOzBN;                                         // first local column
+  const int i0 = (MODE == kUpdate ? args.row_lo : 0) + by * kOzBM;   // first real row
+  const int j0 = bx * kOzBN;                                         // first local column
   // Residual: U is upper, so K' columns below the tile's first row vanish;
   // product with an upper-triangular B: K' rows past the tile's last column do.
   const int c_begin = MODE == kResidual ? i0 / kOzKC : 0;
@@ -237,20 +239,20 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (warp == kOzEpi) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
+      prefetch_tmap(pA);
+      prefetch_tmap(pB);
       int ia = 0;
       for (int c = 0; c < nch; ++c) {
         const int kk = (c_begin + c) * kOzKC;
         const int bb = c & 1;
         if (c >= 2 && !wait(&bempty[bb], ((c >> 1) - 1) & 1)) { fail = 1; break; }
         mbar_arrive_expect_tx(&bfull[bb], kOzBBytes);
-        tma_load_3d(sB + bb * kOzBBytes, &tmB, &bfull[bb], kk, j0, 0);
+        tma_load_3d(sB + bb * kOzBBytes, pB, &bfull[bb], kk, j0, 0);
         for (int s = 0; s < kOzS; ++s, ++ia) {
           const int slot = ia % kOzRing;
           if (ia >= kOzRing && !wait(&aempty[slot], ((ia / kOzRing) - 1) & 1)) { fail = 1; break; }
           mbar_arrive_expect_tx(&afull[slot], kOzABytes);
-          tma_load_3d(sA + slot * kOzABytes, &tmA, &afull[slot], ax0 + kk, i0, s);
+          tma_load_3d(sA + slot * kOzABytes, pA, &afull[slot], ax0 + kk, i0, s);
         }
         if (fail) break;
       }
@@ -355,6 +357,29 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __syncthreads();
   if (fail && threadIdx.x == 0) raise_status(args.status, MSTS_STATUS_TIMEOUT);
   if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kOzThreads, 1)
+k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const __grid_constant__ OzArgs args) {
+  oz_gemm_tile<MODE>(&tmA, &tmB, args, blockIdx.x, blockIdx.y);
+}
+
+// The substitution step of a batch of problems in one launch: problem z =
+// blockIdx.z with its own tensor maps and arguments; CTAs past a problem's
+// tiles leave before any set-up.
+struct OzBatch {
+  CUtensorMap tmA[kMaxProbs];
+  CUtensorMap tmB[kMaxProbs];
+  OzArgs args[kMaxProbs];
+  int tiles_n[kMaxProbs], tiles_m[kMaxProbs];
+};
+
+__global__ void __launch_bounds__(kOzThreads, 1) k_oz_update_batched(const __grid_constant__ OzBatch b) {
+  const int z = blockIdx.z;
+  if ((int)blockIdx.x >= b.tiles_n[z] || (int)blockIdx.y >= b.tiles_m[z]) return;
+  oz_gemm_tile<kUpdate>(&b.tmA[z], &b.tmB[z], b.args[z], blockIdx.x, blockIdx.y);
 }
 
 // ----- host side -------------------------------------------------------------
@@ -587,6 +612,7 @@ cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, in
   plan->cexp = reinterpret_cast<int *>(c);
   plan->m = m; plan->nb = nb; plan->nblk = nblk; plan->KB = KB; plan->nmax = n; plan->conj = conj;
   if (!make_map(&plan->tmA, plan->planes, nblk * KB, 2 * m, kOzBM, 1)) return cudaErrorNotSupported;
+  if (n > 0 && !make_map(&plan->tmB, plan->bp, KB, n, kOzBN, kOzS)) return cudaErrorNotSupported;
   const dim3 grid(nblk, (m + 7) / 8);
   if (conj) k_ozs_prepare<true><<<grid, 256, 0, st>>>(U, ldu, nullptr, 0, m, nb, KB, plan->planes, plan->rexp);
   else k_ozs_prepare<false><<<grid, 256, 0, st>>>(U, ldu, V, ldv, m, nb, KB, plan->planes, plan->rexp);
@@ -960,6 +986,52 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
                        kOzSmem, st>>>(plan.tmA, tmB, a);
   trace_stop(h, st);
   count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_update_batched(const OzBatchStep *steps, int count, uint32_t *status, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (count > kMaxProbs) return cudaErrorInvalidValue;
+  std::unique_ptr<OzBatch> hb(new OzBatch());
+  int max_tn = 0, max_tm = 0;
+  double tiles = 0.0, chunk_tiles = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const OzBatchStep &q = steps[i];
+    hb->tiles_n[i] = hb->tiles_m[i] = 0;
+    if (!q.plan) continue;
+    const OzPlan &plan = *q.plan;
+    const int row_lo = plan.conj ? 2 * q.hi : 0, row_hi = plan.conj ? 2 * plan.m : 2 * q.lo;
+    if (q.ncols <= 0 || row_hi <= row_lo) continue;
+    hb->tmA[i] = plan.tmA;
+    if (q.ncols == plan.nmax) hb->tmB[i] = plan.tmB;
+    else if (!make_map(&hb->tmB[i], plan.bp, plan.KB, q.ncols, kOzBN, kOzS)) return cudaErrorNotSupported;
+    OzArgs a{};
+    a.B = q.B; a.ldb = q.ldb; a.R = q.B; a.ldr = q.ldb;
+    a.rexp = plan.rexp + (size_t)q.b * plan.m;
+    a.cexp = plan.cexp;
+    a.pend = q.pend;
+    a.m = plan.m; a.n = q.ncols; a.K = plan.KB;
+    a.a_x0 = q.b * plan.KB;
+    a.row_lo = row_lo; a.row_hi = row_hi;
+    a.col_base = q.jstart; a.ncols = q.ncols;
+    a.status = status ? status : abort_word();
+    hb->args[i] = a;
+    hb->tiles_n[i] = (q.ncols + kOzBN - 1) / kOzBN;
+    hb->tiles_m[i] = (row_hi - row_lo + kOzBM - 1) / kOzBM;
+    max_tn = std::max(max_tn, hb->tiles_n[i]);
+    max_tm = std::max(max_tm, hb->tiles_m[i]);
+    tiles += (double)hb->tiles_n[i] * hb->tiles_m[i];
+    chunk_tiles += (double)hb->tiles_n[i] * hb->tiles_m[i] * (plan.KB / kOzKC);
+  }
+  if (max_tn == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_oz_update_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  if (e != cudaSuccess) return e;
+  const double mma_flops = chunk_tiles * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+  void *h = trace_on() ? trace_start(2, mma_flops, chunk_tiles * (kOzS * kOzABytes + kOzBBytes), st) : nullptr;
+  k_oz_update_batched<<<dim3(max_tn, max_tm, count), kOzThreads, kOzSmem, st>>>(*hb);
+  trace_stop(h, st);
+  count_launches(1);
+  (void)tiles;
   return cudaGetLastError();
 }
 

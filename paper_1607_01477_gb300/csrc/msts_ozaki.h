@@ -31,6 +31,7 @@ struct OzPlan {
   int m, nb, nblk, KB, nmax;
   bool conj;
   CUtensorMap tmA;
+  CUtensorMap tmB;   // the X planes of a step that updates all nmax columns
 };
 // gen: a generalized problem (U - lambda_j V), whose panels are [U | V].
 size_t ozaki_plan_bytes(int m, int n, int nb, bool gen = false);
@@ -47,4 +48,16 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
                          cudaStream_t st, bool planes_ready = false, const double2 *lam = nullptr,
                          long long lam_stride = 0);
+// One problem's substitution step inside a batched launch (see ozaki_update;
+// the X planes of this block were written by the diagonal-block step).
+struct OzBatchStep {
+  const OzPlan *plan;
+  int b, lo, hi;
+  double2 *B; long long ldb;
+  int jstart, ncols;
+  const int *pend;
+};
+// The steps of `count` (<= 64) problems as one launch of the chunked kernel,
+// problem i in grid slice z = i.
+cudaError_t ozaki_update_batched(const OzBatchStep *steps, int count, uint32_t *status, cudaStream_t st);
 }  // namespace msts

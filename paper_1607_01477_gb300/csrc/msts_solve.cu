@@ -573,6 +573,8 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
   for (int p = 0; p < count; ++p) maxblk = std::max(maxblk, (probs[p].m + NB - 1) / NB);
   const bool tracing = trace_on();
   const bool gen = count > 0 && probs[0].V != nullptr;   // a table is all generalized or none
+  bool any_oz = false;                                   // batched: tensor-core plans, one per problem
+  for (int p = 0; p < count; ++p) any_oz = any_oz || probs[p].oz != nullptr;
   for (int s = 0; s < maxblk; ++s) {
     int dx = 0, rows_max = 0, cols_max = 0;
     long long tiles_big = 0, tiles_mid = 0, total_cols = 0;
@@ -619,6 +621,25 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
                                          probs[0].n - jstart, SAFE ? tab.p[0].pend : nullptr, status,
                                          gflops, st, tab.p[0].oz_bp != nullptr, gen ? probs[0].shifts : nullptr,
                                          probs[0].shift_stride);
+      if (e != cudaSuccess) return e;
+    } else if (rows_max > 0 && count > 1 && any_oz) {
+      // Batched substitution step on the tensor cores: every problem's panel
+      // in one launch (grid slice z = problem).
+      OzBatchStep bs[kMaxProbs];
+      for (int p = 0; p < count; ++p) {
+        const int m = probs[p].m, n = probs[p].n, nblk = (m + NB - 1) / NB;
+        bs[p] = OzBatchStep{};
+        if (s >= nblk || n == 0 || !probs[p].oz) continue;
+        const int b = CONJ ? nblk - 1 - s : s;
+        const int hi = m - b * NB, lo = std::max(0, hi - NB);
+        const int jstart = shortcut ? lo + 1 : 0;
+        bs[p].plan = probs[p].oz;
+        bs[p].b = b; bs[p].lo = lo; bs[p].hi = hi;
+        bs[p].B = probs[p].B; bs[p].ldb = probs[p].ldb;
+        bs[p].jstart = jstart; bs[p].ncols = n - jstart;
+        bs[p].pend = SAFE ? tab.p[p].pend : nullptr;
+      }
+      const cudaError_t e = ozaki_update_batched(bs, count, status, st);
       if (e != cudaSuccess) return e;
     } else if (rows_max > 0) {
       // FP64 throughput per SM is low, so the tile is chosen to give the grid
@@ -683,10 +704,13 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
       maxn = std::max(maxn, q.n);
     }
     if (maxm == 0 || maxn == 0) continue;
-    if (cnt == 1 && probs[base].oz && !probs[base].V) {   // the diagonal step writes the X digit planes
-      tab.p[0].oz_bp = reinterpret_cast<uint32_t *>(probs[base].oz->bp);
-      tab.p[0].oz_cexp = probs[base].oz->cexp;
-      tab.p[0].oz_kb = probs[base].oz->KB;
+    for (int i = 0; i < cnt; ++i) {           // the diagonal step writes the X digit planes
+      const EngineProblem &q = probs[base + i];
+      if (q.oz && !q.V) {
+        tab.p[i].oz_bp = reinterpret_cast<uint32_t *>(q.oz->bp);
+        tab.p[i].oz_cexp = q.oz->cexp;
+        tab.p[i].oz_kb = q.oz->KB;
+      }
     }
     const int sc = shortcut ? 1 : 0;
     if (safe) {

@@ -27,11 +27,12 @@ def test_adjoint_matches_oracle(m, n, nb):
     assert (np.tril(to_np(dU), -1) == 0).all()
 
 
-def test_adjoint_batched_uneven():
+@pytest.mark.parametrize("tensor", [False, True])
+def test_adjoint_batched_uneven(tensor):
     probs = W.batch_problem(batch=5, m_lo=30, m_hi=120, n=7, seed=3)
     g = W.rng(0, 1)
     items = [(U, s, B, W.cn(g, B.shape)) for U, s, B in probs]
-    outs, st = msts.msts_adjoint_batched([tuple(to_dev(a) for a in it) for it in items], nb=32)
+    outs, st = msts.msts_adjoint_batched([tuple(to_dev(a) for a in it) for it in items], nb=32, tensor=tensor)
     for (U, s, B, G), (dU, dB, ds) in zip(items, outs):
         rU, rB, rs = oracle.adjoint(U, s, B, G)
         assert rel(to_np(dU), rU) <= 1e-9 and rel(to_np(dB), rB) <= 1e-9 and rel(to_np(ds), rs) <= 1e-9

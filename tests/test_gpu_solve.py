@@ -138,19 +138,53 @@ def test_nonfinite_input_flagged():
     assert int(st.item()) & 2
 
 
-def test_batched_uneven_sizes_match_single_solves():
+@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("nb", [16, 32, 64])
+def test_batched_uneven_sizes_match_single_solves(tensor, nb):
     probs = W.batch_problem(batch=7, m_lo=20, m_hi=150, n=9, seed=77)
     for safe in (False, True):
         dev_probs = [(to_dev(U), to_dev(s), to_dev(B)) for U, s, B in probs]
-        outs, st = msts.msts_solve_batched(dev_probs, safe=safe, nb=32)
+        outs, st = msts.msts_solve_batched(dev_probs, safe=safe, nb=nb, tensor=tensor)
         for (U, s, B), (_, _, Xd), o in zip(probs, dev_probs, outs):
             if safe:
-                Xo, eo = oracle.safe_solve(U, s, B, 32)
+                Xo, eo = oracle.safe_solve(U, s, B, nb)
                 assert np.array_equal(to_np(o[1]), eo)
             else:
                 Xo = oracle.solve(U, s, B)
             err, tol = forward_close(to_np(Xd), Xo, cond_inf(U, s), U.shape[0])
             assert (err <= tol).all()
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+def test_batched_conj_trans_matches_oracle(tensor):
+    probs = W.batch_problem(batch=5, m_lo=30, m_hi=200, n=6, seed=78)
+    dev_probs = [(to_dev(U), to_dev(s), to_dev(B)) for U, s, B in probs]
+    msts.msts_solve_batched(dev_probs, conj_trans=True, nb=32, tensor=tensor)
+    for (U, s, B), (_, _, Xd) in zip(probs, dev_probs):
+        Xo = oracle.solve(U, s, B, conj_trans=True)
+        err, tol = forward_close(to_np(Xd), Xo, cond_inf(U, s), U.shape[0])
+        assert (err <= tol).all()
+
+
+def test_batched_full_workload_both_paths_backward_stable():
+    """Workload 5 (64 problems, m in 256..2048, 32 shifts): the batched solve on
+    the tensor cores and the batched FP64 solve both with backward error <= 8 m
+    eps on every column, and two problems against the oracle."""
+    probs = W.batch_problem()
+    d64 = [(to_dev(U), to_dev(s), to_dev(B)) for U, s, B in probs]
+    dtc = [(U_, s_, to_dev(B)) for (U_, s_, _), (_, _, B) in zip(d64, probs)]
+    msts.msts_solve_batched(d64, nb=32)
+    msts.msts_solve_batched(dtc, nb=32, tensor=True)
+    for (_, _, X64), (_, _, Xtc), (U, s, B) in zip(d64, dtc, probs):
+        x64, xtc = to_np(X64), to_np(Xtc)
+        m = U.shape[0]
+        assert backward_error(U, s, xtc, B).max() <= 8 * m * EPS
+        assert backward_error(U, s, x64, B).max() <= 8 * m * EPS
+    for i in (0, 17):
+        U, s, B = probs[i]
+        Xo = oracle.solve(U, s, B)
+        err, tol = forward_close(to_np(dtc[i][2]), Xo, cond_inf(U, s), U.shape[0])
+        assert (err <= tol).all()
 
 
 def test_graph_capture_replays_the_solve():
