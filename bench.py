@@ -687,6 +687,23 @@ def batched_fwd_bwd(dev, nb):
         torch.cuda.synchronize()
         fms, bms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
         out[tag] = {"forward_ms": fms, "backward_ms": bms, "tflops": 4 * fwd_fl / ((fms + bms) * 1e-3) / 1e12}
+    # the tensor-core forward step captured once in a CUDA graph and replayed
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        forward()
+        with torch.cuda.graph(graph, stream=side):
+            forward()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    Xeager = [X.clone() for X in Xs]
+    graph.replay()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(); graph.replay(); e[1].record()
+    torch.cuda.synchronize()
+    out["tensor_gemm"]["forward_cuda_graph_ms"] = e[0].elapsed_time(e[1])
+    out["tensor_gemm"]["graph_matches_eager"] = all(bool(torch.equal(a, b)) for a, b in zip(Xs, Xeager))
     return out
 
 
