@@ -352,9 +352,10 @@ int msts_adjoint_batched(const msts_adjoint_problem *probs, int64_t batch, int32
                          void *workspace, size_t workspace_bytes,
                          uint32_t *status, void *stream);
 /* The same with flags: MSTS_TENSOR_GEMM runs the substitution steps of both
- * internal solves (X recomputed, and Lambda) on the tensor cores, all problems
- * of a block step in one launch; workspace from the _flags size query (it adds
- * the digit planes of U and U^H per problem).  Returns -8 for unknown flags. */
+ * internal solves (X recomputed, and Lambda) and the product dU = -triu(Lambda
+ * X^H) on the tensor cores (FP64-accurate digit planes), all problems of a step
+ * in one launch; workspace from the _flags size query (it adds the digit planes
+ * of U, U^H, Lambda and X^H per problem).  Returns -8 for unknown flags. */
 size_t msts_adjoint_batched_flags_workspace_size(const msts_adjoint_problem *probs, int64_t batch,
                                                  int32_t nb, uint32_t flags);
 int msts_adjoint_batched_flags(const msts_adjoint_problem *probs, int64_t batch, int32_t nb,

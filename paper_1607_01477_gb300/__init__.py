@@ -555,7 +555,8 @@ def msts_adjoint(U, shifts, B, GX, *, nb=32, status=None):
 
 def msts_adjoint_batched(problems, *, nb=32, tensor=False, status=None):
     """problems: list of (U, shifts, B, GX).  Returns (list of (dU, dB, ds), status).
-    tensor=True runs the substitution steps of both internal solves on the tensor cores."""
+    tensor=True runs the substitution steps of both internal solves and the product
+    dU = -triu(Lambda X^H) on the tensor cores."""
     lib = load_library()
     arr = (_AdjProblem * len(problems))()
     outs = []

@@ -122,6 +122,7 @@ size_t adjoint_workspace_bytes(const msts_adjoint_problem *probs, int64_t batch,
   for (int64_t i = 0; i < batch; ++i) {
     s += a256(sizeof(double2) * (size_t)probs[i].m * probs[i].n);
     if (tensor && probs[i].m > 0 && probs[i].n > 0) s += 2 * a256(ozaki_plan_bytes((int)probs[i].m, (int)probs[i].n, nb));
+    if (tensor && probs[i].m > 0) s += a256(ozaki_neg_triu_bytes((int)probs[i].m, (int)probs[i].n));
   }
   return s;
 }
@@ -180,8 +181,21 @@ cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb
       k_ds<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(at);
       count_launches(2);
     }
-    k_triu_gemm<<<dim3((maxm + kTBN - 1) / kTBN, (maxm + kTBM - 1) / kTBM, cnt), kTThreads, 0, st>>>(at);
-    count_launches(1);
+    if (tensor) {                              // dU = -triu(Lambda X^H) on the tensor cores
+      OzNegTriuItem it[kMaxProbs];
+      size_t bytes = 0;
+      for (int i = 0; i < cnt; ++i) {
+        const AdjProb &P = at.p[i];
+        it[i] = OzNegTriuItem{P.L, P.ldl, P.X, P.ldx, P.dU, P.lddu, P.m, P.n};
+        if (P.m > 0) bytes += a256(ozaki_neg_triu_bytes(P.m, P.n));
+      }
+      const cudaError_t e = ozaki_neg_triu_batched(it, cnt, cur, status, st);
+      if (e != cudaSuccess) return e;
+      cur += bytes;
+    } else {
+      k_triu_gemm<<<dim3((maxm + kTBN - 1) / kTBN, (maxm + kTBM - 1) / kTBM, cnt), kTThreads, 0, st>>>(at);
+      count_launches(1);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

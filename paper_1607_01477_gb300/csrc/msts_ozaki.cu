@@ -85,13 +85,14 @@ static OzakiBufs carve(void *ws, int m, int n) {
   return o;
 }
 
-// e_r for every row of triu(U) (or of the whole matrix with full): one warp per row.
-__global__ void k_oz_rowexp(const double2 *U, long long ldu, int m, int *rexp, int full) {
+// e_r for every row of triu(U) (or of the whole m x kc matrix with full): one
+// warp per row.
+__global__ void k_oz_rowexp(const double2 *U, long long ldu, int m, int kc, int *rexp, int full) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= m) return;
   int e = -(1 << 29);
-  for (int k = (full ? 0 : r) + lane; k < m; k += 32) e = max(e, bound_exp(U[r + (long long)k * ldu]));
+  for (int k = (full ? 0 : r) + lane; k < kc; k += 32) e = max(e, bound_exp(U[r + (long long)k * ldu]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if (lane == 0) rexp[r] = e < -(1 << 28) ? 0 : e;
@@ -100,13 +101,13 @@ __global__ void k_oz_rowexp(const double2 *U, long long ldu, int m, int *rexp, i
 // Digit planes of A': plane s, row i, column k' at Ap[(s * 2m + i) * K + k'].
 // Thread (k, r) writes rows 2r, 2r+1 at columns 2k, 2k+1 of every plane
 // (zero outside the upper triangle unless full, and in the padding).
-__global__ void k_oz_slice_A(const double2 *U, long long ldu, int m, const int *rexp,
+__global__ void k_oz_slice_A(const double2 *U, long long ldu, int m, int kc, const int *rexp,
                              __nv_bfloat16 *Ap, int K, int full) {
   const int r = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * k >= K) return;
   float dr[kOzS], di[kOzS];
-  if ((full || k >= r) && k < m) {
+  if ((full || k >= r) && k < kc) {
     const double2 u = U[r + (long long)k * ldu];
     digits8(u.x, rexp[r], dr);
     digits8(u.y, rexp[r], di);
@@ -187,7 +188,39 @@ struct OzArgs {
   uint32_t *status;
 };
 
-enum { kResidual = 0, kUpdate = 1, kProduct = 2 };
+// Digit planes of B' = X^H (as real): column c of B' is conj(X(c, 0:kc)), at
+// Bp[(t * mc + c) * K + k'], exponent f_c over that row of X; one CTA per column.
+__global__ void k_oz_slice_BH(const double2 *X, long long ldx, int mc, int kc, int *cexp, __nv_bfloat16 *Bp,
+                              int K) {
+  __shared__ int red[32];
+  const int c = blockIdx.x;
+  int e = -(1 << 29);
+  for (int k = threadIdx.x; k < kc; k += blockDim.x) e = max(e, bound_exp(X[c + (long long)k * ldx]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  e = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, red[w]);
+  if (e < -(1 << 28)) e = 0;
+  if (threadIdx.x == 0) cexp[c] = e;
+  for (int k = threadIdx.x; 2 * k < K; k += blockDim.x) {
+    float dr[kOzS], di[kOzS];
+    if (k < kc) {
+      const double2 x = X[c + (long long)k * ldx];
+      digits8(x.x, e, dr);
+      digits8(-x.y, e, di);
+    } else {
+#pragma unroll
+      for (int t = 0; t < kOzS; ++t) dr[t] = di[t] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < kOzS; ++t)
+      *reinterpret_cast<__nv_bfloat162 *>(Bp + ((size_t)t * mc + c) * K + 2 * k) = __floats2bfloat162_rn(dr[t], di[t]);
+  }
+}
+
+enum { kResidual = 0, kUpdate = 1, kProduct = 2, kNegTriu = 3 };
 
 // One output tile (bx, by) of the product; pA, pB and args point into the
 // kernel's parameter space (a plain launch, or one problem of a batch).
@@ -336,6 +369,8 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap *pA, const CUtens
         const double p = scalbn(fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-63), er + args.cexp[lc]);
         if (MODE == kProduct) {
           reinterpret_cast<double *>(args.R + r + (long long)lc * args.ldr)[part] = p;
+        } else if (MODE == kNegTriu) {             // -triu(P): zero below the diagonal
+          reinterpret_cast<double *>(args.R + r + (long long)lc * args.ldr)[part] = r <= lc ? -p : 0.0;
         } else if (MODE == kResidual) {
           const double2 x = args.X[r + (long long)lc * args.ldx];
           const double2 sj = args.s[lc];
@@ -376,10 +411,22 @@ struct OzBatch {
   int tiles_n[kMaxProbs], tiles_m[kMaxProbs];
 };
 
-__global__ void __launch_bounds__(kOzThreads, 1) k_oz_update_batched(const __grid_constant__ OzBatch b) {
+template <int MODE>
+__global__ void __launch_bounds__(kOzThreads, 1) k_oz_batched(const __grid_constant__ OzBatch b) {
   const int z = blockIdx.z;
   if ((int)blockIdx.x >= b.tiles_n[z] || (int)blockIdx.y >= b.tiles_m[z]) return;
-  oz_gemm_tile<kUpdate>(&b.tmA[z], &b.tmB[z], b.args[z], blockIdx.x, blockIdx.y);
+  if (MODE == kNegTriu) {                 // a tile wholly below the diagonal is zero: no product
+    const OzArgs &a = b.args[z];
+    const int r0 = blockIdx.y * (kOzBM / 2), c0 = blockIdx.x * kOzBN;
+    if (r0 > c0 + kOzBN - 1) {
+      for (int idx = threadIdx.x; idx < (kOzBM / 2) * kOzBN; idx += blockDim.x) {
+        const int r = r0 + idx % (kOzBM / 2), c = c0 + idx / (kOzBM / 2);
+        if (r < a.m && c < a.n) a.R[r + (long long)c * a.ldr] = make_double2(0.0, 0.0);
+      }
+      return;
+    }
+  }
+  oz_gemm_tile<MODE>(&b.tmA[z], &b.tmB[z], b.args[z], blockIdx.x, blockIdx.y);
 }
 
 // ----- host side -------------------------------------------------------------
@@ -428,8 +475,8 @@ static bool make_map(CUtensorMap *map, void *ptr, int K, int rows, int box_rows,
 
 cudaError_t ozaki_prepare(const double2 *U, long long ldu, int m, int n, void *ws, cudaStream_t st) {
   OzakiBufs o = carve(ws, m, n);
-  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(U, ldu, m, o.rexp, 0);
-  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(U, ldu, m, o.rexp, o.Ap, o.K, 0);
+  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(U, ldu, m, m, o.rexp, 0);
+  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(U, ldu, m, m, o.rexp, o.Ap, o.K, 0);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -472,8 +519,8 @@ cudaError_t ozaki_product(const double2 *A, long long lda, int m, const double2 
                           bool triu_b, double2 *C, long long ldc, void *ws, uint32_t *status, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
   OzakiBufs o = carve(ws, m, n);
-  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(A, lda, m, o.rexp, 1);
-  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(A, lda, m, o.rexp, o.Ap, o.K, 1);
+  k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(A, lda, m, m, o.rexp, 1);
+  k_oz_slice_A<<<dim3((o.K / 2 + 255) / 256, m), 256, 0, st>>>(A, lda, m, m, o.rexp, o.Ap, o.K, 1);
   k_oz_slice_B<<<n, 256, 0, st>>>(Bm, ldbm, m, n, o.cexp, o.Bp, o.K, triu_b ? 1 : 0);
   count_launches(3);
   CUtensorMap tmA, tmB;
@@ -1024,14 +1071,68 @@ cudaError_t ozaki_update_batched(const OzBatchStep *steps, int count, uint32_t *
     chunk_tiles += (double)hb->tiles_n[i] * hb->tiles_m[i] * (plan.KB / kOzKC);
   }
   if (max_tn == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_oz_update_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_oz_batched<kUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
   const double mma_flops = chunk_tiles * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
   void *h = trace_on() ? trace_start(2, mma_flops, chunk_tiles * (kOzS * kOzABytes + kOzBBytes), st) : nullptr;
-  k_oz_update_batched<<<dim3(max_tn, max_tm, count), kOzThreads, kOzSmem, st>>>(*hb);
+  k_oz_batched<kUpdate><<<dim3(max_tn, max_tm, count), kOzThreads, kOzSmem, st>>>(*hb);
   trace_stop(h, st);
   count_launches(1);
   (void)tiles;
+  return cudaGetLastError();
+}
+
+// dU = -triu(L X^H) for a batch (the adjoint's product, K = n): per problem
+// the digit planes of L (rows) and of X^H (columns of B' = conjugated rows of
+// X) in its own workspace slice, then every problem's tiles in one launch.
+size_t ozaki_neg_triu_bytes(int m, int n) {
+  const size_t K = (size_t)kpad(n);
+  return a256((size_t)kOzS * 2 * m * K * 2) + a256((size_t)kOzS * m * K * 2) + a256(4 * (size_t)m) * 2;
+}
+
+cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *ws, uint32_t *status,
+                                   cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (count > kMaxProbs) return cudaErrorInvalidValue;
+  std::unique_ptr<OzBatch> hb(new OzBatch());
+  char *cur = static_cast<char *>(ws);
+  int max_tn = 0, max_tm = 0;
+  double chunk_tiles = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const OzNegTriuItem &q = items[i];
+    hb->tiles_n[i] = hb->tiles_m[i] = 0;
+    if (q.m <= 0) continue;
+    const int m = q.m, n = q.n, K = kpad(n > 0 ? n : 1);
+    __nv_bfloat16 *Ap = reinterpret_cast<__nv_bfloat16 *>(cur); cur += a256((size_t)kOzS * 2 * m * K * 2);
+    __nv_bfloat16 *Bp = reinterpret_cast<__nv_bfloat16 *>(cur); cur += a256((size_t)kOzS * m * K * 2);
+    int *rexp = reinterpret_cast<int *>(cur); cur += a256(4 * (size_t)m);
+    int *cexp = reinterpret_cast<int *>(cur); cur += a256(4 * (size_t)m);
+    k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(q.L, q.ldl, m, n, rexp, 1);
+    k_oz_slice_A<<<dim3((K / 2 + 255) / 256, m), 256, 0, st>>>(q.L, q.ldl, m, n, rexp, Ap, K, 1);
+    k_oz_slice_BH<<<m, 256, 0, st>>>(q.X, q.ldx, m, n, cexp, Bp, K);
+    count_launches(3);
+    if (!make_map(&hb->tmA[i], Ap, K, 2 * m, kOzBM, 1) || !make_map(&hb->tmB[i], Bp, K, m, kOzBN, kOzS))
+      return cudaErrorNotSupported;
+    OzArgs a{};
+    a.R = q.dU; a.ldr = q.lddu;
+    a.rexp = rexp; a.cexp = cexp;
+    a.m = m; a.n = m; a.K = K;
+    a.status = status ? status : abort_word();
+    hb->args[i] = a;
+    hb->tiles_n[i] = (m + kOzBN - 1) / kOzBN;
+    hb->tiles_m[i] = (2 * m + kOzBM - 1) / kOzBM;
+    max_tn = std::max(max_tn, hb->tiles_n[i]);
+    max_tm = std::max(max_tm, hb->tiles_m[i]);
+    chunk_tiles += 0.5 * hb->tiles_n[i] * hb->tiles_m[i] * (K / kOzKC);
+  }
+  if (max_tn == 0) return cudaGetLastError();
+  cudaError_t e = cudaFuncSetAttribute(k_oz_batched<kNegTriu>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  if (e != cudaSuccess) return e;
+  const double mma_flops = chunk_tiles * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+  void *h = trace_on() ? trace_start(2, mma_flops, chunk_tiles * (kOzS * kOzABytes + kOzBBytes), st) : nullptr;
+  k_oz_batched<kNegTriu><<<dim3(max_tn, max_tm, count), kOzThreads, kOzSmem, st>>>(*hb);
+  trace_stop(h, st);
+  count_launches(1);
   return cudaGetLastError();
 }
 

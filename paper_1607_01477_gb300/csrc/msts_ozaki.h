@@ -60,4 +60,16 @@ struct OzBatchStep {
 // The steps of `count` (<= 64) problems as one launch of the chunked kernel,
 // problem i in grid slice z = i.
 cudaError_t ozaki_update_batched(const OzBatchStep *steps, int count, uint32_t *status, cudaStream_t st);
+// dU = -triu(L X^H) (L, X m x n, dU m x m, strictly lower part set to zero) for
+// `count` (<= 64) problems, FP64-accurate on the tensor cores; the workspace
+// holds sum over problems of ozaki_neg_triu_bytes(m, n).
+struct OzNegTriuItem {
+  const double2 *L; long long ldl;
+  const double2 *X; long long ldx;
+  double2 *dU; long long lddu;
+  int m, n;
+};
+size_t ozaki_neg_triu_bytes(int m, int n);
+cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *ws, uint32_t *status,
+                                   cudaStream_t st);
 }  // namespace msts
