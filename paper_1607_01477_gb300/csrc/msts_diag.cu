@@ -533,9 +533,50 @@ static cudaError_t launch_nb(int L, const ProbTable &tab, int step, int shortcut
   }
 }
 
-// Lanes per shift: the smallest of 4, 8, min(NB, 32) that yields at least
-// 4 warps per SM (one per sub-partition) over the 152 SMs.
-int diag_lanes(int nb, long long total_cols) {
+// Lanes per shift.  A launch is bound by the dependent chain of its warps
+// rather than by FP64 throughput: its time is set by the lane width L and by
+// k, the number of 128-thread CTAs on the busiest SM, and hardly by how many
+// SMs are busy.  For n_b = 32 the width is the one with the smallest time in
+// tables measured on GB300 (one launch per solve, m = n_b = 32, 304..12160
+// shifts; k = 1..4, then a constant slope per further CTA, microseconds).
+// Every width gives the same results bit for bit.  Other block sizes take the
+// smallest width with at least 4 warps per SM.
+namespace {
+struct LaneCost {
+  float t[4];
+  float slope;
+};
+constexpr LaneCost kPlainCost[4] = {        // L = 4, 8, 16, 32 (plain and conjugate-transposed)
+    {{42.8f, 61.5f, 88.7f, 115.9f}, 27.2f},
+    {{32.4f, 43.2f, 58.6f, 75.0f}, 16.3f},
+    {{26.4f, 35.6f, 43.4f, 54.7f}, 11.6f},
+    {{23.7f, 30.3f, 39.5f, 45.1f}, 9.0f}};
+constexpr LaneCost kSafeCost[4] = {         // the safe solve (Alg. 4 replay, Alg. 5 update)
+    {{60.2f, 82.0f, 115.6f, 149.2f}, 33.6f},
+    {{42.0f, 54.6f, 75.5f, 99.1f}, 24.1f},
+    {{31.7f, 40.7f, 54.6f, 69.4f}, 15.7f},
+    {{27.6f, 33.9f, 44.5f, 56.0f}, 12.7f}};
+double lane_cost(const LaneCost &c, long long k) {
+  return k <= 4 ? c.t[k - 1] : c.t[3] + (double)(k - 4) * c.slope;
+}
+}  // namespace
+
+int diag_lanes(int nb, long long total_cols, bool safe) {
+  if (nb == 32) {
+    const LaneCost *tab = safe ? kSafeCost : kPlainCost;
+    int best = 32;
+    double tbest = 0.0;
+    for (int i = 0, L = 4; L <= 32; ++i, L *= 2) {
+      const long long ctas = (total_cols * L + kDiagThreads - 1) / kDiagThreads;
+      const long long k = std::max(1LL, (ctas + 151) / 152);
+      const double t = lane_cost(tab[i], k);
+      if (i == 0 || t < tbest) {
+        tbest = t;
+        best = L;
+      }
+    }
+    return best;
+  }
   const int lmax = nb < 32 ? nb : 32;
   for (int L = nb >= 64 ? 16 : 4; L < lmax; L *= 2)
     if (total_cols * L >= 32LL * 4 * 152) return L;
@@ -544,7 +585,7 @@ int diag_lanes(int nb, long long total_cols) {
 
 cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int step, int shortcut,
                         int ncols_max, long long total_cols, uint32_t *status, cudaStream_t st, bool gen) {
-  const int L = diag_lanes(nb, total_cols);
+  const int L = diag_lanes(nb, total_cols, safe);
 #define MSTS_DIAG_CASE(NBV)                                                                          \
   case NBV:                                                                                          \
     if (gen && safe) return launch_nb<NBV, true, false, true>(L, tab, step, shortcut, ncols_max, status, st); \

@@ -6,7 +6,7 @@
 
 namespace msts {
 // Lanes per shift for a launch over `total_cols` shifts (all problems).
-int diag_lanes(int nb, long long total_cols);
+int diag_lanes(int nb, long long total_cols, bool safe);
 // Launches the diagonal-block step of block step `step` for every problem of
 // `tab`; ncols_max is the largest number of active shifts of one problem.
 // gen: generalized problems (every problem of the table has V).
