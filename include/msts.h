@@ -20,9 +20,13 @@
  *  - `workspace` is caller-owned device scratch of at least the size returned
  *    by the matching *_workspace_size function, aligned to 256 bytes.  It must
  *    not be used by anything else until the work queued on `stream` finishes.
+ *  - Complex arrays must be 16-byte aligned (the kernels move complex values
+ *    as 16-byte vectors; cudaMalloc, torch and numpy allocations are) and the
+ *    workspace 256-byte aligned.
  *  - Return value: 0 on success; a negative value -k means argument k (1-based)
- *    is invalid and nothing was launched; MSTS_ERR_CUDA means a CUDA launch
- *    failed (cudaGetLastError() tells why).
+ *    is invalid and nothing was launched; MSTS_ERR_ALIGN means a complex array
+ *    or the workspace is not aligned as above (nothing was launched);
+ *    MSTS_ERR_CUDA means a CUDA launch failed (cudaGetLastError() tells why).
  *  - `status` (device, may be NULL) receives, asynchronously, the OR of the
  *    MSTS_STATUS_* bits below raised by the kernels.  The library only ORs
  *    bits into it: clear it before the call.
@@ -74,6 +78,7 @@ typedef struct { double re, im; } msts_z;
                                        results of that call are invalid                     */
 
 #define MSTS_ERR_CUDA (-1000)
+#define MSTS_ERR_ALIGN (-1002)
 
 /* Library version as 10000*major + 100*minor + patch. */
 int msts_version(void);
@@ -455,7 +460,7 @@ int msts_trace_query(int32_t kernel, double *total_ms, int64_t *launches, double
  *    whose work overlaps on the GPU (different streams, or concurrent host
  *    threads without ordering) race on it.  Order such calls on one stream.
  * Returns 0, -k for invalid argument k (numbering as msts_solve without the
- * workspace arguments), MSTS_ERR_STATIC_SCRATCH or MSTS_ERR_CUDA.
+ * workspace arguments), MSTS_ERR_STATIC_SCRATCH, MSTS_ERR_ALIGN or MSTS_ERR_CUDA.
  * ------------------------------------------------------------------------- */
 #define MSTS_ERR_STATIC_SCRATCH (-1001)
 int msts_safe_solve_static(const msts_z *U, int64_t ldu, int64_t m,

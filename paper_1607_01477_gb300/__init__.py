@@ -205,6 +205,8 @@ def _check(rc: int, fn: str):
     if rc != 0:
         if rc == -1000:
             raise RuntimeError(f"{fn}: CUDA launch failed")
+        if rc == -1002:
+            raise ValueError(f"{fn}: a complex array is not 16-byte aligned or the workspace not 256-byte aligned")
         raise ValueError(f"{fn}: invalid argument {-rc}")
 
 

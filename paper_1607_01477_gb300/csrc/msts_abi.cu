@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "../../include/msts.h"
+#include "msts_check.h"
 #include "msts_engine.h"
 #include "msts_ozaki.h"
 
@@ -67,6 +68,7 @@ int msts_solve(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shifts, in
   if ((flags & ~(MSTS_SAFE | MSTS_CONJ_TRANS | MSTS_TENSOR_GEMM)) != 0 || (safe && conj)) return -14;
   const size_t need = msts_solve_workspace_size(m, n, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -12 : -11;
+  if (msts::bad_alignment({U, shifts, B}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || n == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   msts::EngineProblem p = make_problem(U, ldu, m, shifts, 1, n, B, ldb, scales, scale_exp, 0);
@@ -116,11 +118,13 @@ int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb, voi
     if (q.ldu < std::max<int64_t>(1, q.m) || q.ldb < std::max<int64_t>(1, q.m)) return -1;
     if ((q.m > 0 && !q.U) || (q.n > 0 && !q.shifts) || (q.m > 0 && q.n > 0 && !q.B)) return -1;
     if (safe && q.n > 0 && (!q.scales || !q.scale_exp)) return -1;
+    if (msts::bad_alignment({q.U, q.shifts, q.B}, nullptr)) return MSTS_ERR_ALIGN;
     v.push_back(make_problem(q.U, q.ldu, q.m, q.shifts, 1, q.n, q.B, q.ldb, q.scales,
                              q.scale_exp, 0));
   }
   const size_t need = msts_solve_batched_workspace_size(probs, batch, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -5 : -4;
+  if (msts::bad_alignment({}, workspace)) return MSTS_ERR_ALIGN;
   if (batch == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<msts::OzPlan> plans;
@@ -158,6 +162,7 @@ int msts_trevc(const msts_z *T, int64_t ldt, int64_t m, msts_z *Z, int64_t ldz, 
   if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -12;
   const size_t need = msts_trevc_workspace_size(m, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -10 : -9;
+  if (msts::bad_alignment({T, Z}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = msts::engine_trevc_setup(reinterpret_cast<const double2 *>(T), ldt, (int)m,
@@ -204,6 +209,7 @@ int msts_gsolve(const msts_z *U, int64_t ldu, const msts_z *V, int64_t ldv, int6
   if ((flags & ~(uint32_t)(MSTS_SAFE | MSTS_TENSOR_GEMM)) != 0) return -16;
   const size_t need = msts_gsolve_workspace_size(m, n, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -14 : -13;
+  if (msts::bad_alignment({U, V, shifts, B}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || n == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   msts::EngineProblem p = make_problem(U, ldu, m, shifts, 1, n, B, ldb, scales, scale_exp, 0);
@@ -242,6 +248,7 @@ int msts_gtrevc(const msts_z *T, int64_t ldt, const msts_z *S, int64_t lds, int6
   if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -15;
   const size_t need = msts_gtrevc_workspace_size(m, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -13 : -12;
+  if (msts::bad_alignment({T, S, Z, lambda}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   double2 *lam = reinterpret_cast<double2 *>(lambda);

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "msts_check.h"
 #include "msts_common.cuh"
 #include "msts_engine.h"
 #include "msts_ozaki.h"
@@ -239,10 +240,12 @@ int msts_adjoint_batched_flags(const msts_adjoint_problem *probs, int64_t batch,
     if (q.m > 0 && (!q.U || !q.dU)) return -1;
     if (q.n > 0 && (!q.shifts || !q.ds)) return -1;
     if (q.m > 0 && q.n > 0 && (!q.B || !q.GX || !q.dB)) return -1;
+    if (msts::bad_alignment({q.U, q.shifts, q.B, q.GX, q.dU, q.dB, q.ds}, nullptr)) return MSTS_ERR_ALIGN;
   }
   const bool tensor = (flags & MSTS_TENSOR_GEMM) != 0;
   const size_t need = msts::adjoint_workspace_bytes(probs, batch, nb, tensor);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -5 : -4;
+  if (msts::bad_alignment({}, workspace)) return MSTS_ERR_ALIGN;
   if (batch == 0) return 0;
   const cudaError_t e = msts::adjoint_run(probs, batch, nb, workspace, status,
                                           static_cast<cudaStream_t>(stream), tensor);

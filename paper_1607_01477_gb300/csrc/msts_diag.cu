@@ -144,6 +144,16 @@ __device__ __forceinline__ double2 zrecip(double2 p) {
   return make_double2(scale(wr), scale(wi));
 }
 
+// 16 bytes from global to shared memory without passing through registers
+// (cp.async); when !full the 16 bytes are zero-filled and nothing is read.
+// Both addresses are 16-byte aligned (complex arrays are).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool full) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(full ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // GEN: the generalized problem (appendix, Alg. 8/9), U' = U(I1,I1) - s_j V(I1,I1):
 // pivots U(i,i) - s_j V(i,i), AXPY entries U(r,i) - s_j V(r,i) (applied as
 // x_i U(r,i) - (s_j x_i) V(r,i)), and in the safe form the column bounds
@@ -172,30 +182,50 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   const int nbf = hi - lo;
   const int jcta = (shortcut ? lo + 1 : 0) + blockIdx.x * SPC;
   if (jcta >= P.n) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = lane & (L - 1);
+  const int j = jcta + warp * SPW + lane / L;
+  const bool active = j < P.n;
+  const int nbe = !active ? 0 : (shortcut ? min(hi, j) - lo : nbf);   // TREVC: rows >= j stay zero
+  double2 *col = P.B + (long long)(active ? j : 0) * P.ldb + lo;
+
+  // Every global load the step needs is issued here, before U(I1,I1) is
+  // staged, so that a warp waits for one round trip to memory instead of
+  // several in sequence: the shift, the right-hand side, delta and (safe) the
+  // column's scale state and the block's bound C_blk.
+  double2 lam = active ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
+  double2 y[RPL], inv[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) y[q] = l + L * q < nbe ? col[l + L * q] : make_double2(0.0, 0.0);
+  const double delta_u = SAFE ? *P.delta : 0.0, delta_v = SAFE && GEN ? *P.deltaV : 0.0;
+  int e_col = 0;
+  double G_col = 0.0;
+  if (SAFE && active) {
+    e_col = P.e[j];
+    G_col = P.G[j];
+  }
+  const double cblk_u = SAFE ? P.cblk[b] : 0.0, cblk_v = SAFE && GEN ? P.cblkV[b] : 0.0;
+
+  // U(I1,I1) (and V) to shared memory by asynchronous copies: no registers
+  // held, every copy in flight at once, zeros below the diagonal and past the
+  // block written by the copies themselves.
   for (int idx = threadIdx.x; idx < NB * NB; idx += kDiagThreads) {
     const int c = idx / NB, r = idx - c * NB;
-    double2 v = make_double2(0.0, 0.0);
-    if (r <= c && c < nbf) v = P.U[(lo + r) + (long long)(lo + c) * P.ldu];
-    sU[c * LD + r] = v;
-    if (GEN) sV[c * LD + r] = (r <= c && c < nbf) ? P.V[(lo + r) + (long long)(lo + c) * P.ldv] : make_double2(0.0, 0.0);
+    const bool in = r <= c && c < nbf;
+    cp_async16(&sU[c * LD + r], in ? &P.U[(lo + r) + (long long)(lo + c) * P.ldu] : P.U, in);
+    if (GEN) cp_async16(&sV[c * LD + r], in ? &P.V[(lo + r) + (long long)(lo + c) * P.ldv] : P.V, in);
   }
   if (SAFE)
     for (int k = threadIdx.x; k < NB; k += kDiagThreads) {
       sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
       if (GEN) sCV[k] = k < nbf ? P.cinV[lo + k] : 0.0;
     }
+  cp_async_wait_all();
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int l = lane & (L - 1);
-  const int j = jcta + warp * SPW + lane / L;
-  const bool active = j < P.n;
-  const int nbe = !active ? 0 : (shortcut ? min(hi, j) - lo : nbf);   // TREVC: rows >= j stay zero
-  double2 lam = active ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
   if (CONJ) lam = zconj(lam);
-  double2 *col = P.B + (long long)(active ? j : 0) * P.ldb + lo;
   const double al = GEN ? zabs_exp(lam) : 0.0;           // |s_j|
-  const double dlt = !SAFE ? 0.0 : !GEN ? *P.delta : fmax(__dadd_rn(*P.delta, __dmul_rn(al, *P.deltaV)), kDblMin);
+  const double dlt = !SAFE ? 0.0 : !GEN ? delta_u : fmax(__dadd_rn(delta_u, __dmul_rn(al, delta_v)), kDblMin);
   // the unperturbed pivot: U(i,i) - lambda (or - lambda V(i,i))
   auto pivot0 = [&](int i) {
     const double2 d = sU[i * LD + i];
@@ -209,14 +239,12 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   // bound on the off-diagonal column norm of row i's column of U'
   auto ccol = [&](int i) { return GEN ? __dadd_rn(sC[i], __dmul_rn(al, sCV[i])) : sC[i]; };
 
-  double2 y[RPL], inv[RPL];
   int pex[RPL];                          // biased exponent field of max(|Re p|, |Im p|)
   bool zero_piv = false;
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     const int r = l + L * q;
     const bool v = r < nbe;
-    y[q] = v ? col[r] : make_double2(0.0, 0.0);
     const double2 p0 = pivot0(r);
     zero_piv |= v && zzero_words(p0);
     const double2 p = pivot(r);
@@ -475,10 +503,10 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   int ej = 0, pend = 0, k2 = 0;
   double Gj = 0.0;
   if (active) {
-    ej = P.e[j];
-    Gj = P.G[j];
+    ej = e_col;
+    Gj = G_col;
     if (kexp > 0) { ej += kexp; Gj = dscale_exp0(Gj, -kexp); pend = kexp; }
-    const double cb = GEN ? __dadd_rn(P.cblk[b], __dmul_rn(al, P.cblkV[b])) : P.cblk[b];
+    const double cb = GEN ? __dadd_rn(cblk_u, __dmul_rn(al, cblk_v)) : cblk_u;
     Gj = __dadd_rn(Gj, __dmul_rn(cb, N));
     if (Gj >= OM) {
       k2 = choose_k_exp(Gj);

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "../../include/msts.h"
+#include "msts_check.h"
 #include "msts_common.cuh"
 #include "msts_ozaki.h"
 #include "msts_eig.h"
@@ -126,6 +127,7 @@ int msts_back_transform(const msts_z *Q, int64_t ldq, int64_t m, const msts_z *Z
   if (flags & ~(uint32_t)(MSTS_TENSOR_GEMM | MSTS_NORMALIZE_COLUMNS)) return -11;
   const size_t need = msts_back_transform_workspace_size(m, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -9 : -8;
+  if (msts::bad_alignment({Q, Z, X}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const double2 *q = reinterpret_cast<const double2 *>(Q);

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "msts_check.h"
 #include "msts_common.cuh"
 #include "msts_engine.h"
 #include "msts_mixed.h"
@@ -264,6 +265,7 @@ int msts_solve_mixed(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shif
   if (max_iter < 0) return -11;
   if (nb != 16 && nb != 32 && nb != 64) return -12;
   if ((flags & ~(uint32_t)MSTS_RESIDUAL_OZAKI) != 0) return -16;
+  if (msts::bad_alignment({U, shifts, B, X}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || n == 0) {
     if (iters) *iters = 0;
     if (eta) *eta = 0.0;
@@ -304,6 +306,7 @@ int msts_residual(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shifts,
   if (ldx < (m > 1 ? m : 1)) return -9;
   if (ldr < (m > 1 ? m : 1)) return -11;
   if ((flags & ~(uint32_t)MSTS_RESIDUAL_OZAKI) != 0) return -15;
+  if (msts::bad_alignment({U, shifts, B, X, R}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || n == 0) return 0;
   const size_t need = msts_residual_workspace_size(m, n, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -13 : -12;

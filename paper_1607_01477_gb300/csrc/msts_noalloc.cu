@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "../../include/msts.h"
+#include "msts_check.h"
 #include "msts_engine.h"
 
 namespace {
@@ -64,6 +65,7 @@ extern "C" int msts_safe_solve_static(const msts_z *U, int64_t ldu, int64_t m,
   if (n > 0 && !scale_exp) return -9;
   if (nb != 16 && nb != 32 && nb != 64) return -10;
   const size_t need = msts_solve_workspace_size(m, n, nb, MSTS_SAFE);
+  if (msts::bad_alignment({U, shifts, B}, nullptr)) return MSTS_ERR_ALIGN;
   if (need > kStaticScratchBytes) return MSTS_ERR_STATIC_SCRATCH;
   if (m == 0 || n == 0) return 0;
   void *scratch = nullptr;

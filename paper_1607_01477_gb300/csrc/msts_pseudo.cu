@@ -14,6 +14,7 @@
 
 #include <algorithm>
 
+#include "msts_check.h"
 #include "msts_common.cuh"
 #include "msts_engine.h"
 #include "msts_ozaki.h"
@@ -413,6 +414,7 @@ int msts_pseudospectra(const msts_z *T, int64_t ldt, int64_t m, const msts_z *z,
   if (N > 0 && !sigma_min) return -9;
   if (nb != 16 && nb != 32 && nb != 64) return -13;
   if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -17;
+  if (msts::bad_alignment({T, z, V0}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || N == 0) return 0;
   const size_t need = msts_pseudospectra_workspace_size(m, N, iters, nb, flags);
   if (!workspace || workspace_bytes < need) return workspace ? -15 : -14;

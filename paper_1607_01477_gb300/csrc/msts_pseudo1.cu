@@ -28,6 +28,7 @@
 #include <algorithm>
 
 #include "../../include/msts.h"
+#include "msts_check.h"
 #include "msts_eig.h"
 #include "msts_ozaki.h"
 #include "msts_remap.h"
@@ -296,6 +297,7 @@ int msts_pseudospectra_1norm(const msts_z *T, int64_t ldt, int64_t m, const msts
   if ((flags & ~(uint32_t)MSTS_TENSOR_GEMM) != 0) return -11;
   const size_t need = msts_pseudospectra_1norm_workspace_size(m, N, nb, Q != nullptr, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -10 : -9;
+  if (msts::bad_alignment({T, Q, z}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || N == 0) return 0;
   using namespace msts;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -400,6 +402,7 @@ int msts_portrait_grid(const msts_z *T, int64_t ldt, int64_t m, int64_t nx, int6
   if (nx < 1 || ny < 1 || nx > msts::kMaxDim || ny > msts::kMaxDim || nx * ny > ((int64_t)1 << 40)) return -4;
   if (!z) return -5;
   if (!box) return -6;
+  if (msts::bad_alignment({T, z}, nullptr)) return MSTS_ERR_ALIGN;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   msts::k_grid_box<<<1, 256, 0, st>>>(reinterpret_cast<const double2 *>(T), ldt, (int)m, box);
   const long long n = nx * ny;

@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "../../include/msts.h"
+#include "msts_check.h"
 #include "msts_remap.h"
 #include "msts_trace.h"
 
@@ -196,6 +197,7 @@ int msts_solve_variant(int32_t side, int32_t uplo, int32_t trans, const msts_z *
   if ((flags & ~(uint32_t)(MSTS_SAFE | MSTS_TENSOR_GEMM)) != 0) return -14;
   const size_t need = msts_solve_variant_workspace_size(side, uplo, trans, m, n, nb, flags);
   if (need > 0 && (!workspace || workspace_bytes < need)) return workspace ? -12 : -11;
+  if (msts::bad_alignment({A, shifts, B}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || n == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const msts::Plan P = msts::make_plan(side, uplo, trans, m, n, nb, flags);

@@ -163,3 +163,35 @@ def test_pseudospectra_1norm_and_grid_arguments(lib):
     assert g(P, 4, 4, 0, 3, P, P, None) == -4
     assert g(P, 4, 4, 3, 3, None, P, None) == -5
     assert g(P, 4, 4, 3, 3, P, None, None) == -6
+
+
+def test_misaligned_pointers_rejected_without_launch(lib):
+    """Complex arrays must be 16-byte aligned and the workspace 256-byte
+    aligned: the kernels move complex values as 16-byte vectors, so anything
+    else is refused on the host with MSTS_ERR_ALIGN (after the numbered
+    argument checks) instead of reaching a kernel."""
+    ERR = -1002
+    P, A8, W = ctypes.c_void_p(256), ctypes.c_void_p(8), ctypes.c_void_p(1 << 12)
+    big = 1 << 26
+    # msts_solve: U, shifts, B misaligned; workspace misaligned
+    assert lib.msts_solve(A8, 4, 4, P, 1, P, 4, None, None, 32, W, big, None, 0, None) == ERR
+    assert lib.msts_solve(P, 4, 4, A8, 1, P, 4, None, None, 32, W, big, None, 0, None) == ERR
+    assert lib.msts_solve(P, 4, 4, P, 1, A8, 4, None, None, 32, W, big, None, 0, None) == ERR
+    assert lib.msts_solve(P, 4, 4, P, 1, P, 4, None, None, 32, ctypes.c_void_p(16), big, None, 0, None) == ERR
+    # a numbered argument error is still reported first
+    assert lib.msts_solve(A8, 3, 4, P, 1, P, 4, None, None, 32, W, big, None, 0, None) == -2
+    # msts_trevc: T misaligned
+    assert lib.msts_trevc(A8, 4, 4, P, 4, P, P, 32, W, big, None, 0, None) == ERR
+    # msts_gsolve: V misaligned
+    assert lib.msts_gsolve(P, 4, A8, 4, 4, P, 1, P, 4, None, None, 32, W, big, None, 0, None) == ERR
+    # msts_back_transform: X misaligned (no workspace needed without the tensor flag)
+    assert lib.msts_back_transform(P, 4, 4, P, 4, A8, 4, None, 0, None, 0, None) == ERR
+    # msts_solve_variant: B misaligned
+    assert lib.msts_solve_variant(0, 1, 0, P, 4, 4, P, 1, A8, 4, None, None, 32, W, big, None, 0, None) == ERR
+    # msts_pseudospectra: the grid points misaligned
+    assert lib.msts_pseudospectra(P, 4, 4, A8, 1, P, 4, 2, P, None, None, None, 32, W, big, None, 0,
+                                  None) == ERR
+    # msts_portrait_grid: the output grid misaligned
+    assert lib.msts_portrait_grid(P, 4, 4, 2, 2, A8, P, None) == ERR
+    with pytest.raises(ValueError, match="aligned"):
+        msts._check(ERR, "msts_solve")
