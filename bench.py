@@ -427,7 +427,8 @@ def run_native(args):
     out["status_bits"] = [n for b, n in msts.STATUS_BITS.items() if st & b]
 
     if rank == 0 and wl == "trevc":
-        out["cpu_baseline"] = cpu_baseline_trevc(T)
+        out["cpu_baseline"], (cols, Zo, eo) = cpu_baseline_trevc(T)
+        out["parity"] = trevc_parity(Z, se, cols, Zo, eo)
     if rank == 0 and not args.no_extra:
         out["extra"] = extra_measurements(dev, nb)
     if rank == 0:
@@ -859,13 +860,28 @@ def cpu_baseline_trevc(T, stride=2):
     cols = np.arange(0, m, stride)
     oracle.trevc_columns(T, cols[:8], 32)          # load / build the oracle first
     t0 = time.perf_counter()
-    oracle.trevc_columns(T, cols, 32)
+    Zo, eo = oracle.trevc_columns(T, cols, 32)
     dt = time.perf_counter() - t0
     fl = float(sum(4.0 * j * j for j in cols))
-    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"every {stride}nd eigenvector column of the 4096x4096 TREVC matrix "
-                      f"({cols.size} columns, {fl / 1e9:.1f} GFLOP, {dt:.1f} s wall)"}
+    return ({"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+             "kind": "oracle",
+             "sample": f"every {stride}nd eigenvector column of the 4096x4096 TREVC matrix "
+                       f"({cols.size} columns, {fl / 1e9:.1f} GFLOP, {dt:.1f} s wall)"},
+            (cols, Zo, eo))
+
+
+def trevc_parity(Z, se, cols, Zo, eo):
+    """The timed run's eigenvectors against the oracle's on the columns the
+    cpu_baseline computed: scale exponents equal, columns within 1e-8 of the
+    column's largest entry (the bound of the parity tests)."""
+    import torch
+    idx = torch.from_numpy(np.ascontiguousarray(cols)).to(Z.device)
+    Zg = Z[:, idx].cpu().numpy()
+    eg = se[idx].cpu().numpy()
+    rel = np.abs(Zg - Zo).max(axis=0) / np.maximum(np.abs(Zo).max(axis=0), 1e-300)
+    return {"columns": int(cols.size), "against": "the oracle (Alg. 6 on Alg. 5, FP64), same columns",
+            "scale_exp_equal": bool(np.array_equal(eg, eo)), "max_rel_err": float(rel.max()),
+            "tolerance": 1e-8, "pass": bool(np.array_equal(eg, eo) and rel.max() <= 1e-8)}
 
 
 def run_reference(args):

@@ -40,3 +40,27 @@ def test_bench_reductions_over_two_gloo_ranks():
         assert p.exitcode == 0
     for rank, ms, fl, r, w in out:
         assert ms == 11.0 and fl == 3.0 and r == rank and w == 2
+
+
+def test_bench_trevc_parity_flags_a_planted_error():
+    """bench.py pairs its headline with the oracle on the cpu_baseline's
+    columns: a correct Z passes, a perturbed column or exponent fails."""
+    import numpy as np
+    import torch
+
+    import bench
+    import oracle
+    from paper_1607_01477_gb300 import workloads as W
+
+    T = W.trevc_problem(96, seed=5)
+    Zf, ef, _ = oracle.trevc(T, 32)
+    cols = np.arange(0, 96, 2)
+    Zo, eo = oracle.trevc_columns(T, cols, 32)
+    Z, se = torch.from_numpy(np.asfortranarray(Zf)), torch.from_numpy(ef.astype(np.int32))
+    assert bench.trevc_parity(Z, se, cols, Zo, eo)["pass"]
+    Zbad = Z.clone()
+    Zbad[3, 40] += 1e-6 * Zbad[:, 40].abs().max()
+    assert not bench.trevc_parity(Zbad, se, cols, Zo, eo)["pass"]
+    sebad = se.clone()
+    sebad[10] += 1
+    assert not bench.trevc_parity(Z, sebad, cols, Zo, eo)["pass"]
