@@ -561,10 +561,13 @@ static cudaError_t launch_nb(int L, const ProbTable &tab, int step, int shortcut
   }
 }
 
-// Lanes per shift.  A launch is bound by the dependent chain of its warps
-// rather than by FP64 throughput: its time is set by the lane width L and by
-// k, the number of 128-thread CTAs on the busiest SM, and hardly by how many
-// SMs are busy.  For n_b = 32 the width is the one with the smallest time in
+// Lanes per shift.  A warp issues its FP64 instructions at one per 64 cycles
+// whether they depend on each other or not, warps on one sub-partition share
+// that rate, and every warp also waits on its shuffles and memory: a launch
+// lasts as long as its busiest SM, so its time is set by the lane width L (the
+// FP64 instructions a shift costs) and by k, the number of 128-thread CTAs on
+// the busiest SM, hardly by how many SMs are busy.  For n_b = 32 the width is
+// the one with the smallest time in
 // tables measured on GB300 (one launch per solve, m = n_b = 32, 304..12160
 // shifts; k = 1..4, then a constant slope per further CTA, microseconds).
 // Every width gives the same results bit for bit.  Other block sizes take the
