@@ -166,19 +166,27 @@ class ClockSampler:
 KERNEL_SOURCES = {"k_gemm": "msts_solve.cu", "k_diag": "msts_diag.cu", "k_oz_update": "msts_ozaki.cu"}
 
 
+def code_hash(text: str) -> str:
+    """SHA-256 (16 hex digits) of a C/CUDA source with its comments and blank
+    lines removed: a change of comments alone keeps a profile valid."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines()]
+    return hashlib.sha256("\n".join(line for line in lines if line.strip()).encode()).hexdigest()[:16]
+
+
 def kernel_source_hash(kernel: str) -> str:
     src = os.path.join(ROOT, "paper_1607_01477_gb300", "csrc", KERNEL_SOURCES[kernel])
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return code_hash(open(src).read())
 
 
 def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    if it was taken on a different version of the kernel's source file."""
+    if it was taken on a different version of the kernel's source code."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}4096.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    h = re.search(r"code_sha256_16:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not h or not t or h.group(1) != kernel_source_hash(kernel):
         return None
