@@ -13,7 +13,7 @@
  * A[r + c*lda]).  Only the upper triangle of U / T is read.
  * OpenMP is used only across independent shifts / grid points.
  *
- * Readings of the paper fixed here (each is restated in the design doc):
+ * Readings of the paper fixed here (the CUDA library takes the same ones):
  *   - Omega (the overflow threshold of Alg. 4 and Alg. 5) is 2^960.
  *   - Magnitudes in all growth bounds are complex moduli |z| (hypot).
  *   - A pivot U(i,i)-lambda that is exactly zero is replaced by the real
