@@ -204,6 +204,17 @@ def trevc_flops(m: int) -> float:
     return 4.0 / 3.0 * m ** 3
 
 
+def trevc_config(m: int, nb: int, world: int) -> dict:
+    """The safe TREVC workload as both arms of the benchmark name it."""
+    return {"workload": f"safe TREVC (Alg. 6 on Alg. 5), T {m}x{m} complex128, 5% eigenvalues "
+                        f"in clusters of 4 at spacing 1e-10, strictly-upper 10*CN(0,1), all {m} "
+                        "eigenvectors", "m": m, "n_b": nb, "eigenvectors": m,
+            "flops_per_step": "(4/3) m^3 algorithmic",
+            "l2": f"no flush: T ({m * m * 16 / 1e6:.0f} MB) and Z ({m * m * 16 / 1e6:.0f} MB) "
+                  "exceed the 129 MB L2",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_native(args):
     import torch
     import paper_1607_01477_gb300 as msts
@@ -245,14 +256,9 @@ def run_native(args):
 
         flops_per_step = trevc_flops(m)
         unit = "TFLOP/s"
-        config = {"workload": "safe TREVC (Alg. 6 on Alg. 5), T 4096x4096 complex128, 5% eigenvalues "
-                              "in clusters of 4 at spacing 1e-10, strictly-upper 10*CN(0,1), all 4096 "
-                              "eigenvectors", "m": m, "n_b": nb, "eigenvectors": m,
-                  "substitution_gemm": ("tensor cores, FP64-accurate BF16 digit planes" if args.tensor
-                                        else "FP64 FMA"),
-                  "flops_per_step": "(4/3) m^3 algorithmic",
-                  "l2": "no flush: T (268 MB) and Z (268 MB) exceed the 129 MB L2",
-                  "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+        config = trevc_config(m, nb, world)
+        implementation = {"substitution_gemm": ("tensor cores, FP64-accurate BF16 digit planes"
+                                                if args.tensor else "FP64 FMA")}
         # pinned host buffers with the device tensors' column-major strides, so
         # each transfer is one contiguous copy
         h2d_host = torch.empty_strided((m, m), (1, m), dtype=torch.complex128, pin_memory=True)
@@ -429,13 +435,13 @@ def run_native(args):
     out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
-           "clocks": clk.summary()}
+           "config": config, "implementation": implementation, "roofline": roofline, "e2e": e2e,
+           "gpu_launches": int(launches), "clocks": clk.summary()}
     st = int(status.item())
     out["status_bits"] = [n for b, n in msts.STATUS_BITS.items() if st & b]
 
     if rank == 0 and wl == "trevc":
-        out["cpu_baseline"], (cols, Zo, eo) = cpu_baseline_trevc(T)
+        out["cpu_baseline"], (cols, Zo, eo) = cpu_baseline_trevc(T, nb)
         out["parity"] = trevc_parity(Z, se, cols, Zo, eo)
     if rank == 0 and not args.no_extra:
         out["extra"] = extra_measurements(dev, nb)
@@ -860,15 +866,15 @@ def measured_peak(key):
         return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}.get(key)
 
 
-def cpu_baseline_trevc(T, stride=2):
+def cpu_baseline_trevc(T, nb=32, stride=2):
     """The oracle (as it stands) on the host cores: every `stride`-th eigenvector
     column of the same 4096 x 4096 matrix, TFLOP/s at 4 j^2 FLOPs per column j."""
     import oracle
     m = T.shape[0]
     cols = np.arange(0, m, stride)
-    oracle.trevc_columns(T, cols[:8], 32)          # load / build the oracle first
+    oracle.trevc_columns(T, cols[:8], nb)          # load / build the oracle first
     t0 = time.perf_counter()
-    Zo, eo = oracle.trevc_columns(T, cols, 32)
+    Zo, eo = oracle.trevc_columns(T, cols, nb)
     dt = time.perf_counter() - t0
     fl = float(sum(4.0 * j * j for j in cols))
     return ({"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
@@ -904,12 +910,12 @@ def run_reference(args):
     # main line's cpu_baseline uses (~0.8 s on 16 cores), so the oracle's O(m^2)
     # set-up of Alg. 5 is amortised as in a full run
     cols_all = np.arange(0, m)
-    oracle.trevc_columns(T, cols_all[:4], 32)
+    oracle.trevc_columns(T, cols_all[:4], args.nb)
     times = []
     for k in range(args.warmup + args.steps):
         cols = cols_all[(k % 2)::2]                 # a bounded sample per step
         t0 = time.perf_counter()
-        oracle.trevc_columns(T, cols, 32)
+        oracle.trevc_columns(T, cols, args.nb)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append((dt, float(sum(4.0 * j * j for j in cols))))
@@ -920,9 +926,8 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / len(times) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
-           "config": {"workload": "safe TREVC (Alg. 6 on Alg. 5), T 4096x4096 complex128, 5% "
-                                  "eigenvalues in clusters of 4 at spacing 1e-10, strictly-upper "
-                                  "10*CN(0,1)", "m": m, "n_b": 32},
+           "config": trevc_config(m, args.nb, world),
+           "implementation": {"oracle": "plain C, FP64, OpenMP across eigenvector columns"},
            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.num_threads(),
                             "kind": "oracle",
                             "sample": f"{cols_all.size // 2} eigenvector columns per step "
