@@ -73,3 +73,31 @@ def test_selected_columns_match_full_trevc():
     Zc, ec = oracle.trevc_columns(T, cols, 32)
     assert np.array_equal(ec, e[cols])
     assert np.array_equal(Zc, Z[:, cols])
+
+
+def test_full_size_workload_sampled_columns():
+    """The 4096 x 4096 TREVC workload (the benchmark's matrix): 48 sampled
+    columns, among them members of eigenvalue clusters (spacing 1e-10) and the
+    last columns, whose growth drives e_j into the thousands (scales far below
+    the double range).  Each column is zero below its diagonal entry 2^-e_j and
+    has eigen-residual <= 2 m eps."""
+    T = W.trevc_problem(4096)
+    m = T.shape[0]
+    lam = np.diag(T)
+    gap = np.array([np.partition(np.abs(lam - lam[j]), 1)[1] for j in range(m)])
+    clustered = np.flatnonzero(gap < 1e-9)
+    assert clustered.size >= 150
+    g = W.rng(0, 4096)
+    cols = np.unique(np.concatenate([[0, 1, 31, 32, 33], clustered[:8], clustered[-8:],
+                                     g.choice(m, 24, replace=False), [m - 3, m - 2, m - 1]]))
+    Zc, ec = oracle.trevc_columns(T, cols, 32)
+    Tu = np.triu(T)
+    fro = np.linalg.norm(Tu)
+    for k, j in enumerate(cols):
+        z = Zc[:, k]
+        assert z[j] == np.ldexp(1.0, -int(ec[k]))
+        assert (z[j + 1:] == 0).all() and np.isfinite(z).all()
+        zs = z / np.abs(z).max()
+        rho = np.linalg.norm(Tu @ zs - lam[j] * zs) / (fro * np.linalg.norm(zs))
+        assert rho <= 2 * m * EPS, (j, rho)
+    assert ec.max() >= 1000
