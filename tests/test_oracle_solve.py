@@ -81,3 +81,19 @@ def test_trailing_zero_rhs_gives_trailing_zero_solution():
     B[20:, :] = 0
     X = oracle.solve(U, s, B)
     assert (X[20:, :] == 0).all()
+
+
+def test_full_size_mixed_workload_sampled_columns():
+    """The 8192 x 8192 workload with 2048 shifts (annulus diagonal, shifts in
+    the disk of radius 0.4): the oracle's solution of 12 sampled columns has
+    normwise backward error <= 8 m eps (Sec. 2: back substitution is backward
+    stable), the bar the mixed-precision solve is held to after refinement."""
+    U, s, B = W.mixed_problem()
+    m, n = B.shape
+    assert (m, n) == (8192, 2048)
+    idx = np.array([0, 1, 511, 1024, 1500, 2047] + list(W.rng(0, 8192).choice(n, 6, replace=False)))
+    Bs = np.asfortranarray(B[:, idx])
+    X = oracle.solve(U, s[idx], Bs)
+    assert np.isfinite(X).all()
+    eta = backward_error(U, s[idx], X, Bs)
+    assert eta.max() <= 8 * m * EPS
