@@ -71,3 +71,39 @@ def test_adjoint_diagonal_closed_form():
     assert np.allclose(dB, L, rtol=1e-13, atol=0)
     assert np.allclose(dU, np.triu(-(L @ X.conj().T)), rtol=1e-12, atol=1e-13)
     assert np.allclose(ds, (np.conj(X) * L).sum(axis=0), rtol=1e-12)
+
+
+def test_adjoint_at_the_largest_batched_size():
+    """A problem of the batched differentiable workload at its largest order
+    (m = 2048, 32 shifts in the disk of radius 1.5): the oracle's gradients
+    against CPU autograd through torch.linalg.solve_triangular (a library
+    triangular solve per shift), and central differences (h = 1e-6) on random
+    real and imaginary directions within 1e-6."""
+    (U, s, B), = W.batch_problem(batch=1, m_lo=2048, m_hi=2048, seed=2048)
+    m, n = B.shape
+    X = oracle.solve(U, s, B)
+    dU, dB, ds = oracle.adjoint(U, s, B, 2 * X)
+    assert (np.tril(dU, -1) == 0).all()
+
+    Ut = torch.tensor(np.triu(U), requires_grad=True)
+    st = torch.tensor(s, requires_grad=True)
+    Bt = torch.tensor(B, requires_grad=True)
+    eye = torch.eye(m, dtype=torch.complex128)
+    loss = 0
+    for j in range(n):
+        x = torch.linalg.solve_triangular(torch.triu(Ut) - st[j] * eye, Bt[:, j:j + 1], upper=True)
+        loss = loss + (x.abs() ** 2).sum()
+    loss.backward()
+    for a, b in ((dU, torch.triu(Ut.grad).numpy()), (dB, Bt.grad.numpy()), (ds, st.grad.numpy())):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+
+    f = lambda U_, s_, B_: float((np.abs(oracle.solve(U_, s_, B_)) ** 2).sum())
+    g = W.rng(0, 2049)
+    h = 1e-6
+    for part in (1.0, 1j):
+        EU = np.asfortranarray(np.triu(g.standard_normal((m, m))) * part)
+        EB = np.asfortranarray(g.standard_normal((m, n)) * part)
+        Es = g.standard_normal(n) * part
+        fd = (f(U + h * EU, s + h * Es, B + h * EB) - f(U - h * EU, s - h * Es, B - h * EB)) / (2 * h)
+        an = (np.vdot(dU, EU) + np.vdot(dB, EB) + np.vdot(ds, Es)).real
+        assert abs(fd - an) <= 1e-6 * abs(an)
