@@ -41,3 +41,19 @@ def test_diagonal_pseudospectra_fixture():
         V0 = np.asfortranarray(np.ones((d.size, z.size), dtype=np.complex128) + 0.1j)
         sig, *_ = oracle.pseudospectra(T, z, V0, 20)
         assert np.allclose(sig, c["sigma_min"], rtol=1e-12, atol=0)
+
+
+def test_safe_rescale_exponent_fixture():
+    """The rescale exponent of Alg. 4 / Alg. 5 itself, not only x up to scale:
+    e = 2 exactly (the smallest k with 2^-k G < Omega), x exact."""
+    f = G["safe_rescale_exponent_2x2"]
+    U = np.asfortranarray(np.array([[complex(*z) for z in row] for row in f["U"]], dtype=np.complex128))
+    b = np.zeros((2, 1), dtype=np.complex128, order="F")
+    b[f["b_log2"]["row"], 0] = np.ldexp(f["b_log2"]["mantissa"], f["b_log2"]["exp2"])
+    s = np.zeros(1, dtype=np.complex128)
+    x_expect = np.array([np.ldexp(v["mantissa"], v["exp2"]) for v in f["expect"]["x"]])
+    for c in f["cases"]:
+        X, e = oracle.safe_trsv_unblocked(U, s, b) if c["nb"] == 0 else oracle.safe_solve(U, s, b, c["nb"])
+        assert int(e[0]) == f["expect"]["e"], c
+        assert np.array_equal(X[:, 0], x_expect.astype(np.complex128)), c
+        assert np.array_equal(np.triu(U) @ X[:, 0], np.ldexp(1.0, -int(e[0])) * b[:, 0])
