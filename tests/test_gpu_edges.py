@@ -86,3 +86,34 @@ def test_safe_zero_pivot_uses_delta_like_the_oracle(tensor):
     Xg = to_np(X)
     rel = np.abs(Xg - Xo).max(axis=0) / np.abs(Xo).max(axis=0)
     assert rel.max() <= 1e-8
+
+
+def _rescale_fixture(m):
+    """The 2x2 safe-solve fixture of tests/golden (U(0,0) = 1, U(0,m-1) = -5,
+    U(m-1,m-1) = 3, b = 3*2^958 e_{m-1}), embedded in an m x m identity so that
+    with n_b < m the rescale comes from Alg. 5's block bound C_blk = 5."""
+    U = np.eye(m, dtype=np.complex128)
+    U[0, m - 1] = -5.0
+    U[m - 1, m - 1] = 3.0
+    B = np.zeros((m, 1), dtype=np.complex128)
+    B[m - 1, 0] = np.ldexp(3.0, 958)
+    x = np.zeros(m, dtype=np.complex128)
+    x[0], x[m - 1] = np.ldexp(5.0, 956), np.ldexp(1.0, 956)
+    return np.asfortranarray(U), np.asfortranarray(B), x
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("m,nb", [(2, 32), (33, 32), (17, 16)])
+def test_safe_rescale_exponent_fixture(m, nb, tensor):
+    """The exact rescale exponent of Alg. 4 / Alg. 5 (smallest k with
+    2^-k G < Omega; here G = 2^961, so k = 2): the GPU's scale exponent equals
+    the hand-derived one and the oracle's, and x is the exact solution times 2^-2."""
+    U, B, x = _rescale_fixture(m)
+    s = np.zeros(1, dtype=np.complex128)
+    Xd = to_dev(B)
+    _, sc, se, st = msts.msts_solve(to_dev(U), to_dev(s), Xd, safe=True, nb=nb, tensor=tensor)
+    Xo, eo = oracle.safe_solve(U, s, B, nb)
+    assert int(to_np(se)[0]) == 2 == int(eo[0])
+    assert to_np(sc)[0] == 0.25
+    X = to_np(Xd)[:, 0]
+    assert np.abs(X - x).max() <= 4 * np.finfo(float).eps * np.abs(x).max()
