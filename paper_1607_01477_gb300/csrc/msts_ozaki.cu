@@ -268,6 +268,7 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap *pA, const CUtens
     if (!ok) raise_status(args.status, MSTS_STATUS_TIMEOUT);   // tell the other CTAs at once
     return ok;
   };
+  int a_issued = 0, b_issued = 0;             // TMA loads the producer issued
 
   if (warp == kOzEpi) {
     // ---------------- TMA producer ----------------
@@ -281,6 +282,7 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap *pA, const CUtens
         if (c >= 2 && !wait(&bempty[bb], ((c >> 1) - 1) & 1)) { fail = 1; break; }
         mbar_arrive_expect_tx(&bfull[bb], kOzBBytes);
         tma_load_3d(sB + bb * kOzBBytes, pB, &bfull[bb], kk, j0, 0);
+        ++b_issued;
         for (int s = 0; s < kOzS; ++s, ++ia) {
           const int slot = ia % kOzRing;
           if (ia >= kOzRing && !wait(&aempty[slot], ((ia / kOzRing) - 1) & 1)) { fail = 1; break; }
@@ -289,6 +291,7 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap *pA, const CUtens
         }
         if (fail) break;
       }
+      a_issued = ia;
     }
   } else if (warp == kOzEpi + 1) {
     // ---------------- MMA issuer ----------------
@@ -338,7 +341,8 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap *pA, const CUtens
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       const int ab = c & 1;
-      if (!wait(&accfull[ab], (c >> 1) & 1)) { ok = false; break; }
+      // one decision per warp: the reads below are warp-wide (.sync.aligned)
+      if (!__all_sync(0xffffffffu, wait(&accfull[ab], (c >> 1) & 1))) { ok = false; break; }
       tc_fence_after();
 #pragma unroll
       for (int d = 0; d < kOzS; ++d) {                       // diagonal s + t = d + 2
@@ -390,6 +394,21 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap *pA, const CUtens
   }
   tc_fence_before();
   __syncthreads();
+  if (fail) {
+    // A wait gave up.  Before TMEM is freed and the CTA exits, the bulk copies
+    // and MMAs it issued must have landed: wait for the last load into every
+    // buffer and for the MMA drain, each with the time limit only (the abort
+    // bit that the give-up set would end these waits at once).
+    if (warp == kOzEpi && lane == 0) {
+      for (int i = max(0, a_issued - kOzRing); i < a_issued; ++i)
+        mbar_wait(&afull[i % kOzRing], (i / kOzRing) & 1);
+      for (int i = max(0, b_issued - 2); i < b_issued; ++i) mbar_wait(&bfull[i & 1], (i >> 1) & 1);
+    } else if (warp == kOzEpi + 1 && lane == 0) {
+      mbar_wait(&mma_done, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
   if (fail && threadIdx.x == 0) raise_status(args.status, MSTS_STATUS_TIMEOUT);
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
@@ -815,6 +834,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (!ok) raise_status(args.status, MSTS_STATUS_TIMEOUT);
     return ok;
   };
+  int a_issued = 0, b_issued = 0;                   // A reloads and B loads the producer issued
 
   if (warp == kOzuEpiWarps) {
     if (lane == 0) {                                // ---------------- TMA producer
@@ -836,7 +856,9 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (k >= 2 && !wait(&bempty[bb], ((k >> 1) - 1) & 1)) { fail = 1; break; }
         mbar_arrive_expect_tx(&bfull[bb], kOzBBytes);
         tma_load_3d(sB + bb * kOzBBytes, &tmB, &bfull[bb], 0, ct * kOzBN, 0);
+        ++b_issued;
       }
+      a_issued = na;
     }
   } else if (warp == kOzuEpiWarps + 1) {
     if (lane == 0) {                                // ---------------- MMA issuer
@@ -910,7 +932,8 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (t0 < t1) fetch(t0, cur);
     for (int t = t0, k = 0; t < t1; ++t, ++k) {
       const int ab = k & 1;
-      if (!wait(&accfull[ab], (k >> 1) & 1)) { fail = 1; break; }
+      // one decision per warp: the TMEM reads and shuffles below are warp-wide
+      if (!__all_sync(0xffffffffu, wait(&accfull[ab], (k >> 1) & 1))) { fail = 1; break; }
       tc_fence_after();
       if (t + 1 < t1) fetch(t + 1, nxt);            // in flight during this tile
       const int c0 = kCW * cgroup;
@@ -980,6 +1003,18 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
   tc_fence_before();
   __syncthreads();
+  if (fail) {
+    // A wait gave up: the copies and MMAs this CTA issued land before TMEM is
+    // freed (time-limited waits that ignore the abort bit, as in oz_gemm_tile).
+    if (warp == kOzuEpiWarps && lane == 0) {
+      if (a_issued > 0) mbar_wait(&afull, (a_issued - 1) & 1);
+      for (int i = max(0, b_issued - 2); i < b_issued; ++i) mbar_wait(&bfull[i & 1], (i >> 1) & 1);
+    } else if (warp == kOzuEpiWarps + 1 && lane == 0) {
+      mbar_wait(&mma_done, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
   if (fail && threadIdx.x == 0) raise_status(args.status, MSTS_STATUS_TIMEOUT);
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
