@@ -80,6 +80,17 @@ def load_library():
             raise RuntimeError(f"libmsts.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
         lib = ctypes.CDLL(_LIB_PATH)
         lib.msts_version.restype = ctypes.c_int
+        lib.msts_version.argtypes = []
+        lib.msts_launch_count.restype = ctypes.c_uint64
+        lib.msts_launch_count.argtypes = []
+        lib.msts_trace_begin.restype = ctypes.c_int
+        lib.msts_trace_begin.argtypes = [_i64]
+        lib.msts_trace_end.restype = ctypes.c_int
+        lib.msts_trace_end.argtypes = []
+        lib.msts_trace_query.restype = ctypes.c_int
+        lib.msts_trace_query.argtypes = [_i32, _vp, _vp, _vp, _vp]
+        lib.msts_safe_solve_static.restype = ctypes.c_int
+        lib.msts_safe_solve_static.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i32, _vp, _vp]
         lib.msts_solve_workspace_size.restype = _sz
         lib.msts_solve_workspace_size.argtypes = [_i64, _i64, _i32, _u32]
         lib.msts_solve.restype = ctypes.c_int

@@ -24,7 +24,7 @@ def declared_functions():
     for h in os.listdir(os.path.join(ROOT, "include")):
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
-            names |= set(re.findall(r"^\s*(?:int|size_t)\s+(msts_\w+)\s*\(", txt, re.M))
+            names |= set(re.findall(r"^\s*(?:int|size_t|uint64_t)\s+(msts_\w+)\s*\(", txt, re.M))
     return sorted(names)
 
 
@@ -195,3 +195,50 @@ def test_misaligned_pointers_rejected_without_launch(lib):
     assert lib.msts_portrait_grid(P, 4, 4, 2, 2, A8, P, None) == ERR
     with pytest.raises(ValueError, match="aligned"):
         msts._check(ERR, "msts_solve")
+
+
+def declared_prototypes():
+    """name -> (return type, [parameter types]) for every prototype in include/*.h."""
+    protos = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", " ", txt)
+        for ret, name, params in re.findall(r"\b(int|size_t|uint64_t)\s+(msts_\w+)\s*\(([^;{]*?)\)\s*;", txt, re.S):
+            params = " ".join(params.split())
+            types = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+            protos[name] = (ret, types)
+    return protos
+
+
+def _c_kind(decl):
+    """Width/sign class of a C parameter declaration or return type."""
+    if "*" in decl:
+        return "ptr"
+    base = decl.replace("const", "").split()[0]
+    return {"int64_t": ("i", 8, True), "int32_t": ("i", 4, True), "uint32_t": ("i", 4, False),
+            "size_t": ("i", ctypes.sizeof(ctypes.c_size_t), False), "int": ("i", 4, True),
+            "uint64_t": ("i", 8, False), "double": "f64"}[base]
+
+
+def _ctypes_kind(t):
+    if t is ctypes.c_void_p:
+        return "ptr"
+    if t is ctypes.c_double:
+        return "f64"
+    return ("i", ctypes.sizeof(t), t(-1).value < 0)
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Every entry point the binding declares to ctypes has the header's
+    parameter count, widths and signedness, and its return type: a 64-bit
+    size or leading dimension is never passed as a 32-bit int."""
+    protos = declared_prototypes()
+    assert set(protos) == set(declared_functions())
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, f"{name}: no ctypes signature in load_library"
+        assert [_ctypes_kind(t) for t in fn.argtypes] == [_c_kind(p) for p in params], name
+        assert _ctypes_kind(fn.restype) == _c_kind(ret), name
