@@ -16,13 +16,26 @@ Every function cites the passage of the paper it follows:
   solve_blocked      -- Alg. 3 (MultiShiftTrsm), blocked from the bottom
   safe_solve         -- Alg. 5 (SafeMultiShiftTrsm) with Alg. 4 on each block
   safe_trsv_unblocked-- Alg. 4 (SafeTrsv) on the whole shifted matrix
-  trevc              -- Alg. 6 (TriangEig) with the strictly-upper shortcut
+  trevc, trevc_columns -- Alg. 6 (TriangEig) with the strictly-upper shortcut
+                        (all columns, or the listed ones bit for bit)
+  back_transform     -- X = Q Z, the second half of Alg. 6 (Eig)
+  gsolve             -- Alg. 8 per shift (plain definition on U - lambda_j V)
+  safe_gsolve        -- Alg. 9 with the generalized Alg. 4 on each block
+  gtrevc, gtrevc_columns -- Alg. 10 (GeneralizedTriangEig), triangular part
+  solve_variant      -- the lower / transposed / right-hand cases (footnote
+                        to Sec. 2), plain definition per shift
+  safe_solve_variant -- Alg. 5 in the variant's substitution order
   pseudospectra      -- Alg. 7 (Van Loan / Lui) with Lanczos (Sec. 5)
   tridiag_max_eig    -- largest Ritz value of the Lanczos tridiagonal
+  pseudospectra_1norm-- Hager/Higham 1-norm estimate of the resolvent on
+                        shifted triangular solves (footnote to Sec. 5)
+  portrait_grid      -- the automatic grid of SpectralPortrait (Sec. 6)
   adjoint            -- gradient of X = (U - s_j I)^{-1} b_j (not in the paper)
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
-against brute-force dense algebra, closed forms or invariants.
+and ``tests/test_golden.py`` against brute-force dense algebra, closed forms
+or invariants, and ``tests/test_oracle_mutants.py`` shows that those pins fail
+on planted mistakes.  No function is parity unpinned.
 """
 from __future__ import annotations
 
