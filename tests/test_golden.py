@@ -57,3 +57,20 @@ def test_safe_rescale_exponent_fixture():
         assert int(e[0]) == f["expect"]["e"], c
         assert np.array_equal(X[:, 0], x_expect.astype(np.complex128)), c
         assert np.array_equal(np.triu(U) @ X[:, 0], np.ldexp(1.0, -int(e[0])) * b[:, 0])
+
+
+def test_safe_gsolve_rescale_exponent_fixture():
+    """The same exact exponent for the safe generalized solve (Alg. 9), with the
+    off-diagonal growth coming from V only, so the |lambda| ||V|| part of the
+    bounds decides the rescale."""
+    f = G["safe_gsolve_rescale_exponent_2x2"]
+    mat = lambda key: np.asfortranarray(np.array([[complex(*z) for z in row] for row in f[key]], dtype=np.complex128))
+    U, V = mat("U"), mat("V")
+    lam = np.array([complex(*f["lambda"])])
+    b = np.zeros((2, 1), dtype=np.complex128, order="F")
+    b[f["b_log2"]["row"], 0] = np.ldexp(f["b_log2"]["mantissa"], f["b_log2"]["exp2"])
+    x_expect = np.array([np.ldexp(v["mantissa"], v["exp2"]) for v in f["expect"]["x"]], dtype=np.complex128)
+    for c in f["cases"]:
+        X, e = oracle.safe_gsolve(U, V, lam, b, c["nb"])
+        assert int(e[0]) == f["expect"]["e"], c
+        assert np.array_equal(X[:, 0], x_expect), c

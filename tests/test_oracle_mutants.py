@@ -87,6 +87,30 @@ CASES = [
      "return op == 2 ? oz_conj(a) : a;",
      "return a;", 1,
      t_variants, "test_against_dense_solve", ("left", "upper", "C")),
+    ("Sturm count with the wrong sign on b^2/d",
+     "d = (a[i] - x) - b[i - 1] * b[i - 1] / d;",
+     "d = (a[i] - x) + b[i - 1] * b[i - 1] / d;", 1,
+     t_pseudo, "test_tridiag_max_matches_eigvalsh", (5,)),
+    ("right-hand variant of A^H maps to A^H instead of conj(A)",
+     "return trans == 0 ? 1 : (trans == 1 ? 0 : 3);",
+     "return trans == 0 ? 1 : (trans == 1 ? 0 : 2);", 1,
+     t_variants, "test_against_dense_solve", ("right", "upper", "C")),
+    ("portrait grid margin a fifth instead of a quarter",
+     "double h = 0.25 * (w > hgt ? w : hgt);",
+     "double h = 0.2 * (w > hgt ? w : hgt);", 1,
+     t_pseudo1, "test_portrait_grid_properties", ()),
+    ("generalized block bound without |lambda| C_blk(V)",
+     "G = G + (P->cblkU[b] + al * P->cblkV[b]) * N;",
+     "G = G + P->cblkU[b] * N;", 1,
+     t_golden, "test_safe_gsolve_rescale_exponent_fixture", ()),
+    ("generalized column bound without |lambda| cin_V",
+     "cnorm[i] = cnU[i] + al * cnV[i];",
+     "cnorm[i] = cnU[i];", 1,
+     t_golden, "test_safe_gsolve_rescale_exponent_fixture", ()),
+    ("Higham's alternative vector scaled by 1/m instead of 2/(3m)",
+     "double alt = 2.0 * norm1_vec(m, y) / (3.0 * (double)m);",
+     "double alt = 2.0 * norm1_vec(m, y) / (2.0 * (double)m);", 1,
+     t_pseudo1, "test_alternative_vector_estimate_when_it_wins", ()),
     ("1-norm estimator applies Q^T instead of Q^H",
      "s = oz_add(s, oz_mul(oz_conj(AT(Q, ldq, r, i)), x[r]));",
      "s = oz_add(s, oz_mul(AT(Q, ldq, r, i), x[r]));", 1,

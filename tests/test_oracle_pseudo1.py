@@ -133,3 +133,27 @@ def test_portrait_grid_degenerate_spectrum():
     h = 4.0 * 2.0 ** -20                               # 2^-20 max(|Re|, |Im|)
     assert np.array_equal(box, [3.0 - h, 3.0 + h, -4.0 - h, -4.0 + h])
     assert z[4] == 3.0 - 4.0j                          # the centre point of a 3 x 3 grid
+
+
+def test_alternative_vector_estimate_when_it_wins():
+    """Higham's alternative vector x(i) = (-1)^i (1 + i/(m-1)), i = 0..m-1: on
+    small problems where it beats Hager's steps (kind -2), the estimate is
+    exactly 2 ||R x||_1 / (3m) with R = (T - zI)^{-1} from a dense inverse, and
+    it stays a lower bound of ||R||_1.  The inputs are seeded random triangles
+    on which the branch is taken (it rarely is)."""
+    wins = 0
+    for seed in (189, 228, 267, 369, 390):
+        g = W.rng(0, 5000 + seed)
+        m = int(g.integers(2, 9))
+        d = W.disk(g, m, 1.0)
+        T = W.upper(g, m, d, [0.3, 3.0, 30.0][seed % 3])
+        z = W.disk(g, 6, 1.2)
+        est, kind, steps = oracle.pseudospectra_1norm(T, z)[:3]
+        x = np.array([(-1.0) ** i * (1.0 + i / (m - 1)) for i in range(m)])
+        for p in range(z.size):
+            R = np.linalg.inv(np.triu(T) - z[p] * np.eye(m))
+            assert est[p] <= np.abs(R).sum(axis=0).max() * (1 + 1e-12)
+            if kind[p] == -2:
+                wins += 1
+                assert est[p] == pytest.approx(2.0 * np.abs(R @ x).sum() / (3.0 * m), rel=1e-10, abs=0)
+    assert wins >= 3
