@@ -117,3 +117,27 @@ def test_safe_rescale_exponent_fixture(m, nb, tensor):
     assert to_np(sc)[0] == 0.25
     X = to_np(Xd)[:, 0]
     assert np.abs(X - x).max() <= 4 * np.finfo(float).eps * np.abs(x).max()
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("m,nb", [(2, 32), (33, 32), (17, 16)])
+def test_safe_gsolve_rescale_exponent_fixture(m, nb, tensor):
+    """The generalized form of the fixture above (Alg. 9): U = 2I with
+    U(m-1,m-1) = 4 and V = I + 5 e_0 e_{m-1}^T, lambda = 1, so that U - lambda V
+    is the matrix above with its off-diagonal growth coming from V alone;
+    e = 2 exactly and x exact on both GEMM paths."""
+    Ustd, B, x = _rescale_fixture(m)
+    U = 2.0 * np.eye(m, dtype=np.complex128)
+    U[m - 1, m - 1] = 4.0
+    V = np.eye(m, dtype=np.complex128)
+    V[0, m - 1] = 5.0
+    U, V = np.asfortranarray(U), np.asfortranarray(V)
+    assert np.array_equal(U - V, Ustd)
+    lam = np.ones(1, dtype=np.complex128)
+    Xd = to_dev(B)
+    _, sc, se, st = msts.msts_gsolve(to_dev(U), to_dev(V), to_dev(lam), Xd, safe=True, nb=nb, tensor=tensor)
+    Xo, eo = oracle.safe_gsolve(U, V, lam, B, nb)
+    assert int(to_np(se)[0]) == 2 == int(eo[0])
+    assert to_np(sc)[0] == 0.25
+    X = to_np(Xd)[:, 0]
+    assert np.abs(X - x).max() <= 4 * np.finfo(float).eps * np.abs(x).max()
