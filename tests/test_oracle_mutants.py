@@ -87,6 +87,23 @@ CASES = [
      "return op == 2 ? oz_conj(a) : a;",
      "return a;", 1,
      t_variants, "test_against_dense_solve", ("left", "upper", "C")),
+    ("back substitution skips the last row of each AXPY",
+     "for (int64_t r = 0; r < i; ++r)                            /* AXPY */",
+     "for (int64_t r = 0; r + 1 < i; ++r)                            /* AXPY */", 1,
+     t_solve, "test_solve_matches_dense_lapack", (33, 5)),
+    ("rows below the block (I2) not rescaled when t < 1",
+     "/* t < 1: rescale I0 and I2 */\n      for (int64_t r = 0; r < lo; ++r) x[r] = oz_ldexp(x[r], -kk);\n"
+     "      for (int64_t r = hie; r < end; ++r) x[r] = oz_ldexp(x[r], -kk);",
+     "/* t < 1: rescale I0 and I2 */\n      for (int64_t r = 0; r < lo; ++r) x[r] = oz_ldexp(x[r], -kk);", 1,
+     t_safe, "test_pow2_closed_form_bitwise", (1, 8)),
+    ("TREVC shortcut stops one row early",
+     "int64_t end = shortcut ? (j < m ? j : m) : m;   /* active rows [0, end) */",
+     "int64_t end = shortcut ? (j < m ? (j > 0 ? j - 1 : 0) : m) : m;", 1,
+     t_trevc, "test_two_by_two_closed_form", ()),
+    ("Lanczos vector divided by beta^2",
+     "vn[r] = oz_scale(w[r], 1.0 / bn);",
+     "vn[r] = oz_scale(w[r], 1.0 / (bn * bn));", 1,
+     t_pseudo, "test_exact_when_krylov_space_is_full", (16,)),
     ("Sturm count with the wrong sign on b^2/d",
      "d = (a[i] - x) - b[i - 1] * b[i - 1] / d;",
      "d = (a[i] - x) + b[i - 1] * b[i - 1] / d;", 1,
