@@ -128,6 +128,16 @@ CASES = [
      "double alt = 2.0 * norm1_vec(m, y) / (3.0 * (double)m);",
      "double alt = 2.0 * norm1_vec(m, y) / (2.0 * (double)m);", 1,
      t_pseudo1, "test_alternative_vector_estimate_when_it_wins", ()),
+    ("safe lower variant reverses A transposed",
+     "      U[r + c * (int64_t)mm] = rev ? op_entry(A, lda, op, m - 1 - r, m - 1 - c) : op_entry(A, lda, op, r, c);",
+     "      U[r + c * (int64_t)mm] = rev ? op_entry(A, lda, op, m - 1 - c, m - 1 - r) : op_entry(A, lda, op, r, c);", 1,
+     t_variants, "test_safe_pow2_closed_form_bitwise", ("left", "lower", "N", 8)),
+    ("GeneralizedTriangEig eigenvalue S(j,j)/T(j,j) instead of T(j,j)/S(j,j)",
+     "lam[j] = oz_div(AT(T, ldt, j, j), AT(S, lds, j, j));\n    for (int64_t r = 0; r < m; ++r)\n"
+     "      AT(Z, ldz, r, j) = r < j ? oz_sub",
+     "lam[j] = oz_div(AT(S, lds, j, j), AT(T, ldt, j, j));\n    for (int64_t r = 0; r < m; ++r)\n"
+     "      AT(Z, ldz, r, j) = r < j ? oz_sub", 1,
+     t_gen, "test_gtrevc_residual_and_directions", (60,)),
     ("1-norm estimator applies Q^T instead of Q^H",
      "s = oz_add(s, oz_mul(oz_conj(AT(Q, ldq, r, i)), x[r]));",
      "s = oz_add(s, oz_mul(AT(Q, ldq, r, i), x[r]));", 1,
