@@ -437,6 +437,16 @@ int msts_trace_end(void);
 int msts_trace_query(int32_t kernel, double *total_ms, int64_t *launches, double *flops,
                      double *bytes);
 
+/* Failure injection for tests (host side; no counterpart in the paper).  The
+ * tensor-core kernels publish a timeout of a bounded wait in the caller's
+ * status word, or, for a call made with status == NULL, in a word of the
+ * library's own on the current device, which every such call clears on its
+ * stream before its first launch.  msts_inject_fallback_status ORs `bits`
+ * into that word (ordered on `stream`, synchronising it), so a test can check
+ * that a later call without a status word is not cut short by an earlier
+ * give-up.  Returns 0 or MSTS_ERR_CUDA. */
+int msts_inject_fallback_status(uint32_t bits, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Safe multi-shift solve without any allocation (the paper has no
  * counterpart; this is a convenience of this library).

@@ -89,6 +89,8 @@ def load_library():
         lib.msts_trace_end.argtypes = []
         lib.msts_trace_query.restype = ctypes.c_int
         lib.msts_trace_query.argtypes = [_i32, _vp, _vp, _vp, _vp]
+        lib.msts_inject_fallback_status.restype = ctypes.c_int
+        lib.msts_inject_fallback_status.argtypes = [_u32, _vp]
         lib.msts_safe_solve_static.restype = ctypes.c_int
         lib.msts_safe_solve_static.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i32, _vp, _vp]
         lib.msts_solve_workspace_size.restype = _sz

@@ -450,17 +450,61 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_batched(const __grid_const
 
 // ----- host side -------------------------------------------------------------
 // A status word of the library's own for calls made without one (the bounded
-// waits still need somewhere to publish a timeout to the other CTAs).
+// waits still need somewhere to publish a timeout to the other CTAs).  It is
+// cleared on the call's stream before every such call, so a timeout of one
+// call never makes a later one give up; its address is looked up once per
+// device, with that device current.  Calls without a status word that overlap
+// on the GPU (different streams) share it: a timeout in one may end the waits
+// of the other early, which that call cannot report either.
 __device__ uint32_t g_oz_abort_word;
-static uint32_t *abort_word() {
-  static uint32_t *p = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *a = nullptr;
-    if (cudaGetSymbolAddress(&a, g_oz_abort_word) == cudaSuccess) p = static_cast<uint32_t *>(a);
-  });
+constexpr int kAbortDevices = 64;
+static std::mutex g_abort_mu;
+static uint32_t *g_abort_addr[kAbortDevices] = {};
+uint32_t *ozaki_call_status(uint32_t *status, cudaStream_t st) {
+  if (status) return status;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAbortDevices) return nullptr;
+  uint32_t *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_abort_mu);
+    if (!g_abort_addr[dev]) {
+      void *a = nullptr;
+      if (cudaGetSymbolAddress(&a, g_oz_abort_word) == cudaSuccess) g_abort_addr[dev] = static_cast<uint32_t *>(a);
+    }
+    p = g_abort_addr[dev];
+  }
+  if (p && cudaMemsetAsync(p, 0, sizeof(uint32_t), st) != cudaSuccess) return nullptr;
   return p;
 }
+// Host-side fault injection for the tests: ORs `bits` into the library's
+// status word for calls made without one, on the current device, ordered on
+// `stream` (the bits stay until the next call without a status word clears
+// the word).  Returns 0 or MSTS_ERR_CUDA.
+extern "C" int msts_inject_fallback_status(uint32_t bits, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAbortDevices) return MSTS_ERR_CUDA;
+  uint32_t *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_abort_mu);
+    if (!g_abort_addr[dev]) {
+      void *a = nullptr;
+      if (cudaGetSymbolAddress(&a, g_oz_abort_word) == cudaSuccess) g_abort_addr[dev] = static_cast<uint32_t *>(a);
+    }
+    p = g_abort_addr[dev];
+  }
+  if (!p) return MSTS_ERR_CUDA;
+  uint32_t cur = 0;
+  if (cudaMemcpyAsync(&cur, p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return MSTS_ERR_CUDA;
+  cur |= bits;
+  if (cudaMemcpyAsync(p, &cur, sizeof(uint32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return MSTS_ERR_CUDA;
+  return 0;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -512,7 +556,7 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
     return cudaErrorNotSupported;
   OzArgs a{};
   a.B = B; a.ldb = ldb; a.X = X; a.ldx = ldx; a.s = s; a.R = R; a.ldr = ldr;
-  a.rexp = o.rexp; a.cexp = o.cexp; a.m = m; a.n = n; a.K = o.K; a.status = status ? status : abort_word();
+  a.rexp = o.rexp; a.cexp = o.cexp; a.m = m; a.n = n; a.K = o.K; a.status = ozaki_call_status(status, st);
   if (!status && a.status) {
     const cudaError_t ce = cudaMemsetAsync(a.status, 0, sizeof(uint32_t), st);
     if (ce != cudaSuccess) return ce;
@@ -548,7 +592,7 @@ cudaError_t ozaki_product(const double2 *A, long long lda, int m, const double2 
   OzArgs a{};
   a.R = C; a.ldr = ldc;
   a.rexp = o.rexp; a.cexp = o.cexp; a.m = m; a.n = n; a.K = o.K; a.triu_b = triu_b ? 1 : 0;
-  a.status = status ? status : abort_word();
+  a.status = ozaki_call_status(status, st);
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<kProduct>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
   // BF16 MMA FLOPs issued: per tile, its K' chunks of 36 digit pairs x 4
@@ -1040,7 +1084,7 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
   a.a_x0 = b * plan.KB;
   a.row_lo = row_lo; a.row_hi = row_hi;
   a.col_base = jstart; a.ncols = ncols;
-  a.status = status ? status : abort_word();
+  a.status = ozaki_call_status(status, st);
   if (plan.KB == kOzKC) {
     const int tiles_n = (ncols + kOzBN - 1) / kOzBN, tiles_m = (row_hi - row_lo + kOzBM - 1) / kOzBM;
     const int total = tiles_n * tiles_m;
@@ -1096,7 +1140,7 @@ cudaError_t ozaki_update_batched(const OzBatchStep *steps, int count, uint32_t *
     a.a_x0 = q.b * plan.KB;
     a.row_lo = row_lo; a.row_hi = row_hi;
     a.col_base = q.jstart; a.ncols = q.ncols;
-    a.status = status ? status : abort_word();
+    a.status = ozaki_call_status(status, st);
     hb->args[i] = a;
     hb->tiles_n[i] = (q.ncols + kOzBN - 1) / kOzBN;
     hb->tiles_m[i] = (row_hi - row_lo + kOzBM - 1) / kOzBM;
@@ -1152,7 +1196,7 @@ cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *
     a.R = q.dU; a.ldr = q.lddu;
     a.rexp = rexp; a.cexp = cexp;
     a.m = m; a.n = m; a.K = K;
-    a.status = status ? status : abort_word();
+    a.status = ozaki_call_status(status, st);
     hb->args[i] = a;
     hb->tiles_n[i] = (m + kOzBN - 1) / kOzBN;
     hb->tiles_m[i] = (2 * m + kOzBM - 1) / kOzBM;

@@ -7,6 +7,11 @@
 #include <cuda_bf16.h>
 
 namespace msts {
+// The status word a tensor-core call publishes its timeouts in: `status`
+// itself, or (status == NULL) a library word on the current device, cleared
+// on `st` first.  One call that runs several tensor-core launches takes it
+// once and passes it to all of them.
+uint32_t *ozaki_call_status(uint32_t *status, cudaStream_t st);
 // Workspace for the digit planes of triu(U) and X and their exponents.
 size_t ozaki_workspace_bytes(int m, int n);
 // Splits triu(U) into BF16 digit planes (once per matrix).

@@ -669,6 +669,9 @@ static cudaError_t run_nb(const ProbTable &tab, const EngineProblem *probs, int 
 cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe, bool conj,
                        bool shortcut, void *ws, uint32_t *status, cudaStream_t st, bool lp) {
   char *cur = static_cast<char *>(ws);
+  bool any_oz = false;
+  for (int i = 0; i < count; ++i) any_oz = any_oz || probs[i].oz != nullptr;
+  if (any_oz) status = ozaki_call_status(status, st);   // one word (cleared once) for every step
   for (int base = 0; base < count; base += kMaxProbs) {
     const int cnt = std::min(kMaxProbs, count - base);
     ProbTable tab;

@@ -242,3 +242,36 @@ def test_binding_signatures_match_the_header(lib):
         assert fn.argtypes is not None, f"{name}: no ctypes signature in load_library"
         assert [_ctypes_kind(t) for t in fn.argtypes] == [_c_kind(p) for p in params], name
         assert _ctypes_kind(fn.restype) == _c_kind(ret), name
+
+
+def test_static_scratch_entry_rejects_invalid_arguments_without_launch(lib):
+    """msts_safe_solve_static checks its arguments on the host, numbered as
+    msts_solve without the workspace arguments, before anything is launched
+    (no GPU is needed for any of these calls)."""
+    f = lib.msts_safe_solve_static
+    P, A8 = ctypes.c_void_p(256), ctypes.c_void_p(8)
+    assert f(P, 1, -1, P, 1, P, 1, P, P, 32, None, None) == -3          # negative m
+    assert f(P, 3, 4, P, 1, P, 4, P, P, 32, None, None) == -2           # ldu < m
+    assert f(None, 4, 4, P, 1, P, 4, P, P, 32, None, None) == -1        # no U
+    assert f(P, 4, 4, None, 1, P, 4, P, P, 32, None, None) == -4        # no shifts
+    assert f(P, 4, 4, P, 1, None, 4, P, P, 32, None, None) == -6        # no B
+    assert f(P, 4, 4, P, 1, P, 3, P, P, 32, None, None) == -7           # ldb < m
+    assert f(P, 4, 4, P, 1, P, 4, None, P, 32, None, None) == -8        # no scales
+    assert f(P, 4, 4, P, 1, P, 4, P, None, 32, None, None) == -9        # no scale_exp
+    assert f(P, 4, 4, P, 1, P, 4, P, P, 48, None, None) == -10          # bad nb
+    assert f(A8, 4, 4, P, 1, P, 4, P, P, 32, None, None) == -1002       # misaligned U
+    assert f(P, 4, 4, A8, 1, P, 4, P, P, 32, None, None) == -1002       # misaligned shifts
+    assert f(P, 4, 4, P, 1, A8, 4, P, P, 32, None, None) == -1002       # misaligned B
+    assert f(None, 1, 0, None, 0, None, 1, None, None, 32, None, None) == 0   # empty: no-op
+    assert f(P, 4, 4, None, 0, None, 4, None, None, 32, None, None) == 0      # no shifts: no-op
+
+
+def test_static_scratch_entry_rejects_oversized_problem(lib):
+    """A problem whose scratch exceeds the 16 MiB static array is refused with
+    MSTS_ERR_STATIC_SCRATCH before any launch.  The pointers are never
+    dereferenced; the size is checked first so that the call cannot reach a
+    kernel even if the limit changes."""
+    m = n = 20000
+    assert lib.msts_solve_workspace_size(m, n, 32, msts.MSTS_SAFE) > 16 << 20
+    P = ctypes.c_void_p(256)
+    assert lib.msts_safe_solve_static(P, m, m, P, n, P, m, P, P, 32, None, None) == -1001
