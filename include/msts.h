@@ -66,6 +66,9 @@ typedef struct { double re, im; } msts_z;
                                   on the BF16 tensor cores instead of FP64 FMA (single problem);
                                   msts_back_transform: the product X = Q Z likewise */
 #define MSTS_NORMALIZE_COLUMNS 16u /* msts_back_transform: scale every column of X to unit 2-norm */
+#define MSTS_MIXED_FP32_GEMM 32u   /* msts_solve_mixed: the low-precision substitution product with FP32
+                                      FMAs on the CUDA cores instead of the tensor cores' 3-plane
+                                      split-BF16 product */
 
 /* status bits */
 #define MSTS_STATUS_ZERO_PIVOT  1u  /* plain solve: some U(i,i) - s_j == 0 exactly (X is undefined) */
@@ -82,6 +85,18 @@ typedef struct { double re, im; } msts_z;
 
 /* Library version as 10000*major + 100*minor + patch. */
 int msts_version(void);
+
+/* Tuning knobs (no counterpart in the paper; the choices change no result bit,
+ * only the speed).  Process-wide; set them between calls, not while a call is
+ * being launched from another host thread.
+ * MSTS_TUNE_DIAG_LANES: the diagonal-block step for n_b = 32 of the standard
+ *   solves spreads each shift's rows over four warps with 1, 2 or 4 lanes per
+ *   shift; 0 (default) picks the width per launch from the number of active
+ *   shifts, 1 / 2 / 4 force it, -1 takes the one-warp layout (a group of
+ *   lanes per shift inside one warp) instead.
+ * Returns 0, -1 (unknown knob) or -2 (invalid value). */
+#define MSTS_TUNE_DIAG_LANES 1
+int msts_tune_set(int32_t knob, int32_t value);
 
 /* ---------------------------------------------------------------------------
  * Multi-shift triangular solve (Sec. 2, Eq. 2, Alg. 3) and its safe variant
@@ -374,15 +389,24 @@ int msts_adjoint_batched_flags(const msts_adjoint_problem *probs, int64_t batch,
  *                               eta = max_j ||R_j||_inf / (||U - s_j I||_inf ||x_j||_inf + ||b_j||_inf),
  *                               stop if eta <= tol or after max_iter corrections,
  *                               X += solve_lp(R)
- * where solve_lp is the blocked solve of Alg. 3 whose substitution GEMM
- * multiplies in FP32 (diagonal blocks in FP64).
- * B (read only) and X (written, ldx) are m x n.  flags: 0 computes the
- * residual with FP64 FMAs; MSTS_RESIDUAL_OZAKI computes the product triu(U) X
+ * where solve_lp is the blocked solve of Alg. 3 whose substitution GEMM is
+ * a low-precision product (diagonal blocks in FP64).  By default that product
+ * runs on the BF16 tensor cores: U(I0,I1) and X(I1,:) are split into their 3
+ * leading signed 7-bit digit planes (3 BF16 pieces per entry below a power of
+ * two per row of U and per column of X), the 6 plane pairs with s + t <= 4 are
+ * multiplied with FP32 accumulation in tensor memory and their sum is formed
+ * in FP32 (about 2^-20 relative to K max|U(r,:)| max|X(:,j)|; n_b = 16 or 32;
+ * with n_b = 64 the substitution step is the FP64-accurate 8-plane product);
+ * with MSTS_MIXED_FP32_GEMM it is an FP32 FMA product on the CUDA cores.
+ * B (read only) and X (written, ldx) are m x n.  Residual: without
+ * MSTS_RESIDUAL_OZAKI it is computed with FP64 FMAs; MSTS_RESIDUAL_OZAKI computes the product triu(U) X
  * on the BF16 tensor cores from 8 seven-bit digit planes per operand with
  * exact FP32 accumulation per 64-wide K chunk and integer accumulation across
  * chunks (accurate to ~2^-50 relative to K max|U(r,:)| max|X(:,j)|), and
- * needs msts_solve_mixed_workspace_size(m, n, nb, flags) bytes (about
- * 32 m (m + n) bytes more).
+ * needs about 32 m (m + n) bytes more workspace; the tensor-core
+ * low-precision product needs the digit planes of U's block panels (about
+ * 32 m^2 bytes for n_b = 32); msts_solve_mixed_workspace_size(m, n, nb,
+ * flags) gives the total.
  * SYNCHRONOUS: the convergence test reads eta on the host every iteration, so
  * the call returns after the work is done.  *iters (host, may be NULL)
  * receives the number of corrections, *eta the final max eta and
@@ -419,7 +443,9 @@ int msts_residual(const msts_z *U, int64_t ldu, int64_t m,
  * msts_trace_begin(capacity): from now on, bracket each launch of the hot
  *   kernels (MSTS_KERNEL_GEMM: the substitution GEMM or FP64 residual,
  *   MSTS_KERNEL_DIAG: the diagonal-block solve, MSTS_KERNEL_OZAKI: the
- *   tensor-core residual) with CUDA events on its stream, for at most
+ *   tensor-core substitution step and products, MSTS_KERNEL_RESIDUAL: the
+ *   tensor-core residual, MSTS_KERNEL_LANCZOS: the Lanczos step) with CUDA
+ *   events on its stream, for at most
  *   `capacity` launches, recording the algorithmic FLOPs (8 per complex
  *   multiply-add) and algorithmic bytes of each launch.  The 2 x capacity
  *   events are created by this call and destroyed by msts_trace_end, so the
@@ -430,7 +456,9 @@ int msts_residual(const msts_z *U, int64_t ldu, int64_t m,
  * ------------------------------------------------------------------------- */
 #define MSTS_KERNEL_GEMM 0
 #define MSTS_KERNEL_DIAG 1
-#define MSTS_KERNEL_OZAKI 2   /* tensor-core residual; FLOPs = BF16 MMA FLOPs issued */
+#define MSTS_KERNEL_OZAKI 2   /* tensor-core substitution step or product; FLOPs = BF16 MMA FLOPs issued */
+#define MSTS_KERNEL_RESIDUAL 3 /* tensor-core residual of the mixed solve; FLOPs = BF16 MMA FLOPs issued */
+#define MSTS_KERNEL_LANCZOS 4  /* Lanczos step of the pseudospectra (vector passes, HBM-bound) */
 uint64_t msts_launch_count(void);
 int msts_trace_begin(int64_t capacity);
 int msts_trace_end(void);

@@ -26,7 +26,7 @@ __all__ = [
     "MSTS_SAFE", "MSTS_CONJ_TRANS", "STATUS_BITS", "colmajor", "load_library", "library_path",
     "msts_solve", "msts_solve_batched", "msts_trevc", "msts_pseudospectra", "msts_adjoint",
     "msts_adjoint_batched", "msts_solve_mixed", "msts_residual", "MSTS_RESIDUAL_OZAKI",
-    "MSTS_TENSOR_GEMM", "MSTS_NORMALIZE_COLUMNS", "msts_back_transform", "eig",
+    "MSTS_TENSOR_GEMM", "MSTS_NORMALIZE_COLUMNS", "MSTS_MIXED_FP32_GEMM", "msts_back_transform", "eig",
     "msts_gsolve", "msts_gtrevc", "geig", "msts_solve_variant",
     "msts_pseudospectra_1norm", "msts_portrait_grid", "spectral_portrait",
     "MultiShiftSolve", "multishift_solve",
@@ -38,6 +38,7 @@ MSTS_CONJ_TRANS = 2
 MSTS_RESIDUAL_OZAKI = 4
 MSTS_TENSOR_GEMM = 8
 MSTS_NORMALIZE_COLUMNS = 16
+MSTS_MIXED_FP32_GEMM = 32
 STATUS_BITS = {
     1: "ZERO_PIVOT", 2: "NONFINITE", 4: "RANGE", 8: "SCALED", 16: "DELTA", 32: "NOT_CONVERGED",
     64: "TIMEOUT",
@@ -89,6 +90,8 @@ def load_library():
         lib.msts_trace_end.argtypes = []
         lib.msts_trace_query.restype = ctypes.c_int
         lib.msts_trace_query.argtypes = [_i32, _vp, _vp, _vp, _vp]
+        lib.msts_tune_set.restype = ctypes.c_int
+        lib.msts_tune_set.argtypes = [_i32, _i32]
         lib.msts_inject_fallback_status.restype = ctypes.c_int
         lib.msts_inject_fallback_status.argtypes = [_u32, _vp]
         lib.msts_safe_solve_static.restype = ctypes.c_int
@@ -232,6 +235,18 @@ def _status(device, status):
     return torch.zeros(1, dtype=torch.int32, device=device) if status is None else status
 
 
+def _tuned(kind, m, n, tensor, nb):
+    """(nb, context): an explicit nb as given with the library's own layout
+    choice; nb=None takes the autotuner's cached choice for this call kind and
+    shape (timing the candidates on first use) and applies its layout."""
+    import contextlib
+    if nb is not None:
+        return nb, contextlib.nullcontext()
+    from . import autotune
+    nb, layout = autotune.choose(kind, m, n, tensor)
+    return nb, autotune.applied(layout)
+
+
 # --------------------------------------------------------------------------
 # entry points
 # --------------------------------------------------------------------------
@@ -239,6 +254,7 @@ def msts_solve(U, shifts, B, *, safe=False, conj_trans=False, nb=32, tensor=Fals
     """(U - s_j I) X(:,j) = scale_j B(:,j), in place on B (Alg. 3 / Alg. 5).
 
     tensor=True runs the substitution GEMM on the tensor cores (MSTS_TENSOR_GEMM).
+    nb=None takes the autotuner's choice of n_b and diagonal-step layout.
     Returns (B, scales, scale_exp, status); scales/scale_exp are None unless safe.
     """
     lib = load_library()
@@ -251,11 +267,13 @@ def msts_solve(U, shifts, B, *, safe=False, conj_trans=False, nb=32, tensor=Fals
              | (MSTS_TENSOR_GEMM if tensor else 0))
     scales = torch.empty(n, dtype=torch.float64, device=dev) if safe else None
     sexp = torch.empty(n, dtype=torch.int32, device=dev) if safe else None
+    nb, tuned = _tuned("safe" if safe else ("conj" if conj_trans else "plain"), m, n, tensor, nb)
     ws = _workspace(lib.msts_solve_workspace_size(m, n, nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
-    rc = lib.msts_solve(_ptr(U), ldu, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(scales), _ptr(sexp),
-                        nb, wp, wb, _ptr(status), flags, _stream(dev))
+    with tuned:
+        rc = lib.msts_solve(_ptr(U), ldu, m, _ptr(shifts), n, _ptr(B), ldb, _ptr(scales), _ptr(sexp),
+                            nb, wp, wb, _ptr(status), flags, _stream(dev))
     _check(rc, "msts_solve")
     return B, scales, sexp, status
 
@@ -303,7 +321,7 @@ def msts_solve_variant(A, shifts, B, *, side="left", uplo="upper", trans="N", sa
 def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, tensor=False, status=None):
     """Solves every (U, shifts, B) of `problems` in shared launches, in place on each B.
     tensor=True runs every problem's substitution step on the tensor cores, all
-    problems of a block step in one launch.
+    problems of a block step in one launch; nb=None takes the autotuner's choice.
 
     Returns (list of (scales, scale_exp) or None, status).
     """
@@ -325,10 +343,12 @@ def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, tensor=
     if not problems:
         return [], status
     flags = (MSTS_SAFE if safe else 0) | (MSTS_CONJ_TRANS if conj_trans else 0) | (MSTS_TENSOR_GEMM if tensor else 0)
+    nb, tuned = _tuned("batched", max(B.shape[0] for _, _, B in problems), len(problems), tensor, nb)
     ws = _workspace(lib.msts_solve_batched_workspace_size(arr, len(problems), nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
-    rc = lib.msts_solve_batched(arr, len(problems), nb, wp, wb, _ptr(status), flags, _stream(dev))
+    with tuned:
+        rc = lib.msts_solve_batched(arr, len(problems), nb, wp, wb, _ptr(status), flags, _stream(dev))
     _check(rc, "msts_solve_batched")
     return outs, status
 
@@ -336,7 +356,8 @@ def msts_solve_batched(problems, *, safe=False, conj_trans=False, nb=32, tensor=
 def msts_trevc(T, *, nb=32, tensor=False, status=None):
     """Triangular eigenvectors (Alg. 6): returns (Z, scales, scale_exp, status).
 
-    tensor=True runs the substitution GEMM on the tensor cores (MSTS_TENSOR_GEMM)."""
+    tensor=True runs the substitution GEMM on the tensor cores (MSTS_TENSOR_GEMM);
+    nb=None takes the autotuner's choice of n_b and diagonal-step layout."""
     lib = load_library()
     m = T.shape[0]
     ldt = _mat(T, "T", m)
@@ -345,11 +366,13 @@ def msts_trevc(T, *, nb=32, tensor=False, status=None):
     sc = torch.empty(m, dtype=torch.float64, device=dev)
     se = torch.empty(m, dtype=torch.int32, device=dev)
     flags = MSTS_TENSOR_GEMM if tensor else 0
+    nb, tuned = _tuned("trevc", m, m, tensor, nb)
     ws = _workspace(lib.msts_trevc_workspace_size(m, nb, flags), dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
-    rc = lib.msts_trevc(_ptr(T), ldt, m, _ptr(Z), max(1, m), _ptr(sc), _ptr(se), nb, wp, wb,
-                        _ptr(status), flags, _stream(dev))
+    with tuned:
+        rc = lib.msts_trevc(_ptr(T), ldt, m, _ptr(Z), max(1, m), _ptr(sc), _ptr(se), nb, wp, wb,
+                            _ptr(status), flags, _stream(dev))
     _check(rc, "msts_trevc")
     return Z, sc, se, status
 
@@ -463,6 +486,7 @@ def eig(A, *, nb=32, tensor=True, device=None):
 def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, tensor=False, status=None, workspace=None):
     """sigma_min(T - z_p I) for every grid point (Alg. 7 with Lanczos).
 
+    nb=None takes the autotuner's choice of n_b and diagonal-step layout.
     Returns (sigma_min, alpha, beta, steps, status); alpha/beta have shape (N, iters).
     """
     lib = load_library()
@@ -477,13 +501,15 @@ def msts_pseudospectra(T, z, V0, iters=20, *, nb=32, tensor=False, status=None, 
     be = torch.empty((N, iters), dtype=torch.float64, device=dev)
     st = torch.empty(N, dtype=torch.int32, device=dev)
     flags = MSTS_TENSOR_GEMM if tensor else 0
+    nb, tuned = _tuned("pseudo", m, N, tensor, nb)
     need = lib.msts_pseudospectra_workspace_size(m, N, iters, nb, flags)
     ws = workspace if workspace is not None and workspace.numel() >= need + 256 else _workspace(need, dev)
     wp, wb = _ws_ptr(ws)
     status = _status(dev, status)
-    rc = lib.msts_pseudospectra(_ptr(T), ldt, m, _ptr(z), N, _ptr(V0), ldv, iters, _ptr(sig),
-                                _ptr(al), _ptr(be), _ptr(st), nb, wp, wb, _ptr(status), flags,
-                                _stream(dev))
+    with tuned:
+        rc = lib.msts_pseudospectra(_ptr(T), ldt, m, _ptr(z), N, _ptr(V0), ldv, iters, _ptr(sig),
+                                    _ptr(al), _ptr(be), _ptr(st), nb, wp, wb, _ptr(status), flags,
+                                    _stream(dev))
     _check(rc, "msts_pseudospectra")
     return sig, al, be, st, status
 
@@ -618,6 +644,10 @@ def msts_residual(U, shifts, B, X, *, ozaki=False, status=None):
 
 def msts_solve_mixed(U, shifts, B, *, tol=1e-12, max_iter=10, nb=32, flags=0, status=None):
     """Mixed-precision solve with FP64 iterative refinement (synchronous).
+
+    flags: MSTS_RESIDUAL_OZAKI (tensor-core FP64-accurate residual) and
+    MSTS_MIXED_FP32_GEMM (FP32 FMA low-precision product instead of the tensor
+    cores' 3-plane split-BF16 one).
 
     Returns (X, info, status) with info = {"iters", "eta", "eta_before"}.
     """

@@ -1,26 +1,47 @@
-"""Block-size autotuner for the multi-shift solves.
+"""Autotuner for the multi-shift solves: block size n_b and the layout of the
+diagonal-block step.
 
-For a call shape (m, n, mode) it times every supported n_b on seeded synthetic
-inputs of that shape (workload 1's distributions for plain/conj solves,
-workload 2's for the safe solve), through the same C ABI calls the user makes,
-and caches the fastest per (m bucket, n bucket, mode, device name) in a JSON
-file (``$MSTS_AUTOTUNE_CACHE`` or ``~/.cache/msts_autotune.json``).  The GEMM
-tile and the lanes-per-shift of the diagonal step are chosen inside the library
-from the launch shape; n_b is the knob left to tune.
+For a call kind -- ``plain``, ``safe`` or ``conj`` multi-shift solve, ``trevc``,
+``pseudo`` (Lanczos pseudospectra) or ``batched`` -- and a shape, it times every
+candidate on seeded synthetic inputs of that shape (the workloads' own
+distributions), through the same C ABI calls the user makes, and caches the
+fastest per (device name, kind, substitution path, m bucket, n bucket) in a JSON
+file (``$MSTS_AUTOTUNE_CACHE`` or ``~/.cache/msts_autotune.json``).
+
+Candidates: n_b in {16, 32, 64}, and for n_b = 32 the layout of the
+diagonal-block step (``MSTS_TUNE_DIAG_LANES``): the library's own per-launch
+choice from its measured tables (0), the one-warp layout (-1), or the four-warp
+layout with 1, 2 or 4 lanes per shift.  The layouts give the same results bit
+for bit; n_b changes the blocking and therefore the rounding, not the accuracy
+class.  The GEMM tiles follow the launch shape inside the library.
+
+The binding calls ``choose`` when a function is given ``nb=None`` and applies
+the choice for the duration of that call (``applied``); the knob is
+process-wide, so tuned calls should not be issued from several host threads
+at once.
 """
 from __future__ import annotations
 
+import contextlib
 import json
+import math
 import os
 import threading
 
 import torch
 
-from . import colmajor, msts_solve
 from . import workloads as W
 
 NB_CHOICES = (16, 32, 64)
-_lock = threading.Lock()
+LAYOUTS = (0, -1, 1, 2, 4)
+KINDS = ("plain", "safe", "conj", "trevc", "pseudo", "batched")
+TUNE_DIAG_LANES = 1
+_lock = threading.RLock()
+
+
+def candidates():
+    """(nb, layout) pairs: every n_b with the library's choice, and every layout at n_b = 32."""
+    return [(nb, 0) for nb in NB_CHOICES] + [(32, lay) for lay in LAYOUTS if lay != 0]
 
 
 def _cache_path() -> str:
@@ -35,8 +56,8 @@ def _bucket(x: int) -> int:
     return b
 
 
-def _key(m, n, mode, device):
-    return f"{torch.cuda.get_device_name(device)}|{mode}|m{_bucket(m)}|n{_bucket(n)}"
+def _key(kind, m, n, tensor, device):
+    return f"{torch.cuda.get_device_name(device)}|{kind}|{'tensor' if tensor else 'fp64'}|m{_bucket(m)}|n{_bucket(n)}"
 
 
 def _load():
@@ -56,11 +77,46 @@ def _store(cache):
     os.replace(tmp, path)
 
 
-def time_nb(m, n, nb, mode="plain", device="cuda", reps=3):
-    """Median milliseconds of one solve of shape (m, n) with block size nb."""
-    dev = torch.device(device)
+@contextlib.contextmanager
+def applied(layout):
+    """Sets the diagonal-step layout knob for the duration of a call."""
+    from . import load_library
+    lib = load_library()
+    if lib.msts_tune_set(TUNE_DIAG_LANES, int(layout)) != 0:
+        raise ValueError(f"invalid diagonal-step layout {layout}")
+    try:
+        yield
+    finally:
+        lib.msts_tune_set(TUNE_DIAG_LANES, 0)
+
+
+def _runner(kind, m, n, tensor, dev):
+    """A closure running one call of this kind and shape with given (nb, layout)."""
+    from . import (colmajor, msts_pseudospectra, msts_solve, msts_solve_batched, msts_trevc)
     m_t, n_t = _bucket(m), _bucket(n)
-    if mode == "safe":
+    if kind == "trevc":
+        T = colmajor(torch.from_numpy(W.trevc_problem(m_t, seed=11)).to(dev))
+        return lambda nb: msts_trevc(T, nb=nb, tensor=tensor)
+    if kind == "pseudo":
+        # two Lanczos steps: the per-step work of the full run, in proportion
+        Tn, zn, Vn = W.pseudo_problem(m_t, grid=max(1, int(math.ceil(n_t ** 0.5))), seed=11)
+        T = colmajor(torch.from_numpy(Tn).to(dev))
+        z = torch.from_numpy(zn[:n_t]).to(dev)
+        V = colmajor(torch.from_numpy(Vn[:, :n_t].copy()).to(dev))
+        return lambda nb: msts_pseudospectra(T, z, V, 2, nb=nb, tensor=tensor)
+    if kind == "batched":
+        # n is the batch size; m the largest order (orders spread over [m/8, m])
+        probs = W.batch_problem(batch=max(1, n), m_lo=max(1, m // 8), m_hi=max(1, m), n=32, seed=11)
+        dp = [(colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
+               colmajor(torch.from_numpy(B).to(dev))) for U, s, B in probs]
+        Xs = [B.clone() for _, _, B in dp]
+
+        def run(nb):
+            for X, (_, _, B) in zip(Xs, dp):
+                X.copy_(B)
+            return msts_solve_batched([(U, s, X) for (U, s, _), X in zip(dp, Xs)], nb=nb, tensor=tensor)
+        return run
+    if kind == "safe":
         T = W.trevc_problem(m_t, seed=11)
         U = colmajor(torch.from_numpy(T).to(dev))
         g = W.rng(0, 12)
@@ -72,29 +128,48 @@ def time_nb(m, n, nb, mode="plain", device="cuda", reps=3):
         s = torch.from_numpy(sn).to(dev)
         B0 = colmajor(torch.from_numpy(Bn).to(dev))
     X = B0.clone()
-    kw = dict(safe=(mode == "safe"), conj_trans=(mode == "conj"), nb=nb)
-    msts_solve(U, s, X, **kw)                      # warm-up
-    times = []
-    for _ in range(reps):
-        X.copy_(B0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        msts_solve(U, s, X, **kw)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        times.append(e0.elapsed_time(e1))
-    return sorted(times)[len(times) // 2]
+    return lambda nb: msts_solve(U, s, X.copy_(B0), safe=(kind == "safe"), conj_trans=(kind == "conj"),
+                                 nb=nb, tensor=tensor)
 
 
-def best_nb(m, n, mode="plain", device="cuda", refresh=False):
-    """The fastest n_b for this shape (cached); mode in {"plain", "safe", "conj"}."""
-    key = _key(m, n, mode, device)
+def time_candidates(kind, m, n, tensor=False, device="cuda", reps=3):
+    """Median milliseconds of every candidate (nb, layout) for this kind and shape."""
+    if kind not in KINDS:
+        raise ValueError(f"unknown kind {kind}")
+    dev = torch.device(device)
+    run = _runner(kind, m, n, tensor, dev)
+    out = {}
+    for nb, lay in candidates():
+        with applied(lay):
+            run(nb)                                   # warm-up (kernel attributes, caches)
+            torch.cuda.synchronize(dev)
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                run(nb)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                times.append(e0.elapsed_time(e1))
+        out[(nb, lay)] = sorted(times)[len(times) // 2]
+    return out
+
+
+def choose(kind, m, n, tensor=False, device="cuda", refresh=False):
+    """The fastest (nb, layout) for this call kind and shape (cached)."""
+    key = _key(kind, m, n, tensor, device)
     with _lock:
         cache = _load()
         if not refresh and key in cache:
-            return int(cache[key]["nb"])
-        results = {nb: time_nb(m, n, nb, mode, device) for nb in NB_CHOICES}
-        nb = min(results, key=results.get)
-        cache[key] = {"nb": nb, "ms": {str(k): v for k, v in results.items()}}
+            rec = cache[key]
+            return int(rec["nb"]), int(rec["layout"])
+        results = time_candidates(kind, m, n, tensor, device)
+        nb, lay = min(results, key=results.get)
+        cache[key] = {"nb": nb, "layout": lay, "ms": {f"{a},{b}": v for (a, b), v in results.items()}}
         _store(cache)
-        return nb
+        return nb, lay
+
+
+def best_nb(m, n, mode="plain", device="cuda", refresh=False):
+    """The block size of the fastest candidate for a multi-shift solve of this shape."""
+    return choose(mode, m, n, False, device, refresh)[0]

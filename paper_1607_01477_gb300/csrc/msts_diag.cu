@@ -19,6 +19,7 @@
 #include "msts_common.cuh"
 #include "msts_digits.cuh"
 #include "msts_diag.h"
+#include "msts_diag_util.cuh"
 
 namespace msts {
 
@@ -50,109 +51,6 @@ __device__ __forceinline__ long long gmax_ll(long long v) {
   for (int o = L / 2; o > 0; o >>= 1) v = max(v, (long long)__shfl_xor_sync(0xffffffffu, v, o, L));
   return v;
 }
-
-// |z| with exactly the scaled operands and roundings of zabs_fast, the two
-// power-of-two scalings done on the exponent fields (integer operations) when
-// every operand stays a normal number; otherwise zabs_fast itself.
-__device__ __forceinline__ double zabs_exp(double2 z) {
-  const unsigned hx = (unsigned)__double2hiint(z.x) & 0x7fffffffu, lx = (unsigned)__double2loint(z.x);
-  const unsigned hy = (unsigned)__double2hiint(z.y) & 0x7fffffffu, ly = (unsigned)__double2loint(z.y);
-  const bool zx = (hx | lx) == 0u, zy = (hy | ly) == 0u;
-  if (zx && zy) return 0.0;
-  const int fx = (int)(hx >> 20), fy = (int)(hy >> 20);   // biased exponent fields
-  const int e = max(fx, fy) - 1023;
-  const bool ok = max(fx, fy) != 0 && e <= 1021 && (zx || fx - e >= 1) && (zy || fy - e >= 1);
-  if (!ok) return zabs_fast(z);
-  const double a = zx ? 0.0 : __hiloint2double((int)(hx - ((unsigned)e << 20)), (int)lx);
-  const double b = zy ? 0.0 : __hiloint2double((int)(hy - ((unsigned)e << 20)), (int)ly);
-  const double r = sqrt(fma(a, a, b * b));              // in [1, 2 sqrt 2)
-  return __hiloint2double(__double2hiint(r) + (e << 20), __double2loint(r));
-}
-// x 2^s, exact unless the result is subnormal or overflows.
-__device__ __forceinline__ double dscale(double x, int s) {
-  if (s >= 0) {
-    if (s > 1023) {
-      x *= pow2i(1023);
-      s -= 1023;
-    }
-    return x * pow2i(min(s, 1023));
-  }
-  return dshift(x, -s);
-}
-// x >= Omega for x >= 0 (false for NaN), on the exponent field.  (Range
-// tests on all bits of a double may be compiled into FP64 comparisons, which
-// cost as much as an FP64 multiply here.)
-__device__ __forceinline__ bool ge_omega(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x);
-  const unsigned e = (hi >> 20) & 0x7ffu;
-  const bool nan = e == 0x7ffu && (((hi & 0xfffffu) | (unsigned)__double2loint(x)) != 0u);
-  return e >= 0x3ffu + kOmegaExp && !nan;
-}
-// x 2^s for x >= 0 on the exponent field when x and the result are normal,
-// else dscale.
-__device__ __forceinline__ double dscale_exp(double x, int s) {
-  const int hi = __double2hiint(x);
-  const int e = (hi >> 20) & 0x7ff;
-  if (e == 0 || e == 0x7ff || e + s < 1 || e + s > 0x7fe) return dscale(x, s);
-  return __hiloint2double(hi + (s << 20), __double2loint(x));
-}
-// x 2^s on the exponent field, zero kept as it is (its sign too); otherwise
-// as dscale_exp.
-__device__ __forceinline__ double dscale_exp0(double x, int s) {
-  const int hi = __double2hiint(x);
-  if (((hi & 0x7fffffff) | __double2loint(x)) == 0) return x;
-  return dscale_exp(x, s);
-}
-__device__ __forceinline__ double2 zscale_exp(double2 z, int s) {
-  return make_double2(dscale_exp0(z.x, s), dscale_exp0(z.y, s));
-}
-// choose_k for a finite x >= Omega, from the exponent field (the same value as
-// ilogb there).
-__device__ __forceinline__ int choose_k_exp(double x) {
-  const int k = ((__double2hiint(x) >> 20) & 0x7ff) - 1023 - (kOmegaExp - 1);
-  return k < 1 ? 1 : k;
-}
-
-// z == 0 on the bit patterns, word by word.
-__device__ __forceinline__ bool zzero_words(double2 z) {
-  return ((((unsigned)__double2hiint(z.x) | (unsigned)__double2hiint(z.y)) & 0x7fffffffu) |
-          (unsigned)__double2loint(z.x) | (unsigned)__double2loint(z.y)) == 0u;
-}
-
-// 1 / p = conj(p') / |p'|^2 2^-e with p' = p 2^-e (one real division); the
-// scalings act on the exponent fields when every operand stays normal, with
-// the same values as zdiv_fast.
-__device__ __forceinline__ double2 zrecip(double2 p) {
-  const unsigned hx = (unsigned)__double2hiint(p.x) & 0x7fffffffu, hy = (unsigned)__double2hiint(p.y) & 0x7fffffffu;
-  const bool zx = (hx | (unsigned)__double2loint(p.x)) == 0u, zy = (hy | (unsigned)__double2loint(p.y)) == 0u;
-  const int fx = (int)(hx >> 20), fy = (int)(hy >> 20);
-  const int e = max(fx, fy) - 1023;                      // zexp(p) when unclamped
-  const bool ok = max(fx, fy) != 0 && e >= -1021 && e <= 1021 && (zx || fx - e >= 1) && (zy || fy - e >= 1);
-  if (!ok) return zdiv_fast(make_double2(1.0, 0.0), p);
-  const int sh = e << 20;
-  const double a = zx ? 0.0 : __hiloint2double(__double2hiint(p.x) - sh, __double2loint(p.x));
-  const double b = zy ? 0.0 : __hiloint2double(__double2hiint(p.y) - sh, __double2loint(p.y));
-  const double q = 1.0 / fma(a, a, b * b);               // |p'|^2 in [1, 8)
-  const double wr = a * q, wi = -(b * q);                // each zero or of magnitude in (2^-1077, 2]
-  // times 2^-e on the exponent fields where the result stays normal
-  auto scale = [&](double w) {
-    const int f = (__double2hiint(w) >> 20) & 0x7ff;
-    if (f == 0) return w * pow2i(-e);                    // zero or subnormal: exact as zdiv_fast
-    if (f - e < 1 || f - e > 2046) return w * pow2i(-e);
-    return __hiloint2double(__double2hiint(w) - sh, __double2loint(w));
-  };
-  return make_double2(scale(wr), scale(wi));
-}
-
-// 16 bytes from global to shared memory without passing through registers
-// (cp.async); when !full the 16 bytes are zero-filled and nothing is read.
-// Both addresses are 16-byte aligned (complex arrays are).
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool full) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(full ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // GEN: the generalized problem (appendix, Alg. 8/9), U' = U(I1,I1) - s_j V(I1,I1):
 // pivots U(i,i) - s_j V(i,i), AXPY entries U(r,i) - s_j V(r,i) (applied as
@@ -614,8 +512,34 @@ int diag_lanes(int nb, long long total_cols, bool safe) {
   return lmax;
 }
 
+// Four-warp layout (msts_diagw.cu) or one-warp layout for n_b = 32: per-launch
+// times measured on GB300 (m = n_b = 32, one launch per solve, microseconds):
+//   shifts          <= 608   1216   2432   4864   9728
+//   plain one-warp     22.5   25.6   30.3   41.3   60.8
+//         four-warp    25.5   25.9   30.2   37.9   52.4   (L = 4, 4, 4, 2, 1)
+//   safe  one-warp     26.0   31.7   39.9   54.0   82.9
+//         four-warp    33.2   33.4   38.7   52.7   79.1   (L = 4, 4, 4, 2, 1)
+// The four-warp layout pays a named-barrier hand-off per row, so it only wins
+// where enough shifts keep every sub-partition's FP64 pipe busy: above ~4000
+// active shifts (2 lanes per shift up to ~7000, then 1).
+namespace {
+int g_diag_override = 0;
+}
+void set_diag_override(int lanes) { g_diag_override = lanes; }
+
+int diagw_lanes(long long total_cols, bool safe) {
+  (void)safe;
+  if (g_diag_override > 0) return g_diag_override;
+  if (total_cols < 4000) return 0;              // one-warp layout
+  return total_cols <= 7000 ? 2 : 1;
+}
+
 cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int step, int shortcut,
                         int ncols_max, long long total_cols, uint32_t *status, cudaStream_t st, bool gen) {
+  if (nb == 32 && !gen && g_diag_override >= 0) {
+    const int lw = diagw_lanes(total_cols, safe);
+    if (lw > 0) return launch_diagw(tab, safe, conj, step, shortcut, ncols_max, lw, status, st);
+  }
   const int L = diag_lanes(nb, total_cols, safe);
 #define MSTS_DIAG_CASE(NBV)                                                                          \
   case NBV:                                                                                          \
@@ -634,3 +558,12 @@ cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int 
 }
 
 }  // namespace msts
+
+extern "C" {
+int msts_tune_set(int32_t knob, int32_t value) {
+  if (knob != MSTS_TUNE_DIAG_LANES) return -1;
+  if (value != 0 && value != -1 && value != 1 && value != 2 && value != 4) return -2;
+  msts::set_diag_override(value);
+  return 0;
+}
+}  // extern "C"

@@ -13,4 +13,14 @@ int diag_lanes(int nb, long long total_cols, bool safe);
 cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int step, int shortcut,
                         int ncols_max, long long total_cols, uint32_t *status, cudaStream_t st,
                         bool gen = false);
+// The four-warp layout of the step (msts_diagw.cu; n_b = 32, standard
+// problems): `lanes` = 1, 2 or 4 lanes per shift.
+cudaError_t launch_diagw(const ProbTable &tab, bool safe, bool conj, int step, int shortcut, int ncols_max,
+                         int lanes, uint32_t *status, cudaStream_t st);
+// Lanes per shift of the four-warp layout for a launch over total_cols
+// shifts, or 0 where the one-warp layout is faster.
+int diagw_lanes(long long total_cols, bool safe);
+// Tuning override (0 = automatic): lanes per shift of every four-warp launch,
+// or -1 to take the one-warp layout for n_b = 32 as well.
+void set_diag_override(int lanes);
 }  // namespace msts

@@ -1,0 +1,115 @@
+// msts_diag_util.cuh -- exact helpers of the diagonal-block step (both
+// kernel layouts): moduli, reciprocals and power-of-two scalings done on the
+// IEEE exponent fields where the operands stay normal, and 16-byte
+// asynchronous copies to shared memory.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "msts_common.cuh"
+
+namespace msts {
+
+// |z| with exactly the scaled operands and roundings of zabs_fast, the two
+// power-of-two scalings done on the exponent fields (integer operations) when
+// every operand stays a normal number; otherwise zabs_fast itself.
+__device__ __forceinline__ double zabs_exp(double2 z) {
+  const unsigned hx = (unsigned)__double2hiint(z.x) & 0x7fffffffu, lx = (unsigned)__double2loint(z.x);
+  const unsigned hy = (unsigned)__double2hiint(z.y) & 0x7fffffffu, ly = (unsigned)__double2loint(z.y);
+  const bool zx = (hx | lx) == 0u, zy = (hy | ly) == 0u;
+  if (zx && zy) return 0.0;
+  const int fx = (int)(hx >> 20), fy = (int)(hy >> 20);   // biased exponent fields
+  const int e = max(fx, fy) - 1023;
+  const bool ok = max(fx, fy) != 0 && e <= 1021 && (zx || fx - e >= 1) && (zy || fy - e >= 1);
+  if (!ok) return zabs_fast(z);
+  const double a = zx ? 0.0 : __hiloint2double((int)(hx - ((unsigned)e << 20)), (int)lx);
+  const double b = zy ? 0.0 : __hiloint2double((int)(hy - ((unsigned)e << 20)), (int)ly);
+  const double r = sqrt(fma(a, a, b * b));              // in [1, 2 sqrt 2)
+  return __hiloint2double(__double2hiint(r) + (e << 20), __double2loint(r));
+}
+// x 2^s, exact unless the result is subnormal or overflows.
+__device__ __forceinline__ double dscale(double x, int s) {
+  if (s >= 0) {
+    if (s > 1023) {
+      x *= pow2i(1023);
+      s -= 1023;
+    }
+    return x * pow2i(min(s, 1023));
+  }
+  return dshift(x, -s);
+}
+// x >= Omega for x >= 0 (false for NaN), on the exponent field.  (Range
+// tests on all bits of a double may be compiled into FP64 comparisons, which
+// cost as much as an FP64 multiply here.)
+__device__ __forceinline__ bool ge_omega(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const bool nan = e == 0x7ffu && (((hi & 0xfffffu) | (unsigned)__double2loint(x)) != 0u);
+  return e >= 0x3ffu + kOmegaExp && !nan;
+}
+// x 2^s for x >= 0 on the exponent field when x and the result are normal,
+// else dscale.
+__device__ __forceinline__ double dscale_exp(double x, int s) {
+  const int hi = __double2hiint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  if (e == 0 || e == 0x7ff || e + s < 1 || e + s > 0x7fe) return dscale(x, s);
+  return __hiloint2double(hi + (s << 20), __double2loint(x));
+}
+// x 2^s on the exponent field, zero kept as it is (its sign too); otherwise
+// as dscale_exp.
+__device__ __forceinline__ double dscale_exp0(double x, int s) {
+  const int hi = __double2hiint(x);
+  if (((hi & 0x7fffffff) | __double2loint(x)) == 0) return x;
+  return dscale_exp(x, s);
+}
+__device__ __forceinline__ double2 zscale_exp(double2 z, int s) {
+  return make_double2(dscale_exp0(z.x, s), dscale_exp0(z.y, s));
+}
+// choose_k for a finite x >= Omega, from the exponent field (the same value as
+// ilogb there).
+__device__ __forceinline__ int choose_k_exp(double x) {
+  const int k = ((__double2hiint(x) >> 20) & 0x7ff) - 1023 - (kOmegaExp - 1);
+  return k < 1 ? 1 : k;
+}
+
+// z == 0 on the bit patterns, word by word.
+__device__ __forceinline__ bool zzero_words(double2 z) {
+  return ((((unsigned)__double2hiint(z.x) | (unsigned)__double2hiint(z.y)) & 0x7fffffffu) |
+          (unsigned)__double2loint(z.x) | (unsigned)__double2loint(z.y)) == 0u;
+}
+
+// 1 / p = conj(p') / |p'|^2 2^-e with p' = p 2^-e (one real division); the
+// scalings act on the exponent fields when every operand stays normal, with
+// the same values as zdiv_fast.
+__device__ __forceinline__ double2 zrecip(double2 p) {
+  const unsigned hx = (unsigned)__double2hiint(p.x) & 0x7fffffffu, hy = (unsigned)__double2hiint(p.y) & 0x7fffffffu;
+  const bool zx = (hx | (unsigned)__double2loint(p.x)) == 0u, zy = (hy | (unsigned)__double2loint(p.y)) == 0u;
+  const int fx = (int)(hx >> 20), fy = (int)(hy >> 20);
+  const int e = max(fx, fy) - 1023;                      // zexp(p) when unclamped
+  const bool ok = max(fx, fy) != 0 && e >= -1021 && e <= 1021 && (zx || fx - e >= 1) && (zy || fy - e >= 1);
+  if (!ok) return zdiv_fast(make_double2(1.0, 0.0), p);
+  const int sh = e << 20;
+  const double a = zx ? 0.0 : __hiloint2double(__double2hiint(p.x) - sh, __double2loint(p.x));
+  const double b = zy ? 0.0 : __hiloint2double(__double2hiint(p.y) - sh, __double2loint(p.y));
+  const double q = 1.0 / fma(a, a, b * b);               // |p'|^2 in [1, 8)
+  const double wr = a * q, wi = -(b * q);                // each zero or of magnitude in (2^-1077, 2]
+  // times 2^-e on the exponent fields where the result stays normal
+  auto scale = [&](double w) {
+    const int f = (__double2hiint(w) >> 20) & 0x7ff;
+    if (f == 0) return w * pow2i(-e);                    // zero or subnormal: exact as zdiv_fast
+    if (f - e < 1 || f - e > 2046) return w * pow2i(-e);
+    return __hiloint2double(__double2hiint(w) - sh, __double2loint(w));
+  };
+  return make_double2(scale(wr), scale(wi));
+}
+
+// 16 bytes from global to shared memory without passing through registers
+// (cp.async); when !full the 16 bytes are zero-filled and nothing is read.
+// Both addresses are 16-byte aligned (complex arrays are).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool full) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(full ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+}  // namespace msts

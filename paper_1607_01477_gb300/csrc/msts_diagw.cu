@@ -1,0 +1,538 @@
+// msts_diagw.cu -- the diagonal-block step for n_b = 32 (standard problems,
+// Alg. 3 / Alg. 4 on the shifted block U(I1,I1) - lambda_j I, and the
+// forward substitution on the conjugate transpose), with each shift's rows
+// spread over the four warps of a CTA.
+//
+// Why this layout.  The FP64 unit of an SM sub-partition issues one warp
+// instruction per ~64 cycles whatever the number of lanes that need it.  With
+// one group of lanes per shift inside one warp, the per-row multiply
+// x_i = y_i (1 / p_i) and the partially predicated AXPY occupy whole warp
+// instructions for a few useful lanes.  Here L = 1, 2 or 4 lanes hold one
+// shift (32 / L shifts per CTA) and the rows of the block are dealt out to the
+// four warps: row r lives in warp r mod 4, lane (r / 4) mod L of the shift's
+// group, register slot r / (4 L).  Every FP64 instruction of the AXPY then
+// serves 32 / L shifts at once with no idle lane for L = 1, the per-row
+// multiply is issued by one warp only, and the four warps (one per
+// sub-partition) share the work of every shift.  The owner of row i publishes
+// x_i in shared memory and releases a named barrier; the other warps wait on
+// it.  The owner of the next row applies x_i to that row first, publishes its
+// own x, and only then applies x_i to the rest of its rows (one-row
+// lookahead), so the serial chain per row is one complex multiply-add and one
+// complex multiply.
+//
+// Every value sees the same operations in the same order as in the one-warp
+// layout (msts_diag.cu): the same reciprocals, the same fused multiply-adds
+// row by row, the same power-of-two rescales, the same replay of Alg. 4's
+// decisions; the results are the same bit for bit.  The right-hand sides and
+// the results move between global and shared memory in coalesced column
+// order.  Blocks where the replay cannot be exact (a subnormal pivot, a
+// rescale beyond 2^600) take the serial safeguarded loop of Alg. 4, one
+// thread per shift.
+#include "msts_common.cuh"
+#include "msts_diag.h"
+#include "msts_diag_util.cuh"
+#include "msts_digits.cuh"
+
+namespace msts {
+namespace {
+
+constexpr int kWNB = 32;                 // block size n_b
+constexpr int kWWarps = 4;               // warps per CTA: row owners
+constexpr int kWThreads = 32 * kWWarps;
+constexpr int kWLD = kWNB + 1;           // column stride of the staged U(I1,I1), in complex entries
+constexpr int kWLDY = kWNB + 1;          // column stride of the staged right-hand sides
+
+__device__ __forceinline__ void nbar_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kWThreads) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kWThreads) : "memory");
+}
+// named barrier of row i (ids 1..8; 0 is __syncthreads): every warp meets the
+// barriers of the rows in the same order and never runs more than one row
+// ahead of a barrier it waits on, so ids repeat safely every 8 rows.
+__device__ __forceinline__ int row_bar(int i) { return 1 + (i & 7); }
+
+template <int L>
+struct WShape {
+  static constexpr int SPC = 32 / L;               // shifts per CTA
+  static constexpr int RPT = kWNB / (kWWarps * L); // rows per thread
+};
+
+template <int L, bool SAFE>
+constexpr size_t diagw_smem() {
+  constexpr int SPC = WShape<L>::SPC;
+  return sizeof(double2) * ((size_t)kWNB * kWLD + (size_t)kWNB * SPC + (size_t)SPC * kWLDY) +
+         sizeof(double) * kWNB + sizeof(int) * ((size_t)kWNB * SPC + kWWarps * SPC + SPC) +
+         sizeof(long long) * kWWarps * SPC + 16;
+}
+
+template <int L, bool SAFE, bool CONJ>
+__global__ void __launch_bounds__(kWThreads)
+k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *status) {
+  constexpr int SPC = WShape<L>::SPC, RPT = WShape<L>::RPT, NB = kWNB, LD = kWLD, LDY = kWLDY;
+  constexpr int SLOT = kWWarps * L;      // rows per register slot
+  static_assert(!(SAFE && CONJ), "the safe solve is upper only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *sU = reinterpret_cast<double2 *>(smem_raw);      // U(I1,I1), column-major, LD
+  double2 *sX = sU + NB * LD;                                // x_i of every shift: [i SPC + js]
+  double2 *sY = sX + NB * SPC;                               // per-shift columns: [js LDY + r]
+  double *sC = reinterpret_cast<double *>(sY + SPC * LDY);   // within-block column norms
+  int *sPex = reinterpret_cast<int *>(sC + NB);              // pivot exponent fields [i SPC + js]
+  int *sRedI = sPex + NB * SPC;                              // [w SPC + js]
+  int *sShift = sRedI + kWWarps * SPC;                       // [js]
+  long long *sRedL = reinterpret_cast<long long *>(
+      (reinterpret_cast<uintptr_t>(sShift + SPC) + 7) & ~uintptr_t(7));   // [w SPC + js]
+
+  pdl_wait();                            // B, the safe state and the planes' buffer come from the kernel before
+  const Prob &P = tab.p[blockIdx.z];
+  if (step >= P.nblk) return;
+  const int b = CONJ ? P.nblk - 1 - step : step;
+  int lo, hi;
+  block_range(P, b, NB, lo, hi);
+  const int nbf = hi - lo;
+  const int jstart = shortcut ? lo + 1 : 0;
+  const int jcta = jstart + blockIdx.x * SPC;
+  if (jcta >= P.n) return;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int js = lane / L, h = lane % L;
+  const int j = jcta + js;
+  const bool active = j < P.n;
+  auto nbe_of = [&](int jj) { return shortcut ? min(hi, jj) - lo : nbf; };   // TREVC: rows >= j stay zero
+  const int nbe = active ? nbe_of(j) : 0;
+  auto row_of = [&](int q) { return w + 4 * (h + L * q); };
+
+  // Global loads first (one round trip): the shift, delta and (safe) the
+  // column's scale state and C_blk; then U(I1,I1) and the block's right-hand
+  // sides by asynchronous 16-byte copies in coalesced order.
+  double2 lam = active ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
+  const double dlt = SAFE ? *P.delta : 0.0;
+  int e_col = 0;
+  double G_col = 0.0;
+  if (SAFE && active) {
+    e_col = P.e[j];
+    G_col = P.G[j];
+  }
+  const double cblk = SAFE ? P.cblk[b] : 0.0;
+  for (int idx = tid; idx < NB * NB; idx += kWThreads) {
+    const int c = idx / NB, r = idx - c * NB;
+    const bool in = r <= c && c < nbf;
+    cp_async16(&sU[c * LD + r], in ? &P.U[(lo + r) + (long long)(lo + c) * P.ldu] : P.U, in);
+  }
+  for (int idx = tid; idx < SPC * NB; idx += kWThreads) {
+    const int c = idx / NB, r = idx - c * NB, jj = jcta + c;
+    const bool in = jj < P.n && r < nbe_of(jj);
+    cp_async16(&sY[c * LDY + r], in ? &P.B[(long long)jj * P.ldb + lo + r] : P.B, in);
+  }
+  if (SAFE)
+    for (int k = tid; k < NB; k += kWThreads) sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
+  cp_async_wait_all();
+  __syncthreads();
+
+  if (CONJ) lam = zconj(lam);
+  auto pivot0 = [&](int i) {
+    const double2 d = sU[i * LD + i];
+    return zsub(CONJ ? zconj(d) : d, lam);
+  };
+  auto pivot = [&](int i) {
+    double2 p = pivot0(i);
+    if (SAFE && zzero_words(p)) p = make_double2(dlt, 0.0);   // U(i,i) = lambda -> delta (Sec. 3)
+    return p;
+  };
+
+  double2 y[RPT], inv[RPT];
+  int pex[RPT];
+  bool zero_piv = false;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = row_of(q);
+    const bool v = r < nbe;
+    y[q] = sY[js * LDY + r];
+    const double2 p0 = pivot0(r);
+    zero_piv |= v && zzero_words(p0);
+    const double2 p = pivot(r);
+    inv[q] = v ? zrecip(p) : make_double2(0.0, 0.0);
+    pex[q] = (int)(max(absbits(p.x), absbits(p.y)) >> 52);
+    if (SAFE) sPex[r * SPC + js] = pex[q];
+  }
+  if (zero_piv) raise_status(status, SAFE ? MSTS_STATUS_DELTA : MSTS_STATUS_ZERO_PIVOT);
+
+  // max_r |y_r| over the shift's block rows (all four warps), as in the
+  // one-warp layout: common power-of-two scale, then the largest square.
+  auto maxabs = [&]() {
+    int E = -1022;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) E = max(E, zexp(y[q]));
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o, L));
+    __syncthreads();
+    if (h == 0) sRedI[w * SPC + js] = E;
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < kWWarps; ++v) E = max(E, sRedI[v * SPC + js]);
+    const double sc = pow2i(-E);
+    long long m2 = 0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const double a = y[q].x * sc, bb = y[q].y * sc;
+      m2 = max(m2, __double_as_longlong(fma(a, a, bb * bb)));
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) m2 = max(m2, (long long)__shfl_xor_sync(0xffffffffu, m2, o, L));
+    if (h == 0) sRedL[w * SPC + js] = m2;
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < kWWarps; ++v) m2 = max(m2, sRedL[v * SPC + js]);
+    return sqrt(__longlong_as_double(m2)) * pow2i(E);
+  };
+
+  // ----- the substitution -----------------------------------------------------
+  // Safe variant, phase A: the block is solved in a power-of-two scaling of
+  // its own, kept clear of overflow by integer bounds on the exponents (every
+  // thread of a shift runs the same bound chain); rescales apply to all rows.
+  double G0 = 0.0;
+  int Eb = 0, Kown = 0;
+  bool patho = false;
+  int kpre[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) kpre[q] = 0;
+  if (SAFE) {
+    G0 = maxabs();
+    Eb = G0 == 0.0 ? -1100 : (int)(__double_as_longlong(G0) >> 52) - 1022;
+  }
+  // Alg. 4's bound chain for row i: returns the rescale exponent taken there.
+  auto chain = [&](int i) -> int {
+    const int pi = sPex[i * SPC + js];
+    patho |= i < nbe && pi == 0;         // subnormal pivot: |p| >= 2^(pi - 1023) fails
+    const int eC = (int)(__double_as_longlong(sC[i]) >> 52) - 1022;
+    const int xb = Eb + 1025 - pi;
+    int cand = i < nbe ? max(xb + max(eC, 0), Eb) + 1 : Eb;
+    int kk = 0;
+    if (cand > 1010) {                   // keep clear of overflow
+      kk = cand - 900;
+      patho |= kk > 600;                 // e.g. a pivot near the bottom of the range
+      Kown += kk;
+      cand -= kk;
+    }
+    Eb = cand;
+    return kk;
+  };
+  auto rescale_slot = [&](int q, int kk) { y[q] = zscale_exp(y[q], -kk); };
+
+  // the AXPY of x_i into the rows of slot q (qs: slot of row i)
+  auto axpy_slot = [&](int q, int qs, int i, double2 x) {
+    const int r = row_of(q);
+    if (!CONJ) {
+      if (q < qs || (q == qs && r < i)) y[q] = zfms(y[q], x, sU[i * LD + r]);
+    } else {
+      if (q > qs || (q == qs && r > i)) y[q] = zfms(y[q], x, zconj(sU[r * LD + i]));
+    }
+  };
+  // Row i (slot qn of its owner) by its owner warp: x_i = y_i / p_i, published.
+  auto produce = [&](int qn, int i, int kk) {
+    const int hi_ = (i >> 2) & (L - 1);
+    if (SAFE && kk) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+        if (q == qn) rescale_slot(q, kk);
+    }
+    double2 yq = y[0], iq = inv[0];
+#pragma unroll
+    for (int q = 1; q < RPT; ++q)
+      if (q == qn) { yq = y[q]; iq = inv[q]; }
+    double2 x = zmul(yq, iq);
+    if (L > 1) x = make_double2(__shfl_sync(0xffffffffu, x.x, hi_, L), __shfl_sync(0xffffffffu, x.y, hi_, L));
+    if (h == hi_) {
+      if (SAFE) sY[js * LDY + i] = yq;   // the row's value at its diagonal step (for the replay)
+      sX[i * SPC + js] = x;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+        if (q == qn) {
+          y[q] = x;
+          if (SAFE) kpre[q] = Kown;
+        }
+    }
+    __threadfence_block();
+    nbar_arrive(row_bar(i));
+    return x;
+  };
+
+  // chain state: kk_cur is the rescale of the current row, kk_nxt of the next
+  {
+    const int i0 = CONJ ? 0 : NB - 1;
+    int kk_cur = SAFE ? chain(i0) : 0;
+    double2 xown = make_double2(0.0, 0.0);
+    if (w == (i0 & 3)) {                 // prologue: the first row's owner
+      if (SAFE && kk_cur) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) rescale_slot(q, kk_cur);
+      }
+      xown = produce(CONJ ? 0 : RPT - 1, i0, 0);
+    }
+    bool rescaled_ahead = w == (i0 & 3);  // this warp applied kk_cur to all its rows already
+#pragma unroll
+    for (int s_ = 0; s_ < RPT; ++s_) {
+      const int qs = CONJ ? s_ : RPT - 1 - s_;
+#pragma unroll 1
+      for (int u_ = 0; u_ < SLOT; ++u_) {
+        const int k = CONJ ? u_ : SLOT - 1 - u_;
+        const int i = SLOT * qs + k;
+        const bool last = CONJ ? i == NB - 1 : i == 0;
+        const int inext = CONJ ? i + 1 : i - 1;
+        const int kk_nxt = (SAFE && !last) ? chain(inext) : 0;
+        if (SAFE && kk_cur && !rescaled_ahead) {
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) rescale_slot(q, kk_cur);
+        }
+        double2 x;
+        if (w == (i & 3)) {
+          x = xown;
+        } else {
+          nbar_sync(row_bar(i));
+          x = sX[i * SPC + js];
+        }
+        rescaled_ahead = false;
+        if (!last && w == (inext & 3)) {
+          // next row's owner: that row first, publish it, then the rest
+          const bool same = CONJ ? k < SLOT - 1 : k > 0;
+          if (same) {
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+              if (q == qs) axpy_slot(q, qs, i, x);
+            xown = produce(qs, inext, kk_nxt);
+          } else {
+            constexpr int dq = CONJ ? 1 : -1;
+            const int qn = qs + dq;          // compile-time after unrolling
+            if (qn >= 0 && qn < RPT) {
+#pragma unroll
+              for (int q = 0; q < RPT; ++q)
+                if (q == qn) axpy_slot(q, qs, i, x);
+              xown = produce(qn, inext, kk_nxt);
+            }
+          }
+          const int qn = same ? qs : qs + (CONJ ? 1 : -1);
+#pragma unroll
+          for (int q = 0; q < RPT; ++q)
+            if (q != qn) {
+              axpy_slot(q, qs, i, x);
+              if (SAFE && kk_nxt) rescale_slot(q, kk_nxt);
+            }
+          rescaled_ahead = true;
+        } else {
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) axpy_slot(q, qs, i, x);
+        }
+        kk_cur = kk_nxt;
+      }
+    }
+  }
+  __syncthreads();                       // every x_i read; sX and sY free for reuse
+
+  int kexp = 0;
+  if (SAFE) {
+    double *sA = reinterpret_cast<double *>(sX);                       // a_i = |x_i| C_i   [i SPC + js]
+    int *sEm = reinterpret_cast<int *>(sA + NB * SPC);                 // exponent of M_i   [i SPC + js]
+    auto ccol = [&](int i) { return sC[i]; };
+    const bool any_patho = __syncthreads_or(active && patho);
+    if (!any_patho) {
+      // phase B: per owned row, a_r = |x_r| C_r in the final own scaling and
+      // the exponent of M_r = |y_r| / |p_r| in the unscaled one
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = row_of(q);
+        double a = 0.0;
+        int em = -(1 << 28);
+        if (r < nbe) {
+          a = __dmul_rn(zabs_exp(y[q]), ccol(r));
+          const double2 yp = sY[js * LDY + r];
+          if (!zzero_words(yp)) {
+            // floor(log2 M) <= ey - ep + 1 for normal operands; Alg. 4's test
+            // (M 2^(kpre - Ka) >= Omega with Ka >= 0) can only fire above it.
+            const int ey = (int)(((unsigned)max(__double2hiint(yp.x) & 0x7fffffff,
+                                                __double2hiint(yp.y) & 0x7fffffff)) >> 20);
+            const int up = ey - pex[q] + 1 + kpre[q];
+            em = (ey != 0 && pex[q] != 0 && up < kOmegaExp) ? up : ratio_exp_fast(yp, pivot(r)) + kpre[q];
+          }
+        }
+        sA[r * SPC + js] = a;
+        sEm[r * SPC + js] = em;
+      }
+      __syncthreads();
+      // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this block
+      int Ka = 0;
+      double G = G0;
+#pragma unroll 4
+      for (int u_ = 0; u_ < NB; ++u_) {
+        const int i = NB - 1 - u_;
+        if (i < nbe) {
+          const double ai = sA[i * SPC + js];
+          const int eM = sEm[i * SPC + js] - Ka;
+          if (eM >= kOmegaExp) {             // M >= Omega: rescale b first
+            const int kk = eM - (kOmegaExp - 1);
+            Ka += kk;
+            G = dscale_exp(G, -kk);
+          }
+          G = __dadd_rn(G, dscale_exp(ai, Kown - Ka));
+          if (ge_omega(G)) {                 // protect the AXPY
+            const int kk = choose_k_exp(G);
+            Ka += kk;
+            G = dscale_exp(G, -kk);
+          }
+        }
+      }
+      // phase D: to Alg. 4's scaling
+      kexp = Ka;
+      if (Kown != Ka) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) y[q] = zscale_exp(y[q], Kown - Ka);
+      }
+    } else {
+      // The serial safeguarded back substitution (Alg. 4, second branch) from
+      // the block's right-hand side, one thread per shift, the shift's rows in
+      // shared memory; the same operations in the same order as the one-warp
+      // layout's serial path.
+      if (w == 0 && h == 0) {
+        double2 *ys = sY + js * LDY;
+        for (int r = 0; r < NB; ++r) ys[r] = r < nbe ? P.B[(long long)j * P.ldb + lo + r] : make_double2(0.0, 0.0);
+        double G = G0;
+        for (int u_ = 0; u_ < NB; ++u_) {
+          const int i = NB - 1 - u_;
+          const double2 yi = ys[i];
+          int eM = -100000;
+          if (i < nbe && !zzero_words(yi)) eM = ratio_exp_fast(yi, pivot(i));
+          if (eM >= kOmegaExp) {             // M >= Omega: rescale b first
+            const int kk = eM - (kOmegaExp - 1);
+            for (int r = 0; r < NB; ++r) ys[r] = zshift(ys[r], kk);
+            kexp += kk;
+            G = dshift(G, kk);
+          }
+          // diagonal step by a division: the reciprocal of a subnormal pivot may overflow
+          double2 xi = i < nbe ? zdiv_fast(ys[i], pivot(i)) : make_double2(0.0, 0.0);
+          ys[i] = xi;
+          if (i < nbe) {
+            G = __dadd_rn(G, __dmul_rn(zabs_exp(xi), ccol(i)));
+            if (ge_omega(G)) {               // protect the AXPY
+              const int kk = choose_k(G);
+              for (int r = 0; r < NB; ++r) ys[r] = zshift(ys[r], kk);
+              xi = zshift(xi, kk);
+              kexp += kk;
+              G = dshift(G, kk);
+            }
+          }
+          for (int r = 0; r < i; ++r) ys[r] = zfms(ys[r], xi, sU[i * LD + r]);
+        }
+        sShift[js] = kexp;
+      }
+      __syncthreads();
+      kexp = sShift[js];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) y[q] = sY[js * LDY + row_of(q)];
+    }
+  }
+
+  // Alg. 5: t < 1 rescales the rest of the column (lazily: the substitution
+  // step applies it to I0 and the final fix-up to I2), then
+  // G(j) += C_blk ||X(I1,j)||_inf with a whole-column rescale at Omega.
+  int ej = 0, pend = 0, k2 = 0;
+  double Gj = 0.0;
+  if (SAFE) {
+    const double N = maxabs();
+    if (active) {
+      ej = e_col;
+      Gj = G_col;
+      if (kexp > 0) { ej += kexp; Gj = dscale_exp0(Gj, -kexp); pend = kexp; }
+      Gj = __dadd_rn(Gj, __dmul_rn(cblk, N));
+      if (Gj >= omega()) {
+        k2 = choose_k_exp(Gj);
+        ej += k2;
+        Gj = dscale_exp(Gj, -k2);
+        pend += k2;
+      }
+    }
+  }
+
+  // results through shared memory: coalesced column stores, and the digit
+  // planes of X(I1,:) with one exponent per column for the tensor-core step
+  __syncthreads();                       // sY free (replay / serial path done)
+  int e = -(1 << 29);
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const double2 xo = (SAFE && k2) ? zscale_exp(y[q], -k2) : y[q];
+    sY[js * LDY + row_of(q)] = xo;
+    e = max(e, bound_exp(xo));
+  }
+  const bool planes = P.oz_bp != nullptr && (CONJ ? P.m - hi : lo) > 0;
+  if (planes) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o, L));
+    if (h == 0) sRedI[w * SPC + js] = e;
+  }
+  if (SAFE && active && w == 0 && h == 0) {
+    P.e[j] = ej;
+    P.G[j] = Gj;
+    P.pend[j] = pend;
+    P.E[(long long)b * P.n + j] = ej;
+    if (pend > 0) raise_status(status, MSTS_STATUS_SCALED);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < SPC * NB; idx += kWThreads) {
+    const int c = idx / NB, r = idx - c * NB, jj = jcta + c;
+    if (jj < P.n && r < nbe_of(jj)) P.B[(long long)jj * P.ldb + lo + r] = sY[c * LDY + r];
+  }
+  if (planes) {
+    if (tid < SPC) {
+      int ec = sRedI[tid];
+#pragma unroll
+      for (int v = 1; v < kWWarps; ++v) ec = max(ec, sRedI[v * SPC + tid]);
+      sShift[tid] = ec < -(1 << 28) ? 0 : ec;
+    }
+    __syncthreads();
+    const int ncols = P.n - jstart, kw = P.oz_kb / 2;
+    for (int idx = tid; idx < SPC * kw; idx += kWThreads) {
+      const int c = idx / kw, r = idx - c * kw, jj = jcta + c;
+      if (jj >= P.n) continue;
+      const int cc = jj - jstart;
+      if (r == 0) P.oz_cexp[cc] = sShift[c];
+      uint32_t wd[kOzS];
+      if (r < NB) {
+        digit_pairs(sY[c * LDY + r], sShift[c], wd);
+      } else {
+#pragma unroll
+        for (int t = 0; t < kOzS; ++t) wd[t] = 0u;   // K padding beyond n_b rows
+      }
+#pragma unroll
+      for (int t = 0; t < kOzS; ++t) P.oz_bp[(size_t)(t * ncols + cc) * kw + r] = wd[t];
+    }
+  }
+}
+
+template <int L, bool SAFE, bool CONJ>
+cudaError_t launch_w(const ProbTable &tab, int step, int shortcut, int ncols_max, uint32_t *status,
+                     cudaStream_t st) {
+  constexpr size_t smem = diagw_smem<L, SAFE>();
+  constexpr int SPC = WShape<L>::SPC;
+  cudaError_t e = cudaFuncSetAttribute(k_diagw<L, SAFE, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_diagw<L, SAFE, CONJ>, dim3((ncols_max + SPC - 1) / SPC, 1, tab.count), dim3(kWThreads),
+                    smem, st, tab, step, shortcut, status);
+}
+
+template <bool SAFE, bool CONJ>
+cudaError_t launch_wl(int L, const ProbTable &tab, int step, int shortcut, int ncols_max, uint32_t *status,
+                      cudaStream_t st) {
+  if (L >= 4) return launch_w<4, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+  if (L == 2) return launch_w<2, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+  return launch_w<1, SAFE, CONJ>(tab, step, shortcut, ncols_max, status, st);
+}
+
+}  // namespace
+
+cudaError_t launch_diagw(const ProbTable &tab, bool safe, bool conj, int step, int shortcut, int ncols_max,
+                         int lanes, uint32_t *status, cudaStream_t st) {
+  if (safe) return launch_wl<true, false>(lanes, tab, step, shortcut, ncols_max, status, st);
+  if (conj) return launch_wl<false, true>(lanes, tab, step, shortcut, ncols_max, status, st);
+  return launch_wl<false, false>(lanes, tab, step, shortcut, ncols_max, status, st);
+}
+
+}  // namespace msts

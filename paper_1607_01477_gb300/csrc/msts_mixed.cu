@@ -7,10 +7,13 @@
 //            stop when max_j eta_j <= tol (or at the iteration cap)
 //            X += solve_lp(R)
 //
-// solve_lp is the blocked multi-shift solve whose substitution GEMM multiplies
-// in FP32 (the diagonal blocks stay FP64).  The residual is computed in FP64
-// DFMA (k_residual) or, with MSTS_RESIDUAL_OZAKI, by the FP64-accurate
-// tensor-core product of msts_ozaki.cu.
+// solve_lp is the blocked multi-shift solve whose substitution GEMM is a
+// low-precision product (the diagonal blocks stay FP64): by default the
+// tensor cores' 3-plane split-BF16 product with FP32 accumulation
+// (k_oz_update<3>, msts_ozaki.cu), with MSTS_MIXED_FP32_GEMM an FP32 FMA
+// product on the CUDA cores.  The residual is computed in FP64 DFMA
+// (k_residual) or, with MSTS_RESIDUAL_OZAKI, by the FP64-accurate tensor-core
+// product of msts_ozaki.cu.
 #include <algorithm>
 #include <vector>
 
@@ -157,7 +160,7 @@ size_t mixed_workspace_bytes(int m, int n, int nb, uint32_t flags) {
   s += a256(sizeof(double) * (size_t)m);              // off-diagonal row sums
   s += a256(sizeof(double) * 2);                      // max eta
   if (flags & MSTS_RESIDUAL_OZAKI) s += ozaki_workspace_bytes(m, n);
-  (void)nb;
+  if (!(flags & MSTS_MIXED_FP32_GEMM)) s += a256(ozaki_plan_bytes(m, n, nb));
   return s;
 }
 
@@ -186,6 +189,9 @@ cudaError_t mixed_run(const double2 *U, long long ldu, int m, const double2 *s, 
   double *rs = reinterpret_cast<double *>(cur); cur += a256(sizeof(double) * (size_t)m);
   double *emax = reinterpret_cast<double *>(cur); cur += a256(sizeof(double) * 2);
   void *oz_ws = cur;
+  if (flags & MSTS_RESIDUAL_OZAKI) cur += ozaki_workspace_bytes(m, n);
+  const bool tensor_lp = !(flags & MSTS_MIXED_FP32_GEMM);
+  OzPlan plan{};
   const int cgrid = std::max(1, std::min(8192, (int)(((long long)m * n + 255) / 256)));
 
   EngineProblem Px{};
@@ -198,6 +204,12 @@ cudaError_t mixed_run(const double2 *U, long long ldu, int m, const double2 *s, 
   if (flags & MSTS_RESIDUAL_OZAKI) {
     e = ozaki_prepare(U, ldu, m, n, oz_ws, st);
     if (e != cudaSuccess) return e;
+  }
+  if (tensor_lp) {     // digit planes of U's block panels, for every low-precision solve
+    e = ozaki_plan_prepare(&plan, U, ldu, m, n, nb, false, cur, st);
+    if (e != cudaSuccess) return e;
+    Px.oz = &plan;
+    Pr.oz = &plan;
   }
   k_offdiag_rowsums<<<(m + 7) / 8, 256, 0, st>>>(U, ldu, m, rs);
   k_copy_or_add<<<cgrid, 256, 0, st>>>(B, ldb, X, ldx, m, n, 0);
@@ -264,7 +276,7 @@ int msts_solve_mixed(const msts_z *U, int64_t ldu, int64_t m, const msts_z *shif
   if (!(tol >= 0.0)) return -10;
   if (max_iter < 0) return -11;
   if (nb != 16 && nb != 32 && nb != 64) return -12;
-  if ((flags & ~(uint32_t)MSTS_RESIDUAL_OZAKI) != 0) return -16;
+  if ((flags & ~(uint32_t)(MSTS_RESIDUAL_OZAKI | MSTS_MIXED_FP32_GEMM)) != 0) return -16;
   if (msts::bad_alignment({U, shifts, B, X}, workspace)) return MSTS_ERR_ALIGN;
   if (m == 0 || n == 0) {
     if (iters) *iters = 0;

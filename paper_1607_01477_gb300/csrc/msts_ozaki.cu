@@ -570,7 +570,7 @@ cudaError_t ozaki_residual(const double2 *U, long long ldu, int m, const double2
   for (int y = 0; y < tiles_m; ++y)
     mma_flops += (double)(o.K / kOzKC - (y * kOzBM) / kOzKC) * tiles_n;
   mma_flops *= 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
-  void *h = trace_on() ? trace_start(2, mma_flops, (double)kOzS * (2.0 * m * o.K + (double)n * o.K), st)
+  void *h = trace_on() ? trace_start(3, mma_flops, (double)kOzS * (2.0 * m * o.K + (double)n * o.K), st)
                        : nullptr;
   k_oz_gemm<kResidual><<<dim3((n + kOzBN - 1) / kOzBN, (2 * m + kOzBM - 1) / kOzBM), kOzThreads, kOzSmem, st>>>(tmA, tmB, a);
   trace_stop(h, st);
@@ -835,19 +835,52 @@ __device__ __noinline__ double update_out_slow(double v, int pe, int h, uint32_t
 // W = sum_d D_d 2^(42 - 7d) (exact for d <= 6, the last diagonal truncated
 // below 2^-56; |W| < 2^62 because every digit expansion is below 1) and applies
 // B = 2^-pend B - W 2^(e_r + f_j - 56) with a single FP64 subtraction.
-constexpr size_t kOzuSmem = (size_t)kOzS * kOzABytes + 2 * kOzBBytes + 1024;
+//
+// The same kernel with NP = 3 planes (kOzLpPlanes) is the low-precision
+// substitution product of the mixed-precision solve: each operand keeps its 3
+// leading 7-bit digit planes (a split of every entry into 3 BF16 pieces, 21
+// bits below the row's or column's power of two), the 6 plane pairs with
+// s + t <= 4 are multiplied with FP32 accumulation in TMEM, and the epilogue
+// sums the 3 diagonals in FP32 and subtracts the product from B in FP64:
+// accurate to about 2^-20 relative to K' max|U(r,:)| max|X(:,j)|, the
+// accuracy class of an FP32 product, which the FP64 refinement then corrects.
+constexpr int kOzLpPlanes = 3;
+template <int NP>
+constexpr size_t ozu_smem() {
+  return (size_t)NP * kOzABytes + 2 * (size_t)NP * kOzBN * kOzKC * 2 + 1024;
+}
 constexpr int kOzPersistentCtas = 152;             // one CTA per SM
 constexpr int kOzuEpiWarps = 16;                   // epilogue warps (4 per sub-partition)
 constexpr int kOzuThreads = 32 * kOzuEpiWarps + 64; // + producer + MMA
 
+// float f times 2^ex as a double from the IEEE fields (exact: every float is a
+// double); `slow` is set when f is subnormal or the result leaves the normal range.
+__device__ __forceinline__ double f32_ldexp(float f, int ex, bool &slow) {
+  const uint32_t u = __float_as_uint(f);
+  const int e8 = (int)((u >> 23) & 0xffu);
+  const uint32_t man = u & 0x7fffffu;
+  const int E = e8 - 127 + 1023 + ex;
+  slow |= (e8 == 0 && man != 0u) || (e8 != 0 && (E <= 0 || E >= 2047));
+  if (e8 == 0) return __hiloint2double((int)(u & 0x80000000u), 0);   // +-0
+  return __hiloint2double((int)((u & 0x80000000u) | ((uint32_t)E << 20) | (man >> 3)), (int)(man << 29));
+}
+__device__ __noinline__ double update_out_slow_lp(double v, int pe, float W, int ex) {
+  return (pe ? dshift(v, pe) : v) - scalbn((double)W, ex);
+}
+
+template <int NP>
 __global__ void __launch_bounds__(kOzuThreads, 1)
 k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ OzArgs args, int tiles_n, int tiles_total) {
   using namespace tc;
+  static_assert(NP == kOzS || NP == kOzLpPlanes, "8 planes (FP64-accurate) or 3 (low precision)");
+  constexpr uint32_t kBBytes = (uint32_t)NP * kOzBN * kOzKC * 2;   // B planes of one tile
+  constexpr int kAcc = NP * kOzBN;                                  // TMEM columns per buffer
+  constexpr uint32_t kTmemCols = 2 * kAcc > 256 ? 512 : 256;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  uint8_t *sA = base;                               // 8 resident A planes x 16 KB
-  uint8_t *sB = base + kOzS * kOzABytes;            // 2 buffers x 32 KB of B planes
+  uint8_t *sA = base;                               // NP resident A planes x 16 KB
+  uint8_t *sB = base + NP * kOzABytes;              // 2 buffers of NP B planes
   __shared__ uint64_t afull, aempty, bfull[2], bempty[2], accfull[2], accempty[2], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ int fail;
@@ -855,7 +888,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int per = (tiles_total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * per, t1 = min(tiles_total, t0 + per);
 
-  if (warp == 0) tmem_alloc(&tmem_base, 512);
+  if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
   if (threadIdx.x == 0) {
     mbar_init(&afull, 1);
     mbar_init(&aempty, 1);
@@ -890,16 +923,16 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int rt = t / tiles_n, ct = t - rt * tiles_n;
         if (rt != prev_rt) {                        // new row tile: reload the A planes
           if (na > 0 && !wait(&aempty, (na - 1) & 1)) { fail = 1; break; }
-          mbar_arrive_expect_tx(&afull, kOzS * kOzABytes);
-          for (int q = 0; q < kOzS; ++q)
+          mbar_arrive_expect_tx(&afull, NP * kOzABytes);
+          for (int q = 0; q < NP; ++q)
             tma_load_3d(sA + q * kOzABytes, &tmA, &afull, args.a_x0, args.row_lo + rt * kOzBM, q);
           ++na;
           prev_rt = rt;
         }
         const int bb = k & 1;
         if (k >= 2 && !wait(&bempty[bb], ((k >> 1) - 1) & 1)) { fail = 1; break; }
-        mbar_arrive_expect_tx(&bfull[bb], kOzBBytes);
-        tma_load_3d(sB + bb * kOzBBytes, &tmB, &bfull[bb], 0, ct * kOzBN, 0);
+        mbar_arrive_expect_tx(&bfull[bb], kBBytes);
+        tma_load_3d(sB + bb * kBBytes, &tmB, &bfull[bb], 0, ct * kOzBN, 0);
         ++b_issued;
       }
       a_issued = na;
@@ -922,13 +955,13 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (k >= 2 && !wait(&accempty[ab], ((k >> 1) - 1) & 1)) { fail = 1; break; }
         if (!wait(&bfull[bb], (k >> 1) & 1)) { fail = 1; break; }
         tc_fence_after();
-        const uint32_t bbase = smem_u32(sB + bb * kOzBBytes);
-        const uint32_t dbase = tmem + ab * kOzAccCols;
-        for (int q = 0; q < kOzS; ++q) {
-          // A plane q+1 against B planes 1..8-q at once (N = 32 (8 - q) written
-          // at column 32 q), as in the chunked kernel above.
+        const uint32_t bbase = smem_u32(sB + bb * kBBytes);
+        const uint32_t dbase = tmem + ab * kAcc;
+        for (int q = 0; q < NP; ++q) {
+          // A plane q+1 against B planes 1..NP-q at once (N = 32 (NP - q)
+          // written at column 32 q), as in the chunked kernel above.
           const uint32_t abase = smem_u32(sA + q * kOzABytes);
-          const uint32_t idesc_q = idesc_bf16(kOzBM, kOzBN * (kOzS - q));
+          const uint32_t idesc_q = idesc_bf16(kOzBM, kOzBN * (NP - q));
 #pragma unroll
           for (int kk = 0; kk < kOzKC / 16; ++kk)
             mma_bf16(dbase + (uint32_t)(q * kOzBN), sdesc_k128(abase + 32 * kk), sdesc_k128(bbase + 32 * kk),
@@ -962,7 +995,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const int r = i >> 1, part = i & 1;
       in.row_ok = i < args.row_hi;
       in.nval = min(kOzBN, args.ncols - ct * kOzBN);
-      in.cx = lane < in.nval ? args.cexp[ct * kOzBN + lane] - 56 : 0;
+      in.cx = lane < in.nval ? args.cexp[ct * kOzBN + lane] - (NP == kOzS ? 56 : 14) : 0;
       in.pe = (lane < in.nval && args.pend) ? args.pend[args.col_base + ct * kOzBN + lane] : 0;
       in.er = in.row_ok ? args.rexp[r] : 0;
       const int c0 = kCW * cgroup;
@@ -984,57 +1017,95 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
       for (int h = 0; h < kPasses; ++h) {
         const int cp = c0 + kQ * h;                 // first column of this pass
-        // W = sum_d D_d 2^(42 - 7d), the diagonals paired first in int32:
-        // |D_d| <= (d + 1) 64 127^2, so D_{2c} 2^7 + D_{2c+1} < 2^30 for d <= 7.
-        // (D_0..D_3 are below 2^22 and are read without a conversion.)
-        uint32_t v[kOzS][kQ];                       // all diagonals of the pass, one wait
-#pragma unroll
-        for (int d = 0; d < kOzS; ++d) tmem_ld4(tmem + lane_addr + ab * kOzAccCols + d * kOzBN + cp, v[d]);
-        tmem_ld_wait();
-        int P[kOzS / 2][kQ];
-#pragma unroll
-        for (int c = 0; c < kOzS / 2; ++c)
-#pragma unroll
-          for (int j = 0; j < kQ; ++j)
-            P[c][j] = c < 2 ? f32_small_pair(v[2 * c][j], v[2 * c + 1][j])
-                            : __float2int_rn(__uint_as_float(v[2 * c][j])) * (1 << kOzBits) +
-                                  __float2int_rn(__uint_as_float(v[2 * c + 1][j]));   // exact integers
-        if (h == kPasses - 1) {
-          tc_fence_before();
-          mbar_arrive(&accempty[ab]);
-        }
-        int Wh[kQ];
-        uint32_t Wl[kQ];
-#pragma unroll
-        for (int j = 0; j < kQ; ++j) fold_w(P[0][j], P[1][j], P[2][j], P[3][j], Wh[j], Wl[j]);
-        // Branch-free outputs: the pending scaling on the exponent field and
-        // the product by w_ldexp_fast; a pass where either leaves the normal
-        // range is redone with the FP64 routines.
         double out[kQ];
-        bool slow = false;
+        if constexpr (NP == kOzLpPlanes) {
+          // FP32 accumulation: W = D_0 + 2^-7 (D_1 + 2^-7 D_2), the product
+          // W 2^(e_r + f_j - 14) subtracted from B in FP64.
+          uint32_t v[NP][kQ];
 #pragma unroll
-        for (int j = 0; j < kQ; ++j) {
-          const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
-          const int pe = __shfl_sync(0xffffffffu, cur.pe, cp + j);
-          const double v = cur.b[kQ * h + j];
-          const int vh = __double2hiint(v), vl = __double2loint(v);
-          const int ev = (vh >> 20) & 0x7ff;
-          const bool nz = ((vh & 0x7fffffff) | vl) != 0;
-          // Only normal values are scaled on the exponent field (zero stays
-          // zero); subnormals, values that would become subnormal, inf and
-          // NaN go the slow way.  (Word-wise tests: a test of all bits but
-          // the sign against zero may be compiled into an FP64 comparison.)
-          slow |= pe != 0 && nz && (ev <= pe || ev == 0x7ff);
-          const int vh2 = (pe != 0 && nz) ? vh - (pe << 20) : vh;
-          out[j] = __hiloint2double(vh2, vl) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
-        }
-        slow = slow && cur.row_ok;                  // rows past the range hold no planes
-        if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
+          for (int d = 0; d < NP; ++d) tmem_ld4(tmem + lane_addr + ab * kAcc + d * kOzBN + cp, v[d]);
+          tmem_ld_wait();
+          if (h == kPasses - 1) {
+            tc_fence_before();
+            mbar_arrive(&accempty[ab]);
+          }
+          float Wf[kQ];
+          bool slow = false;
 #pragma unroll
+          for (int j = 0; j < kQ; ++j) {
+            Wf[j] = fmaf(fmaf(__uint_as_float(v[2][j]), 0x1p-7f, __uint_as_float(v[1][j])), 0x1p-7f,
+                         __uint_as_float(v[0][j]));
+            const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
+            const int pe = __shfl_sync(0xffffffffu, cur.pe, cp + j);
+            const double bv = cur.b[kQ * h + j];
+            const int vh = __double2hiint(bv), vl = __double2loint(bv);
+            const int ev = (vh >> 20) & 0x7ff;
+            const bool nz = ((vh & 0x7fffffff) | vl) != 0;
+            slow |= pe != 0 && nz && (ev <= pe || ev == 0x7ff);
+            const int vh2 = (pe != 0 && nz) ? vh - (pe << 20) : vh;
+            out[j] = __hiloint2double(vh2, vl) - f32_ldexp(Wf[j], ex, slow);
+          }
+          slow = slow && cur.row_ok;
+          if (__any_sync(0xffffffffu, slow)) {
+#pragma unroll
+            for (int j = 0; j < kQ; ++j) {
+              const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
+              const int pe = __shfl_sync(0xffffffffu, cur.pe, cp + j);
+              out[j] = update_out_slow_lp(cur.b[kQ * h + j], pe, Wf[j], ex);
+            }
+          }
+        } else {
+          // W = sum_d D_d 2^(42 - 7d), the diagonals paired first in int32:
+          // |D_d| <= (d + 1) 64 127^2, so D_{2c} 2^7 + D_{2c+1} < 2^30 for d <= 7.
+          // (D_0..D_3 are below 2^22 and are read without a conversion.)
+          uint32_t v[kOzS][kQ];                       // all diagonals of the pass, one wait
+  #pragma unroll
+          for (int d = 0; d < kOzS; ++d) tmem_ld4(tmem + lane_addr + ab * kAcc + d * kOzBN + cp, v[d]);
+          tmem_ld_wait();
+          int P[kOzS / 2][kQ];
+  #pragma unroll
+          for (int c = 0; c < kOzS / 2; ++c)
+  #pragma unroll
+            for (int j = 0; j < kQ; ++j)
+              P[c][j] = c < 2 ? f32_small_pair(v[2 * c][j], v[2 * c + 1][j])
+                              : __float2int_rn(__uint_as_float(v[2 * c][j])) * (1 << kOzBits) +
+                                    __float2int_rn(__uint_as_float(v[2 * c + 1][j]));   // exact integers
+          if (h == kPasses - 1) {
+            tc_fence_before();
+            mbar_arrive(&accempty[ab]);
+          }
+          int Wh[kQ];
+          uint32_t Wl[kQ];
+  #pragma unroll
+          for (int j = 0; j < kQ; ++j) fold_w(P[0][j], P[1][j], P[2][j], P[3][j], Wh[j], Wl[j]);
+          // Branch-free outputs: the pending scaling on the exponent field and
+          // the product by w_ldexp_fast; a pass where either leaves the normal
+          // range is redone with the FP64 routines.
+          bool slow = false;
+  #pragma unroll
           for (int j = 0; j < kQ; ++j) {
             const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
             const int pe = __shfl_sync(0xffffffffu, cur.pe, cp + j);
-            out[j] = update_out_slow(cur.b[kQ * h + j], pe, Wh[j], Wl[j], ex);
+            const double v = cur.b[kQ * h + j];
+            const int vh = __double2hiint(v), vl = __double2loint(v);
+            const int ev = (vh >> 20) & 0x7ff;
+            const bool nz = ((vh & 0x7fffffff) | vl) != 0;
+            // Only normal values are scaled on the exponent field (zero stays
+            // zero); subnormals, values that would become subnormal, inf and
+            // NaN go the slow way.  (Word-wise tests: a test of all bits but
+            // the sign against zero may be compiled into an FP64 comparison.)
+            slow |= pe != 0 && nz && (ev <= pe || ev == 0x7ff);
+            const int vh2 = (pe != 0 && nz) ? vh - (pe << 20) : vh;
+            out[j] = __hiloint2double(vh2, vl) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
+          }
+          slow = slow && cur.row_ok;                  // rows past the range hold no planes
+          if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
+  #pragma unroll
+            for (int j = 0; j < kQ; ++j) {
+              const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
+              const int pe = __shfl_sync(0xffffffffu, cur.pe, cp + j);
+              out[j] = update_out_slow(cur.b[kQ * h + j], pe, Wh[j], Wl[j], ex);
+            }
           }
         }
         double *pj = cur.base + kQ * h * ldr2;
@@ -1060,12 +1131,12 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     __syncthreads();
   }
   if (fail && threadIdx.x == 0) raise_status(args.status, MSTS_STATUS_TIMEOUT);
-  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
-                         cudaStream_t st, bool planes_ready, const double2 *lam, long long lam_stride) {
+                         cudaStream_t st, bool planes_ready, const double2 *lam, long long lam_stride, bool lp) {
   const int row_lo = plan.conj ? 2 * hi : 0, row_hi = plan.conj ? 2 * plan.m : 2 * lo;
   if (ncols <= 0 || row_hi <= row_lo) return cudaSuccess;
   if (!planes_ready) {
@@ -1073,8 +1144,9 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
                                                   plan.cexp, lam, lam_stride);
     count_launches(1);
   }
+  lp = lp && plan.KB == kOzKC;          // the 3-plane product exists in the persistent form only
   CUtensorMap tmB;
-  if (!make_map(&tmB, plan.bp, plan.KB, ncols, kOzBN, kOzS)) return cudaErrorNotSupported;
+  if (!make_map(&tmB, plan.bp, plan.KB, ncols, kOzBN, lp ? kOzLpPlanes : kOzS)) return cudaErrorNotSupported;
   OzArgs a{};
   a.B = B; a.ldb = ldb; a.R = B; a.ldr = ldb;
   a.rexp = plan.rexp + (size_t)b * plan.m;
@@ -1088,12 +1160,23 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
   if (plan.KB == kOzKC) {
     const int tiles_n = (ncols + kOzBN - 1) / kOzBN, tiles_m = (row_hi - row_lo + kOzBM - 1) / kOzBM;
     const int total = tiles_n * tiles_m;
-    cudaError_t e = cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzuSmem);
-    if (e != cudaSuccess) return e;
-    const double mma_flops = (double)total * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
-    void *h = trace_on() ? trace_start(2, mma_flops, (double)total * kOzBBytes, st) : nullptr;
-    e = launch_pdl(k_oz_update, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads), kOzuSmem, st,
-                   plan.tmA, tmB, a, tiles_n, total);
+    // BF16 MMA FLOPs issued: NP (NP + 1) / 2 digit pairs x 4 K-steps of 128 x 32 x 16 per tile
+    const int np = lp ? kOzLpPlanes : kOzS;
+    const double mma_flops = (double)total * (np * (np + 1) / 2) * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+    void *h = trace_on() ? trace_start(2, mma_flops, (double)total * np * kOzBN * kOzKC * 2, st) : nullptr;
+    cudaError_t e;
+    if (lp) {
+      e = cudaFuncSetAttribute(k_oz_update<kOzLpPlanes>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ozu_smem<kOzLpPlanes>());
+      if (e == cudaSuccess)
+        e = launch_pdl(k_oz_update<kOzLpPlanes>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
+                       ozu_smem<kOzLpPlanes>(), st, plan.tmA, tmB, a, tiles_n, total);
+    } else {
+      e = cudaFuncSetAttribute(k_oz_update<kOzS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ozu_smem<kOzS>());
+      if (e == cudaSuccess)
+        e = launch_pdl(k_oz_update<kOzS>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
+                       ozu_smem<kOzS>(), st, plan.tmA, tmB, a, tiles_n, total);
+    }
     trace_stop(h, st);
     count_launches(1);
     return e != cudaSuccess ? e : cudaGetLastError();

@@ -49,10 +49,12 @@ cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, in
 // the diagonal-block step (otherwise they are sliced here first).  lam (a
 // generalized plan): the shifts, column j's at lam[j lam_stride]; the update
 // is then B(I0,:) -= U(I0,I1) X(I1,:) - V(I0,I1) (lam X(I1,:)).
+// lp: the low-precision product of the mixed solve (3 digit planes per
+// operand, FP32 accumulation; n_b <= 32, else the FP64-accurate product).
 cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, long long ldb,
                          int jstart, int ncols, const int *pend, uint32_t *status, double flops,
                          cudaStream_t st, bool planes_ready = false, const double2 *lam = nullptr,
-                         long long lam_stride = 0);
+                         long long lam_stride = 0, bool lp = false);
 // One problem's substitution step inside a batched launch (see ozaki_update;
 // the X planes of this block were written by the diagonal-block step).
 struct OzBatchStep {

@@ -379,7 +379,13 @@ cudaError_t pseudo_run(const double2 *T, long long ldt, int m, const double2 *z,
     if (e != cudaSuccess) return e;
     e = engine_run(&Pc, 1, nb, false, true, false, engine_ws, status, st);              // (T - zI)^{-H}
     if (e != cudaSuccess) return e;
+    // algorithmic bytes of the step: w read and written, v_0..v_k read twice
+    // (projections and their removal), v_{k+1} written; FLOPs of the same passes
+    void *h = trace_on() ? trace_start(4, 8.0 * (2.0 * (k + 1) + 2.0) * m * (double)N,
+                                       16.0 * (2.0 * (k + 1) + 3.0) * m * (double)N, st)
+                         : nullptr;
     launch_lanczos_step(S, k, st);
+    trace_stop(h, st);
     count_launches(2);
   }
   k_ritz<<<(N + 127) / 128, 128, 0, st>>>(S, sigma_min);

@@ -620,7 +620,7 @@ static cudaError_t run_steps(const ProbTable &tab, const EngineProblem *probs, i
       const cudaError_t e = ozaki_update(*probs[0].oz, b, lo, hi, probs[0].B, probs[0].ldb, jstart,
                                          probs[0].n - jstart, SAFE ? tab.p[0].pend : nullptr, status,
                                          gflops, st, tab.p[0].oz_bp != nullptr, gen ? probs[0].shifts : nullptr,
-                                         probs[0].shift_stride);
+                                         probs[0].shift_stride, lp);
       if (e != cudaSuccess) return e;
     } else if (rows_max > 0 && count > 1 && any_oz) {
       // Batched substitution step on the tensor cores: every problem's panel

@@ -1,8 +1,9 @@
 // msts_trace.cu -- launch counting and per-kernel CUDA-event timing.
 //
 // Every kernel launch of the library bumps a process-wide counter.  Between
-// msts_trace_begin() and msts_trace_end() the launches of the two hot kernels
-// (the substitution GEMM and the diagonal-block solve) are also bracketed by
+// msts_trace_begin() and msts_trace_end() the launches of the hot kernels
+// (the substitution GEMM on either path, the diagonal-block solve, the
+// tensor-core residual and the Lanczos step) are also bracketed by
 // CUDA events on the launching stream, together with the algorithmic work of
 // each launch, so that a caller can compute achieved FLOP/s per kernel.
 #include <atomic>

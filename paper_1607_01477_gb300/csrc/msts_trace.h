@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 
 namespace msts {
-constexpr int kTraceKernels = 3;   // MSTS_KERNEL_GEMM, MSTS_KERNEL_DIAG, MSTS_KERNEL_OZAKI
+constexpr int kTraceKernels = 5;   // MSTS_KERNEL_GEMM, _DIAG, _OZAKI, _RESIDUAL, _LANCZOS
 void count_launches(int n);
 bool trace_on();
 // Records a start event on `st` for one launch of `kernel` doing `flops`

@@ -13,10 +13,17 @@ from gpu_util import EPS, cond_inf, forward_close, to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("m,n,nb", [(300, 40, 32), (129, 7, 16), (64, 64, 64), (1, 3, 32)])
-def test_mixed_matches_oracle(m, n, nb):
+FP32_GEMM, OZ = msts.MSTS_MIXED_FP32_GEMM, msts.MSTS_RESIDUAL_OZAKI
+
+
+@pytest.mark.parametrize("flags", [0, FP32_GEMM, OZ, OZ | FP32_GEMM])
+@pytest.mark.parametrize("m,n,nb", [(300, 40, 32), (129, 7, 16), (64, 64, 64), (1, 3, 32), (600, 40, 32)])
+def test_mixed_matches_oracle(m, n, nb, flags):
+    """Both low-precision products (the tensor cores' 3-plane split-BF16 one by
+    default, FP32 FMA on request) with both residuals (FP64 FMA, tensor-core
+    digit planes) reach eta <= 1e-12 and the oracle's solution."""
     U, s, B = W.mixed_problem(m, n, seed=500 + m)
-    X, info, st = msts.msts_solve_mixed(to_dev(U), to_dev(s), to_dev(B), tol=1e-12, nb=nb)
+    X, info, st = msts.msts_solve_mixed(to_dev(U), to_dev(s), to_dev(B), tol=1e-12, nb=nb, flags=flags)
     Xg = to_np(X)
     assert info["eta"] <= 1e-12
     assert info["eta_before"] > info["eta"] or info["eta_before"] <= 1e-12
@@ -28,11 +35,13 @@ def test_mixed_matches_oracle(m, n, nb):
     assert int(st.item()) == 0
 
 
-def test_mixed_first_solve_is_low_precision():
-    """Before refinement the FP32-product solve is far from FP64 (eta ~ 1e-7);
-    one or two corrections reach the 1e-12 target."""
+@pytest.mark.parametrize("flags", [0, FP32_GEMM])
+def test_mixed_first_solve_is_low_precision(flags):
+    """Before refinement the low-precision solve is far from FP64 (the 3-plane
+    tensor-core product and the FP32 product alike: eta ~ 1e-7); one to three
+    corrections reach the 1e-12 target."""
     U, s, B = W.mixed_problem(512, 32, seed=9)
-    X, info, st = msts.msts_solve_mixed(to_dev(U), to_dev(s), to_dev(B), tol=1e-12)
+    X, info, st = msts.msts_solve_mixed(to_dev(U), to_dev(s), to_dev(B), tol=1e-12, flags=flags)
     assert 1e-10 < info["eta_before"] < 1e-4
     assert 1 <= info["iters"] <= 3
 
@@ -50,8 +59,8 @@ def test_mixed_full_size_sampled_columns():
     product, and 6 sampled columns are compared with the oracle."""
     U, s, B = W.mixed_problem()
     Ud, sd, Bd = to_dev(U), to_dev(s), to_dev(B)
-    X, info, st = msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12)
-    assert info["eta"] <= 1e-12
+    X, info, st = msts.msts_solve_mixed(Ud, sd, Bd, tol=1e-12, flags=OZ)
+    assert info["eta"] <= 1e-12 and 1e-10 < info["eta_before"] < 1e-4
     Ut = torch.triu(Ud)
     R = Bd - (Ut @ X - X * sd[None, :])
     rown = Ut.abs().sum(dim=1) - torch.diagonal(Ut).abs()

@@ -72,7 +72,7 @@ def test_static_scratch_solve_matches_workspace_solve_bitwise():
     the oracle's Alg. 5 on scale exponents (equal) and X (1e-8 per column)."""
     f = _entry()
     nb = 32
-    for call, (m, n, seed, nzero) in enumerate([(300, 24, 44, 0), (97, 11, 71, 3)]):
+    for call, (m, n, seed, nzero) in enumerate([(300, 24, 44, 0), (200, 11, 71, 3)]):
         T, shifts, B = _rescaling_problem(m, n, seed, nzero)
         Td, sd = _dev(T), _dev(shifts)
         Xw = _dev(B)
