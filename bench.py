@@ -63,6 +63,9 @@ def parse():
                          "(Sec. 7.1) and the Fox-Li n = 3200 portrait (Sec. 7.3)")
     ap.add_argument("--nb", type=int, default=None,
                     help="block size; default: the autotuner's choice of n_b and diagonal-step layout")
+    ap.add_argument("--layout", type=int, default=None, choices=[0, -1, 1, 2, 4],
+                    help="diagonal-step layout with --nb (0: the library's table; -1: one-warp; 1/2/4: "
+                         "four-warp with that many lanes per shift)")
     ap.add_argument("--tensor", type=int, default=1,
                     help="1: substitution GEMM on the tensor cores (MSTS_TENSOR_GEMM); 0: FP64 FMA")
     return ap.parse_args()
@@ -237,7 +240,7 @@ def run_native(args):
                                      ctypes.c_void_p, ctypes.c_void_p]
 
     wl = args.workload
-    nb, layout = args.nb, 0
+    nb, layout = args.nb, args.layout or 0
     if nb is None:
         from paper_1607_01477_gb300 import autotune
         nb, layout = autotune.choose("trevc", 4096, 4096, bool(args.tensor))
@@ -269,7 +272,8 @@ def run_native(args):
         implementation = {"substitution_gemm": ("tensor cores, FP64-accurate BF16 digit planes"
                                                 if args.tensor else "FP64 FMA"),
                           "n_b": nb, "diag_layout": layout,
-                          "tuning": "autotuner (n_b x diagonal-step layout)" if args.nb is None else "fixed by --nb"}
+                          "tuning": ("autotuner (n_b x diagonal-step layout)" if args.nb is None
+                                     else "fixed by --nb / --layout")}
         # pinned host buffers with the device tensors' column-major strides, so
         # each transfer is one contiguous copy
         h2d_host = torch.empty_strided((m, m), (1, m), dtype=torch.complex128, pin_memory=True)

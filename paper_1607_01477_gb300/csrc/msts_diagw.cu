@@ -3,9 +3,10 @@
 // forward substitution on the conjugate transpose), with each shift's rows
 // spread over the four warps of a CTA.
 //
-// Why this layout.  The FP64 unit of an SM sub-partition issues one warp
-// instruction per ~64 cycles whatever the number of lanes that need it.  With
-// one group of lanes per shift inside one warp, the per-row multiply
+// Why this layout.  FP64 arithmetic on this part runs at about 2 lane
+// operations per clock per SM, one warp instruction per ~16 cycles shared by
+// the SM's four sub-partitions, whatever the number of lanes that need it.
+// With one group of lanes per shift inside one warp, the per-row multiply
 // x_i = y_i (1 / p_i) and the partially predicated AXPY occupy whole warp
 // instructions for a few useful lanes.  Here L = 1, 2 or 4 lanes hold one
 // shift (32 / L shifts per CTA) and the rows of the block are dealt out to the
@@ -19,6 +20,13 @@
 // own x, and only then applies x_i to the rest of its rows (one-row
 // lookahead), so the serial chain per row is one complex multiply-add and one
 // complex multiply.
+//
+// Measured: the layout spends ~4x fewer FP64 instructions per shift than the
+// one-warp layout, but the hand-off per row (barrier, shared-memory round trip,
+// the critical multiply-adds queued behind the other warps' FP64 work) makes a
+// CTA take ~24-44 us per block however few shifts it holds; it is faster only
+// where the FP64 pipes are the bound, i.e. with many shifts per SM (the
+// dispatch takes it from measured per-launch tables, msts_diag.cu).
 //
 // Every value sees the same operations in the same order as in the one-warp
 // layout (msts_diag.cu): the same reciprocals, the same fused multiply-adds
