@@ -170,7 +170,10 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # roofline helpers
 # --------------------------------------------------------------------------
-KERNEL_SOURCES = {"k_gemm": "msts_solve.cu", "k_diag": "msts_diag.cu", "k_oz_update": "msts_ozaki.cu"}
+# the sources whose code a profile of each traced kernel family depends on (the
+# diagonal step's two layouts and their dispatch)
+KERNEL_SOURCES = {"k_gemm": ("msts_solve.cu",), "k_diag": ("msts_diag.cu", "msts_diagw.cu"),
+                  "k_oz_update": ("msts_ozaki.cu",)}
 
 
 def code_hash(text: str) -> str:
@@ -182,8 +185,9 @@ def code_hash(text: str) -> str:
 
 
 def kernel_source_hash(kernel: str) -> str:
-    src = os.path.join(ROOT, "paper_1607_01477_gb300", "csrc", KERNEL_SOURCES[kernel])
-    return code_hash(open(src).read())
+    text = "\n".join(open(os.path.join(ROOT, "paper_1607_01477_gb300", "csrc", f)).read()
+                     for f in KERNEL_SOURCES[kernel])
+    return code_hash(text)
 
 
 def profiled_traffic(kernel: str, workload: str):
