@@ -512,26 +512,29 @@ int diag_lanes(int nb, long long total_cols, bool safe) {
   return lmax;
 }
 
-// Four-warp layout (msts_diagw.cu) or one-warp layout for n_b = 32: per-launch
-// times measured on GB300 (m = n_b = 32, one launch per solve, microseconds):
-//   shifts          <= 608   1216   2432   4864   9728
-//   plain one-warp     22.5   25.6   30.3   41.3   60.8
-//         four-warp    25.5   25.9   30.2   37.9   52.4   (L = 4, 4, 4, 2, 1)
-//   safe  one-warp     26.0   31.7   39.9   54.0   82.9
-//         four-warp    33.2   33.4   38.7   52.7   79.1   (L = 4, 4, 4, 2, 1)
-// The four-warp layout pays a named-barrier hand-off per row, so it only wins
-// where enough shifts keep every sub-partition's FP64 pipe busy: above ~4000
-// active shifts (2 lanes per shift up to ~7000, then 1).
+// Four-warp layout (msts_diagw.cu) or one-warp layout for n_b = 32, from
+// per-launch times measured on GB300 (microseconds):
+//   safe, TREVC of the 4096 workload (ncu launch list, per block step):
+//     active shifts     31    543   1055   1311   2079   2591   3359   3871
+//     one-warp        22.9   25.7   34.1   45.2   45.8   71.4   69.4   70.1
+//     four-warp L=4   31.5   36.3   36.4   42.2   42.8   54.4   54.7   67.4
+//     four-warp L=2   49.3   52.3   52.6   54.2   54.8   63.9   63.6   63.9
+//   single-block solves (m = n_b = 32, CUDA events), shifts 608 / 2432 / 4864 / 9728:
+//     plain one-warp 22.1 / 30.4 / 40.3 / 60.4, four-warp best 23.9 (L=4) / 29.2 (L=2)
+//       / 37.5 (L=2) / 52.9 (L=1); safe one-warp 25.9 / 40.0 / 53.8 / 83.3, four-warp
+//       best 33.8 (L=4) / 39.9 (L=4) / 52.9 (L=2) / 79.5 (L=1).
+// The four-warp layout pays a named-barrier hand-off per row, so it wins only
+// where enough shifts keep the FP64 pipes busy.
 namespace {
 int g_diag_override = 0;
 }
 void set_diag_override(int lanes) { g_diag_override = lanes; }
 
 int diagw_lanes(long long total_cols, bool safe) {
-  (void)safe;
   if (g_diag_override > 0) return g_diag_override;
-  if (total_cols < 4000) return 0;              // one-warp layout
-  return total_cols <= 7000 ? 2 : 1;
+  if (total_cols < (safe ? 1200 : 2000)) return 0;   // one-warp layout
+  if (total_cols < (safe ? 3800 : 3500)) return 4;
+  return total_cols < 7000 ? 2 : 1;
 }
 
 cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int step, int shortcut,
