@@ -490,6 +490,8 @@ def extra_measurements(dev, nb, paper_comparisons=False):
     U, s, B = W.plain_problem()
     Ud, sd, Bd = (msts.colmajor(torch.from_numpy(U).to(dev)), torch.from_numpy(s).to(dev),
                   msts.colmajor(torch.from_numpy(B).to(dev)))
+    import oracle
+    Xo1 = oracle.solve(U, s, B)
     res["plain_256x64"] = {"n_b": "32 (the workload's block size); *_tuned: the autotuner's n_b and layout"}
     for tag, tensor, nbx in (("fp64_gemm", False, nb), ("tensor_gemm", True, nb),
                              ("fp64_gemm_tuned", False, None), ("tensor_gemm_tuned", True, None)):
@@ -504,7 +506,25 @@ def extra_measurements(dev, nb, paper_comparisons=False):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        res["plain_256x64"][tag] = {"us_per_solve": ms * 1e3, "tflops": 4 * 256 ** 2 * 64 / (ms * 1e-3) / 1e12}
+        X.copy_(Bd)
+        msts.msts_solve(Ud, sd, X, nb=nbx, tensor=tensor)
+        Xg = X.cpu().numpy()
+        err = float((np.abs(Xg - Xo1).max(axis=0) / np.abs(Xo1).max(axis=0)).max())
+        res["plain_256x64"][tag] = {"us_per_solve": ms * 1e3, "tflops": 4 * 256 ** 2 * 64 / (ms * 1e-3) / 1e12,
+                                    "forward_error_vs_oracle": err}
+    # the tensor-path solve captured once in a CUDA graph and replayed (no host launch cost)
+    Xr = Bd.clone()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        msts.msts_solve(Ud, sd, Xr.copy_(Bd), nb=nb, tensor=True)
+        with torch.cuda.graph(graph, stream=side):
+            msts.msts_solve(Ud, sd, Xr.copy_(Bd), nb=nb, tensor=True)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    msg, rg = median_ms(graph.replay, 50)
+    res["plain_256x64"]["tensor_gemm"]["cuda_graph_us_per_solve_median"] = msg * 1e3
+    del graph
     res["pseudospectra_2000_grid100x100"] = pseudospectra_measurement(dev, nb)
     res["batched_adjoint_64x(256..2048)x32"] = batched_fwd_bwd(dev, nb)
     res["mixed_8192x2048"] = mixed_vs_fp64(dev, nb)

@@ -3,9 +3,10 @@
 // forward substitution on the conjugate transpose), with each shift's rows
 // spread over the four warps of a CTA.
 //
-// Why this layout.  FP64 arithmetic on this part runs at about 2 lane
-// operations per clock per SM, one warp instruction per ~16 cycles shared by
-// the SM's four sub-partitions, whatever the number of lanes that need it.
+// Why this layout.  FP64 arithmetic on this part issues one warp instruction
+// per 64 cycles per warp, dependent or not (76 with four warps on an SM, half
+// that rate each for two warps on one sub-partition): about 1.7 lane
+// operations per clock per SM, whatever the number of lanes that need them.
 // With one group of lanes per shift inside one warp, the per-row multiply
 // x_i = y_i (1 / p_i) and the partially predicated AXPY occupy whole warp
 // instructions for a few useful lanes.  Here L = 1, 2 or 4 lanes hold one
@@ -366,28 +367,35 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
         sEm[r * SPC + js] = em;
       }
       __syncthreads();
-      // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this block
-      int Ka = 0;
-      double G = G0;
+      // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this
+      // block.  One warp runs the chain of each shift (its 32 dependent FP64
+      // additions would otherwise be issued by all four) and shares Ka.
+      if (w == 0) {
+        int Ka = 0;
+        double G = G0;
 #pragma unroll 4
-      for (int u_ = 0; u_ < NB; ++u_) {
-        const int i = NB - 1 - u_;
-        if (i < nbe) {
-          const double ai = sA[i * SPC + js];
-          const int eM = sEm[i * SPC + js] - Ka;
-          if (eM >= kOmegaExp) {             // M >= Omega: rescale b first
-            const int kk = eM - (kOmegaExp - 1);
-            Ka += kk;
-            G = dscale_exp(G, -kk);
-          }
-          G = __dadd_rn(G, dscale_exp(ai, Kown - Ka));
-          if (ge_omega(G)) {                 // protect the AXPY
-            const int kk = choose_k_exp(G);
-            Ka += kk;
-            G = dscale_exp(G, -kk);
+        for (int u_ = 0; u_ < NB; ++u_) {
+          const int i = NB - 1 - u_;
+          if (i < nbe) {
+            const double ai = sA[i * SPC + js];
+            const int eM = sEm[i * SPC + js] - Ka;
+            if (eM >= kOmegaExp) {           // M >= Omega: rescale b first
+              const int kk = eM - (kOmegaExp - 1);
+              Ka += kk;
+              G = dscale_exp(G, -kk);
+            }
+            G = __dadd_rn(G, dscale_exp(ai, Kown - Ka));
+            if (ge_omega(G)) {               // protect the AXPY
+              const int kk = choose_k_exp(G);
+              Ka += kk;
+              G = dscale_exp(G, -kk);
+            }
           }
         }
+        if (h == 0) sShift[js] = Ka;
       }
+      __syncthreads();
+      const int Ka = sShift[js];
       // phase D: to Alg. 4's scaling
       kexp = Ka;
       if (Kown != Ka) {
