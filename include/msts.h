@@ -94,8 +94,16 @@ int msts_version(void);
  *   shift; 0 (default) picks the width per launch from the number of active
  *   shifts, 1 / 2 / 4 force it, -1 takes the one-warp layout (a group of
  *   lanes per shift inside one warp) instead.
- * Returns 0, -1 (unknown knob) or -2 (invalid value). */
+ * MSTS_TUNE_ALG4_CHAIN: the safe solves take Alg. 4's rescaling decisions on
+ *   each diagonal block from a closed form (the final rescale exponent is the
+ *   largest of the ratio tests' and of the exponent of the bound's full sum,
+ *   estimated in FP32 and checked) and run the serial decision chain only
+ *   where that estimate cannot decide; 1 runs the chain in every block, 0
+ *   (default) restores the closed form.  Both give the same bits.  Set on the
+ *   current device; synchronises it.
+ * Returns 0, -1 (unknown knob), -2 (invalid value) or -3 (CUDA error). */
 #define MSTS_TUNE_DIAG_LANES 1
+#define MSTS_TUNE_ALG4_CHAIN 2
 int msts_tune_set(int32_t knob, int32_t value);
 
 /* ---------------------------------------------------------------------------

@@ -25,6 +25,10 @@ namespace msts {
 
 constexpr int kDiagThreads = 128;
 
+// 1: Alg. 4's decisions by the serial chain in every block (tuning knob; the
+// closed form gives the same values)
+__device__ int g_alg4_chain_d = 0;
+
 template <int L>
 __device__ __forceinline__ double gshfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src, L); }
 template <int L>
@@ -243,11 +247,12 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   // two commutes exactly with every later operation of the substitution (as
   // long as no value is subnormal), so the block is solved once in a scaling
   // of its own, kept clear of overflow by integer bounds on the exponents and
-  // rare rescales (phase A).  Alg. 4's two tests are then replayed from per-row
-  // quantities computed in parallel over the lanes (phase B): the chain of G
-  // sums and rescales (phase C) costs one addition and one exact scaling per
-  // row.  The block is finally brought to Alg. 4's scaling (phase D); every
-  // value is then the one the serial safeguarded loop computes.
+  // rare rescales (phase A).  Alg. 4's two tests are then decided from per-row
+  // quantities computed in parallel over the lanes (phase B): the block's
+  // cumulative rescale exponent has a closed form (alg4_block_ka), and the
+  // serial chain of G sums and rescales (phase C) runs only where that form
+  // cannot decide.  The block is finally brought to Alg. 4's scaling (phase
+  // D); every value is then the one the serial safeguarded loop computes.
   const double G0 = maxabs();                         // G before the first row (Alg. 4)
   // phase A: |y| < 2^Eb for every row; Kown = this block's own scaling
   int Eb = G0 == 0.0 ? -1100 : (int)(__double_as_longlong(G0) >> 52) - 1022;
@@ -292,17 +297,21 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   }
   int kexp = 0;
   if (!__any_sync(0xffffffffu, active && patho)) {
-  // phase B: per owned row, a_r = |x_r| C_r in the final own scaling and the
-  // exponent of M_r = |y_r| / |p_r| in the unscaled one
-  double a[RPL];
+  // phase B: per owned row, the exponent of M_r = |y_r| / |p_r| in the
+  // unscaled form, and the term a_r 2^Kown of S = G0 + sum_r a_r 2^Kown
+  // (a_r = |x_r| C_r, x_r in the final own scaling) estimated in FP32
   int em[RPL];
+  int em_max = kBoundNone, tmax = kBoundNone, tmin = -kBoundNone;
+  float tf[RPL];
+  int te[RPL];
+  bool odd = false;
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     const int r = l + L * q;
-    a[q] = 0.0;
     em[q] = -(1 << 28);
+    tf[q] = 0.0f;
+    te[q] = kBoundNone;
     if (r < nbe) {
-      a[q] = __dmul_rn(zabs_exp(y[q]), ccol(r));
       if (!zzero_words(ypre[q])) {
         // floor(log2 M) <= ey - ep + 1 for normal operands; Alg. 4's test
         // (M 2^(kpre - Ka) >= Omega with Ka >= 0) can only fire above it.
@@ -312,11 +321,41 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
         em[q] = (ey != 0 && pex[q] != 0 && up < kOmegaExp) ? up
                                                           : ratio_exp_fast(ypre[q], pivot(r)) + kpre[q];
       }
+      int e;
+      tf[q] = abs_prod_est(y[q], ccol(r), e, odd);
+      if (tf[q] != 0.0f) {
+        odd |= e < -1020;                             // a_r itself near the subnormal range
+        te[q] = e + Kown;
+      }
+      alg4_term_exps(tf[q], te[q], tmax, tmin);
     }
+    em_max = max(em_max, em[q]);
   }
-  // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this block
+  float tg = 0.0f;                                    // G0, counted once per shift
+  int eg = kBoundNone;
+  if (l == 0) {
+    tg = dbl_lead_f(G0, eg, odd);
+    alg4_term_exps(tg, eg, tmax, tmin);
+  }
+  em_max = gmax_i<L>(em_max);
+  tmax = gmax_i<L>(tmax);
+  tmin = -gmax_i<L>(-tmin);
+  odd = gmax_i<L>((int)odd) != 0;
+  float sp = f_scale_down(tg, eg - tmax);
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) sp += f_scale_down(tf[q], te[q] - tmax);
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o, L);
+  // phase C: Alg. 4's decisions, Ka its cumulative rescale of this block, in
+  // closed form (see alg4_block_ka); a warp with a shift it cannot decide
+  // runs the serial chain from the exact a_r.
   int Ka = 0;
-  {
+  const bool decided = alg4_block_ka(em_max, tmax, tmin, sp, odd, Ka) && g_alg4_chain_d == 0;
+  if (!__all_sync(0xffffffffu, !active || decided)) {
+    Ka = 0;
+    double a[RPL];                                    // a_r, exactly
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) a[q] = l + L * q < nbe ? __dmul_rn(zabs_exp(y[q]), ccol(l + L * q)) : 0.0;
     double G = G0;
 #pragma unroll
     for (int s_ = 0; s_ < RPL; ++s_) {
@@ -564,6 +603,11 @@ cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int 
 
 extern "C" {
 int msts_tune_set(int32_t knob, int32_t value) {
+  if (knob == MSTS_TUNE_ALG4_CHAIN) {
+    if (value != 0 && value != 1) return -2;
+    if (cudaMemcpyToSymbol(msts::g_alg4_chain_d, &value, sizeof(int)) != cudaSuccess) return -3;
+    return msts::set_alg4_chain_w(value) == cudaSuccess ? 0 : -3;
+  }
   if (knob != MSTS_TUNE_DIAG_LANES) return -1;
   if (value != 0 && value != -1 && value != 1 && value != 2 && value != 4) return -2;
   msts::set_diag_override(value);

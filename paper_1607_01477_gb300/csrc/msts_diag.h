@@ -23,4 +23,7 @@ int diagw_lanes(long long total_cols, bool safe);
 // Tuning override (0 = automatic): lanes per shift of every four-warp launch,
 // or -1 to take the one-warp layout for n_b = 32 as well.
 void set_diag_override(int lanes);
+// Tuning knob of the four-warp layout: 1 takes Alg. 4's decisions by the
+// serial chain in every block (the one-warp layout's flag is in msts_diag.cu).
+cudaError_t set_alg4_chain_w(int on);
 }  // namespace msts

@@ -71,6 +71,77 @@ __device__ __forceinline__ int choose_k_exp(double x) {
   return k < 1 ? 1 : k;
 }
 
+// Alg. 4's decisions on one block without its serial chain (both layouts).
+//
+// Write S = G 2^Ka for the running bound G of Alg. 4 and Ka the block's
+// cumulative rescale exponent so far.  A rescale changes G and Ka but not S,
+// and every addition G += a_i 2^(Kown - Ka) rounds S exactly as it rounds G
+// (power-of-two scalings commute with rounding while every value is normal),
+// so S_k is the plain running sum of G0 and the a_i 2^Kown, nondecreasing.
+// The test "M_i >= Omega" rescales to Ka = em_i - (kOmegaExp - 1), the test
+// "G >= Omega" to Ka = e(S_k) - (kOmegaExp - 1) (e: the unbiased exponent),
+// each only when that raises Ka.  Ka is therefore a running maximum, and the
+// block's final value is
+//     Ka = max(0, max_i em_i - (kOmegaExp - 1), e(S_N) - (kOmegaExp - 1)).
+// e(S_N) comes from an estimate of S_N accurate to 2^-18 relative (moduli and
+// sum in FP32 on the leading significand bits, exponents as integers); it
+// decides e(S_N) unless S_N lies within 2^-15 of a power of two.  Blocks where
+// it cannot decide, or where some term of the chain could leave the normal
+// range, run the chain itself.
+constexpr int kBoundNone = -(1 << 28);
+// |v| = f 2^e with f in [1, 2) from the leading 23 significand bits (relative
+// error below 2^-23); f = 0 for v = 0; odd is set for subnormal, inf and NaN.
+__device__ __forceinline__ float dbl_lead_f(double v, int &e, bool &odd) {
+  const unsigned hi = (unsigned)__double2hiint(v) & 0x7fffffffu, lo = (unsigned)__double2loint(v);
+  const int f = (int)(hi >> 20);
+  e = kBoundNone;
+  if ((hi | lo) == 0u) return 0.0f;
+  if (f == 0 || f == 0x7ff) {
+    odd = true;
+    return 0.0f;
+  }
+  e = f - 1023;
+  return __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+// f 2^d for f in [1, 8) or 0 and d <= 0, on the exponent field; 0 below 2^-40.
+__device__ __forceinline__ float f_scale_down(float f, int d) {
+  return (f == 0.0f || d < -40) ? 0.0f : __uint_as_float(__float_as_uint(f) + ((unsigned)d << 23));
+}
+// a = |z| c (c >= 0) as t 2^e with t in [1, 6): FP32 modulus of z's leading
+// bits (relative error below 2^-21); t = 0, e = kBoundNone for a = 0.
+__device__ __forceinline__ float abs_prod_est(double2 z, double c, int &e, bool &odd) {
+  int ex, ey, ec;
+  const float fx = dbl_lead_f(z.x, ex, odd), fy = dbl_lead_f(z.y, ey, odd), fc = dbl_lead_f(c, ec, odd);
+  const int E = max(ex, ey);
+  e = kBoundNone;
+  if (fc == 0.0f || E == kBoundNone) return 0.0f;
+  const float a = f_scale_down(fx, ex - E), b = f_scale_down(fy, ey - E);   // the larger one is in [1, 2)
+  e = E + ec;
+  return sqrtf(fmaf(a, a, b * b)) * fc;
+}
+// One term t 2^e of S into a running (max exponent, min exponent) pair.
+__device__ __forceinline__ void alg4_term_exps(float t, int e, int &emax, int &emin) {
+  if (t != 0.0f) {
+    emax = max(emax, e);
+    emin = min(emin, e);
+  }
+}
+// The final Ka from the reduced quantities: em_max, the largest term exponent
+// tmax, the smallest tmin, the FP32 sum s of the terms scaled by 2^-tmax
+// (s >= 1 when some term is nonzero), odd.  Returns false when the chain must
+// decide instead.
+__device__ __forceinline__ bool alg4_block_ka(int em_max, int tmax, int tmin, float s, bool odd, int &Ka) {
+  Ka = max(0, em_max - (kOmegaExp - 1));
+  if (odd) return false;
+  if (tmax == kBoundNone) return true;                  // S_N = 0: no "G >= Omega" rescale
+  const unsigned b = __float_as_uint(s);
+  const unsigned man = b & 0x7fffffu;
+  if (man < 256u || man > 0x7fffffu - 256u) return false;   // within 2^-15 of a power of two
+  const int eS = tmax + (int)(b >> 23) - 127;
+  Ka = max(Ka, eS - (kOmegaExp - 1));
+  return tmin - Ka >= -1020;                            // every term and bound stays normal
+}
+
 // z == 0 on the bit patterns, word by word.
 __device__ __forceinline__ bool zzero_words(double2 z) {
   return ((((unsigned)__double2hiint(z.x) | (unsigned)__double2hiint(z.y)) & 0x7fffffffu) |

@@ -31,8 +31,9 @@
 //
 // Every value sees the same operations in the same order as in the one-warp
 // layout (msts_diag.cu): the same reciprocals, the same fused multiply-adds
-// row by row, the same power-of-two rescales, the same replay of Alg. 4's
-// decisions; the results are the same bit for bit.  The right-hand sides and
+// row by row, the same power-of-two rescales, the same decisions of Alg. 4
+// (closed form, or the serial chain where it cannot decide); the results are
+// the same bit for bit.  The right-hand sides and
 // the results move between global and shared memory in coalesced column
 // order.  Blocks where the replay cannot be exact (a subnormal pivot, a
 // rescale beyond 2^600) take the serial safeguarded loop of Alg. 4, one
@@ -43,6 +44,11 @@
 #include "msts_digits.cuh"
 
 namespace msts {
+
+// 1: Alg. 4's decisions by the serial chain in every block (tuning knob; the
+// closed form gives the same values)
+__device__ int g_alg4_chain_w = 0;
+
 namespace {
 
 constexpr int kWNB = 32;                 // block size n_b
@@ -344,15 +350,20 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
     auto ccol = [&](int i) { return sC[i]; };
     const bool any_patho = __syncthreads_or(active && patho);
     if (!any_patho) {
-      // phase B: per owned row, a_r = |x_r| C_r in the final own scaling and
-      // the exponent of M_r = |y_r| / |p_r| in the unscaled one
+      // phase B: per owned row, the exponent of M_r = |y_r| / |p_r| in the
+      // unscaled form, and the term a_r 2^Kown of S = G0 + sum_r a_r 2^Kown
+      // (a_r = |x_r| C_r, x_r in the final own scaling) estimated in FP32
+      int em_max = kBoundNone, tmax = kBoundNone, tmin = -kBoundNone;
+      float tf[RPT];
+      int te[RPT];
+      bool odd = false;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = row_of(q);
-        double a = 0.0;
         int em = -(1 << 28);
+        tf[q] = 0.0f;
+        te[q] = kBoundNone;
         if (r < nbe) {
-          a = __dmul_rn(zabs_exp(y[q]), ccol(r));
           const double2 yp = sY[js * LDY + r];
           if (!zzero_words(yp)) {
             // floor(log2 M) <= ey - ep + 1 for normal operands; Alg. 4's test
@@ -362,42 +373,99 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
             const int up = ey - pex[q] + 1 + kpre[q];
             em = (ey != 0 && pex[q] != 0 && up < kOmegaExp) ? up : ratio_exp_fast(yp, pivot(r)) + kpre[q];
           }
+          int e;
+          tf[q] = abs_prod_est(y[q], ccol(r), e, odd);
+          if (tf[q] != 0.0f) {
+            odd |= e < -1020;                   // a_r itself near the subnormal range
+            te[q] = e + Kown;
+          }
+          alg4_term_exps(tf[q], te[q], tmax, tmin);
         }
-        sA[r * SPC + js] = a;
-        sEm[r * SPC + js] = em;
+        sEm[r * SPC + js] = em;                 // for the chain, if it has to run
+        em_max = max(em_max, em);
+      }
+      float tg = 0.0f;                          // G0, counted once per shift
+      int eg = kBoundNone;
+      if (w == 0 && h == 0) {
+        tg = dbl_lead_f(G0, eg, odd);
+        alg4_term_exps(tg, eg, tmax, tmin);
+      }
+      // the shift's maxima and minimum: its L lanes, then its four warps
+      int *sR = reinterpret_cast<int *>(sA);   // [k][w][js], k = em_max, tmax, tmin, odd
+      float *sRf = reinterpret_cast<float *>(sR + 4 * kWWarps * SPC);
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) {
+        em_max = max(em_max, __shfl_xor_sync(0xffffffffu, em_max, o, L));
+        tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o, L));
+        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o, L));
+        odd |= __shfl_xor_sync(0xffffffffu, (int)odd, o, L) != 0;
+      }
+      if (h == 0) {
+        sR[(0 * kWWarps + w) * SPC + js] = em_max;
+        sR[(1 * kWWarps + w) * SPC + js] = tmax;
+        sR[(2 * kWWarps + w) * SPC + js] = tmin;
+        sR[(3 * kWWarps + w) * SPC + js] = (int)odd;
       }
       __syncthreads();
-      // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this
-      // block.  One warp runs the chain of each shift (its 32 dependent FP64
-      // additions would otherwise be issued by all four) and shares Ka.
-      if (w == 0) {
-        int Ka = 0;
-        double G = G0;
+#pragma unroll
+      for (int v = 0; v < kWWarps; ++v) {
+        em_max = max(em_max, sR[(0 * kWWarps + v) * SPC + js]);
+        tmax = max(tmax, sR[(1 * kWWarps + v) * SPC + js]);
+        tmin = min(tmin, sR[(2 * kWWarps + v) * SPC + js]);
+        odd |= sR[(3 * kWWarps + v) * SPC + js] != 0;
+      }
+      // the FP32 sum of the terms scaled by 2^-tmax
+      float sp = f_scale_down(tg, eg - tmax);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) sp += f_scale_down(tf[q], te[q] - tmax);
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o, L);
+      if (h == 0) sRf[w * SPC + js] = sp;
+      __syncthreads();
+      const float ssum = (sRf[0 * SPC + js] + sRf[1 * SPC + js]) + (sRf[2 * SPC + js] + sRf[3 * SPC + js]);
+      int Kest = 0;
+      const bool decided = alg4_block_ka(em_max, tmax, tmin, ssum, odd, Kest) && g_alg4_chain_w == 0;
+      kexp = Kest;
+      if (__syncthreads_or(active && !decided)) {
+        // the chain itself, from the exact a_r (the whole CTA)
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int r = row_of(q);
+          sA[r * SPC + js] = r < nbe ? __dmul_rn(zabs_exp(y[q]), ccol(r)) : 0.0;
+        }
+        __syncthreads();
+        // phase C: Alg. 4's decisions; Ka = its cumulative rescale of this
+        // block.  One warp runs the chain of each shift (its 32 dependent FP64
+        // additions would otherwise be issued by all four) and shares Ka.
+        if (w == 0) {
+          int Ka = 0;
+          double G = G0;
 #pragma unroll 4
-        for (int u_ = 0; u_ < NB; ++u_) {
-          const int i = NB - 1 - u_;
-          if (i < nbe) {
-            const double ai = sA[i * SPC + js];
-            const int eM = sEm[i * SPC + js] - Ka;
-            if (eM >= kOmegaExp) {           // M >= Omega: rescale b first
-              const int kk = eM - (kOmegaExp - 1);
-              Ka += kk;
-              G = dscale_exp(G, -kk);
-            }
-            G = __dadd_rn(G, dscale_exp(ai, Kown - Ka));
-            if (ge_omega(G)) {               // protect the AXPY
-              const int kk = choose_k_exp(G);
-              Ka += kk;
-              G = dscale_exp(G, -kk);
+          for (int u_ = 0; u_ < NB; ++u_) {
+            const int i = NB - 1 - u_;
+            if (i < nbe) {
+              const double ai = sA[i * SPC + js];
+              const int eM = sEm[i * SPC + js] - Ka;
+              if (eM >= kOmegaExp) {           // M >= Omega: rescale b first
+                const int kk = eM - (kOmegaExp - 1);
+                Ka += kk;
+                G = dscale_exp(G, -kk);
+              }
+              G = __dadd_rn(G, dscale_exp(ai, Kown - Ka));
+              if (ge_omega(G)) {               // protect the AXPY
+                const int kk = choose_k_exp(G);
+                Ka += kk;
+                G = dscale_exp(G, -kk);
+              }
             }
           }
+          if (h == 0) sShift[js] = Ka;
         }
-        if (h == 0) sShift[js] = Ka;
+        __syncthreads();
+        kexp = sShift[js];
       }
-      __syncthreads();
-      const int Ka = sShift[js];
       // phase D: to Alg. 4's scaling
-      kexp = Ka;
+      const int Ka = kexp;
       if (Kown != Ka) {
 #pragma unroll
         for (int q = 0; q < RPT; ++q) y[q] = zscale_exp(y[q], Kown - Ka);
@@ -543,6 +611,8 @@ cudaError_t launch_wl(int L, const ProbTable &tab, int step, int shortcut, int n
 }
 
 }  // namespace
+
+cudaError_t set_alg4_chain_w(int on) { return cudaMemcpyToSymbol(g_alg4_chain_w, &on, sizeof(int)); }
 
 cudaError_t launch_diagw(const ProbTable &tab, bool safe, bool conj, int step, int shortcut, int ncols_max,
                          int lanes, uint32_t *status, cudaStream_t st) {

@@ -766,55 +766,48 @@ __device__ __forceinline__ int f32_small_pair(uint32_t a, uint32_t b) {
 }
 
 // W = P01 2^35 + P23 2^21 + P45 2^7 + floor(P67 / 2^7) as two 32-bit words
-// (h signed high word, l low word).
+// (h signed high word, l low word): two wide multiply-adds (the multiply-add
+// pipe, which the epilogue leaves mostly idle) and one add of the top term.
 __device__ __forceinline__ void fold_w(int P01, int P23, int P45, int P67, int &h, uint32_t &l) {
-  const uint32_t l2 = (uint32_t)P23 << 21, l3 = (uint32_t)P45 << 7, l4 = (uint32_t)(P67 >> 7);
-  int hh = (P01 << 3) + (P23 >> 11) + (P45 >> 25) + (P67 >> 31);
-  uint32_t ll;
-  asm("{\n\t"
-      "add.cc.u32 %0, %2, %3;\n\t"
-      "addc.u32 %1, %1, 0;\n\t"
-      "add.cc.u32 %0, %0, %4;\n\t"
-      "addc.u32 %1, %1, 0;\n\t"
-      "}"
-      : "=r"(ll), "+r"(hh)
-      : "r"(l2), "r"(l3), "r"(l4));
-  h = hh;
-  l = ll;
+  long long t;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(t) : "r"(P45), "r"(1 << 7), "l"((long long)(P67 >> 7)));
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(t) : "r"(P23), "r"(1 << 21), "l"(t));
+  h = (int)(t >> 32) + (P01 << 3);                     // |P01| < 2^28: no overflow
+  l = (uint32_t)t;
 }
 
 // (h, l) 2^ex rounded to the nearest double (ties to even), from 32-bit
 // integer operations only; |W| < 2^62.  Sets slow when the result leaves the
-// normal range: the caller then uses i64_ldexp.
+// normal range, and for 0 < |W| < 2^32 (rare: a product 2^-24 below its
+// digit scale), so that the normalisation needs one leading-zero count: the
+// caller then uses i64_ldexp, which gives the same value.
 __device__ __forceinline__ double w_ldexp_fast(int h, uint32_t l, int ex, bool &slow) {
-  const bool neg = h < 0;
-  uint32_t nl, nh;                                      // -(h, l)
+  const uint32_t sg = (uint32_t)(h >> 31);              // 0 or all ones
+  uint32_t al, ah;                                      // |W| = (W ^ sg) - sg
   asm("{\n\t"
-      "sub.cc.u32 %0, 0, %2;\n\t"
-      "subc.u32 %1, 0, %3;\n\t"
+      "sub.cc.u32 %0, %2, %4;\n\t"
+      "subc.u32 %1, %3, %4;\n\t"
       "}"
-      : "=r"(nl), "=r"(nh)
-      : "r"(l), "r"((uint32_t)h));
-  const uint32_t ah = neg ? nh : (uint32_t)h, al = neg ? nl : l;
-  const bool big = ah != 0, zero = (ah | al) == 0;
-  const int lzh = __clz((int)ah), lzl = __clz((int)al);
-  const int lz = big ? lzh : 32 + lzl;                  // leading zeros of the 64-bit magnitude
+      : "=r"(al), "=r"(ah)
+      : "r"(l ^ sg), "r"((uint32_t)h ^ sg), "r"(sg));
+  const bool zero = (ah | al) == 0u;
+  const int lz = __clz((int)ah) & 31;                   // ah != 0 on the fast path
   const int E = 1023 + 63 - lz + ex;                    // biased exponent
-  slow |= !zero && (E <= 0 || E >= 2046);
-  const uint32_t th = big ? __funnelshift_l(al, ah, lzh) : al << (lzl & 31);   // normalised: bit 63 set
-  const uint32_t tl = big ? al << (lzh & 31) : 0u;
-  const uint32_t sh = th >> 11, sl = __funnelshift_r(tl, th, 11);          // 53-bit significand
-  const uint32_t rest = tl & 0x7ffu;
-  const uint32_t inc = (rest > 0x400u || (rest == 0x400u && (sl & 1u))) ? 1u : 0u;
-  uint32_t rh = ((uint32_t)(E - 1) << 20) + sh, rl;
+  slow |= !zero && (ah == 0u || (unsigned)(E - 1) >= 2045u);
+  const uint32_t th = __funnelshift_l(al, ah, lz), tl = al << lz;   // normalised: bit 63 set
+  const uint32_t sh = th >> 11, sl0 = __funnelshift_r(tl, th, 11);  // 53-bit significand
+  const uint32_t inc = ((tl & 0x7ffu) + 0x3ffu + (sl0 & 1u)) >> 11;  // nearest, ties to even
+  uint32_t sl, rh = sh;
   asm("{\n\t"
       "add.cc.u32 %0, %2, %3;\n\t"
       "addc.u32 %1, %1, 0;\n\t"
       "}"
-      : "=r"(rl), "+r"(rh)
-      : "r"(sl), "r"(inc));
-  rh |= neg ? 0x80000000u : 0u;
-  return __hiloint2double(zero ? 0 : (int)rh, zero ? 0 : (int)rl);
+      : "=r"(sl), "+r"(rh)
+      : "r"(sl0), "r"(inc));
+  // (E - 1) << 20 plus the significand with its leading one adds that one into
+  // the exponent field; a rounding carry to 2^53 moves it up one more.
+  rh = (((uint32_t)(E - 1) << 20) + rh) | ((uint32_t)h & 0x80000000u);
+  return __hiloint2double(zero ? 0 : (int)rh, zero ? 0 : (int)sl);
 }
 
 // One output of the update through the FP64 routines (the rare cases that
@@ -987,7 +980,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       double *base;                                 // &B(row, first column of this warp)
       int cx, pe;                                   // lane j: f_j - 56 and pend of column j
       int er, nval;
-      bool row_ok;
+      bool row_ok, any_pe;                          // any_pe: some column of the tile has a pending scaling
     };
     auto fetch = [&](int t, TileIn &in) {
       const int rt = t / tiles_n, ct = t - rt * tiles_n;
@@ -997,6 +990,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       in.nval = min(kOzBN, args.ncols - ct * kOzBN);
       in.cx = lane < in.nval ? args.cexp[ct * kOzBN + lane] - (NP == kOzS ? 56 : 14) : 0;
       in.pe = (lane < in.nval && args.pend) ? args.pend[args.col_base + ct * kOzBN + lane] : 0;
+      in.any_pe = __any_sync(0xffffffffu, in.pe != 0);
       in.er = in.row_ok ? args.rexp[r] : 0;
       const int c0 = kCW * cgroup;
       in.base = reinterpret_cast<double *>(args.R + r + (long long)(args.col_base + ct * kOzBN + c0) * args.ldr) + part;
@@ -1080,8 +1074,16 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           for (int j = 0; j < kQ; ++j) fold_w(P[0][j], P[1][j], P[2][j], P[3][j], Wh[j], Wl[j]);
           // Branch-free outputs: the pending scaling on the exponent field and
           // the product by w_ldexp_fast; a pass where either leaves the normal
-          // range is redone with the FP64 routines.
+          // range is redone with the FP64 routines.  Tiles with no pending
+          // scaling (the common case) skip its tests.
           bool slow = false;
+          if (!cur.any_pe) {
+  #pragma unroll
+            for (int j = 0; j < kQ; ++j) {
+              const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
+              out[j] = cur.b[kQ * h + j] - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
+            }
+          } else {
   #pragma unroll
           for (int j = 0; j < kQ; ++j) {
             const int ex = cur.er + __shfl_sync(0xffffffffu, cur.cx, cp + j);
@@ -1097,6 +1099,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             slow |= pe != 0 && nz && (ev <= pe || ev == 0x7ff);
             const int vh2 = (pe != 0 && nz) ? vh - (pe << 20) : vh;
             out[j] = __hiloint2double(vh2, vl) - w_ldexp_fast(Wh[j], Wl[j], ex, slow);
+          }
           }
           slow = slow && cur.row_ok;                  // rows past the range hold no planes
           if (__any_sync(0xffffffffu, slow)) {        // rare; same values where both apply
