@@ -75,7 +75,6 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   double *sC = reinterpret_cast<double *>(sU + (GEN ? 2 : 1) * NB * LD);   // within-block column norms
   double *sCV = sC + NB;                                 // those of V (GEN)
 
-  pdl_wait();                            // B, the safe state and U' may come from the kernel before
   const Prob &P = tab.p[blockIdx.z];
   if (step >= P.nblk) return;
   const int b = CONJ ? P.nblk - 1 - step : step;
@@ -91,10 +90,32 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   const int nbe = !active ? 0 : (shortcut ? min(hi, j) - lo : nbf);   // TREVC: rows >= j stay zero
   double2 *col = P.B + (long long)(active ? j : 0) * P.ldb + lo;
 
-  // Every global load the step needs is issued here, before U(I1,I1) is
-  // staged, so that a warp waits for one round trip to memory instead of
-  // several in sequence: the shift, the right-hand side, delta and (safe) the
-  // column's scale state and the block's bound C_blk.
+  // U(I1,I1) (and V) to shared memory by asynchronous copies: no registers
+  // held, every copy in flight at once, zeros below the diagonal and past the
+  // block written by the copies themselves.  No kernel of the solve writes U,
+  // V or the column norms, so after the first block step these copies start
+  // before the wait for the previous kernel (they overlap its last CTAs).
+  auto stage_u = [&]() {
+    for (int idx = threadIdx.x; idx < NB * NB; idx += kDiagThreads) {
+      const int c = idx / NB, r = idx - c * NB;
+      const bool in = r <= c && c < nbf;
+      cp_async16(&sU[c * LD + r], in ? &P.U[(lo + r) + (long long)(lo + c) * P.ldu] : P.U, in);
+      if (GEN) cp_async16(&sV[c * LD + r], in ? &P.V[(lo + r) + (long long)(lo + c) * P.ldv] : P.V, in);
+    }
+    if (SAFE)
+      for (int k = threadIdx.x; k < NB; k += kDiagThreads) {
+        sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
+        if (GEN) sCV[k] = k < nbf ? P.cinV[lo + k] : 0.0;
+      }
+  };
+  if (step > 0) stage_u();
+  pdl_wait();                            // B and the safe state come from the kernel before
+  if (step == 0) stage_u();
+
+  // Every other global load the step needs is issued here, so that a warp
+  // waits for one round trip to memory instead of several in sequence: the
+  // shift, the right-hand side, delta and (safe) the column's scale state and
+  // the block's bound C_blk.
   double2 lam = active ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
   double2 y[RPL], inv[RPL];
 #pragma unroll
@@ -108,20 +129,6 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   }
   const double cblk_u = SAFE ? P.cblk[b] : 0.0, cblk_v = SAFE && GEN ? P.cblkV[b] : 0.0;
 
-  // U(I1,I1) (and V) to shared memory by asynchronous copies: no registers
-  // held, every copy in flight at once, zeros below the diagonal and past the
-  // block written by the copies themselves.
-  for (int idx = threadIdx.x; idx < NB * NB; idx += kDiagThreads) {
-    const int c = idx / NB, r = idx - c * NB;
-    const bool in = r <= c && c < nbf;
-    cp_async16(&sU[c * LD + r], in ? &P.U[(lo + r) + (long long)(lo + c) * P.ldu] : P.U, in);
-    if (GEN) cp_async16(&sV[c * LD + r], in ? &P.V[(lo + r) + (long long)(lo + c) * P.ldv] : P.V, in);
-  }
-  if (SAFE)
-    for (int k = threadIdx.x; k < NB; k += kDiagThreads) {
-      sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
-      if (GEN) sCV[k] = k < nbf ? P.cinV[lo + k] : 0.0;
-    }
   cp_async_wait_all();
   __syncthreads();
 
@@ -318,8 +325,14 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
         const int ey = (int)(((unsigned)max(__double2hiint(ypre[q].x) & 0x7fffffff,
                                             __double2hiint(ypre[q].y) & 0x7fffffff)) >> 20);
         const int up = ey - pex[q] + 1 + kpre[q];
-        em[q] = (ey != 0 && pex[q] != 0 && up < kOmegaExp) ? up
-                                                          : ratio_exp_fast(ypre[q], pivot(r)) + kpre[q];
+        if (ey != 0 && pex[q] != 0 && up < kOmegaExp) {
+          em[q] = up;
+        } else {
+          bool ok;
+          const double2 pr = pivot(r);
+          const int re = ratio_exp_est(ypre[q], pr, ok);
+          em[q] = (ok ? re : ratio_exp_fast(ypre[q], pr)) + kpre[q];
+        }
       }
       int e;
       tf[q] = abs_prod_est(y[q], ccol(r), e, odd);

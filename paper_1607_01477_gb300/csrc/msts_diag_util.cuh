@@ -107,17 +107,42 @@ __device__ __forceinline__ float dbl_lead_f(double v, int &e, bool &odd) {
 __device__ __forceinline__ float f_scale_down(float f, int d) {
   return (f == 0.0f || d < -40) ? 0.0f : __uint_as_float(__float_as_uint(f) + ((unsigned)d << 23));
 }
-// a = |z| c (c >= 0) as t 2^e with t in [1, 6): FP32 modulus of z's leading
-// bits (relative error below 2^-21); t = 0, e = kBoundNone for a = 0.
+// |z| as t 2^e with t in [1, 3): FP32 modulus of z's leading bits (relative
+// error below 2^-22); t = 0, e = kBoundNone for z = 0.
+__device__ __forceinline__ float abs_est(double2 z, int &e, bool &odd) {
+  int ex, ey;
+  const float fx = dbl_lead_f(z.x, ex, odd), fy = dbl_lead_f(z.y, ey, odd);
+  e = max(ex, ey);
+  if (e == kBoundNone) return 0.0f;
+  const float a = f_scale_down(fx, ex - e), b = f_scale_down(fy, ey - e);   // the larger one is in [1, 2)
+  return sqrtf(fmaf(a, a, b * b));
+}
+// a = |z| c (c >= 0) as t 2^e with t in [1, 6) (relative error below 2^-21);
+// t = 0, e = kBoundNone for a = 0.
 __device__ __forceinline__ float abs_prod_est(double2 z, double c, int &e, bool &odd) {
-  int ex, ey, ec;
-  const float fx = dbl_lead_f(z.x, ex, odd), fy = dbl_lead_f(z.y, ey, odd), fc = dbl_lead_f(c, ec, odd);
-  const int E = max(ex, ey);
+  int ez, ec;
+  const float tz = abs_est(z, ez, odd), fc = dbl_lead_f(c, ec, odd);
   e = kBoundNone;
-  if (fc == 0.0f || E == kBoundNone) return 0.0f;
-  const float a = f_scale_down(fx, ex - E), b = f_scale_down(fy, ey - E);   // the larger one is in [1, 2)
-  e = E + ec;
-  return sqrtf(fmaf(a, a, b * b)) * fc;
+  if (fc == 0.0f || tz == 0.0f) return 0.0f;
+  e = ez + ec;
+  return tz * fc;
+}
+// floor(log2(|y| / |p|)) from the FP32 moduli (ratio_exp_fast's value, which
+// uses FP64 squares): ok is cleared where the quotient lies within 2^-15 of a
+// power of two (the estimate is within 2^-20) or an operand is zero,
+// subnormal or not finite; the caller then takes ratio_exp_fast.
+__device__ __forceinline__ int ratio_exp_est(double2 y, double2 p, bool &ok) {
+  bool odd = false;
+  int ey, ep;
+  const float ty = abs_est(y, ey, odd), tp = abs_est(p, ep, odd);
+  if (odd || ty == 0.0f || tp == 0.0f) {
+    ok = false;
+    return 0;
+  }
+  const unsigned b = __float_as_uint(__fdividef(ty, tp));
+  const unsigned man = b & 0x7fffffu;
+  ok = man >= 256u && man <= 0x7fffffu - 256u;
+  return ey - ep + (int)(b >> 23) - 127;
 }
 // One term t 2^e of S into a running (max exponent, min exponent) pair.
 __device__ __forceinline__ void alg4_term_exps(float t, int e, int &emax, int &emin) {

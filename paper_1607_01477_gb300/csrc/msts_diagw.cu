@@ -99,7 +99,6 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
   long long *sRedL = reinterpret_cast<long long *>(
       (reinterpret_cast<uintptr_t>(sShift + SPC) + 7) & ~uintptr_t(7));   // [w SPC + js]
 
-  pdl_wait();                            // B, the safe state and the planes' buffer come from the kernel before
   const Prob &P = tab.p[blockIdx.z];
   if (step >= P.nblk) return;
   const int b = CONJ ? P.nblk - 1 - step : step;
@@ -117,9 +116,24 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
   const int nbe = active ? nbe_of(j) : 0;
   auto row_of = [&](int q) { return w + 4 * (h + L * q); };
 
-  // Global loads first (one round trip): the shift, delta and (safe) the
-  // column's scale state and C_blk; then U(I1,I1) and the block's right-hand
-  // sides by asynchronous 16-byte copies in coalesced order.
+  // U(I1,I1) by asynchronous 16-byte copies.  No kernel of the solve writes U
+  // or the column norms, so after the first block step these copies start
+  // before the wait for the previous kernel (they overlap its last CTAs).
+  auto stage_u = [&]() {
+    for (int idx = tid; idx < NB * NB; idx += kWThreads) {
+      const int c = idx / NB, r = idx - c * NB;
+      const bool in = r <= c && c < nbf;
+      cp_async16(&sU[c * LD + r], in ? &P.U[(lo + r) + (long long)(lo + c) * P.ldu] : P.U, in);
+    }
+    if (SAFE)
+      for (int k = tid; k < NB; k += kWThreads) sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
+  };
+  if (step > 0) stage_u();
+  pdl_wait();                            // B, the safe state and the planes' buffer come from the kernel before
+  if (step == 0) stage_u();
+  // Global loads (one round trip): the shift, delta and (safe) the column's
+  // scale state and C_blk; then the block's right-hand sides by asynchronous
+  // 16-byte copies in coalesced order.
   double2 lam = active ? P.shifts[(long long)j * P.shift_stride] : make_double2(0.0, 0.0);
   const double dlt = SAFE ? *P.delta : 0.0;
   int e_col = 0;
@@ -129,18 +143,11 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
     G_col = P.G[j];
   }
   const double cblk = SAFE ? P.cblk[b] : 0.0;
-  for (int idx = tid; idx < NB * NB; idx += kWThreads) {
-    const int c = idx / NB, r = idx - c * NB;
-    const bool in = r <= c && c < nbf;
-    cp_async16(&sU[c * LD + r], in ? &P.U[(lo + r) + (long long)(lo + c) * P.ldu] : P.U, in);
-  }
   for (int idx = tid; idx < SPC * NB; idx += kWThreads) {
     const int c = idx / NB, r = idx - c * NB, jj = jcta + c;
     const bool in = jj < P.n && r < nbe_of(jj);
     cp_async16(&sY[c * LDY + r], in ? &P.B[(long long)jj * P.ldb + lo + r] : P.B, in);
   }
-  if (SAFE)
-    for (int k = tid; k < NB; k += kWThreads) sC[k] = k < nbf ? P.cin[lo + k] : 0.0;
   cp_async_wait_all();
   __syncthreads();
 
@@ -371,7 +378,14 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
             const int ey = (int)(((unsigned)max(__double2hiint(yp.x) & 0x7fffffff,
                                                 __double2hiint(yp.y) & 0x7fffffff)) >> 20);
             const int up = ey - pex[q] + 1 + kpre[q];
-            em = (ey != 0 && pex[q] != 0 && up < kOmegaExp) ? up : ratio_exp_fast(yp, pivot(r)) + kpre[q];
+            if (ey != 0 && pex[q] != 0 && up < kOmegaExp) {
+              em = up;
+            } else {
+              bool ok;
+              const double2 pr = pivot(r);
+              const int re = ratio_exp_est(yp, pr, ok);
+              em = (ok ? re : ratio_exp_fast(yp, pr)) + kpre[q];
+            }
           }
           int e;
           tf[q] = abs_prod_est(y[q], ccol(r), e, odd);

@@ -53,29 +53,48 @@ __device__ __forceinline__ long long half_bits(long long m) {   // bits of m / 2
   return m >= (1LL << 53) ? m - (1LL << 52) : 0;
 }
 
-// One warp per column k: cin[k] = max_{lo(k) <= r < k} |U(r,k)| (within its own
+// The set-up and fix-up kernels below give each column a CTA of kColThreads
+// threads (the columns of a triangle differ in length; one warp per column
+// left them bound by the latency of its serial loop).
+constexpr int kColThreads = 256;
+// Maximum of v over the CTA (every thread gets it); red holds kColThreads / 32 values.
+__device__ __forceinline__ long long cta_max_ll(long long v, long long *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, (long long)__shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();                                       // red free from an earlier call
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = red[0];
+#pragma unroll
+  for (int w = 1; w < kColThreads / 32; ++w) v = max(v, red[w]);
+  return v;
+}
+
+// One CTA per column k: cin[k] = max_{lo(k) <= r < k} |U(r,k)| (within its own
 // block, diagonal excluded) and cup[k] = max_{r < lo(k)} |U(r,k)| (above it);
 // with useV the same for V into cinV, cupV (generalized problem).
-__global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32_t *status, int useV) {
+__global__ void __launch_bounds__(kColThreads)
+k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32_t *status, int useV) {
   const Prob &P = tab.p[blockIdx.z];
+  __shared__ long long red[kColThreads / 32];
   if (P.n == 0 || (useV && !P.V)) return;
   if (!useV && blockIdx.x == 0 && threadIdx.x == 0) *P.delta = 0.0;   // the zero-pivot flag of k_zero_scan
-  const int lane = threadIdx.x & 31;
-  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int k = blockIdx.x;
   if (k >= P.m) return;
   const int b = (P.m - 1 - k) / nb;
   int lo, hi;
   block_range(P, b, nb, lo, hi);
   // Maxima of squared moduli (as bits: nonnegative doubles order like their
   // bits), one square root per column at the end (|U(i,k)| < 2^48 is the
-  // documented range, so the squares cannot overflow).
+  // documented range, so the squares cannot overflow).  Each thread's running
+  // maxima of the larger components select its candidates: the element of
+  // largest modulus in each range is one of them.
   long long Min = 0, Mup = 0, Mall = 0, cin = 0, cup = 0, amax = 0;
   bool finite = true;
   const double2 *col = useV ? P.V + (long long)k * P.ldv : P.U + (long long)k * P.ldu;
 #pragma unroll 4
-  for (int r0 = 0; r0 <= k; r0 += 32) {                  // warp-uniform trip count
-    const int r = r0 + lane;
-    const double2 u = r <= k ? col[r] : make_double2(0.0, 0.0);
+  for (int r = threadIdx.x; r <= k; r += kColThreads) {
+    const double2 u = col[r];
     finite &= zfinite_bits(u);
     const long long m = zmaxbits(u);
     const bool in_in = r >= lo && r < k, in_up = r < lo;
@@ -84,21 +103,18 @@ __global__ void k_colnorms(const __grid_constant__ ProbTable tab, int nb, uint32
     if (in_up) Mup = max(Mup, m);
     const bool cand = m != 0 && (m >= half_bits(Mall) || (in_in && m >= half_bits(Min)) ||
                                  (in_up && m >= half_bits(Mup)));
-    if (__any_sync(0xffffffffu, cand)) {
-      const long long a2 = cand ? __double_as_longlong(fma(u.x, u.x, u.y * u.y)) : 0;
+    if (cand) {
+      const long long a2 = __double_as_longlong(fma(u.x, u.x, u.y * u.y));
       amax = max(amax, a2);
       if (in_in) cin = max(cin, a2);
       if (in_up) cup = max(cup, a2);
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    cin = max(cin, (long long)__shfl_xor_sync(0xffffffffu, cin, o));
-    cup = max(cup, (long long)__shfl_xor_sync(0xffffffffu, cup, o));
-    amax = max(amax, (long long)__shfl_xor_sync(0xffffffffu, amax, o));
-  }
-  const bool all_finite = __all_sync(0xffffffffu, finite);
-  if (lane == 0) {
+  const bool all_finite = __syncthreads_and(finite);
+  cin = cta_max_ll(cin, red);
+  cup = cta_max_ll(cup, red);
+  amax = cta_max_ll(amax, red);
+  if (threadIdx.x == 0) {
     (useV ? P.cinV : P.cin)[k] = sqrt(__longlong_as_double(cin));
     (useV ? P.cupV : P.cup)[k] = sqrt(__longlong_as_double(cup));
     if (!all_finite) raise_status(status, MSTS_STATUS_NONFINITE);
@@ -217,45 +233,42 @@ __global__ void k_safe_finish(const __grid_constant__ ProbTable tab, int nb) {
   }
 }
 
-// One warp per column: G(j) = ||B(:,j)||_inf over the active rows, e_j = 0.
+// One CTA per column: G(j) = ||B(:,j)||_inf over the active rows, e_j = 0.
 // The scaled square sums are formed only for the candidates of the maximum
 // (see zmaxbits), with the same values as for all elements.
-__global__ void k_safe_init(const __grid_constant__ ProbTable tab, int shortcut, uint32_t *status) {
+__global__ void __launch_bounds__(kColThreads)
+k_safe_init(const __grid_constant__ ProbTable tab, int shortcut, uint32_t *status) {
   const Prob &P = tab.p[blockIdx.z];
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  __shared__ long long red[kColThreads / 32];
+  const int j = blockIdx.x;
   if (j >= P.n) return;
   const int end = shortcut ? min(j, P.m) : P.m;
   bool finite = true;
   const double2 *col = P.B + (long long)j * P.ldb;
   long long M = 0;
 #pragma unroll 4
-  for (int r = lane; r < end; r += 32) {
+  for (int r = threadIdx.x; r < end; r += kColThreads) {
     const double2 v = col[r];
     finite &= zfinite_bits(v);
     M = max(M, zmaxbits(v));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) M = max(M, (long long)__shfl_xor_sync(0xffffffffu, M, o));
+  const bool all_finite = __syncthreads_and(finite);
+  M = cta_max_ll(M, red);
   const int E = min(max((int)(M >> 52) - 1023, -1022), 1022);   // zexp of the largest component
   const double sc = pow2i(-E);
   const long long thr = half_bits(M);
   long long g2 = 0;
 #pragma unroll 4
-  for (int r0 = 0; r0 < end; r0 += 32) {                 // warp-uniform trip count
-    const int r = r0 + lane;
-    const double2 v = r < end ? col[r] : make_double2(0.0, 0.0);
-    const bool cand = r < end && M != 0 && zmaxbits(v) >= thr;
-    if (__any_sync(0xffffffffu, cand)) {
+  for (int r = threadIdx.x; r < end; r += kColThreads) {  // the column again, from L2
+    const double2 v = col[r];
+    if (M != 0 && zmaxbits(v) >= thr) {
       const double a = v.x * sc, bb = v.y * sc;
-      if (cand) g2 = max(g2, __double_as_longlong(fma(a, a, bb * bb)));
+      g2 = max(g2, __double_as_longlong(fma(a, a, bb * bb)));
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) g2 = max(g2, (long long)__shfl_xor_sync(0xffffffffu, g2, o));
-  const double g = sqrt(__longlong_as_double(g2)) * pow2i(E);
-  const bool all_finite = __all_sync(0xffffffffu, finite);
-  if (lane == 0) {
+  g2 = cta_max_ll(g2, red);
+  if (threadIdx.x == 0) {
+    const double g = sqrt(__longlong_as_double(g2)) * pow2i(E);
     P.G[j] = g;
     P.e[j] = 0;
     P.pend[j] = 0;
@@ -480,15 +493,16 @@ k_gemm_f32(const __grid_constant__ ProbTable tab, int step, int shortcut) {
 
 // Final lazy rescale (safe variant): block b of column j was finished with
 // exponent E[b][j]; it still owes 2^-(e_j - E[b][j]).  Also writes s_j.
-__global__ void k_fixup(const __grid_constant__ ProbTable tab, int nb, int shortcut) {
+__global__ void __launch_bounds__(kColThreads)
+k_fixup(const __grid_constant__ ProbTable tab, int nb, int shortcut) {
   const Prob &P = tab.p[blockIdx.z];
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x;                              // one CTA per column, its warps over the blocks
   if (j >= P.n) return;
   const int ej = P.e[j];
   const int end = shortcut ? min(j, P.m) : P.m;
   double2 *col = P.B + (long long)j * P.ldb;
-  for (int b = 0; b < P.nblk; ++b) {
+  for (int b = warp; b < P.nblk; b += kColThreads / 32) {
     int lo, hi;
     block_range(P, b, nb, lo, hi);
     if (lo >= end) continue;
@@ -497,7 +511,7 @@ __global__ void k_fixup(const __grid_constant__ ProbTable tab, int nb, int short
     const int top = min(hi, end);
     for (int r = lo + lane; r < top; r += 32) col[r] = zshift(col[r], d);
   }
-  if (lane == 0) {
+  if (threadIdx.x == 0) {
     const double s = scalbn(1.0, -ej);
     if (P.scales) P.scales[j] = s;
     if (P.scale_exp) P.scale_exp[j] = ej;
@@ -718,13 +732,13 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
     const int sc = shortcut ? 1 : 0;
     if (safe) {
       const bool gen = probs[base].V != nullptr;
-      k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status, 0);
-      if (gen) k_colnorms<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, status, 1);
+      k_colnorms<<<dim3(maxm, 1, cnt), kColThreads, 0, st>>>(tab, nb, status, 0);
+      if (gen) k_colnorms<<<dim3(maxm, 1, cnt), kColThreads, 0, st>>>(tab, nb, status, 1);
       k_zero_scan<<<dim3((maxn + 255) / 256, (maxm + 255) / 256, cnt), 256, 0, st>>>(tab, sc);
       k_rowsums<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, 0);
       if (gen) k_rowsums<<<dim3((maxm + 7) / 8, 1, cnt), 256, 0, st>>>(tab, 1);
       k_safe_finish<<<dim3(1, 1, cnt), 256, 0, st>>>(tab, nb);
-      k_safe_init<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, sc, status);
+      k_safe_init<<<dim3(maxn, 1, cnt), kColThreads, 0, st>>>(tab, sc, status);
       count_launches(gen ? 7 : 5);
     }
     cudaError_t err;
@@ -736,7 +750,7 @@ cudaError_t engine_run(const EngineProblem *probs, int count, int nb, bool safe,
     }
     if (err != cudaSuccess) return err;
     if (safe) {
-      k_fixup<<<dim3((maxn + 7) / 8, 1, cnt), 256, 0, st>>>(tab, nb, sc);
+      k_fixup<<<dim3(maxn, 1, cnt), kColThreads, 0, st>>>(tab, nb, sc);
       count_launches(1);
     }
     err = cudaGetLastError();

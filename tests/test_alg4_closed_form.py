@@ -10,7 +10,9 @@ The closed form claims Ka = max(0, max em_i - 959, e(S_N) - 959), S_N the
 running FP64 sum of G0 and the a_i 2^Kown, with e(S_N) decided from an FP32
 estimate unless S_N is within 2^-15 of a power of two.  The model follows the
 kernel's arithmetic: a_i = fl(|x_i| C_i) in FP64 for the chain, and the
-estimate from the leading 23 significand bits of x_i and C_i in FP32.
+estimate from the leading 23 significand bits of x_i and C_i in FP32.  The
+ratio exponents em_i themselves come from an FP32 estimate of |y_i| / |p_i|
+(ratio_exp_est), which must equal the FP64 routine wherever it decides.
 """
 import math
 
@@ -149,3 +151,52 @@ def test_no_term_no_rescale_and_ratio_tests_alone():
     x = [complex(1.0, 1.0)] * 3
     a = [abs(z) for z in x]
     assert closed(1.0, x, [1.0] * 3, em, 0) == chain(1.0, a, em, 0) == 1000 - 959
+
+
+def ratio_exp_fp64(y: complex, p: complex) -> int:
+    """floor(log2(|y| / |p|)) from FP64 squares of the scaled components (the
+    kernels' exact routine)."""
+    def scaled(z):
+        f = max(exp2_of(abs(z.real)) if z.real else -1022, exp2_of(abs(z.imag)) if z.imag else -1022)
+        a, b = math.ldexp(z.real, -f), math.ldexp(z.imag, -f)
+        n = a * a + b * b
+        if n >= 4.0:
+            f, n = f + 1, n * 0.25
+        return f, n
+    fy, ny = scaled(y)
+    fp, np_ = scaled(p)
+    return fy - fp - (1 if ny < np_ else 0)
+
+
+def ratio_exp_fp32(y: complex, p: complex):
+    """The FP32 estimate: None where it defers to the FP64 routine."""
+    def est(z):
+        fx, ex = lead_f(z.real)
+        fy, ey = lead_f(z.imag)
+        e = max(ex, ey)
+        a, b = scale_down(fx, ex - e), scale_down(fy, ey - e)
+        return np.float32(np.sqrt(np.float32(np.float32(a * a) + np.float32(b * b)))), e
+    ty, ey = est(y)
+    tp, ep = est(p)
+    r = np.float32(ty / tp)
+    m, er = math.frexp(float(r))
+    man = int((m * 2.0 - 1.0) * 2 ** 23)
+    if man < 256 or man > 0x7FFFFF - 256:
+        return None
+    return ey - ep + er - 1
+
+
+def test_ratio_exponent_estimate_matches_fp64_routine():
+    g = np.random.default_rng(99)
+    decided = 0
+    n = 20000
+    for _ in range(n):
+        y = complex(g.standard_normal(), g.standard_normal()) * 2.0 ** int(g.integers(-900, 900))
+        p = complex(g.standard_normal(), g.standard_normal()) * 2.0 ** int(g.integers(-60, 4))
+        if g.random() < 0.1:                      # a purely real or imaginary operand
+            y = complex(y.real, 0.0)
+        est = ratio_exp_fp32(y, p)
+        if est is not None:
+            decided += 1
+            assert est == ratio_exp_fp64(y, p) == math.floor(math.log2(abs(y) / abs(p)))
+    assert decided >= 0.99 * n
