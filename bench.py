@@ -109,6 +109,98 @@ def sum_over_ranks(x: float, dist, device=None) -> float:
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
+class NvmlClockSampler:
+    """SM clock, power draw and clock-event reasons of the bench's GPU, read
+    through NVML (read-only queries) by a host thread every few milliseconds;
+    summary() keeps the samples inside the window marked by start()/stop()
+    (the timed region).  Raises OSError when NVML cannot be used, so that the
+    caller falls back to nvidia-smi."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, dev_index: int, period_s: float = 0.005):
+        import ctypes
+        import threading
+        self.ct, self.period = ctypes, period_s
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError as e:
+            raise OSError(f"NVML not loadable: {e}")
+        if self.nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        uuid = None
+        try:
+            u = torch.cuda.get_device_properties(dev_index).uuid
+            uuid = ("GPU-" + str(u)).encode()
+        except Exception:
+            pass
+        rc = self.nv.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(uuid), ctypes.byref(self.h)) if uuid else 1
+        self.how = "by UUID"
+        if rc != 0:
+            self.how = "by index"
+            if self.nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(dev_index), ctypes.byref(self.h)) != 0:
+                raise OSError("no NVML handle for the device")
+        mx = ctypes.c_uint()
+        if self.nv.nvmlDeviceGetMaxClockInfo(self.h, ctypes.c_uint(1), ctypes.byref(mx)) != 0:
+            raise OSError("nvmlDeviceGetMaxClockInfo failed")
+        self.max_mhz = float(mx.value)
+        self.samples, self.window = [], None
+        self.stop_evt = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        ct = self.ct
+        clk, pw, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        get_r = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_evt.is_set():
+            t = time.perf_counter()
+            ok = self.nv.nvmlDeviceGetClockInfo(self.h, ct.c_uint(1), ct.byref(clk)) == 0
+            okp = self.nv.nvmlDeviceGetPowerUsage(self.h, ct.byref(pw)) == 0
+            okr = get_r(self.h, ct.byref(rs)) == 0
+            if ok:
+                self.samples.append((t, float(clk.value), pw.value / 1000.0 if okp else None,
+                                     rs.value if okr else 0))
+            self.stop_evt.wait(self.period)
+
+    def __enter__(self):
+        self.thread.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop_evt.set()
+        self.thread.join(timeout=5)
+
+    def start(self):
+        self.window = [time.perf_counter(), None]
+
+    def stop(self):
+        if self.window:
+            self.window[1] = time.perf_counter()
+
+    def summary(self):
+        smp = self.samples
+        if self.window and self.window[1]:
+            inside = [x for x in smp if self.window[0] <= x[0] <= self.window[1]]
+            smp = inside or smp
+        if not smp:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"], "source": "nvml"}
+        reasons = sorted({nm for x in smp for bit, nm in self.REASONS.items() if x[3] & bit})
+        return {"sm_mhz": float(np.median([x[1] for x in smp])), "sm_max_mhz": self.max_mhz,
+                "samples": len(smp), "reasons": reasons,
+                "power_w_median": float(np.median([x[2] for x in smp if x[2] is not None] or [0.0])),
+                "source": f"NVML ({self.how}), every ~5 ms inside the timed region"}
+
+
+def clock_sampler(dev_index: int):
+    """The NVML sampler, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(dev_index)
+    except OSError:
+        return ClockSampler(dev_index)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -141,6 +233,12 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
             self.fh.close()
+
+    def start(self):
+        pass
+
+    def stop(self):
+        pass
 
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
@@ -349,15 +447,17 @@ def run_native(args):
     launches0 = lib.msts_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with clock_sampler(local) as clk:
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+        clk.start()
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.stop()
     launches = lib.msts_launch_count() - launches0
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ms, dist, dev)
@@ -1123,12 +1223,14 @@ def run_residual(args):
     lib.msts_trace_begin(400 * args.steps + 64)
     launches0 = lib.msts_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with clock_sampler(0) as clk:
+        clk.start()
         e0.record()
         for _ in range(args.steps):
             step()
         e1.record()
         torch.cuda.synchronize()
+        clk.stop()
     lib.msts_trace_end()
     ms = e0.elapsed_time(e1) / args.steps
     tms, tn, tf, tb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()

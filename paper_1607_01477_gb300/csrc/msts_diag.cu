@@ -74,6 +74,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   double2 *sV = sU + NB * LD;                            // V(I1,I1) (GEN)
   double *sC = reinterpret_cast<double *>(sU + (GEN ? 2 : 1) * NB * LD);   // within-block column norms
   double *sCV = sC + NB;                                 // those of V (GEN)
+  double2 *sInv = reinterpret_cast<double2 *>(sC + (GEN ? 2 : 1) * NB);   // 1 / p_i: [i SPC + shift]
 
   const Prob &P = tab.p[blockIdx.z];
   if (step >= P.nblk) return;
@@ -85,7 +86,8 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
   if (jcta >= P.n) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = lane & (L - 1);
-  const int j = jcta + warp * SPW + lane / L;
+  const int gs = warp * SPW + lane / L;   // this shift within the CTA
+  const int j = jcta + gs;
   const bool active = j < P.n;
   const int nbe = !active ? 0 : (shortcut ? min(hi, j) - lo : nbf);   // TREVC: rows >= j stay zero
   double2 *col = P.B + (long long)(active ? j : 0) * P.ldb + lo;
@@ -158,9 +160,25 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
     zero_piv |= v && zzero_words(p0);
     const double2 p = pivot(r);
     inv[q] = v ? zrecip(p) : make_double2(0.0, 0.0);
+    sInv[r * SPC + gs] = inv[q];
     pex[q] = (int)(max(absbits(p.x), absbits(p.y)) >> 52);
   }
+  __syncwarp();                          // sInv: read by the lanes of the same group
   if (zero_piv) raise_status(status, SAFE ? MSTS_STATUS_DELTA : MSTS_STATUS_ZERO_PIVOT);
+
+  // x_i = y_i (1 / p_i) for row i = L qi + li, broadcast in the group: Re x_i
+  // by the owner lane li, Im x_i by its partner li ^ 1 (zmul's two
+  // multiply-adds, the same operations), half the FP64 instructions of the
+  // multiply on the row's chain; the partner takes y_i from the owner and
+  // 1 / p_i from shared memory.
+  auto xrow = [&](int qi, int li) {
+    const double yr = gshfl<L>(y[qi].x, li), yi = gshfl<L>(y[qi].y, li);
+    const double2 ip = sInv[(L * qi + li) * SPC + gs];
+    const bool re = l == li;
+    const double m1 = __hiloint2double(__double2hiint(yi) ^ (re ? (int)0x80000000 : 0), __double2loint(yi));
+    const double part = fma(yr, re ? ip.x : ip.y, m1 * (re ? ip.y : ip.x));
+    return make_double2(gshfl<L>(part, li), gshfl<L>(part, li ^ 1));
+  };
 
   // One row of the substitution: x_i = y_i / piv_i by the owner lane, broadcast
   // in the group, AXPY on the rows each lane owns.
@@ -190,7 +208,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
 #pragma unroll 1
       for (int u_ = 0; u_ < L; ++u_) {
         const int li = CONJ ? u_ : L - 1 - u_;
-        const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);   // zero for rows >= nbe
+        const double2 xi = xrow(qi, li);   // zero for rows >= nbe
         if (l == li) y[qi] = xi;
         axpy(qi, li, xi);
       }
@@ -240,11 +258,11 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
 #pragma unroll
     for (int q = 0; q < RPL; ++q) E = max(E, zexp(y[q]));
     E = gmax_i<L>(E);
-    const double sc = pow2i(-E);
     long long m2 = 0;                                  // max of the scaled squares, as bits (>= 0)
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
-      const double a = y[q].x * sc, bb = y[q].y * sc;
+      // y 2^-E on the exponent fields (exact: the products by 2^-E)
+      const double a = dscale_exp0(y[q].x, -E), bb = dscale_exp0(y[q].y, -E);
       m2 = max(m2, __double_as_longlong(fma(a, a, bb * bb)));
     }
     return sqrt(__longlong_as_double(gmax_ll<L>(m2))) * pow2i(E);
@@ -292,7 +310,7 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
       Kown += kk;
       cand -= kk;
     }
-    const double2 xi = gshfl_z<L>(zmul(y[qi], inv[qi]), li);
+    const double2 xi = xrow(qi, li);
     if (l == li) {
       ypre[qi] = y[qi];
       kpre[qi] = Kown;
@@ -484,8 +502,9 @@ k_diag(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t *
 template <int NB, int L, bool SAFE, bool CONJ, bool GEN>
 static cudaError_t launch(const ProbTable &tab, int step, int shortcut, int ncols_max,
                           uint32_t *status, cudaStream_t st) {
-  constexpr size_t smem = (GEN ? 2 : 1) * ((size_t)NB * (NB + 1) * sizeof(double2) + NB * sizeof(double));
   constexpr int SPC = (kDiagThreads / 32) * (32 / L);
+  constexpr size_t smem = (GEN ? 2 : 1) * ((size_t)NB * (NB + 1) * sizeof(double2) + NB * sizeof(double)) +
+                          (size_t)NB * SPC * sizeof(double2);   // + the inverses of the pivots
   cudaError_t e = cudaFuncSetAttribute(k_diag<NB, L, SAFE, CONJ, GEN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -77,7 +77,8 @@ struct WShape {
 template <int L, bool SAFE>
 constexpr size_t diagw_smem() {
   constexpr int SPC = WShape<L>::SPC;
-  return sizeof(double2) * ((size_t)kWNB * kWLD + (size_t)kWNB * SPC + (size_t)SPC * kWLDY) +
+  return sizeof(double2) * ((size_t)kWNB * kWLD + (size_t)kWNB * SPC + (size_t)SPC * kWLDY +
+                             (L > 1 ? (size_t)kWNB * SPC : 0)) +
          sizeof(double) * kWNB + sizeof(int) * ((size_t)kWNB * SPC + kWWarps * SPC + SPC) +
          sizeof(long long) * kWWarps * SPC + 16;
 }
@@ -92,7 +93,8 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
   double2 *sU = reinterpret_cast<double2 *>(smem_raw);      // U(I1,I1), column-major, LD
   double2 *sX = sU + NB * LD;                                // x_i of every shift: [i SPC + js]
   double2 *sY = sX + NB * SPC;                               // per-shift columns: [js LDY + r]
-  double *sC = reinterpret_cast<double *>(sY + SPC * LDY);   // within-block column norms
+  double2 *sInv = sY + SPC * LDY;                            // 1 / p_i (L > 1): [i SPC + js]
+  double *sC = reinterpret_cast<double *>(sInv + (L > 1 ? NB * SPC : 0));   // within-block column norms
   int *sPex = reinterpret_cast<int *>(sC + NB);              // pivot exponent fields [i SPC + js]
   int *sRedI = sPex + NB * SPC;                              // [w SPC + js]
   int *sShift = sRedI + kWWarps * SPC;                       // [js]
@@ -174,9 +176,11 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
     zero_piv |= v && zzero_words(p0);
     const double2 p = pivot(r);
     inv[q] = v ? zrecip(p) : make_double2(0.0, 0.0);
+    if (L > 1) sInv[r * SPC + js] = inv[q];
     pex[q] = (int)(max(absbits(p.x), absbits(p.y)) >> 52);
     if (SAFE) sPex[r * SPC + js] = pex[q];
   }
+  __syncwarp();                          // sInv: a row's inverse is read in its own warp
   if (zero_piv) raise_status(status, SAFE ? MSTS_STATUS_DELTA : MSTS_STATUS_ZERO_PIVOT);
 
   // max_r |y_r| over the shift's block rows (all four warps), as in the
@@ -192,11 +196,11 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < kWWarps; ++v) E = max(E, sRedI[v * SPC + js]);
-    const double sc = pow2i(-E);
     long long m2 = 0;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-      const double a = y[q].x * sc, bb = y[q].y * sc;
+      // y 2^-E on the exponent fields (exact: the products by 2^-E)
+      const double a = dscale_exp0(y[q].x, -E), bb = dscale_exp0(y[q].y, -E);
       m2 = max(m2, __double_as_longlong(fma(a, a, bb * bb)));
     }
 #pragma unroll
@@ -262,8 +266,20 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
 #pragma unroll
     for (int q = 1; q < RPT; ++q)
       if (q == qn) { yq = y[q]; iq = inv[q]; }
-    double2 x = zmul(yq, iq);
-    if (L > 1) x = make_double2(__shfl_sync(0xffffffffu, x.x, hi_, L), __shfl_sync(0xffffffffu, x.y, hi_, L));
+    double2 x;
+    if (L > 1) {
+      // x_i = y_i (1 / p_i): Re x_i by the owner lane, Im x_i by its partner
+      // (zmul's two multiply-adds, the same operations), half the FP64
+      // instructions of the multiply on the row's chain
+      const double yr = __shfl_sync(0xffffffffu, yq.x, hi_, L), yi = __shfl_sync(0xffffffffu, yq.y, hi_, L);
+      const double2 ip = sInv[i * SPC + js];
+      const bool re = h == hi_;
+      const double m1 = __hiloint2double(__double2hiint(yi) ^ (re ? (int)0x80000000 : 0), __double2loint(yi));
+      const double part = fma(yr, re ? ip.x : ip.y, m1 * (re ? ip.y : ip.x));
+      x = make_double2(__shfl_sync(0xffffffffu, part, hi_, L), __shfl_sync(0xffffffffu, part, hi_ ^ 1, L));
+    } else {
+      x = zmul(yq, iq);
+    }
     if (h == hi_) {
       if (SAFE) sY[js * LDY + i] = yq;   // the row's value at its diagonal step (for the replay)
       sX[i * SPC + js] = x;
