@@ -131,14 +131,17 @@ int msts_solve_batched(const msts_problem *probs, int64_t batch, int32_t nb, voi
   if (flags & MSTS_TENSOR_GEMM) {
     plans.resize((size_t)batch);
     char *cur = static_cast<char *>(workspace) + align256(msts::engine_workspace_bytes(v.data(), (int)batch, nb, safe));
+    std::vector<msts::OzPlanSrc> src;
     for (int64_t i = 0; i < batch; ++i) {
       if (probs[i].m == 0 || probs[i].n == 0) continue;
-      if (msts::ozaki_plan_prepare(&plans[(size_t)i], v[(size_t)i].U, probs[i].ldu, (int)probs[i].m, (int)probs[i].n,
-                                   nb, conj, cur, st) != cudaSuccess)
+      if (msts::ozaki_plan_init(&plans[(size_t)i], (int)probs[i].m, (int)probs[i].n, nb, conj, cur) != cudaSuccess)
         return MSTS_ERR_CUDA;
+      src.push_back(msts::OzPlanSrc{&plans[(size_t)i], v[(size_t)i].U, probs[i].ldu});
       cur += align256(msts::ozaki_plan_bytes((int)probs[i].m, (int)probs[i].n, nb));
       v[(size_t)i].oz = &plans[(size_t)i];
     }
+    // the U planes of the whole batch in one launch
+    if (msts::ozaki_plans_prepare(src.data(), (int)src.size(), st) != cudaSuccess) return MSTS_ERR_CUDA;
   }
   return cuda_rc(msts::engine_run(v.data(), (int)batch, nb, safe, conj, false, workspace, status, st));
 }

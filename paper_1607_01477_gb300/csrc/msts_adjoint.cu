@@ -140,6 +140,7 @@ cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb
     AdjTable at;
     at.count = cnt;
     int maxm = 0, maxn = 0;
+    std::vector<OzPlanSrc> src;                // the U planes of the chunk, prepared in one launch each way
     for (int i = 0; i < cnt; ++i) {
       const msts_adjoint_problem &q = probs[base + i];
       double2 *X = reinterpret_cast<double2 *>(cur);
@@ -160,12 +161,14 @@ cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb
                         (int)q.m, (int)q.n};
       if (tensor && q.m > 0 && q.n > 0) {
         const size_t pb = a256(ozaki_plan_bytes((int)q.m, (int)q.n, nb));
-        cudaError_t e = ozaki_plan_prepare(&plans[2 * i], fwd[i].U, q.ldu, (int)q.m, (int)q.n, nb, false, cur, st);
+        cudaError_t e = ozaki_plan_init(&plans[2 * i], (int)q.m, (int)q.n, nb, false, cur);
         if (e != cudaSuccess) return e;
         cur += pb;
-        e = ozaki_plan_prepare(&plans[2 * i + 1], fwd[i].U, q.ldu, (int)q.m, (int)q.n, nb, true, cur, st);
+        e = ozaki_plan_init(&plans[2 * i + 1], (int)q.m, (int)q.n, nb, true, cur);
         if (e != cudaSuccess) return e;
         cur += pb;
+        src.push_back(OzPlanSrc{&plans[2 * i], fwd[i].U, q.ldu});
+        src.push_back(OzPlanSrc{&plans[2 * i + 1], fwd[i].U, q.ldu});
         fwd[i].oz = &plans[2 * i];
         adj[i].oz = &plans[2 * i + 1];
       }
@@ -173,6 +176,10 @@ cudaError_t adjoint_run(const msts_adjoint_problem *probs, int64_t batch, int nb
       maxn = std::max<int>(maxn, (int)q.n);
     }
     if (maxm == 0) continue;
+    if (!src.empty()) {
+      const cudaError_t e = ozaki_plans_prepare(src.data(), (int)src.size(), st);
+      if (e != cudaSuccess) return e;
+    }
     if (maxn > 0) {
       k_copy_cols<<<dim3(std::max(1, std::min(16, (maxm + 255) / 256)), maxn, 2 * cnt), 256, 0, st>>>(ct);
       cudaError_t e = engine_run(fwd.data(), cnt, nb, false, false, false, nullptr, status, st);

@@ -594,8 +594,13 @@ int diag_lanes(int nb, long long total_cols, bool safe) {
 //     plain one-warp 22.1 / 30.4 / 40.3 / 60.4, four-warp best 23.9 (L=4) / 29.2 (L=2)
 //       / 37.5 (L=2) / 52.9 (L=1); safe one-warp 25.9 / 40.0 / 53.8 / 83.3, four-warp
 //       best 33.8 (L=4) / 39.9 (L=4) / 52.9 (L=2) / 79.5 (L=1).
-// The four-warp layout pays a named-barrier hand-off per row, so it wins only
-// where enough shifts keep the FP64 pipes busy.
+// Rechecked with the closed-form Alg. 4 decisions and the two-lane row multiply
+// (whole-workload medians, every launch forced to one layout): TREVC 4096 per
+// launch 9.06 ms, four-warp L = 4 / 2 / 1 9.25 / 10.85 / 14.99, one-warp 9.50 (the
+// last block steps, ~4000 shifts, now favour L = 4: 53.4 against 56.9 us);
+// pseudospectra 2000^2 at 10^4 shifts (plain solves) L = 1 / 2 / 4 506 / 497 / 523 ms,
+// one-warp 516 ms.  The four-warp layout pays a named-barrier hand-off per row,
+// so it wins only where enough shifts keep the FP64 pipes busy.
 namespace {
 int g_diag_override = 0;
 }
@@ -604,8 +609,8 @@ void set_diag_override(int lanes) { g_diag_override = lanes; }
 int diagw_lanes(long long total_cols, bool safe) {
   if (g_diag_override > 0) return g_diag_override;
   if (total_cols < (safe ? 1200 : 2000)) return 0;   // one-warp layout
-  if (total_cols < (safe ? 3800 : 3500)) return 4;
-  return total_cols < 7000 ? 2 : 1;
+  if (total_cols < (safe ? 4500 : 3500)) return 4;
+  return total_cols < 12000 ? 2 : 1;
 }
 
 cudaError_t launch_diag(const ProbTable &tab, int nb, bool safe, bool conj, int step, int shortcut,

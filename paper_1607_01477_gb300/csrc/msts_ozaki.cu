@@ -49,6 +49,7 @@
 
 namespace msts {
 
+constexpr int kNumSMsOz = 152;   // SMs of the part (grid sizing)
 constexpr int kOzKC = 64;        // K' per chunk: one 128-byte swizzle row of BF16
 constexpr int kOzBM = 128;       // real rows per tile (= TMEM lanes)
 constexpr int kOzBN = 32;        // columns per tile
@@ -633,14 +634,12 @@ size_t ozaki_plan_bytes(int m, int n, int nb, bool gen) {
 
 // With V (generalized problem, upper only) the panel row is
 // [U(r, lo:hi) | V(r, lo:hi)], one exponent for both halves.
+// Row r of block b's panel: its exponent and its 8 digit planes (one warp).
 template <bool CONJ>
-__global__ void k_ozs_prepare(const double2 *U, long long ldu, const double2 *V, long long ldv, int m, int nb,
-                              int KB, __nv_bfloat16 *planes, int *rexp) {
+__device__ __forceinline__ void ozs_prepare_row(const double2 *U, long long ldu, const double2 *V, long long ldv,
+                                                int m, int nb, int KB, int nblk, __nv_bfloat16 *planes, int *rexp,
+                                                int b, int r) {
   const int lane = threadIdx.x & 31;
-  const int r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int b = blockIdx.x;
-  if (r >= m) return;
-  const int nblk = gridDim.x;
   const int hi = m - b * nb, lo = hi - nb < 0 ? 0 : hi - nb, w = hi - lo;
   const bool used = CONJ ? r >= hi : r < lo;
   // Rows that the substitution of this block never updates are left unwritten:
@@ -673,6 +672,36 @@ __global__ void k_ozs_prepare(const double2 *U, long long ldu, const double2 *V,
       *reinterpret_cast<__nv_bfloat162 *>(planes + (q * rows + 2 * (size_t)r + 1) * width + col) =
           __floats2bfloat162_rn(di[q], dr[q]);
     }
+  }
+}
+
+template <bool CONJ>
+__global__ void k_ozs_prepare(const double2 *U, long long ldu, const double2 *V, long long ldv, int m, int nb,
+                              int KB, __nv_bfloat16 *planes, int *rexp) {
+  const int r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= m) return;
+  ozs_prepare_row<CONJ>(U, ldu, V, ldv, m, nb, KB, gridDim.x, planes, rexp, blockIdx.x, r);
+}
+// The planes of every problem of a batch in one launch (problem in grid.z).
+struct OzPrepItem {
+  const double2 *U;
+  long long ldu;
+  int m, nb, KB, nblk;
+  __nv_bfloat16 *planes;
+  int *rexp;
+};
+struct OzPrepTable {
+  OzPrepItem p[kMaxProbs];
+};
+// Each CTA walks (block, 8-row group) pairs of its problem with a grid stride,
+// so that the grid is sized by the work rather than by the largest problem.
+template <bool CONJ>
+__global__ void k_ozs_prepare_batched(const __grid_constant__ OzPrepTable t) {
+  const OzPrepItem &q = t.p[blockIdx.z];
+  const int groups = (q.m + 7) / 8, items = groups * q.nblk, warp = threadIdx.x >> 5;
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int b = w % q.nblk, r = (w / q.nblk) * 8 + warp;
+    if (r < q.m) ozs_prepare_row<CONJ>(q.U, q.ldu, nullptr, 0, q.m, q.nb, q.KB, q.nblk, q.planes, q.rexp, b, r);
   }
 }
 
@@ -711,10 +740,9 @@ __global__ void k_ozs_slice_X(const double2 *B, long long ldb, int lo, int w, in
   }
 }
 
-cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, int m, int n, int nb,
-                               bool conj, void *ws, cudaStream_t st, const double2 *V, long long ldv) {
-  if (V && conj) return cudaErrorInvalidValue;
-  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb, V != nullptr);
+cudaError_t ozaki_plan_init(OzPlan *plan, int m, int n, int nb, bool conj, void *ws, bool gen) {
+  if (gen && conj) return cudaErrorInvalidValue;
+  const int nblk = (m + nb - 1) / nb, KB = kb_of(nb, gen);
   char *c = static_cast<char *>(ws);
   plan->planes = reinterpret_cast<__nv_bfloat16 *>(c); c += a256((size_t)kOzS * 2 * m * (size_t)nblk * KB * 2);
   plan->rexp = reinterpret_cast<int *>(c); c += a256(4 * (size_t)nblk * m);
@@ -723,11 +751,45 @@ cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, in
   plan->m = m; plan->nb = nb; plan->nblk = nblk; plan->KB = KB; plan->nmax = n; plan->conj = conj;
   if (!make_map(&plan->tmA, plan->planes, nblk * KB, 2 * m, kOzBM, 1)) return cudaErrorNotSupported;
   if (n > 0 && !make_map(&plan->tmB, plan->bp, KB, n, kOzBN, kOzS)) return cudaErrorNotSupported;
-  const dim3 grid(nblk, (m + 7) / 8);
-  if (conj) k_ozs_prepare<true><<<grid, 256, 0, st>>>(U, ldu, nullptr, 0, m, nb, KB, plan->planes, plan->rexp);
-  else k_ozs_prepare<false><<<grid, 256, 0, st>>>(U, ldu, V, ldv, m, nb, KB, plan->planes, plan->rexp);
+  return cudaSuccess;
+}
+
+cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, int m, int n, int nb,
+                               bool conj, void *ws, cudaStream_t st, const double2 *V, long long ldv) {
+  cudaError_t e = ozaki_plan_init(plan, m, n, nb, conj, ws, V != nullptr);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(plan->nblk, (m + 7) / 8);
+  if (conj) k_ozs_prepare<true><<<grid, 256, 0, st>>>(U, ldu, nullptr, 0, m, nb, plan->KB, plan->planes, plan->rexp);
+  else k_ozs_prepare<false><<<grid, 256, 0, st>>>(U, ldu, V, ldv, m, nb, plan->KB, plan->planes, plan->rexp);
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t ozaki_plans_prepare(const OzPlanSrc *src, int count, cudaStream_t st) {
+  for (int base = 0; base < count; base += kMaxProbs) {
+    const int cnt = std::min(kMaxProbs, count - base);
+    for (int conj = 0; conj < 2; ++conj) {
+      OzPrepTable t;
+      int k = 0, maxm = 0, maxb = 0;
+      for (int i = 0; i < cnt; ++i) {
+        const OzPlanSrc &q = src[base + i];
+        if (q.plan->conj != (conj != 0) || q.plan->m == 0) continue;
+        t.p[k++] = OzPrepItem{q.U, q.ldu, q.plan->m, q.plan->nb, q.plan->KB, q.plan->nblk, q.plan->planes,
+                              q.plan->rexp};
+        maxm = std::max(maxm, q.plan->m);
+        maxb = std::max(maxb, q.plan->nblk);
+      }
+      if (k == 0) continue;
+      const int items = maxb * ((maxm + 7) / 8);
+      const dim3 grid(std::min(items, 4 * kNumSMsOz), 1, k);
+      if (conj) k_ozs_prepare_batched<true><<<grid, 256, 0, st>>>(t);
+      else k_ozs_prepare_batched<false><<<grid, 256, 0, st>>>(t);
+      count_launches(1);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 // W 2^ex rounded to the nearest double, assembled with integer operations

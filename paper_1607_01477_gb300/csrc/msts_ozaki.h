@@ -43,6 +43,17 @@ size_t ozaki_plan_bytes(int m, int n, int nb, bool gen = false);
 cudaError_t ozaki_plan_prepare(OzPlan *plan, const double2 *U, long long ldu, int m, int n, int nb,
                                bool conj, void *ws, cudaStream_t st, const double2 *V = nullptr,
                                long long ldv = 0);
+// The two halves of ozaki_plan_prepare for a batch: ozaki_plan_init carves a
+// plan's buffers from ws and encodes its tensor maps (host only);
+// ozaki_plans_prepare then writes the U planes of every plan of the batch,
+// one launch per 64 plans of each orientation.
+cudaError_t ozaki_plan_init(OzPlan *plan, int m, int n, int nb, bool conj, void *ws, bool gen = false);
+struct OzPlanSrc {
+  const OzPlan *plan;
+  const double2 *U;
+  long long ldu;
+};
+cudaError_t ozaki_plans_prepare(const OzPlanSrc *src, int count, cudaStream_t st);
 // B(rows, jstart..jstart+ncols) = 2^-pend B - U-panel(b) X(I1, .), rows above the
 // block (upper) or below it (conj); `flops` is recorded by the tracer.
 // planes_ready: the X digit planes and exponents of this block were written by
