@@ -923,10 +923,21 @@ __device__ __noinline__ double update_out_slow_lp(double v, int pe, float W, int
   return (pe ? dshift(v, pe) : v) - scalbn((double)W, ex);
 }
 
-template <int NP>
-__global__ void __launch_bounds__(kOzuThreads, 1)
-k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            const __grid_constant__ OzArgs args, int tiles_n, int tiles_total) {
+// The tiles of one launch: MAXP problems' output tiles (each row-major over its
+// row and column tiles), concatenated; tile t belongs to the problem p with
+// tile_base[p] <= t < tile_base[p + 1].  One problem for the substitution
+// step of a single solve, every problem of a batch for a batched one.
+template <int MAXP>
+struct OzUpdTab {
+  CUtensorMap tmA[MAXP];
+  CUtensorMap tmB[MAXP];
+  OzArgs args[MAXP];
+  int tiles_n[MAXP], tile_base[MAXP + 1];
+  int tiles_total;
+};
+
+template <int NP, int MAXP>
+__global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_constant__ OzUpdTab<MAXP> T) {
   using namespace tc;
   static_assert(NP == kOzS || NP == kOzLpPlanes, "8 planes (FP64-accurate) or 3 (low precision)");
   constexpr uint32_t kBBytes = (uint32_t)NP * kOzBN * kOzKC * 2;   // B planes of one tile
@@ -940,8 +951,14 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   __shared__ uint32_t tmem_base;
   __shared__ int fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per = (tiles_total + gridDim.x - 1) / gridDim.x;
-  const int t0 = blockIdx.x * per, t1 = min(tiles_total, t0 + per);
+  const int per = (T.tiles_total + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * per, t1 = min(T.tiles_total, t0 + per);
+  // problem p of tile t (t increases along each role's walk, so p only advances)
+  auto locate = [&](int t, int &p) {
+    if constexpr (MAXP > 1)
+      while (t >= T.tile_base[p + 1]) ++p;
+  };
+  uint32_t *const status = T.args[0].status;       // one status word for the launch
 
   if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
   if (threadIdx.x == 0) {
@@ -962,32 +979,37 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   auto wait = [&](uint64_t *bar, uint32_t parity) {
-    const bool ok = mbar_wait(bar, parity, args.status, MSTS_STATUS_TIMEOUT);
-    if (!ok) raise_status(args.status, MSTS_STATUS_TIMEOUT);
+    const bool ok = mbar_wait(bar, parity, status, MSTS_STATUS_TIMEOUT);
+    if (!ok) raise_status(status, MSTS_STATUS_TIMEOUT);
     return ok;
   };
   int a_issued = 0, b_issued = 0;                   // A reloads and B loads the producer issued
 
   if (warp == kOzuEpiWarps) {
     if (lane == 0) {                                // ---------------- TMA producer
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
+      if (MAXP == 1) {
+        prefetch_tmap(&T.tmA[0]);
+        prefetch_tmap(&T.tmB[0]);
+      }
       pdl_wait();                                   // the X planes come from the diagonal step
-      int prev_rt = -1, na = 0;
+      int prev_rt = -1, prev_p = -1, na = 0, p = 0;
       for (int t = t0, k = 0; t < t1; ++t, ++k) {
-        const int rt = t / tiles_n, ct = t - rt * tiles_n;
-        if (rt != prev_rt) {                        // new row tile: reload the A planes
+        locate(t, p);
+        const int lt = t - T.tile_base[p], tn = T.tiles_n[p];
+        const int rt = lt / tn, ct = lt - rt * tn;
+        if (rt != prev_rt || p != prev_p) {         // new row tile: reload the A planes
           if (na > 0 && !wait(&aempty, (na - 1) & 1)) { fail = 1; break; }
           mbar_arrive_expect_tx(&afull, NP * kOzABytes);
           for (int q = 0; q < NP; ++q)
-            tma_load_3d(sA + q * kOzABytes, &tmA, &afull, args.a_x0, args.row_lo + rt * kOzBM, q);
+            tma_load_3d(sA + q * kOzABytes, &T.tmA[p], &afull, T.args[p].a_x0, T.args[p].row_lo + rt * kOzBM, q);
           ++na;
           prev_rt = rt;
+          prev_p = p;
         }
         const int bb = k & 1;
         if (k >= 2 && !wait(&bempty[bb], ((k >> 1) - 1) & 1)) { fail = 1; break; }
         mbar_arrive_expect_tx(&bfull[bb], kBBytes);
-        tma_load_3d(sB + bb * kBBytes, &tmB, &bfull[bb], 0, ct * kOzBN, 0);
+        tma_load_3d(sB + bb * kBBytes, &T.tmB[p], &bfull[bb], 0, ct * kOzBN, 0);
         ++b_issued;
       }
       a_issued = na;
@@ -997,14 +1019,16 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       // wait in hardware for the diagonal step rather than spinning on the
       // first barrier beside its CTAs
       pdl_wait();
-      int prev_rt = -1, na = 0;
+      int prev_rt = -1, prev_p = -1, na = 0, p = 0;
       for (int t = t0, k = 0; t < t1 && !fail; ++t, ++k) {
-        const int rt = t / tiles_n;
-        if (rt != prev_rt) {
+        locate(t, p);
+        const int rt = (t - T.tile_base[p]) / T.tiles_n[p];
+        if (rt != prev_rt || p != prev_p) {
           if (na > 0) mma_commit(&aempty);          // old planes free once their MMAs finish
           if (!wait(&afull, na & 1)) { fail = 1; break; }
           ++na;
           prev_rt = rt;
+          prev_p = p;
         }
         const int bb = k & 1, ab = k & 1;
         if (k >= 2 && !wait(&accempty[ab], ((k >> 1) - 1) & 1)) { fail = 1; break; }
@@ -1035,19 +1059,25 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // previous tile is processed, so no memory latency sits between tiles.
     const int quarter = warp & 3, cgroup = warp >> 2;
     const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
-    const long long ldr2 = 2 * args.ldr;            // column stride in doubles
     constexpr int kCW = kOzBN * 4 / kOzuEpiWarps, kQ = 4, kPasses = kCW / kQ;
     struct TileIn {
       double b[kCW];                                // B(row, columns of this warp)
       double *base;                                 // &B(row, first column of this warp)
+      long long ldr2;                               // column stride of B in doubles
       int cx, pe;                                   // lane j: f_j - 56 and pend of column j
       int er, nval;
       bool row_ok, any_pe;                          // any_pe: some column of the tile has a pending scaling
     };
+    int pf = 0;                                     // problem of the tile being fetched
     auto fetch = [&](int t, TileIn &in) {
-      const int rt = t / tiles_n, ct = t - rt * tiles_n;
+      locate(t, pf);
+      const OzArgs &args = T.args[pf];
+      const int lt = t - T.tile_base[pf], tn = T.tiles_n[pf];
+      const int rt = lt / tn, ct = lt - rt * tn;
       const int i = args.row_lo + rt * kOzBM + 32 * quarter + lane;   // real row of A'
       const int r = i >> 1, part = i & 1;
+      const long long ldr2 = 2 * args.ldr;
+      in.ldr2 = ldr2;
       in.row_ok = i < args.row_hi;
       in.nval = min(kOzBN, args.ncols - ct * kOzBN);
       in.cx = lane < in.nval ? args.cexp[ct * kOzBN + lane] - (NP == kOzS ? 56 : 14) : 0;
@@ -1173,6 +1203,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
           }
         }
+        const long long ldr2 = cur.ldr2;
         double *pj = cur.base + kQ * h * ldr2;
 #pragma unroll
         for (int j = 0; j < kQ; ++j, pj += ldr2)
@@ -1195,7 +1226,7 @@ k_oz_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     tc_fence_before();
     __syncthreads();
   }
-  if (fail && threadIdx.x == 0) raise_status(args.status, MSTS_STATUS_TIMEOUT);
+  if (fail && threadIdx.x == 0) raise_status(status, MSTS_STATUS_TIMEOUT);
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
@@ -1229,18 +1260,27 @@ cudaError_t ozaki_update(const OzPlan &plan, int b, int lo, int hi, double2 *B, 
     const int np = lp ? kOzLpPlanes : kOzS;
     const double mma_flops = (double)total * (np * (np + 1) / 2) * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
     void *h = trace_on() ? trace_start(2, mma_flops, (double)total * np * kOzBN * kOzKC * 2, st) : nullptr;
+    OzUpdTab<1> tab;
+    tab.tmA[0] = plan.tmA;
+    tab.tmB[0] = tmB;
+    tab.args[0] = a;
+    tab.tiles_n[0] = tiles_n;
+    tab.tile_base[0] = 0;
+    tab.tile_base[1] = total;
+    tab.tiles_total = total;
     cudaError_t e;
     if (lp) {
-      e = cudaFuncSetAttribute(k_oz_update<kOzLpPlanes>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_oz_update<kOzLpPlanes, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)ozu_smem<kOzLpPlanes>());
       if (e == cudaSuccess)
-        e = launch_pdl(k_oz_update<kOzLpPlanes>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
-                       ozu_smem<kOzLpPlanes>(), st, plan.tmA, tmB, a, tiles_n, total);
+        e = launch_pdl(k_oz_update<kOzLpPlanes, 1>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
+                       ozu_smem<kOzLpPlanes>(), st, tab);
     } else {
-      e = cudaFuncSetAttribute(k_oz_update<kOzS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ozu_smem<kOzS>());
+      e = cudaFuncSetAttribute(k_oz_update<kOzS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ozu_smem<kOzS>());
       if (e == cudaSuccess)
-        e = launch_pdl(k_oz_update<kOzS>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
-                       ozu_smem<kOzS>(), st, plan.tmA, tmB, a, tiles_n, total);
+        e = launch_pdl(k_oz_update<kOzS, 1>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
+                       ozu_smem<kOzS>(), st, tab);
     }
     trace_stop(h, st);
     count_launches(1);
@@ -1298,6 +1338,35 @@ cudaError_t ozaki_update_batched(const OzBatchStep *steps, int count, uint32_t *
     chunk_tiles += (double)hb->tiles_n[i] * hb->tiles_m[i] * (plan.KB / kOzKC);
   }
   if (max_tn == 0) return cudaSuccess;
+  if (chunk_tiles == tiles) {
+    // one K chunk per block (n_b <= 32): the persistent kernel over every
+    // problem's tiles, a row tile's U planes resident across its column tiles
+    std::unique_ptr<OzUpdTab<kMaxProbs>> tb(new OzUpdTab<kMaxProbs>());
+    int k = 0, total = 0;
+    for (int i = 0; i < count; ++i) {
+      const int nt = hb->tiles_n[i] * hb->tiles_m[i];
+      if (nt == 0) continue;
+      tb->tmA[k] = hb->tmA[i];
+      tb->tmB[k] = hb->tmB[i];
+      tb->args[k] = hb->args[i];
+      tb->tiles_n[k] = hb->tiles_n[i];
+      tb->tile_base[k] = total;
+      total += nt;
+      ++k;
+    }
+    for (int i = k; i <= kMaxProbs; ++i) tb->tile_base[i] = total;   // past the last problem
+    tb->tiles_total = total;
+    cudaError_t e = cudaFuncSetAttribute(k_oz_update<kOzS, kMaxProbs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ozu_smem<kOzS>());
+    if (e != cudaSuccess) return e;
+    const double mma_flops = tiles * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+    void *h = trace_on() ? trace_start(2, mma_flops, tiles * kOzS * kOzBN * kOzKC * 2, st) : nullptr;
+    e = launch_pdl(k_oz_update<kOzS, kMaxProbs>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
+                   ozu_smem<kOzS>(), st, *tb);
+    trace_stop(h, st);
+    count_launches(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(k_oz_batched<kUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
   if (e != cudaSuccess) return e;
   const double mma_flops = chunk_tiles * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
