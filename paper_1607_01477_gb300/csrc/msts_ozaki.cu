@@ -936,7 +936,35 @@ struct OzUpdTab {
   int tiles_total;
 };
 
-template <int NP, int MAXP>
+// Position of tile t in its problem, for tiles visited in increasing order:
+// row-major over the rectangle of row and column tiles, or (TRI) over the
+// tiles that meet the upper triangle of an m x m output, row tile rt holding
+// the column tiles 2 rt .. tiles_n - 1 (a row tile spans 64 complex rows).
+template <int MAXP, bool TRI>
+struct TileCursor {
+  int p = 0, rt = 0, rs = 0, cnt = -1;
+  __device__ __forceinline__ void at(const OzUpdTab<MAXP> &T, int t, int &prob, int &row_t, int &col_t) {
+    const int p0 = p;
+    if constexpr (MAXP > 1)
+      while (t >= T.tile_base[p + 1]) ++p;
+    const int lt = t - T.tile_base[p], tn = T.tiles_n[p];
+    if constexpr (!TRI) {
+      row_t = lt / tn;
+      col_t = lt - row_t * tn;
+    } else {
+      if (p != p0 || cnt < 0) { rt = 0; rs = 0; cnt = tn; }
+      while (lt >= rs + cnt) { rs += cnt; ++rt; cnt = max(0, tn - 2 * rt); }
+      row_t = rt;
+      col_t = 2 * rt + (lt - rs);
+    }
+    prob = p;
+  }
+};
+
+// TRI: the adjoint's dU = -triu(P) (P = L X^H, nothing read from the output):
+// the tiles meeting the upper triangle, each output -P, strictly lower
+// entries 0 (the tiles wholly below the diagonal are zeroed apart).
+template <int NP, int MAXP, bool TRI = false>
 __global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_constant__ OzUpdTab<MAXP> T) {
   using namespace tc;
   static_assert(NP == kOzS || NP == kOzLpPlanes, "8 planes (FP64-accurate) or 3 (low precision)");
@@ -953,11 +981,6 @@ __global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = (T.tiles_total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * per, t1 = min(T.tiles_total, t0 + per);
-  // problem p of tile t (t increases along each role's walk, so p only advances)
-  auto locate = [&](int t, int &p) {
-    if constexpr (MAXP > 1)
-      while (t >= T.tile_base[p + 1]) ++p;
-  };
   uint32_t *const status = T.args[0].status;       // one status word for the launch
 
   if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
@@ -992,11 +1015,11 @@ __global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_const
         prefetch_tmap(&T.tmB[0]);
       }
       pdl_wait();                                   // the X planes come from the diagonal step
-      int prev_rt = -1, prev_p = -1, na = 0, p = 0;
+      int prev_rt = -1, prev_p = -1, na = 0;
+      TileCursor<MAXP, TRI> cur;
       for (int t = t0, k = 0; t < t1; ++t, ++k) {
-        locate(t, p);
-        const int lt = t - T.tile_base[p], tn = T.tiles_n[p];
-        const int rt = lt / tn, ct = lt - rt * tn;
+        int p, rt, ct;
+        cur.at(T, t, p, rt, ct);
         if (rt != prev_rt || p != prev_p) {         // new row tile: reload the A planes
           if (na > 0 && !wait(&aempty, (na - 1) & 1)) { fail = 1; break; }
           mbar_arrive_expect_tx(&afull, NP * kOzABytes);
@@ -1019,10 +1042,11 @@ __global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_const
       // wait in hardware for the diagonal step rather than spinning on the
       // first barrier beside its CTAs
       pdl_wait();
-      int prev_rt = -1, prev_p = -1, na = 0, p = 0;
+      int prev_rt = -1, prev_p = -1, na = 0;
+      TileCursor<MAXP, TRI> cur;
       for (int t = t0, k = 0; t < t1 && !fail; ++t, ++k) {
-        locate(t, p);
-        const int rt = (t - T.tile_base[p]) / T.tiles_n[p];
+        int p, rt, ct;
+        cur.at(T, t, p, rt, ct);
         if (rt != prev_rt || p != prev_p) {
           if (na > 0) mma_commit(&aempty);          // old planes free once their MMAs finish
           if (!wait(&afull, na & 1)) { fail = 1; break; }
@@ -1067,13 +1091,13 @@ __global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_const
       int cx, pe;                                   // lane j: f_j - 56 and pend of column j
       int er, nval;
       bool row_ok, any_pe;                          // any_pe: some column of the tile has a pending scaling
+      int rc, cc;                                   // TRI: this thread's complex row, the warp's first column
     };
-    int pf = 0;                                     // problem of the tile being fetched
+    TileCursor<MAXP, TRI> fc;                       // the tile being fetched
     auto fetch = [&](int t, TileIn &in) {
-      locate(t, pf);
+      int pf, rt, ct;
+      fc.at(T, t, pf, rt, ct);
       const OzArgs &args = T.args[pf];
-      const int lt = t - T.tile_base[pf], tn = T.tiles_n[pf];
-      const int rt = lt / tn, ct = lt - rt * tn;
       const int i = args.row_lo + rt * kOzBM + 32 * quarter + lane;   // real row of A'
       const int r = i >> 1, part = i & 1;
       const long long ldr2 = 2 * args.ldr;
@@ -1086,9 +1110,11 @@ __global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_const
       in.er = in.row_ok ? args.rexp[r] : 0;
       const int c0 = kCW * cgroup;
       in.base = reinterpret_cast<double *>(args.R + r + (long long)(args.col_base + ct * kOzBN + c0) * args.ldr) + part;
+      in.rc = r;
+      in.cc = args.col_base + ct * kOzBN + c0;
       const double *pj = in.base;
 #pragma unroll
-      for (int j = 0; j < kCW; ++j, pj += ldr2) in.b[j] = (in.row_ok && c0 + j < in.nval) ? *pj : 0.0;
+      for (int j = 0; j < kCW; ++j, pj += ldr2) in.b[j] = (!TRI && in.row_ok && c0 + j < in.nval) ? *pj : 0.0;
     };
     TileIn cur, nxt;
     pdl_wait();                                     // B, exponents and pending scalings of the diagonal step
@@ -1202,6 +1228,11 @@ __global__ void __launch_bounds__(kOzuThreads, 1) k_oz_update(const __grid_const
               out[j] = update_out_slow(cur.b[kQ * h + j], pe, Wh[j], Wl[j], ex);
             }
           }
+        }
+        if constexpr (TRI) {                        // strictly below the diagonal: zero
+#pragma unroll
+          for (int j = 0; j < kQ; ++j)
+            if (cur.rc > cur.cc + kQ * h + j) out[j] = 0.0;
         }
         const long long ldr2 = cur.ldr2;
         double *pj = cur.base + kQ * h * ldr2;
@@ -1386,8 +1417,9 @@ size_t ozaki_neg_triu_bytes(int m, int n) {
   return a256((size_t)kOzS * 2 * m * K * 2) + a256((size_t)kOzS * m * K * 2) + a256(4 * (size_t)m) * 2;
 }
 
-cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *ws, uint32_t *status,
-                                   cudaStream_t st) {
+// The chunked form (more than 64 shifts: several K chunks per tile).
+static cudaError_t ozaki_neg_triu_chunked(const OzNegTriuItem *items, int count, void *ws, uint32_t *status,
+                                          cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   if (count > kMaxProbs) return cudaErrorInvalidValue;
   std::unique_ptr<OzBatch> hb(new OzBatch());
@@ -1430,6 +1462,90 @@ cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *
   trace_stop(h, st);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// The entries of dU in the tiles wholly below the diagonal (complex rows
+// 64 rt.., columns 32 ct.. with ct < 2 rt; k_oz_update<.., TRI> writes the
+// others), every problem of a batch: one column per y, problem in z.
+struct OzZeroItem {
+  double2 *dU;
+  long long ld;
+  int m;
+};
+struct OzZeroTable {
+  OzZeroItem p[kMaxProbs];
+};
+__global__ void k_oz_zero_lower(const __grid_constant__ OzZeroTable t) {
+  const OzZeroItem &q = t.p[blockIdx.z];
+  for (int c = blockIdx.y; c < q.m; c += gridDim.y) {
+    const int r0 = (kOzBM / 2) * ((c / kOzBN) / 2 + 1);
+    for (int r = r0 + (int)(blockIdx.x * blockDim.x + threadIdx.x); r < q.m; r += gridDim.x * blockDim.x)
+      q.dU[r + (long long)c * q.ld] = make_double2(0.0, 0.0);
+  }
+}
+
+cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *ws, uint32_t *status,
+                                   cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (count > kMaxProbs) return cudaErrorInvalidValue;
+  std::unique_ptr<OzUpdTab<kMaxProbs>> tb(new OzUpdTab<kMaxProbs>());
+  OzZeroTable zt;
+  char *cur = static_cast<char *>(ws);
+  int k = 0, total = 0, maxm = 0;
+  double tiles = 0.0;
+  bool one_chunk = true;
+  for (int i = 0; i < count; ++i)
+    if (items[i].m > 0 && kpad(items[i].n > 0 ? items[i].n : 1) != kOzKC) one_chunk = false;
+  if (!one_chunk) return ozaki_neg_triu_chunked(items, count, ws, status, st);
+  for (int i = 0; i < count; ++i) {
+    const OzNegTriuItem &q = items[i];
+    if (q.m <= 0) continue;
+    const int m = q.m, n = q.n, K = kpad(n > 0 ? n : 1);
+    __nv_bfloat16 *Ap = reinterpret_cast<__nv_bfloat16 *>(cur); cur += a256((size_t)kOzS * 2 * m * K * 2);
+    __nv_bfloat16 *Bp = reinterpret_cast<__nv_bfloat16 *>(cur); cur += a256((size_t)kOzS * m * K * 2);
+    int *rexp = reinterpret_cast<int *>(cur); cur += a256(4 * (size_t)m);
+    int *cexp = reinterpret_cast<int *>(cur); cur += a256(4 * (size_t)m);
+    k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(q.L, q.ldl, m, n, rexp, 1);
+    k_oz_slice_A<<<dim3((K / 2 + 255) / 256, m), 256, 0, st>>>(q.L, q.ldl, m, n, rexp, Ap, K, 1);
+    k_oz_slice_BH<<<m, 256, 0, st>>>(q.X, q.ldx, m, n, cexp, Bp, K);
+    count_launches(3);
+    if (!make_map(&tb->tmA[k], Ap, K, 2 * m, kOzBM, 1) || !make_map(&tb->tmB[k], Bp, K, m, kOzBN, kOzS))
+      return cudaErrorNotSupported;
+    OzArgs a{};
+    a.B = q.dU; a.ldb = q.lddu; a.R = q.dU; a.ldr = q.lddu;
+    a.rexp = rexp; a.cexp = cexp;
+    a.m = m; a.n = m; a.K = K;
+    a.a_x0 = 0;
+    a.row_lo = 0; a.row_hi = 2 * m;
+    a.col_base = 0; a.ncols = m;
+    a.status = ozaki_call_status(status, st);
+    tb->args[k] = a;
+    const int tn = (m + kOzBN - 1) / kOzBN, tm = (2 * m + kOzBM - 1) / kOzBM;
+    int nt = 0;
+    for (int rt = 0; rt < tm; ++rt) nt += std::max(0, tn - 2 * rt);   // the tiles meeting the upper triangle
+    tb->tiles_n[k] = tn;
+    tb->tile_base[k] = total;
+    total += nt;
+    tiles += nt;
+    zt.p[k] = OzZeroItem{q.dU, q.lddu, m};
+    maxm = std::max(maxm, m);
+    ++k;
+  }
+  if (k == 0) return cudaGetLastError();
+  for (int i = k; i <= kMaxProbs; ++i) tb->tile_base[i] = total;
+  tb->tiles_total = total;
+  k_oz_zero_lower<<<dim3(1, std::min(maxm, 65535), k), 256, 0, st>>>(zt);
+  count_launches(1);
+  cudaError_t e = cudaFuncSetAttribute(k_oz_update<kOzS, kMaxProbs, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ozu_smem<kOzS>());
+  if (e != cudaSuccess) return e;
+  const double mma_flops = tiles * 36.0 * (kOzKC / 16) * 2.0 * kOzBM * kOzBN * 16;
+  void *h = trace_on() ? trace_start(2, mma_flops, tiles * kOzS * kOzBN * kOzKC * 2, st) : nullptr;
+  e = launch_pdl(k_oz_update<kOzS, kMaxProbs, true>, dim3(std::min(total, kOzPersistentCtas)), dim3(kOzuThreads),
+                 ozu_smem<kOzS>(), st, *tb);
+  trace_stop(h, st);
+  count_launches(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace msts
