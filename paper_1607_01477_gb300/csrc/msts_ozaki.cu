@@ -1464,6 +1464,56 @@ static cudaError_t ozaki_neg_triu_chunked(const OzNegTriuItem *items, int count,
   return cudaGetLastError();
 }
 
+// The operands of dU = -triu(L X^H) for every problem of a batch (one K chunk:
+// n <= 32): blockIdx.y = 0, one warp per row r of L, its exponent e_r and the
+// A planes of row r (the layout of k_oz_slice_A); blockIdx.y = 1, one warp per
+// row c of X, the exponent f_c of conj(X(c, :)) and its B planes (the layout
+// of k_oz_slice_BH).  Problem in grid.z.
+struct OzAdjSliceItem {
+  const double2 *L; long long ldl;
+  const double2 *X; long long ldx;
+  int m, n;
+  __nv_bfloat16 *Ap, *Bp;
+  int *rexp, *cexp;
+};
+struct OzAdjSliceTable {
+  OzAdjSliceItem p[kMaxProbs];
+};
+__global__ void k_oz_slice_adj(const __grid_constant__ OzAdjSliceTable t) {
+  const OzAdjSliceItem &q = t.p[blockIdx.z];
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= q.m) return;
+  const bool a_side = blockIdx.y == 0;
+  const double2 *src = a_side ? q.L : q.X;
+  const long long ld = a_side ? q.ldl : q.ldx;
+  const double2 v = lane < q.n ? src[r + (long long)lane * ld] : make_double2(0.0, 0.0);
+  int e = bound_exp(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (e < -(1 << 28)) e = 0;
+  if (lane == 0) (a_side ? q.rexp : q.cexp)[r] = e;
+  float dr[kOzS], di[kOzS];
+  digits8(v.x, e, dr);
+  digits8(a_side ? v.y : -v.y, e, di);
+  constexpr int K = kOzKC;
+  if (a_side) {
+    const size_t rows = 2 * (size_t)q.m;
+#pragma unroll
+    for (int s = 0; s < kOzS; ++s) {
+      *reinterpret_cast<__nv_bfloat162 *>(q.Ap + (s * rows + 2 * (size_t)r) * K + 2 * lane) =
+          __floats2bfloat162_rn(dr[s], -di[s]);     // row 2r:   (Re L, -Im L)
+      *reinterpret_cast<__nv_bfloat162 *>(q.Ap + (s * rows + 2 * (size_t)r + 1) * K + 2 * lane) =
+          __floats2bfloat162_rn(di[s], dr[s]);      // row 2r+1: (Im L,  Re L)
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < kOzS; ++s)
+      *reinterpret_cast<__nv_bfloat162 *>(q.Bp + ((size_t)s * q.m + r) * K + 2 * lane) =
+          __floats2bfloat162_rn(dr[s], di[s]);
+  }
+}
+
 // The entries of dU in the tiles wholly below the diagonal (complex rows
 // 64 rt.., columns 32 ct.. with ct < 2 rt; k_oz_update<.., TRI> writes the
 // others), every problem of a batch: one column per y, problem in z.
@@ -1490,6 +1540,7 @@ cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *
   if (count > kMaxProbs) return cudaErrorInvalidValue;
   std::unique_ptr<OzUpdTab<kMaxProbs>> tb(new OzUpdTab<kMaxProbs>());
   OzZeroTable zt;
+  OzAdjSliceTable sl;
   char *cur = static_cast<char *>(ws);
   int k = 0, total = 0, maxm = 0;
   double tiles = 0.0;
@@ -1505,10 +1556,7 @@ cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *
     __nv_bfloat16 *Bp = reinterpret_cast<__nv_bfloat16 *>(cur); cur += a256((size_t)kOzS * m * K * 2);
     int *rexp = reinterpret_cast<int *>(cur); cur += a256(4 * (size_t)m);
     int *cexp = reinterpret_cast<int *>(cur); cur += a256(4 * (size_t)m);
-    k_oz_rowexp<<<(m + 7) / 8, 256, 0, st>>>(q.L, q.ldl, m, n, rexp, 1);
-    k_oz_slice_A<<<dim3((K / 2 + 255) / 256, m), 256, 0, st>>>(q.L, q.ldl, m, n, rexp, Ap, K, 1);
-    k_oz_slice_BH<<<m, 256, 0, st>>>(q.X, q.ldx, m, n, cexp, Bp, K);
-    count_launches(3);
+    sl.p[k] = OzAdjSliceItem{q.L, q.ldl, q.X, q.ldx, m, n, Ap, Bp, rexp, cexp};
     if (!make_map(&tb->tmA[k], Ap, K, 2 * m, kOzBM, 1) || !make_map(&tb->tmB[k], Bp, K, m, kOzBN, kOzS))
       return cudaErrorNotSupported;
     OzArgs a{};
@@ -1534,8 +1582,9 @@ cudaError_t ozaki_neg_triu_batched(const OzNegTriuItem *items, int count, void *
   if (k == 0) return cudaGetLastError();
   for (int i = k; i <= kMaxProbs; ++i) tb->tile_base[i] = total;
   tb->tiles_total = total;
+  k_oz_slice_adj<<<dim3((maxm + 7) / 8, 2, k), 256, 0, st>>>(sl);
   k_oz_zero_lower<<<dim3(1, std::min(maxm, 65535), k), 256, 0, st>>>(zt);
-  count_launches(1);
+  count_launches(2);
   cudaError_t e = cudaFuncSetAttribute(k_oz_update<kOzS, kMaxProbs, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ozu_smem<kOzS>());
   if (e != cudaSuccess) return e;
