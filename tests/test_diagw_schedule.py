@@ -1,7 +1,8 @@
 """Host-side model of the four-warp diagonal-block step's schedule
 (csrc/msts_diagw.cu): the per-warp sequence of rescales, AXPYs, productions of
 x_i and named-barrier operations, written out from the kernel's loop
-structure, run for every lane width and both directions.
+structure, run for every lane width and both directions of the cyclic row
+layout and for the chunk-pair layout of upper solves with four lanes.
 
 It checks what the kernel's correctness rests on: (1) every row value sees the
 same operations in the same order as in the serial substitution (the rescale of
@@ -59,23 +60,113 @@ def warp_program(w, L, conj, rescale_rows):
     return ops
 
 
-def rows_of(w, L, q):
+def chunk_program(w, rescale_rows):
+    """The chunk-pair layout (upper, L = 4): warp w holds chunk w (slot 0) and
+    chunk 7 - w (slot 1), four consecutive rows each; chunk c is owned by warp
+    7 - c (c >= 4) or c; an owner of a chunk c >= 4 defers its slot 0's
+    operations of the chunk to the chunk's last row."""
+    ops = []
+    kk = rescale_rows.get
+
+    def produce(q, i):
+        if kk(i):
+            ops.append(("rescale", q, i))
+        ops.extend([("produce", q, i), ("arrive", i)])
+
+    ahead = False
+    if w == 0:
+        if kk(NB - 1):
+            ops.extend(("rescale", q, NB - 1) for q in range(2))
+        ops.extend([("produce", 1, NB - 1), ("arrive", NB - 1)])   # no rescale inside
+        ahead = True
+    for c in range(7, 3, -1):
+        own = w == 7 - c
+        for k in range(3, -1, -1):
+            i = 4 * c + k
+            if kk(i) and not ahead:
+                ops.extend(("rescale", q, i) for q in range(2))
+            if not own:
+                ops.append(("sync", i))
+            ahead = False
+            if own:
+                if k > 0:
+                    ops.append(("axpy", 1, i))
+                    produce(1, i - 1)
+                    ahead = True
+                else:
+                    for d in (2, 1, 0):
+                        ops.append(("axpy", 0, 4 * c + d + 1))
+                        if kk(4 * c + d):
+                            ops.append(("rescale", 0, 4 * c + d))
+                    ops.append(("axpy", 0, i))
+                    if c == 4:
+                        produce(0, i - 1)
+                        if kk(i - 1):
+                            ops.append(("rescale", 1, i - 1))
+                        ahead = True
+            elif k == 0 and w == 8 - c:
+                ops.append(("axpy", 1, i))
+                produce(1, i - 1)
+                ops.append(("axpy", 0, i))
+                if kk(i - 1):
+                    ops.append(("rescale", 0, i - 1))
+                ahead = True
+            else:
+                ops.append(("axpy", 0, i))
+                if w > 7 - c:
+                    ops.append(("axpy", 1, i))
+    for c in range(3, -1, -1):
+        own = w == c
+        for k in range(3, -1, -1):
+            i = 4 * c + k
+            if kk(i) and not ahead:
+                ops.extend(("rescale", q, i) for q in range(2))
+            if not own:
+                ops.append(("sync", i))
+            ahead = False
+            if (own and k > 0) or (not own and k == 0 and w == c - 1):
+                ops.append(("axpy", 0, i))
+                produce(0, i - 1)
+                if kk(i - 1):
+                    ops.append(("rescale", 1, i - 1))
+                ahead = True
+            elif w < c:
+                ops.append(("axpy", 0, i))
+    return ops
+
+
+def program(layout, w, L, conj, rescale_rows):
+    return chunk_program(w, rescale_rows) if layout == "chunk" else warp_program(w, L, conj, rescale_rows)
+
+
+def rows_of(w, L, q, layout="cyclic"):
+    if layout == "chunk":
+        return [4 * (w if q == 0 else 7 - w) + h for h in range(4)]
     return [w + 4 * (h + L * q) for h in range(L)]
 
 
-@pytest.mark.parametrize("L", [1, 2, 4])
-@pytest.mark.parametrize("conj", [False, True])
-def test_every_value_sees_the_serial_order(L, conj):
-    rng = random.Random(17 + L + 10 * conj)
+LAYOUTS = [("cyclic", L, conj) for L in (1, 2, 4) for conj in (False, True)] + [("chunk", 4, False)]
+
+
+def test_layouts_cover_every_row_once():
+    for layout, L, conj in LAYOUTS:
+        RPT = NB // (4 * L)
+        rows = sorted(r for w in range(4) for q in range(RPT) for r in rows_of(w, L, q, layout))
+        assert rows == list(range(NB)), (layout, L)
+
+
+@pytest.mark.parametrize("layout,L,conj", LAYOUTS)
+def test_every_value_sees_the_serial_order(layout, L, conj):
+    rng = random.Random(17 + L + 10 * conj + 100 * (layout == "chunk"))
     order = list(range(NB)) if conj else list(range(NB - 1, -1, -1))
     for _ in range(40):
         resc = {i: rng.random() < 0.25 for i in range(NB)}
         seen = {r: [] for r in range(NB)}
         for w in range(4):
-            for op in warp_program(w, L, conj, resc):
+            for op in program(layout, w, L, conj, resc):
                 if op[0] in ("rescale", "axpy", "produce"):
                     _, q, i = op
-                    for r in rows_of(w, L, q):
+                    for r in rows_of(w, L, q, layout):
                         if op[0] == "rescale":
                             seen[r].append(("R", i))
                         elif op[0] == "axpy" and (r > i if conj else r < i):
@@ -94,12 +185,11 @@ def test_every_value_sees_the_serial_order(L, conj):
             assert seen[r] == want, (L, conj, r)
 
 
-@pytest.mark.parametrize("L", [1, 2, 4])
-@pytest.mark.parametrize("conj", [False, True])
-def test_barriers_complete_without_deadlock_or_id_reuse(L, conj):
+@pytest.mark.parametrize("layout,L,conj", LAYOUTS)
+def test_barriers_complete_without_deadlock_or_id_reuse(layout, L, conj):
     order = list(range(NB)) if conj else list(range(NB - 1, -1, -1))
     pos = {r: n for n, r in enumerate(order)}
-    progs = {w: [op for op in warp_program(w, L, conj, {}) if op[0] in ("arrive", "sync")] for w in range(4)}
+    progs = {w: [op for op in program(layout, w, L, conj, {}) if op[0] in ("arrive", "sync")] for w in range(4)}
     for w in range(4):
         assert [op[1] for op in progs[w]] == order      # one barrier operation per row, in row order
     pc = {w: 0 for w in range(4)}
