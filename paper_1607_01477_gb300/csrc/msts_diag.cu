@@ -600,7 +600,12 @@ int diag_lanes(int nb, long long total_cols, bool safe) {
 // last block steps, ~4000 shifts, now favour L = 4: 53.4 against 56.9 us);
 // pseudospectra 2000^2 at 10^4 shifts (plain solves) L = 1 / 2 / 4 506 / 497 / 523 ms,
 // one-warp 516 ms.  The four-warp layout pays a named-barrier hand-off per row,
-// so it wins only where enough shifts keep the FP64 pipes busy.
+// so it wins only where enough shifts keep the FP64 pipes busy.  Rechecked after
+// the chunk-pair row layout of upper four-lane solves (TREVC 4096 with the
+// one-warp / four-warp switch at 600, 900, 1200, 1600 shifts: 8.78 / 8.74 /
+// 8.71 / 8.73 ms; the L = 4 / 2 switch at 4500, 6000 or never: equal within
+// 0.01 ms; pseudospectra 494 ms with these plain thresholds, 503-511 ms with
+// four other sets): the thresholds below stay.
 namespace {
 int g_diag_override = 0;
 }
