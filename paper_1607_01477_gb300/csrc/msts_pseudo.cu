@@ -25,6 +25,7 @@ namespace msts {
 constexpr int kLzThreads = 256;
 constexpr int kLzWarps = kLzThreads / 32;
 constexpr int kMaxIters = 64;
+constexpr int kLzGroup = 2;              // Lanczos vectors per warp reduction (a power of two <= 16)
 
 struct LanczosState {
   double2 *V;        // (K+1) Lanczos vectors, vector k of point p at V + k*vstride + p*m
@@ -204,20 +205,46 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_step_r(LanczosState S, i
   for (int q = 0; q < RW; ++q) n0 += w[q].x * w[q].x + w[q].y * w[q].y;
   n0 = block_sum(n0, red);
   for (int pass = 0; pass < 2; ++pass) {
-    for (int i = 0; i <= k; ++i) {
-      const double2 *vi = S.V + (long long)i * S.vstride + (long long)p * m;
-      double2 sacc = make_double2(0.0, 0.0);
+    // v_i^H w for kLzGroup vectors at a time: each thread's partial sums (over
+    // its elements in increasing order), then one reduce-scatter butterfly
+    // over the warp for all of them (lanes l and l ^ o add at offsets 16, 8,
+    // 4, 2, 1 as in a per-value tree, so every sum is the same; with two
+    // vectors per group, 3 FP64 additions per vector instead of 10).
+    for (int i0 = 0; i0 <= k; i0 += kLzGroup) {
+      double v[2 * kLzGroup];            // Re, Im of the group's partial sums
+#pragma unroll
+      for (int g = 0; g < 2 * kLzGroup; ++g) v[g] = 0.0;
 #pragma unroll
       for (int q = 0; q < RW; ++q) {
         const int r = threadIdx.x + kLzThreads * q;
-        if (r < m) sacc = zfma_cj(sacc, vi[r], w[q]);
+#pragma unroll
+        for (int g = 0; g < kLzGroup; ++g)
+          if (r < m && i0 + g <= k) {
+            const double2 t = zfma_cj(make_double2(v[2 * g], v[2 * g + 1]),
+                                      S.V[(long long)(i0 + g) * S.vstride + (long long)p * m + r], w[q]);
+            v[2 * g] = t.x;
+            v[2 * g + 1] = t.y;
+          }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
-        sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+      for (int o = 16, n = 2 * kLzGroup; o > 0; o >>= 1) {
+        if (n > 1) {                     // keep the half named by this lane's bit o, add the partner's
+          const bool up = (lane & o) != 0;
+          n >>= 1;
+#pragma unroll
+          for (int g = 0; g < n; ++g) {
+            const double send = up ? v[g] : v[g + n], keep = up ? v[g + n] : v[g];
+            v[g] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
+        } else {
+          v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
       }
-      if (lane == 0) part[i][warp] = sacc;
+      // lane l now holds value (l / (32 / (2 kLzGroup))) of the group
+      constexpr int kSpan = 32 / (2 * kLzGroup);
+      const int vi = lane / kSpan;
+      if (lane % kSpan == 0 && i0 + (vi >> 1) <= k)
+        reinterpret_cast<double *>(&part[i0 + (vi >> 1)][warp])[vi & 1] = v[0];
     }
     __syncthreads();
     for (int i = threadIdx.x; i <= k; i += kLzThreads) {
@@ -227,16 +254,22 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_step_r(LanczosState S, i
       h[i] = t;
     }
     __syncthreads();
+    // w -= V h, vector by vector (every element still takes v_0 .. v_k in
+    // order; the loads of one vector are independent of each other)
+    for (int i = 0; i <= k; ++i) {
+      const double2 hi = h[i];
+      const double2 *vi = S.V + (long long)i * S.vstride + (long long)p * m;
+#pragma unroll
+      for (int q = 0; q < RW; ++q) {
+        const int r = threadIdx.x + kLzThreads * q;
+        if (r < m) w[q] = zfms(w[q], vi[r], hi);
+      }
+    }
     double n1 = 0.0;
 #pragma unroll
     for (int q = 0; q < RW; ++q) {
       const int r = threadIdx.x + kLzThreads * q;
-      if (r < m) {
-        double2 x = w[q];
-        for (int i = 0; i <= k; ++i) x = zfms(x, S.V[(long long)i * S.vstride + (long long)p * m + r], h[i]);
-        w[q] = x;
-        n1 += x.x * x.x + x.y * x.y;
-      }
+      if (r < m) n1 += w[q].x * w[q].x + w[q].y * w[q].y;
     }
     __syncthreads();
     if (pass == 0 && !(block_sum(n1, red) < 0.5 * n0)) break;   // CTA-uniform
