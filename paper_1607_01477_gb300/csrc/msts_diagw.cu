@@ -99,6 +99,14 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
   // block against 48 in the cyclic layout (31 carry useful work), the same
   // number for every warp.
   constexpr bool CHUNK = L == 4 && !CONJ;
+  // The conjugate-transposed solves with L = 4 use the same layout with the
+  // cyclic layout's loop (the next row first, then the rest; chunk c owned by
+  // warp c or 7 - c).  The loop is written for chunks of L rows in groups of
+  // eight (warp w: chunks 8 b + w and 8 b + 7 - w in slots 2 b, 2 b + 1), but
+  // at L = 2 it measured slower than the cyclic layout (pseudospectra 2000^2:
+  // 537 against 486 ms), and at L = 1 every slot is one row, so the cyclic
+  // layout wastes nothing: both stay cyclic.
+  constexpr bool CHUNKG = L == 4 && CONJ;
   static_assert(!(SAFE && CONJ), "the safe solve is upper only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *sU = reinterpret_cast<double2 *>(smem_raw);      // U(I1,I1), column-major, LD
@@ -127,7 +135,9 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
   const bool active = j < P.n;
   auto nbe_of = [&](int jj) { return shortcut ? min(hi, jj) - lo : nbf; };   // TREVC: rows >= j stay zero
   const int nbe = active ? nbe_of(j) : 0;
-  auto row_of = [&](int q) { return CHUNK ? 4 * (q == 0 ? w : 7 - w) + h : w + 4 * (h + L * q); };
+  // chunk held in slot q (chunk-pair layouts)
+  auto chunk_of = [&](int q) { return 8 * (q >> 1) + ((q & 1) ? 7 - w : w); };
+  auto row_of = [&](int q) { return (CHUNK || CHUNKG) ? L * chunk_of(q) + h : w + 4 * (h + L * q); };
 
   // U(I1,I1) by asynchronous 16-byte copies.  No kernel of the solve writes U
   // or the column norms, so after the first block step these copies start
@@ -267,7 +277,7 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
   };
   // Row i (slot qn of its owner) by its owner warp: x_i = y_i / p_i, published.
   auto produce = [&](int qn, int i, int kk) {
-    const int hi_ = CHUNK ? (i & 3) : (i >> 2) & (L - 1);
+    const int hi_ = (CHUNK || CHUNKG) ? (i & (L - 1)) : (i >> 2) & (L - 1);
     if (SAFE && kk) {
 #pragma unroll
       for (int q = 0; q < RPT; ++q)
@@ -410,6 +420,74 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
         }
         kk_cur = kk_nxt;
       }
+    }
+  } else if constexpr (CHUNKG) {
+    // chunk c's owner and the slot that holds it there
+    auto owner_of = [](int c) { const int t = c & 7; return t < 4 ? t : 7 - t; };
+    auto slot_of = [](int c) { return 2 * (c >> 3) + ((c & 7) >= 4 ? 1 : 0); };
+    // slot q still has rows on the unsolved side of row i
+    auto pending = [&](int q, int i) {
+      const int r0 = L * chunk_of(q);
+      return CONJ ? r0 + L - 1 > i : r0 < i;
+    };
+    auto axpy_rows = [&](int q, int i, double2 x) {
+      const int r = row_of(q);
+      if (!CONJ) {
+        if (r < i) y[q] = zfms(y[q], x, sU[i * LD + r]);
+      } else {
+        if (r > i) y[q] = zfms(y[q], x, zconj(sU[r * LD + i]));
+      }
+    };
+    const int i0 = CONJ ? 0 : NB - 1;
+    int kk_cur = SAFE ? chain(i0) : 0;
+    double2 xown = make_double2(0.0, 0.0);
+    bool rescaled_ahead = false;
+    if (w == owner_of(i0 / L)) {         // prologue: the first row's owner
+      if (SAFE && kk_cur) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) rescale_slot(q, kk_cur);
+      }
+      xown = produce(slot_of(i0 / L), i0, 0);
+      rescaled_ahead = true;
+    }
+#pragma unroll 1
+    for (int n = 0; n < NB; ++n) {
+      const int i = CONJ ? n : NB - 1 - n;
+      const bool last = n == NB - 1;
+      const int inext = CONJ ? i + 1 : i - 1;
+      const int kk_nxt = (SAFE && !last) ? chain(inext) : 0;
+      if (SAFE && kk_cur && !rescaled_ahead) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) rescale_slot(q, kk_cur);
+      }
+      double2 x;
+      if (w == owner_of(i / L)) {
+        x = xown;
+      } else {
+        nbar_sync(row_bar(i));
+        x = sX[i * SPC + js];
+      }
+      rescaled_ahead = false;
+      if (!last && w == owner_of(inext / L)) {
+        // next row's owner: that row's slot first, publish it, then the rest
+        const int qn = slot_of(inext / L);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q == qn) axpy_rows(q, i, x);
+        xown = produce(qn, inext, kk_nxt);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q != qn) {
+            if (pending(q, i)) axpy_rows(q, i, x);
+            if (SAFE && kk_nxt) rescale_slot(q, kk_nxt);
+          }
+        rescaled_ahead = true;
+      } else {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (pending(q, i)) axpy_rows(q, i, x);
+      }
+      kk_cur = kk_nxt;
     }
   } else {
     const int i0 = CONJ ? 0 : NB - 1;

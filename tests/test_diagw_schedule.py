@@ -2,7 +2,8 @@
 (csrc/msts_diagw.cu): the per-warp sequence of rescales, AXPYs, productions of
 x_i and named-barrier operations, written out from the kernel's loop
 structure, run for every lane width and both directions of the cyclic row
-layout and for the chunk-pair layout of upper solves with four lanes.
+layout and for the chunk-pair layouts of solves with four lanes (upper and
+conjugate-transposed).
 
 It checks what the kernel's correctness rests on: (1) every row value sees the
 same operations in the same order as in the serial substitution (the rescale of
@@ -135,17 +136,100 @@ def chunk_program(w, rescale_rows):
     return ops
 
 
+def chunkg_program(w, L, conj, rescale_rows):
+    """The general chunk-pair loop (the kernel's conjugate L = 4 solves; also
+    modelled at L = 2): chunks
+    of L consecutive rows, warp w holding chunks 8 b + w (slot 2 b) and
+    8 b + 7 - w (slot 2 b + 1); the cyclic layout's loop with this ownership."""
+    RPT = NB // (4 * L)
+    kk = rescale_rows.get
+
+    def chunk_of(q):
+        return 8 * (q >> 1) + (7 - w if q & 1 else w)
+
+    def owner_of(c):
+        t = c & 7
+        return t if t < 4 else 7 - t
+
+    def slot_of(c):
+        return 2 * (c >> 3) + (1 if (c & 7) >= 4 else 0)
+
+    def pending(q, i):
+        r0 = L * chunk_of(q)
+        return r0 + L - 1 > i if conj else r0 < i
+
+    ops = []
+    i0 = 0 if conj else NB - 1
+    ahead = False
+    if w == owner_of(i0 // L):
+        if kk(i0):
+            ops.extend(("rescale", q, i0) for q in range(RPT))
+        ops.extend([("produce", slot_of(i0 // L), i0), ("arrive", i0)])
+        ahead = True
+    for n in range(NB):
+        i = n if conj else NB - 1 - n
+        last = n == NB - 1
+        nxt = i + 1 if conj else i - 1
+        if kk(i) and not ahead:
+            ops.extend(("rescale", q, i) for q in range(RPT))
+        if w != owner_of(i // L):
+            ops.append(("sync", i))
+        ahead = False
+        if not last and w == owner_of(nxt // L):
+            qn = slot_of(nxt // L)
+            ops.append(("axpy", qn, i))
+            if kk(nxt):
+                ops.append(("rescale", qn, nxt))
+            ops.extend([("produce", qn, nxt), ("arrive", nxt)])
+            for q in range(RPT):
+                if q != qn:
+                    if pending(q, i):
+                        ops.append(("axpy", q, i))
+                    if kk(nxt):
+                        ops.append(("rescale", q, nxt))
+            ahead = True
+        else:
+            ops.extend(("axpy", q, i) for q in range(RPT) if pending(q, i))
+    return ops
+
+
 def program(layout, w, L, conj, rescale_rows):
-    return chunk_program(w, rescale_rows) if layout == "chunk" else warp_program(w, L, conj, rescale_rows)
+    if layout == "chunk":
+        return chunk_program(w, rescale_rows)
+    if layout == "chunkg":
+        return chunkg_program(w, L, conj, rescale_rows)
+    return warp_program(w, L, conj, rescale_rows)
 
 
 def rows_of(w, L, q, layout="cyclic"):
     if layout == "chunk":
         return [4 * (w if q == 0 else 7 - w) + h for h in range(4)]
+    if layout == "chunkg":
+        c = 8 * (q >> 1) + (7 - w if q & 1 else w)
+        return [L * c + h for h in range(L)]
     return [w + 4 * (h + L * q) for h in range(L)]
 
 
-LAYOUTS = [("cyclic", L, conj) for L in (1, 2, 4) for conj in (False, True)] + [("chunk", 4, False)]
+# every layout the kernel runs (cyclic at L = 1, 2; chunk-pair at L = 4, the
+# upper form with deferral and the conjugate one on the general loop), the
+# cyclic L = 4 it used before, and the general loop at L = 2, which the kernel
+# does not use (it measured slower) but which the model still checks
+LAYOUTS = ([("cyclic", L, conj) for L in (1, 2, 4) for conj in (False, True)] + [("chunk", 4, False)]
+           + [("chunkg", 2, False), ("chunkg", 2, True), ("chunkg", 4, True)])
+
+
+def test_slot_multiply_adds_per_warp():
+    """Slot multiply-adds each warp issues per block (counting only those with a
+    row to update): equal for all warps in the chunk-pair layouts, and below
+    the busiest warp's count in the cyclic layout, which bounds its block."""
+    def count(layout, L, conj, w):        # multiply-adds with at least one row to update
+        return sum(1 for op in program(layout, w, L, conj, {}) if op[0] == "axpy"
+                   and any((r > op[2]) if conj else (r < op[2]) for r in rows_of(w, L, op[1], layout)))
+    for L, conj in ((2, False), (2, True), (4, True)):
+        got = {count("chunkg", L, conj, w) for w in range(4)}
+        assert len(got) == 1, (L, conj, got)
+        assert got.pop() < max(count("cyclic", L, conj, w) for w in range(4))
+    assert {count("chunk", 4, False, w) for w in range(4)} == {34}
 
 
 def test_layouts_cover_every_row_once():
