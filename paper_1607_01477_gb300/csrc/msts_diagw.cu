@@ -20,10 +20,10 @@
 // it.  The owner of the next row applies x_i to that row first, publishes its
 // own x, and only then applies x_i to the rest of its rows (one-row
 // lookahead), so the serial chain per row is one complex multiply-add and one
-// complex multiply.  Upper solves with L = 4 deal the rows out in chunks of
-// four consecutive rows instead (warp w: chunks w and 7 - w), which issues
-// about a third fewer multiply-add instructions per warp; a chunk's owner
-// produces its four rows without a hand-off.
+// complex multiply.  Solves with L = 4 deal the rows out in chunks of four
+// consecutive rows instead (warp w: chunks w and 7 - w), which issues about a
+// third fewer multiply-add instructions per warp; in upper solves a chunk's
+// owner produces its four rows without a hand-off.
 //
 // Measured: the layout spends ~4x fewer FP64 instructions per shift than the
 // one-warp layout, but the hand-off per row (barrier, shared-memory round trip,
