@@ -99,13 +99,15 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
   // block against 48 in the cyclic layout (31 carry useful work), the same
   // number for every warp.
   constexpr bool CHUNK = L == 4 && !CONJ;
-  // The conjugate-transposed solves with L = 4 use the same layout with the
-  // cyclic layout's loop (the next row first, then the rest; chunk c owned by
-  // warp c or 7 - c).  The loop is written for chunks of L rows in groups of
-  // eight (warp w: chunks 8 b + w and 8 b + 7 - w in slots 2 b, 2 b + 1), but
-  // at L = 2 it measured slower than the cyclic layout (pseudospectra 2000^2:
-  // 537 against 486 ms), and at L = 1 every slot is one row, so the cyclic
-  // layout wastes nothing: both stay cyclic.
+  // The conjugate-transposed solves with L = 4 use the same layout on the
+  // cyclic layout's loop (the next row first, then the rest), the owner of a
+  // chunk leaving its other slot's share of the chunk's x_i until it has
+  // produced the chunk's last row.  The loop is written for chunks of L rows
+  // in groups of eight (warp w: chunks 8 b + w and 8 b + 7 - w in slots 2 b,
+  // 2 b + 1), but at L = 2 it measured slower than the cyclic layout on the
+  // pseudospectra workload (554 ms, 537 without the deferral, against 486) for
+  // a reason not found, so L = 2 stays cyclic; with L = 1 every slot is one
+  // row and the cyclic layout wastes nothing.
   constexpr bool CHUNKG = L == 4 && CONJ;
   static_assert(!(SAFE && CONJ), "the safe solve is upper only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -438,8 +440,10 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
         if (r > i) y[q] = zfms(y[q], x, zconj(sU[r * LD + i]));
       }
     };
+    static_assert(!SAFE || L == 2, "safe solves are upper, and upper L = 4 takes the loop above");
     const int i0 = CONJ ? 0 : NB - 1;
     int kk_cur = SAFE ? chain(i0) : 0;
+    int dk = 0;                          // safe, L = 2: the rescale after the deferred x_i
     double2 xown = make_double2(0.0, 0.0);
     bool rescaled_ahead = false;
     if (w == owner_of(i0 / L)) {         // prologue: the first row's owner
@@ -460,14 +464,44 @@ k_diagw(const __grid_constant__ ProbTable tab, int step, int shortcut, uint32_t 
 #pragma unroll
         for (int q = 0; q < RPT; ++q) rescale_slot(q, kk_cur);
       }
+      const int kc = CONJ ? L - 1 - (i & (L - 1)) : (i & (L - 1));   // rows after i in its chunk
+      const bool own = w == owner_of(i / L);
       double2 x;
-      if (w == owner_of(i / L)) {
+      if (own) {
         x = xown;
       } else {
         nbar_sync(row_bar(i));
         x = sX[i * SPC + js];
       }
       rescaled_ahead = false;
+      if (own && kc > 0) {
+        // the chunk's next row is this warp's: its slot, publish; the other
+        // slots take x_i (and the rescale after it) after the chunk's last row
+        const int qn = slot_of(i / L);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q == qn) axpy_rows(q, i, x);
+        xown = produce(qn, inext, kk_nxt);
+        if (SAFE) dk = kk_nxt;
+        rescaled_ahead = true;
+        kk_cur = kk_nxt;
+        continue;
+      }
+      if (own && L > 1) {                // the chunk's last row: the deferred share, in order
+        __syncwarp();                    // the chunk's x_i, stored by this warp's lanes
+        const int qo = slot_of(i / L);
+#pragma unroll
+        for (int d = L - 1; d >= 1; --d) {
+          const int rd = CONJ ? i - d : i + d;
+          const double2 xd = sX[rd * SPC + js];
+#pragma unroll
+          for (int q = 0; q < RPT; ++q)
+            if (q != qo) {
+              if (pending(q, rd)) axpy_rows(q, rd, xd);
+              if (SAFE && dk) rescale_slot(q, dk);
+            }
+        }
+      }
       if (!last && w == owner_of(inext / L)) {
         // next row's owner: that row's slot first, publish it, then the rest
         const int qn = slot_of(inext / L);

@@ -138,9 +138,11 @@ def chunk_program(w, rescale_rows):
 
 def chunkg_program(w, L, conj, rescale_rows):
     """The general chunk-pair loop (the kernel's conjugate L = 4 solves; also
-    modelled at L = 2): chunks
+    modelled at L = 2, which the kernel keeps cyclic): chunks
     of L consecutive rows, warp w holding chunks 8 b + w (slot 2 b) and
-    8 b + 7 - w (slot 2 b + 1); the cyclic layout's loop with this ownership."""
+    8 b + 7 - w (slot 2 b + 1); the cyclic layout's loop with this ownership,
+    the owner of a chunk leaving its other slots' share of the chunk's x_i (and
+    the rescales after them) until it has produced the chunk's last row."""
     RPT = NB // (4 * L)
     kk = rescale_rows.get
 
@@ -170,11 +172,31 @@ def chunkg_program(w, L, conj, rescale_rows):
         i = n if conj else NB - 1 - n
         last = n == NB - 1
         nxt = i + 1 if conj else i - 1
+        kc = (L - 1 - i % L) if conj else i % L          # rows after this one in its chunk
+        own = w == owner_of(i // L)
         if kk(i) and not ahead:
             ops.extend(("rescale", q, i) for q in range(RPT))
-        if w != owner_of(i // L):
+        if not own:
             ops.append(("sync", i))
         ahead = False
+        if own and kc > 0:                                # defer the other slots' share
+            qn = slot_of(i // L)
+            ops.append(("axpy", qn, i))
+            if kk(nxt):
+                ops.append(("rescale", qn, nxt))
+            ops.extend([("produce", qn, nxt), ("arrive", nxt)])
+            ahead = True
+            continue
+        if own and L > 1:                                 # the chunk's last row: replay
+            qo = slot_of(i // L)
+            for d in range(L - 1, 0, -1):
+                rd = i - d if conj else i + d
+                for q in range(RPT):
+                    if q != qo and pending(q, rd):
+                        ops.append(("axpy", q, rd))
+                rn = rd + 1 if conj else rd - 1           # the rescale taken at the next row
+                if kk(rn):
+                    ops.extend(("rescale", q, rn) for q in range(RPT) if q != qo)
         if not last and w == owner_of(nxt // L):
             qn = slot_of(nxt // L)
             ops.append(("axpy", qn, i))
